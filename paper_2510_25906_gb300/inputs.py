@@ -1,0 +1,336 @@
+"""Seeded synthetic workloads: meshes and initial cell averages.
+
+This module generates inputs only. It holds none of the method's arithmetic:
+no faces, stencils, reconstructions, detectors or fluxes. Both the CUDA path
+and the CPU oracle consume exactly the arrays built here.
+
+Mesh format (shared by every consumer):
+    dim        2 or 3
+    nodes      float64 [n_nodes, dim]
+    cell_type  uint8   [n_cells]   TRI=1, QUAD=2, TET=3, HEX=4
+    cell_ptr   int64   [n_cells+1] CSR offsets into cell_idx
+    cell_idx   int32   [...]       vertex ids in the fixed local order below
+    period     float64 [dim]       periodic length per axis, 0 = not periodic
+
+Local vertex order: TRI and QUAD counter-clockwise; HEX v0..v3 the bottom
+face counter-clockwise seen from +z, v4..v7 the top face above them.
+Periodic meshes carry separate nodes on opposite sides (x=0 and x=L); faces
+are paired across the period by their positions.
+
+State format: conserved variables, float64 [nv, n_cells] (structure of
+arrays), nv = dim + 2, order (rho, rho*u, rho*v[, rho*w], E).
+
+Workloads (seeded, synthetic, shaped like the paper's):
+  * ``density_wave_tri``: periodic unit square, structured n x n quads cut
+    along one diagonal, interior nodes jittered by +-0.2h; rho = 1 + 0.2
+    sin(2 pi (x + y)), u = v = 1, p = 1 (the smooth advected wave).
+  * ``quadrant_mixed``: [0,1]^2, n x n quads of which a seeded half are cut
+    into two triangles along a seeded diagonal, interior nodes jittered; the
+    four constant states of the paper's 2D Riemann problem (Sec. 3.5, the
+    2D Riemann problem equation), placed by quadrant about (0.5, 0.5).
+  * ``turbulence_hex``: periodic [0, 2 pi]^3, n^3 uniform hexahedra; uniform
+    density and pressure (rho = 1, p = 1/gamma, so c = 1) and a seeded
+    solenoidal velocity with energy spectrum E(k) ~ k^4 exp(-2 k^2 / k0^2),
+    k0 = 4, scaled to turbulent Mach number 0.6 (the decaying-turbulence
+    stand-in for the paper's 128^3 Taylor-Green mesh, Sec. 3.6).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+TRI, QUAD, TET, HEX = 1, 2, 3, 4
+GAMMA = 1.4
+
+
+@dataclass
+class Mesh:
+    dim: int
+    nodes: np.ndarray
+    cell_type: np.ndarray
+    cell_ptr: np.ndarray
+    cell_idx: np.ndarray
+    period: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_type.shape[0])
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.nodes.shape[0])
+
+    def cell_vertices(self, c: int) -> np.ndarray:
+        return self.nodes[self.cell_idx[self.cell_ptr[c]:self.cell_ptr[c + 1]]]
+
+    def vertex_means(self) -> np.ndarray:
+        """Arithmetic mean of each cell's vertices, [n_cells, dim]."""
+        counts = np.diff(self.cell_ptr)
+        out = np.zeros((self.n_cells, self.dim))
+        for k in np.unique(counts):
+            sel = np.nonzero(counts == k)[0]
+            idx = self.cell_idx[self.cell_ptr[sel][:, None] + np.arange(k)[None, :]]
+            out[sel] = self.nodes[idx].mean(axis=1)
+        return out
+
+
+def _finish(dim, nodes, types, conn_lists, period, name, **meta) -> Mesh:
+    counts = np.array([len(c) for c in conn_lists], dtype=np.int64)
+    ptr = np.zeros(len(conn_lists) + 1, dtype=np.int64)
+    np.cumsum(counts, out=ptr[1:])
+    idx = np.concatenate([np.asarray(c, dtype=np.int32) for c in conn_lists]) if conn_lists else np.zeros(0, np.int32)
+    return Mesh(dim, np.ascontiguousarray(nodes, dtype=np.float64), np.asarray(types, dtype=np.uint8),
+                ptr, idx, np.asarray(period, dtype=np.float64), name, dict(meta))
+
+
+def _grid_nodes_2d(n: int, lx: float, ly: float, jitter: float, rng) -> np.ndarray:
+    """(n+1)^2 nodes, node (i, j) at id j*(n+1)+i; interior nodes jittered."""
+    i = np.arange(n + 1)
+    xs = (i * lx) / n
+    ys = (i * ly) / n
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    nodes = np.stack([X.ravel(), Y.ravel()], axis=1)
+    if jitter > 0:
+        hx, hy = lx / n, ly / n
+        jj, ii = np.meshgrid(i, i, indexing="ij")
+        interior = ((ii > 0) & (ii < n) & (jj > 0) & (jj < n)).ravel()
+        d = rng.random((nodes.shape[0], 2)) * 2.0 - 1.0
+        nodes[interior, 0] += jitter * hx * d[interior, 0]
+        nodes[interior, 1] += jitter * hy * d[interior, 1]
+    return nodes
+
+
+def structured_tri_mesh(n: int, periodic: bool = True, jitter: float = 0.2, seed: int = 1,
+                        lx: float = 1.0, ly: float = 1.0) -> Mesh:
+    """n x n quads, each cut along its (i,j)->(i+1,j+1) diagonal: 2 n^2 triangles."""
+    rng = np.random.default_rng(seed)
+    nodes = _grid_nodes_2d(n, lx, ly, jitter, rng)
+    nid = lambda i, j: j * (n + 1) + i
+    conn = []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
+            conn.append((a, b, c))
+            conn.append((a, c, d))
+    period = [lx, ly] if periodic else [0.0, 0.0]
+    return _finish(2, nodes, [TRI] * len(conn), conn, period, f"tri{n}", n=n, seed=seed)
+
+
+def structured_quad_mesh(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, periodic=(False, False),
+                         jitter: float = 0.0, seed: int = 0) -> Mesh:
+    """nx x ny quadrilaterals on [0,lx]x[0,ly] (node (i,j) at id j*(nx+1)+i)."""
+    rng = np.random.default_rng(seed)
+    xs = (np.arange(nx + 1) * lx) / nx
+    ys = (np.arange(ny + 1) * ly) / ny
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    nodes = np.stack([X.ravel(), Y.ravel()], axis=1)
+    if jitter > 0:
+        jj, ii = np.meshgrid(np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+        interior = ((ii > 0) & (ii < nx) & (jj > 0) & (jj < ny)).ravel()
+        d = rng.random((nodes.shape[0], 2)) * 2.0 - 1.0
+        nodes[interior, 0] += jitter * (lx / nx) * d[interior, 0]
+        nodes[interior, 1] += jitter * (ly / ny) * d[interior, 1]
+    nid = lambda i, j: j * (nx + 1) + i
+    conn = [(nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)) for j in range(ny) for i in range(nx)]
+    period = [lx if periodic[0] else 0.0, ly if periodic[1] else 0.0]
+    return _finish(2, nodes, [QUAD] * len(conn), conn, period, f"quad{nx}x{ny}")
+
+
+def mixed_tri_quad_mesh(n: int, seed: int = 2, p_split: float = 0.5, jitter: float = 0.2,
+                        periodic: bool = False) -> Mesh:
+    """[0,1]^2 with n x n quads; each is cut into two triangles with probability
+    p_split along a seeded diagonal, the rest stay quadrilaterals."""
+    rng = np.random.default_rng(seed)
+    nodes = _grid_nodes_2d(n, 1.0, 1.0, jitter, rng)
+    split = rng.random(n * n) < p_split
+    diag = rng.random(n * n) < 0.5
+    nid = lambda i, j: j * (n + 1) + i
+    conn, types = [], []
+    for j in range(n):
+        for i in range(n):
+            a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
+            q = j * n + i
+            if not split[q]:
+                conn.append((a, b, c, d)); types.append(QUAD)
+            elif diag[q]:
+                conn.append((a, b, c)); types.append(TRI)
+                conn.append((a, c, d)); types.append(TRI)
+            else:
+                conn.append((a, b, d)); types.append(TRI)
+                conn.append((b, c, d)); types.append(TRI)
+    period = [1.0, 1.0] if periodic else [0.0, 0.0]
+    return _finish(2, nodes, types, conn, period, f"mixed{n}", n=n, seed=seed)
+
+
+def structured_hex_mesh(n: int, length: float = 2.0 * math.pi, periodic: bool = True,
+                        jitter: float = 0.0, seed: int = 3, ny: int | None = None, nz: int | None = None) -> Mesh:
+    """n x ny x nz uniform hexahedra on [0,L]^3, cell (i,j,k) at id (k*ny+j)*n+i."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    rng = np.random.default_rng(seed)
+    hx, hy, hz = length / n, length / ny, length / nz
+    xs = (np.arange(n + 1) * length) / n
+    ys = (np.arange(ny + 1) * length) / ny
+    zs = (np.arange(nz + 1) * length) / nz
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if jitter > 0:
+        K, J, I = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(n + 1), indexing="ij")
+        interior = ((I > 0) & (I < n) & (J > 0) & (J < ny) & (K > 0) & (K < nz)).ravel()
+        d = rng.random((nodes.shape[0], 3)) * 2.0 - 1.0
+        nodes[interior] += jitter * np.array([hx, hy, hz]) * d[interior]
+    sx, sy = n + 1, (n + 1) * (ny + 1)
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(n), indexing="ij")
+    base = (k * sy + j * sx + i).ravel()
+    offs = np.array([0, 1, 1 + sx, sx, sy, sy + 1, sy + 1 + sx, sy + sx])
+    conn = (base[:, None] + offs[None, :]).astype(np.int32)
+    ncell = conn.shape[0]
+    ptr = np.arange(ncell + 1, dtype=np.int64) * 8
+    period = [length] * 3 if periodic else [0.0] * 3
+    return Mesh(3, np.ascontiguousarray(nodes), np.full(ncell, HEX, np.uint8), ptr, conn.ravel().copy(),
+                np.asarray(period, np.float64), f"hex{n}", {"n": n, "seed": seed})
+
+
+# ---------------------------------------------------------------------------
+# Initial states
+# ---------------------------------------------------------------------------
+
+def _gl(n: int):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def cell_average_2d(mesh: Mesh, f, npts: int = 8) -> np.ndarray:
+    """Cell averages of f(x, y) over triangles and quadrilaterals by a
+    collapsed / tensor Gauss-Legendre rule with npts points per direction."""
+    s, ws = _gl(npts)
+    S, T = np.meshgrid(s, s, indexing="ij")
+    W = np.outer(ws, ws)
+    out = np.zeros(mesh.n_cells)
+    counts = np.diff(mesh.cell_ptr)
+    for nv in (3, 4):
+        sel = np.nonzero(counts == nv)[0]
+        if sel.size == 0:
+            continue
+        v = mesh.nodes[mesh.cell_idx[mesh.cell_ptr[sel][:, None] + np.arange(nv)[None, :]]]  # [c, nv, 2]
+        if nv == 3:
+            p0, p1, p2 = v[:, 0], v[:, 1], v[:, 2]
+            X = p0[:, None, None, :] + S[None, :, :, None] * (p1 - p0)[:, None, None, :] \
+                + (S * T)[None, :, :, None] * (p2 - p1)[:, None, None, :]
+            e1, e2 = p1 - p0, p2 - p1
+            det = np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+            J = det[:, None, None] * S[None]
+        else:
+            p0, p1, p2, p3 = v[:, 0], v[:, 1], v[:, 2], v[:, 3]
+            Sx, Tx = S[None, :, :, None], T[None, :, :, None]
+            X = (1 - Sx) * (1 - Tx) * p0[:, None, None] + Sx * (1 - Tx) * p1[:, None, None] \
+                + Sx * Tx * p2[:, None, None] + (1 - Sx) * Tx * p3[:, None, None]
+            dXs = (1 - Tx) * (p1 - p0)[:, None, None] + Tx * (p2 - p3)[:, None, None]
+            dXt = (1 - Sx) * (p3 - p0)[:, None, None] + Sx * (p2 - p1)[:, None, None]
+            J = np.abs(dXs[..., 0] * dXt[..., 1] - dXs[..., 1] * dXt[..., 0])
+        vals = f(X[..., 0], X[..., 1])
+        out[sel] = (vals * J * W[None]).sum(axis=(1, 2)) / (J * W[None]).sum(axis=(1, 2))
+    return out
+
+
+def conserved_2d(rho, u, v, p, gamma: float = GAMMA) -> np.ndarray:
+    rho, u, v, p = (np.asarray(a, dtype=np.float64) for a in (rho, u, v, p))
+    return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
+
+
+def density_wave_state(mesh: Mesh, t: float = 0.0, amp: float = 0.2, gamma: float = GAMMA) -> np.ndarray:
+    """Cell averages of rho = 1 + amp sin(2 pi (x - t + y - t)), u = v = 1, p = 1.
+    With constant velocity and pressure the averages of rho*u, rho*v and E
+    follow from the average of rho."""
+    rb = cell_average_2d(mesh, lambda x, y: 1.0 + amp * np.sin(2.0 * np.pi * ((x - t) + (y - t))))
+    return np.stack([rb, rb, rb, 1.0 / (gamma - 1.0) + rb])
+
+
+QUADRANT_STATES = {  # (rho, u, v, p), paper Sec. 3.5 (2D Riemann problem), domain shifted by +0.5
+    "left_top": (0.5323, 1.206, 0.0, 0.3),
+    "right_top": (1.5, 0.0, 0.0, 1.5),
+    "left_bottom": (0.138, 1.206, 1.206, 0.029),
+    "right_bottom": (0.5323, 0.0, 1.206, 0.3),
+}
+
+
+def quadrant_state(mesh: Mesh, gamma: float = GAMMA) -> np.ndarray:
+    """Four constant states by quadrant about (0.5, 0.5); the value at each
+    cell's vertex mean is taken as its cell average."""
+    c = mesh.vertex_means()
+    left, top = c[:, 0] < 0.5, c[:, 1] >= 0.5
+    prim = np.zeros((mesh.n_cells, 4))
+    prim[left & top] = QUADRANT_STATES["left_top"]
+    prim[~left & top] = QUADRANT_STATES["right_top"]
+    prim[left & ~top] = QUADRANT_STATES["left_bottom"]
+    prim[~left & ~top] = QUADRANT_STATES["right_bottom"]
+    return conserved_2d(prim[:, 0], prim[:, 1], prim[:, 2], prim[:, 3], gamma)
+
+
+def solenoidal_velocity(n: int, seed: int = 3, k0: float = 4.0, mach_t: float = 0.6, c: float = 1.0) -> np.ndarray:
+    """Seeded divergence-free velocity on an n^3 periodic grid of [0, 2 pi)^3
+    sampled at cell centres, [3, n, n, n] indexed (k, j, i) = (z, y, x).
+    Spectrum E(k) ~ k^4 exp(-2 k^2 / k0^2); rms |u| = mach_t * c."""
+    rng = np.random.default_rng(seed)
+    kk = np.fft.fftfreq(n, d=1.0 / n)
+    KZ, KY, KX = np.meshgrid(kk, kk, kk, indexing="ij")
+    K2 = KX * KX + KY * KY + KZ * KZ
+    Kmag = np.sqrt(K2)
+    amp = np.zeros_like(Kmag)
+    nz = Kmag > 0
+    # per-mode amplitude so that the shell-summed energy follows E(k)
+    amp[nz] = np.sqrt(Kmag[nz] ** 4 * np.exp(-2.0 * K2[nz] / (k0 * k0)) / (4.0 * np.pi * K2[nz]))
+    uh = (rng.standard_normal((3, n, n, n)) + 1j * rng.standard_normal((3, n, n, n))) * amp[None]
+    kvec = np.stack([KX, KY, KZ])
+    kdotu = (kvec * uh).sum(axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        proj = np.where(nz, kdotu / np.where(nz, K2, 1.0), 0.0)
+    uh = uh - kvec * proj[None]
+    # sample at cell centres x = (i + 1/2) h: phase shift exp(i k h / 2)
+    h = 2.0 * np.pi / n
+    shift = np.exp(1j * (KX + KY + KZ) * 0.5 * h)
+    u = np.real(np.fft.ifftn(uh * shift[None], axes=(1, 2, 3)))
+    rms = math.sqrt(float((u * u).sum(axis=0).mean()))
+    return u * (mach_t * c / rms)
+
+
+def turbulence_state(mesh: Mesh, seed: int = 3, k0: float = 4.0, mach_t: float = 0.6,
+                     gamma: float = GAMMA) -> np.ndarray:
+    n = int(mesh.meta["n"])
+    assert mesh.n_cells == n ** 3
+    u = solenoidal_velocity(n, seed, k0, mach_t).reshape(3, -1)  # cell id (k*n+j)*n+i matches (k,j,i)
+    rho = np.ones(mesh.n_cells)
+    p = np.full(mesh.n_cells, 1.0 / gamma)
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u).sum(axis=0)
+    return np.stack([rho, rho * u[0], rho * u[1], rho * u[2], E])
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (sizes as the paper's workloads; small variants for tests)
+# ---------------------------------------------------------------------------
+
+def workload(name: str, scale: int | None = None):
+    """Return (mesh, U0, defaults) for a named workload.
+
+    density_wave   2,048 periodic jittered triangles (n=32), r=2, Rusanov, FP64
+    quadrant       ~249,696 mixed tri/quad cells (n=408), HLLC
+    turbulence     128^3 = 2,097,152 periodic hexahedra, r=3, HLLC
+    ``scale`` overrides n for a smaller (or larger) instance of the same shape.
+    """
+    if name == "density_wave":
+        n = 32 if scale is None else scale
+        m = structured_tri_mesh(n, periodic=True, jitter=0.2, seed=1)
+        return m, density_wave_state(m), {"order": 3, "flux": "rusanov", "cfl": 0.5, "steps": 10}
+    if name == "quadrant":
+        n = 408 if scale is None else scale
+        m = mixed_tri_quad_mesh(n, seed=2)
+        return m, quadrant_state(m), {"order": 3, "flux": "hllc", "cfl": 0.5, "steps": 200}
+    if name == "turbulence":
+        n = 128 if scale is None else scale
+        m = structured_hex_mesh(n, 2.0 * math.pi, periodic=True, seed=3)
+        return m, turbulence_state(m, seed=3), {"order": 4, "flux": "hllc", "cfl": 0.5, "steps": 100}
+    raise KeyError(name)

@@ -1,0 +1,588 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+No test here compares the oracle with itself or retypes one of its formulas:
+each check is a closed form, an invariant, a special case reducing to a
+library routine, a statement the paper makes, or brute force on a tiny mesh.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_25906_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------
+# quadrature and geometry
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
+def test_gauss_legendre_exactness(n):
+    x, w = O.gauss_legendre(n)
+    for k in range(2 * n):
+        assert abs((w * x ** k).sum() - 1.0 / (k + 1)) < 1e-14
+    # degree 2n is not integrated exactly
+    assert abs((w * x ** (2 * n)).sum() - 1.0 / (2 * n + 1)) > 1e-12
+
+
+def test_cell_monomial_integrals_closed_form():
+    # unit right triangle: int x^a y^b = a! b! / (a+b+2)!
+    tri = I.Mesh(2, np.array([[0., 0.], [1., 0.], [0., 1.], [1., 1.]]), np.array([1, 1], np.uint8),
+                 np.array([0, 3, 6]), np.array([0, 1, 2, 1, 3, 2], np.int32), np.zeros(2))
+    om = O.Mesh(tri)
+    for a in range(5):
+        for b in range(5 - a):
+            ex = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs(om.monomial_integral(0, a, b) - ex) < 1e-15
+    # unit square split as quads / unit cube: int x^a y^b z^c = 1/((a+1)(b+1)(c+1))
+    q = I.structured_quad_mesh(1, 1)
+    oq = O.Mesh(q)
+    for a in range(5):
+        for b in range(5):
+            assert abs(oq.monomial_integral(0, a, b) - 1.0 / ((a + 1) * (b + 1))) < 1e-15
+    h = I.structured_hex_mesh(1, 1.0, periodic=False)
+    oh = O.Mesh(h)
+    for a, b, c in [(0, 0, 0), (1, 2, 3), (4, 0, 2), (3, 3, 3)]:
+        assert abs(oh.monomial_integral(0, a, b, c) - 1.0 / ((a + 1) * (b + 1) * (c + 1))) < 1e-14
+
+
+def test_bilinear_quad_integral_matches_two_triangles():
+    m = I.structured_quad_mesh(3, 3, jitter=0.3, seed=4)
+    om = O.Mesh(m)
+    c = 4  # the interior, jittered quad
+    v = m.cell_vertices(c)
+    tri = I.Mesh(2, v, np.array([1, 1], np.uint8), np.array([0, 3, 6]), np.array([0, 1, 2, 0, 2, 3], np.int32), np.zeros(2))
+    ot = O.Mesh(tri)
+    for a, b in [(0, 0), (1, 0), (0, 1), (2, 3), (4, 1)]:
+        assert abs(om.monomial_integral(c, a, b) - ot.monomial_integral(0, a, b) - ot.monomial_integral(1, a, b)) < 1e-14
+
+
+@pytest.mark.parametrize("maker,measure", [
+    (lambda: I.structured_tri_mesh(12, periodic=True, jitter=0.2, seed=1), 1.0),
+    (lambda: I.mixed_tri_quad_mesh(14, seed=2), 1.0),
+    (lambda: I.mixed_tri_quad_mesh(10, seed=7, periodic=True), 1.0),
+    (lambda: I.structured_hex_mesh(6, 2 * math.pi, periodic=True), (2 * math.pi) ** 3),
+    (lambda: I.structured_hex_mesh(5, 1.0, periodic=False, jitter=0.2, seed=9), 1.0),
+])
+def test_geometry_invariants(maker, measure):
+    m = maker()
+    om = O.Mesh(m)
+    vol, cen = om.geometry()
+    assert (vol > 0).all()
+    assert abs(vol.sum() - measure) < 1e-13 * measure
+    nbr, nbrf = om.connectivity()
+    fo, fn, nrm, area, sh = om.faces()
+    # every interior face has exactly two cells, and the pairing is symmetric
+    for c in range(m.n_cells):
+        nf = {1: 3, 2: 4, 4: 6}[int(m.cell_type[c])]
+        for f in range(nf):
+            j = nbr[c, f]
+            if j >= 0:
+                assert nbr[j, nbrf[c, f]] == c and nbrf[j, nbrf[c, f]] == f
+    # closed cells: sum of outward area vectors vanishes
+    closure = np.zeros((m.n_cells, 3))
+    np.add.at(closure, fo, nrm * area[:, None])
+    inner = fn >= 0
+    np.add.at(closure, fn[inner], -(nrm * area[:, None])[inner])
+    scale = area.max()
+    assert np.abs(closure).max() < 1e-13 * scale
+    # periodic shifts are whole periods
+    per = m.period
+    for d in range(m.dim):
+        if per[d] > 0:
+            k = sh[:, d] / per[d]
+            assert np.allclose(k, np.round(k), atol=0)
+    if all(p > 0 for p in per[:m.dim]):
+        assert (fn >= 0).all()
+
+
+# ---------------------------------------------------------------------------
+# stencils
+# ---------------------------------------------------------------------------
+
+def _face_adjacency(m, om):
+    nbr, _ = om.connectivity()
+    return nbr
+
+
+def _brute_stencil(m, om, c, M):
+    """Independent restatement of the stencil rule: face-adjacency layers,
+    whole layers while they fit, then the first layer that does not fit by
+    ascending (quantised squared distance / h^2, id)."""
+    nbr = _face_adjacency(m, om)
+    vol, _ = om.geometry()
+    vm = m.vertex_means()
+    per = m.period
+    h2 = vol[c] if m.dim == 2 else np.cbrt(vol[c]) ** 2
+    seen = {c}
+    layer = [c]
+    taken = []
+    for L in range(1, 17):
+        nxt = []
+        for a in layer:
+            for j in nbr[a]:
+                if j >= 0 and j not in seen:
+                    seen.add(j)
+                    nxt.append(j)
+        if not nxt:
+            break
+
+        def key(j):
+            dx = vm[j] - vm[c]
+            for d in range(m.dim):
+                if per[d] > 0:
+                    dx[d] -= per[d] * np.round(dx[d] / per[d])
+            return (int(np.rint(np.dot(dx, dx) / h2 * 2 ** 20)), j)
+
+        nxt.sort(key=key)
+        room = M - len(taken)
+        taken += [(L,) + key(j) for j in nxt[:room]]
+        layer = nxt
+        if len(taken) == M:
+            break
+    taken.sort()
+    return [t[2] for t in taken]
+
+
+@pytest.mark.parametrize("maker,order", [
+    (lambda: I.structured_tri_mesh(10, periodic=True, jitter=0.2, seed=3), 3),
+    (lambda: I.mixed_tri_quad_mesh(10, seed=2), 5),
+    (lambda: I.structured_hex_mesh(6, 1.0, periodic=True), 4),
+])
+def test_stencil_rule_brute_force(maker, order):
+    m = maker()
+    om = O.Mesh(m)
+    s = O.Scheme(om, order=order)
+    nbr, _ = om.connectivity()
+    for c in range(0, m.n_cells, max(1, m.n_cells // 25)):
+        st, _ = s.stencil(c)
+        assert len(set(st.tolist())) == s.M and c not in st
+        for j in nbr[c]:
+            if j >= 0:
+                assert j in st  # every face neighbour belongs to the stencil
+        assert st.tolist() == _brute_stencil(m, om, c, s.M)
+
+
+def test_stencil_size_rule():
+    # M = 2 K(r, d), K(r, d) = prod_{l=1..d}(r+l)/d!  (Sec. 2.1)
+    expect2d = {2: 6, 3: 12, 4: 20, 5: 30, 6: 42}
+    m = I.structured_tri_mesh(12, periodic=True, jitter=0.1, seed=1)
+    om = O.Mesh(m)
+    for order, M in expect2d.items():
+        s = O.Scheme(om, order=order)
+        assert s.M == M and s.N == M // 2 - 1
+    h = I.structured_hex_mesh(8, 1.0, periodic=True)
+    oh = O.Mesh(h)
+    s = O.Scheme(oh, order=4)
+    assert (s.M, s.N) == (40, 19)
+
+
+def test_uniform_hex_stencil_distance_pattern_translation_invariant():
+    m = I.structured_hex_mesh(8, 1.0, periodic=True)
+    om = O.Mesh(m)
+    s = O.Scheme(om, order=4)
+    vm = m.vertex_means()
+
+    def pattern(c):
+        st, _ = s.stencil(c)
+        dx = vm[st] - vm[c]
+        dx -= np.round(dx)
+        return sorted(np.round((dx * 8) ** 2 @ np.ones(3)).astype(int).tolist())
+
+    p0 = pattern(0)
+    assert p0 == [1] * 6 + [2] * 12 + [3] * 8 + [4] * 6 + [5] * 8
+    for c in (17, 100, 511, 300):
+        assert pattern(c) == p0
+
+
+# ---------------------------------------------------------------------------
+# least squares and the reconstructions
+# ---------------------------------------------------------------------------
+
+def test_pseudo_inverse_against_lapack():
+    m = I.mixed_tri_quad_mesh(12, seed=5)
+    s = O.Scheme(O.Mesh(m), order=5)
+    for c in (3, 50, 111):
+        A = s.operator(c, "A")
+        Vr = s.operator(c, "Vr")
+        P = s.operator(c, "P")
+        Ap = P / Vr[1:][None, :]
+        assert np.abs(Ap @ A - np.eye(s.N)).max() < 1e-15 * np.linalg.cond(A)
+        assert np.abs(Ap - np.linalg.pinv(A)).max() < 1e-10 * np.abs(Ap).max()
+
+
+def _poly2d(rng, r):
+    coef = {(a, b): rng.standard_normal() for a in range(r + 1) for b in range(r + 1 - a)}
+    return lambda x, y: sum(c * x ** a * y ** b for (a, b), c in coef.items())
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5])
+def test_linear_reconstruction_reproduces_polynomials(order):
+    """Cell means of a degree-r polynomial give back its face-point values."""
+    r = order - 1
+    m = I.mixed_tri_quad_mesh(12, seed=5)
+    s = O.Scheme(O.Mesh(m), order=order)
+    rng = np.random.default_rng(order)
+    f = _poly2d(rng, r)
+    rho = I.cell_average_2d(m, f, npts=8)
+    U = np.stack([rho, 0.5 * rho, -rho, rho + 4.0])
+    for c in range(0, m.n_cells, 5):
+        V = s.reconstruct(U, c, O.LIN)
+        P = s.face_points(c)
+        ex = f(P[:, 0], P[:, 1])
+        assert np.abs(V[:, 0] - ex).max() < 1e-11 * (1 + np.abs(ex).max())
+        assert np.abs(V[:, 2] + ex).max() < 1e-11 * (1 + np.abs(ex).max())
+
+
+def test_hex_reconstruction_reproduces_cubics():
+    m = I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.15, seed=4)
+    s = O.Scheme(O.Mesh(m), order=4)
+    rng = np.random.default_rng(11)
+    terms = [(a, b, c) for a in range(4) for b in range(4 - a) for c in range(4 - a - b)]
+    coef = rng.standard_normal(len(terms))
+    om = s.mesh
+    vol, _ = om.geometry()
+    rho = np.array([sum(k * om.monomial_integral(c, *t, npts=6) for k, t in zip(coef, terms)) for c in range(m.n_cells)]) / vol
+    U = np.stack([rho, 0 * rho, 0 * rho, 0 * rho, rho + 5.0])
+    for c in (0, 57, 171, 200, 342):
+        V = s.reconstruct(U, c, O.LIN)
+        P = s.face_points(c)
+        ex = sum(k * P[:, 0] ** t[0] * P[:, 1] ** t[1] * P[:, 2] ** t[2] for k, t in zip(coef, terms))
+        assert np.abs(V[:, 0] - ex).max() < 1e-10 * (1 + np.abs(ex).max())
+
+
+def test_cweno_exact_on_linear_data_and_weights_reduce_to_linear():
+    """Degree-1 data: every stencil gives the same polynomial, so all
+    indicators agree, tau = 0, omega = lambda (Sec. 2.3) and CWENOZ is exact."""
+    m = I.mixed_tri_quad_mesh(12, seed=5)
+    lam1p = 1e3
+    s = O.Scheme(O.Mesh(m), order=4, lambda1p=lam1p)
+    rho = I.cell_average_2d(m, lambda x, y: 1.0 + 0.3 * x - 0.7 * y)
+    U = np.stack([rho, rho, rho, rho + 3])
+    for c in (10, 77, 150):
+        om_, si, _ = s.cweno_info(U, c, 0)
+        st = len(om_)
+        lam1 = 1 - 1 / lam1p
+        lam = np.r_[lam1, np.full(st - 1, (1 - lam1) / (st - 1))]
+        assert np.abs(si - si[0]).max() < 1e-12 * max(1.0, si[0])
+        assert np.abs(om_ - lam).max() < 1e-12
+        V = s.reconstruct(U, c, O.CW)
+        P = s.face_points(c)
+        assert np.abs(V[:, 0] - (1.0 + 0.3 * P[:, 0] - 0.7 * P[:, 1])).max() < 1e-12
+
+
+def test_smoothness_indicator_closed_form():
+    """SI of p = xi^2 on the reference triangle (h_c = 1): int (2 xi)^2 +
+    int 2^2 over the unit right triangle = 1/3 + 2 = 7/3; of p = xi: 1/2."""
+    m = I.structured_tri_mesh(10, periodic=False, jitter=0.2, seed=2)
+    s = O.Scheme(O.Mesh(m), order=3)
+    for c in (42, 97, 121):
+        x0, Ji = s.refmap(c)
+        xi = lambda x, y: Ji[0, 0] * (x - x0[0]) + Ji[0, 1] * (y - x0[1])
+        for f, ex in ((lambda x, y: xi(x, y) ** 2, 7.0 / 3.0), (lambda x, y: xi(x, y), 0.5)):
+            rho = I.cell_average_2d(m, f, npts=8)
+            st, _ = s.stencil(c)
+            a = s.operator(c, "P") @ (rho[st] - rho[c])
+            si = a @ s.operator(c, "OI") @ a
+            assert abs(si - ex) < 1e-11
+
+
+def test_cweno_weights_are_convex_and_favour_smooth_stencils():
+    m = I.structured_quad_mesh(16, 16, jitter=0.1, seed=3)
+    s = O.Scheme(O.Mesh(m), order=3)
+    vm = m.vertex_means()
+    rho = np.where(vm[:, 0] < 0.5, 1.0, 0.2)
+    U = np.stack([rho, 0 * rho, 0 * rho, 2.5 + 0 * rho])
+    c = 7 * 16 + 8  # cell just right of the jump
+    om_, si, _ = s.cweno_info(U, c, 0)
+    assert abs(om_.sum() - 1) < 1e-14 and (om_ >= 0).all()
+    # the directional stencil pointing away from the jump (+x face, local face 1)
+    # is smooth: SI = 0 and its weight is the largest relative to lambda
+    assert si[1 + 1] < 1e-14
+    assert np.argmax(om_[1:]) == 1
+
+
+def test_muscl_barth_jespersen_bounds():
+    m = I.mixed_tri_quad_mesh(14, seed=6)
+    s = O.Scheme(O.Mesh(m), order=3)
+    om = s.mesh
+    nbr, _ = om.connectivity()
+    rng = np.random.default_rng(1)
+    U = np.stack([1 + rng.random(m.n_cells), rng.standard_normal(m.n_cells), rng.standard_normal(m.n_cells),
+                  5 + rng.random(m.n_cells)])
+    for c in range(0, m.n_cells, 11):
+        V = s.reconstruct(U, c, O.MU)
+        nb = [j for j in nbr[c] if j >= 0] + [c]
+        lo, hi = U[:, nb].min(axis=1), U[:, nb].max(axis=1)
+        assert (V >= lo - 1e-14).all() and (V <= hi + 1e-14).all()
+    # linear data well inside the bounds: theta = 1 reproduces the plane
+    rho = I.cell_average_2d(m, lambda x, y: 2.0 + 1e-3 * (x + 2 * y))
+    U = np.stack([rho, rho, rho, rho + 3])
+    c = 150
+    V = s.reconstruct(U, c, O.MU)
+    P = s.face_points(c)
+    ex = 2.0 + 1e-3 * (P[:, 0] + 2 * P[:, 1])
+    nb = [j for j in nbr[c] if j >= 0] + [c]
+    if ex.min() >= rho[nb].min() and ex.max() <= rho[nb].max():
+        assert np.abs(V[:, 0] - ex).max() < 1e-13
+
+
+def test_harten_bound_closed_form():
+    """|q - qbar| <= 0.9 max(|qbar|, 1e-14) on density and pressure (Sec. 2.4)."""
+    m = I.structured_tri_mesh(8, periodic=True, jitter=0.1, seed=1)
+    s = O.Scheme(O.Mesh(m), order=3)
+    U = np.tile(np.array([[2.0], [0.0], [0.0], [2.5]]), (1, m.n_cells))  # p = 1
+    Q = s.Q(0)
+    base = np.tile(U[:, 0], (Q, 1))
+    for frac, ok in ((0.85, True), (0.95, False), (-0.85, True), (-0.95, False)):
+        V = base.copy()
+        V[2, 0] = 2.0 * (1 + frac)
+        V[2, 3] = 2.5 + 0.5 * (V[2, 0] - 2.0) * 0  # keep pressure: E unchanged, zero velocity
+        V[2, 3] = 2.5
+        assert s.harten_ok(U, 0, V) == ok
+    for frac, ok in ((0.89, True), (0.91, False)):
+        V = base.copy()
+        V[1, 3] = 2.5 * (1 + frac)  # p scales with E at rest
+        assert s.harten_ok(U, 0, V) == ok
+
+
+# ---------------------------------------------------------------------------
+# detector (Sec. 2.5) and the paper's presets
+# ---------------------------------------------------------------------------
+
+def _evolved_quadrant(n=16, steps=3):
+    m = I.mixed_tri_quad_mesh(n, seed=2)
+    U = I.quadrant_state(m)
+    s = O.Scheme(O.Mesh(m), order=3, flux="hllc")
+    for _ in range(steps):
+        U = s.rk3_step(U, s.dt(U, 0.5))
+    return m, s, U
+
+
+def test_quadrant_states_golden():
+    g = _golden("quadrant_states.json")
+    for k, v in I.QUADRANT_STATES.items():
+        assert list(v) == g[k]
+
+
+def test_nad_presets_are_invariants():
+    presets = _golden("nad_presets.json")
+    m, s0, U = _evolved_quadrant()
+    om = s0.mesh
+    counts = {}
+    for name in ("default", "linear_cweno", "linear_muscl", "muscl_cweno"):
+        s = O.Scheme(om, order=3, flux="hllc", **presets[name])
+        _, raw, tag, fin = s.residual(U)
+        counts[name] = np.bincount(raw, minlength=3)
+        if name == "linear_cweno":
+            assert counts[name][O.MU] == 0
+        if name == "linear_muscl":
+            assert counts[name][O.CW] == 0
+        if name == "muscl_cweno":
+            # only deactivated cells stay linear: compare with a detector that is never deactivated
+            s_on = O.Scheme(om, order=3, flux="hllc", kappa=0.0, **presets[name])
+            _, raw_on, _, _ = s_on.residual(U)
+            assert (raw_on != O.LIN).all()
+    assert counts["default"][O.MU] > 0 and counts["default"][O.CW] > 0
+
+
+def test_uniform_state_is_all_linear():
+    m = I.mixed_tri_quad_mesh(10, seed=2)
+    s = O.Scheme(O.Mesh(m), order=3, flux="hllc")
+    U = I.conserved_2d(np.full(m.n_cells, 1.3), np.full(m.n_cells, 0.2), np.full(m.n_cells, -0.1), np.full(m.n_cells, 0.9))
+    _, raw, tag, fin = s.residual(U)
+    assert (raw == O.LIN).all() and (fin == O.LIN).all()
+
+
+def test_step_on_quad_strip_flags_jump_and_its_neighbourhood():
+    """A density/pressure jump across x = 0.5 on a uniform quad strip.  The
+    linear candidate over- and under-shoots next to the jump, but by less
+    than beta_m = 0.5 of the local range, so the default detector puts the two
+    cells at the jump in the CWENOZ band (eqs. NADMUSCL, NADCWENOZ); the
+    all-zero margins of panel (d) put them in MUSCL.  Tagging spreads the class
+    to the face neighbours; cells whose neighbours all agree are deactivated
+    (eq. NADDeactivatedCriteria) and stay linear."""
+    presets = _golden("nad_presets.json")
+    nx, ny = 24, 12
+    m = I.structured_quad_mesh(nx, ny, 1.0, 0.5, periodic=(False, True))
+    vm = m.vertex_means()
+    left = vm[:, 0] < 0.5
+    U = I.conserved_2d(np.where(left, 1.0, 0.125), 0 * vm[:, 0], 0 * vm[:, 0], np.where(left, 1.0, 0.1))
+    col = np.arange(m.n_cells) % nx
+    at_jump = (col == 11) | (col == 12)
+    near = (col >= 10) & (col <= 13)
+    for order in (3, 5):
+        for name, cls in (("default", O.CW), ("linear_muscl", O.MU)):
+            s = O.Scheme(O.Mesh(m), order=order, flux="hllc", **presets[name])
+            _, raw, tag, fin = s.residual(U)
+            assert (raw[at_jump] == cls).all() and (raw[~at_jump] == O.LIN).all()
+            assert (tag[near] == cls).all() and (tag[~near] == O.LIN).all()
+
+
+def test_hybrid_equals_linear_when_detector_is_deactivated():
+    """Sec. 3.1: with no troubled cell the hybrid operates as the linear scheme."""
+    m = I.structured_tri_mesh(16, periodic=True, jitter=0.2, seed=1)
+    U = I.density_wave_state(m)
+    om = O.Mesh(m)
+    hy = O.Scheme(om, order=3, kappa=1.0, n_exp=2.0 / 3.0)
+    li = O.Scheme(om, order=3, scheme="linear")
+    Rh, raw, _, fin = hy.residual(U)
+    Rl, _, _, _ = li.residual(U)
+    assert (raw == O.LIN).all()
+    assert np.array_equal(Rh, Rl)
+
+
+# ---------------------------------------------------------------------------
+# fluxes
+# ---------------------------------------------------------------------------
+
+def _cons(rho, u, p, g=1.4):
+    u = np.asarray(u, float)
+    return np.r_[rho, rho * u, p / (g - 1) + 0.5 * rho * u @ u]
+
+
+def _phys(U, n, g=1.4):
+    rho, m, E = U[0], U[1:-1], U[-1]
+    u = m / rho
+    p = (g - 1) * (E - 0.5 * rho * u @ u)
+    un = u @ n
+    return np.r_[rho * un, m * un + p * n, (E + p) * un]
+
+
+@pytest.mark.parametrize("kind", ["rusanov", "hllc", "hll"])
+def test_flux_consistency_and_antisymmetry(kind):
+    rng = np.random.default_rng(3)
+    for d in (2, 3):
+        for _ in range(20):
+            n = rng.standard_normal(d); n /= np.linalg.norm(n)
+            UL = _cons(0.5 + rng.random(), rng.standard_normal(d), 0.5 + rng.random())
+            UR = _cons(0.5 + rng.random(), rng.standard_normal(d), 0.5 + rng.random())
+            assert np.allclose(O.flux(kind, UL, UL, n), _phys(UL, n), rtol=1e-14, atol=1e-14)
+            assert np.allclose(O.flux(kind, UL, UR, n), -O.flux(kind, UR, UL, -n), rtol=1e-12, atol=1e-13)
+
+
+def test_supersonic_upwinding():
+    n = np.array([1.0, 0.0])
+    UL = _cons(1.0, [3.0, 0.2], 1.0)
+    UR = _cons(0.5, [2.8, -0.1], 0.7)
+    for kind in ("hllc", "hll"):
+        assert np.allclose(O.flux(kind, UL, UR, n), _phys(UL, n), rtol=1e-14)
+        assert np.allclose(O.flux(kind, UR, UL, -n), _phys(UL, -n), rtol=1e-14)
+
+
+def test_hllc_preserves_stationary_contact():
+    """Toro: HLLC resolves an isolated stationary contact exactly; HLL and
+    Rusanov smear it (mass flux != 0)."""
+    n = np.array([0.0, 1.0, 0.0])
+    UL, UR = _cons(1.0, [0.3, 0.0, -0.2], 1.0), _cons(0.2, [0.3, 0.0, -0.2], 1.0)
+    F = O.flux("hllc", UL, UR, n)
+    assert abs(F[0]) < 1e-15 and abs(F[2] - 1.0) < 1e-15 and abs(F[4]) < 1e-15
+    assert abs(O.flux("hll", UL, UR, n)[0]) > 1e-3
+    assert abs(O.flux("rusanov", UL, UR, n)[0]) > 1e-3
+
+
+def test_rusanov_textbook():
+    n = np.array([0.6, 0.8])
+    UL, UR = _cons(1.0, [0.1, 0.2], 1.0), _cons(0.8, [-0.3, 0.1], 0.6)
+    cl, cr = math.sqrt(1.4 * 1.0 / 1.0), math.sqrt(1.4 * 0.6 / 0.8)
+    s = max(abs(0.1 * 0.6 + 0.2 * 0.8) + cl, abs(-0.3 * 0.6 + 0.1 * 0.8) + cr)
+    ex = 0.5 * (_phys(UL, n) + _phys(UR, n)) - 0.5 * s * (UR - UL)
+    assert np.allclose(O.flux("rusanov", UL, UR, n), ex, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# residual, time stepping and order of accuracy
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("maker,order,flux", [
+    (lambda: I.structured_tri_mesh(12, periodic=True, jitter=0.2, seed=1), 3, "rusanov"),
+    (lambda: I.mixed_tri_quad_mesh(12, seed=8, periodic=True), 5, "hllc"),
+    (lambda: I.structured_hex_mesh(6, 2 * math.pi, periodic=True), 4, "hllc"),
+])
+def test_free_stream_and_conservation(maker, order, flux):
+    m = maker()
+    om = O.Mesh(m)
+    vol, _ = om.geometry()
+    s = O.Scheme(om, order=order, flux=flux)
+    n = m.n_cells
+    if m.dim == 2:
+        Uu = I.conserved_2d(np.full(n, 1.2), np.full(n, 0.4), np.full(n, -0.3), np.full(n, 0.8))
+    else:
+        Uu = np.tile(np.array([[1.2], [0.3], [-0.2], [0.1], [3.0]]), (1, n))
+    R, *_ = s.residual(Uu)
+    scale = np.abs(Uu).max() * 4 / vol.min() ** (1.0 / m.dim)
+    assert np.abs(R).max() < 64 * 2.2e-16 * scale
+    # periodic: volume-weighted residuals sum to zero (no boundary flux)
+    rng = np.random.default_rng(0)
+    if m.dim == 2:
+        U = I.conserved_2d(1 + 0.3 * rng.random(n), rng.standard_normal(n) * 0.3, rng.standard_normal(n) * 0.3, 1 + 0.3 * rng.random(n))
+    else:
+        U = I.turbulence_state(m, seed=1)
+        U[0] *= 1 + 0.2 * rng.random(n)
+    R, raw, tag, fin = s.residual(U)
+    tot = (R * vol).sum(axis=1)
+    assert np.abs(tot).max() < 1e-12 * (np.abs(R) * vol).sum()
+
+
+def test_transmissive_boundary_conserves_up_to_boundary_flux():
+    """Non-periodic domain, uniform state: the boundary flux F(U).n sums to
+    zero over the closed boundary, so the residual vanishes."""
+    m = I.mixed_tri_quad_mesh(10, seed=2)
+    s = O.Scheme(O.Mesh(m), order=3, flux="hllc")
+    n = m.n_cells
+    U = I.conserved_2d(np.full(n, 0.7), np.full(n, 1.1), np.full(n, 0.4), np.full(n, 1.3))
+    R, *_ = s.residual(U)
+    assert np.abs(R).max() < 1e-11
+
+
+def test_ssp_rk3_amplification_factor():
+    lam = np.array([-1.0, -0.3, 0.5, -2.0])
+    dt = 0.4
+    U = O.rk3_generic(np.ones(4), dt, lambda u: lam * u)
+    z = lam * dt
+    assert np.allclose(U, 1 + z + z ** 2 / 2 + z ** 3 / 6, rtol=1e-15, atol=1e-15)
+
+
+def test_sampled_residual_matches_full():
+    m = I.mixed_tri_quad_mesh(14, seed=2)
+    U = I.quadrant_state(m)
+    s = O.Scheme(O.Mesh(m), order=3, flux="hllc")
+    U = s.rk3_step(U, s.dt(U, 0.5))
+    R, raw, tag, fin = s.residual(U)
+    smp = np.array([0, 5, 101, 200, m.n_cells - 1])
+    Rs, raws, tags, fins = s.residual(U, sample=smp)
+    assert np.array_equal(Rs[:, smp], R[:, smp])
+    assert np.array_equal(fins[smp], fin[smp])
+
+
+@pytest.mark.slow
+def test_order_of_accuracy_density_wave():
+    """The smooth density wave rho(x - t, y - t) converges at the design
+    order r + 1 = 3 in the volume-weighted L2 norm (eq. NormsofErrors)."""
+    errs = []
+    T = 0.1
+    for n in (12, 24, 48):
+        m = I.structured_tri_mesh(n, periodic=True, jitter=0.2, seed=1)
+        om = O.Mesh(m)
+        vol, _ = om.geometry()
+        s = O.Scheme(om, order=3, flux="rusanov", scheme="linear")
+        U = I.density_wave_state(m)
+        dt0 = s.dt(U, 0.5)
+        nsteps = int(math.ceil(T / dt0))
+        dt = T / nsteps
+        for _ in range(nsteps):
+            U = s.rk3_step(U, dt)
+        ex = I.density_wave_state(m, t=T)
+        errs.append(math.sqrt(((U[0] - ex[0]) ** 2 * vol).sum() / vol.sum()))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert 2.6 < rates[-1] < 3.6, (errs, rates)
