@@ -1,0 +1,352 @@
+"""Benchmark: SSP-RK3 steps of the hybrid residual on one or more GB300s.
+
+A "step" is one three-stage SSP Runge-Kutta step, i.e. three passes of the
+whole hot path (linear candidate + detector, tagging + compaction, CWENOZ,
+MUSCL, Harten bound, fluxes) plus the stage updates, over the whole mesh.
+Metric: cell-residual evaluations per second (3 per cell per step).
+
+Default workload: the 2D four-state quadrant Riemann problem on the seeded
+mixed triangle/quadrilateral mesh of the unit square (408 x 408 quads, half
+of them cut into triangles: 249,601 cells), order 3 (r = 2), HLLC, FP32
+operators with FP64 Runge-Kutta accumulation, hybrid scheme.  The JSON line
+also carries hybrid vs pure CWENOZ and FP32 vs FP64 at orders 3 and 5.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank advances its own replica of the workload
+(no collective on the data path); value = all ranks' cell-residuals / max
+time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-residuals/s (hybrid vs CWENOZ, FP32 vs FP64) and % of HBM roofline"
+UNIT = "cell-residuals/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(mesh, band=0.05):
+    vm = mesh.vertex_means()
+    return np.nonzero(np.abs(vm[:, 1] - 0.5) < band)[0].astype(np.int64)
+
+
+def _oracle_steps(mesh, U, order, flux, scheme, steps, warmup, band=0.05):
+    """Time the FP64 oracle (single thread) on a band of cells across the
+    domain centre (every quadrant interface crosses it): one 'step' = three
+    residual evaluations of the band, the work of one SSP-RK3 step there."""
+    import oracle as O
+    om = O.Mesh(mesh)
+    s = O.Scheme(om, order=order, flux=flux, scheme=scheme)
+    smp = _oracle_sample(mesh, band)
+    for _ in range(max(1, warmup)):
+        s.residual(U, sample=smp)          # the first call also builds the operators
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for _ in range(3):
+            s.residual(U, sample=smp)
+    dt = time.perf_counter() - t0
+    return 3.0 * smp.size * steps / dt, smp.size, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_25906_gb300 import inputs as I
+    mesh, U, dflt = I.workload(args.workload)
+    v, ns, dt = _oracle_steps(mesh, U, args.order, dflt["flux"], args.scheme, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args, mesh, note="FP64 CPU oracle, single thread"),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{ns} cells (|y - 0.5| < 0.05) of the {mesh.n_cells}-cell mesh, 3 residual "
+                                   f"evaluations per step, operators built before timing"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args, mesh, **extra):
+    names = {"quadrant": "2D quadrant Riemann problem, seeded mixed tri/quad mesh of [0,1]^2",
+             "turbulence": "3D decaying turbulence, periodic [0,2pi]^3, uniform hexahedra",
+             "density_wave": "2D smooth density wave, periodic jittered triangles"}
+    cfg = {"workload": f"{names[args.workload]}, {mesh.n_cells} cells, order {args.order} {args.scheme}, "
+                       f"SSP-RK3, {args.precision}",
+           "cells": mesh.n_cells, "order": args.order, "scheme": args.scheme, "precision": args.precision,
+           "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{args.gpus}"}
+    cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# GPU timing
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _k1_bytes(mesh, s, b):
+    """Algorithmic bytes of one launch of the linear-candidate + detector
+    kernel: per cell U_i (nv b), stencil ids (4 M), L (Q M b), face-neighbour
+    ids (4 nf), threshold (b), face-point states written (Q nv b), class (1)."""
+    nf = np.where(mesh.cell_type == 4, 6, np.where(mesh.cell_type == 2, 4, 3)).astype(np.int64)
+    Q = nf * s.nfp
+    per = s.nv * b + 4 * s.M + Q * s.M * b + 4 * nf + b + Q * s.nv * b + 1
+    return int(per.sum())
+
+
+def time_steps(H, torch, g, U0, steps, warmup, cfl, dev, with_timer=False):
+    """Warm up, capture one step in a CUDA graph, then time `steps` replays,
+    each bracketed by CUDA events on the launching stream, with an L2 flush
+    (untimed) before each."""
+    st = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    U = torch.tensor(U0, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            g.step(U, cfl=cfl, stream=st)
+        torch.cuda.synchronize(dev)
+        n0 = H.launch_count()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=st):
+            g.step(U, cfl=cfl)
+        per_step_launches = H.launch_count() - n0
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(st)
+            graph.replay()
+            ev[k][1].record(st)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return ms, wall, per_step_launches * steps, U
+
+
+def kernel_pass(H, torch, g, U0, steps, cfl, dev):
+    """Eager steps with the library's per-kernel event timer (events recorded
+    on the launch stream around every kernel), L2 flushed between steps."""
+    st = torch.cuda.Stream(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    U = torch.tensor(U0, dtype=torch.float64, device=dev)
+    g.kernel_timer(True)
+    g.kernel_times(reset=True)
+    with torch.cuda.stream(st):
+        for _ in range(steps):
+            flush.zero_()
+            g.step(U, cfl=cfl, stream=st)
+            times = g.kernel_times()
+    g.kernel_timer(False)
+    return times
+
+
+def e2e_pass(g, torch, U0, steps, cfl):
+    """hfv_advance_host per step: pinned host state in, one step, state out."""
+    Uh = torch.tensor(U0, dtype=torch.float64).pin_memory().numpy()
+    g.advance_host(Uh, 1, cfl=cfl)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        g.advance_host(Uh, 1, cfl=cfl)
+    return time.perf_counter() - t0, Uh.nbytes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="quadrant", choices=["quadrant", "turbulence", "density_wave"])
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--scheme", default="hybrid", choices=["hybrid", "cweno", "linear", "muscl"])
+    ap.add_argument("--variants", type=int, default=1, help="also time hybrid/CWENOZ x FP32/FP64 at orders 3, 5")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = _env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_25906_gb300.hfv as H
+    from paper_2510_25906_gb300 import build as B
+    from paper_2510_25906_gb300 import inputs as I
+
+    if not os.path.exists(H.LIB_PATH):
+        B.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    mesh, U0, dflt = I.workload(args.workload)
+    cfl = dflt["cfl"]
+    gm = H.Mesh(mesh)
+
+    def make(order, scheme, precision):
+        return H.Scheme(gm, order=order, flux=dflt["flux"], scheme=scheme, precision=precision)
+
+    g = make(args.order, args.scheme, args.precision)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        ms, wall, launches, Ufin = time_steps(H, torch, g, U0, args.steps, args.warmup, cfl, dev)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t.item())
+    cells = mesh.n_cells
+    value = world * 3.0 * cells * args.steps / (ms_max * 1e-3)
+
+    # class histogram of the final state
+    cls = torch.empty(cells, dtype=torch.uint8, device=dev)
+    Uf = Ufin.float() if g.fp32 else Ufin
+    g.residual(Uf.contiguous(), class_out=cls)
+    hist = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+
+    # dominant kernel: linear candidate + detector
+    times = kernel_pass(H, torch, g, U0, args.steps, cfl, dev)
+    peak, peak_kind = _peaks()
+    k_ms, k_n = times["linear"]
+    b = 4 if g.fp32 else 8
+    kbytes = _k1_bytes(mesh, g, b)
+    achieved = kbytes / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
+    tot_ms = sum(v[0] for v in times.values())
+    roofline = {"kernel": "k_linear (gather + linear candidate + detector + Harten test)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": kbytes, "avg_launch_us": 1e3 * k_ms / max(k_n, 1),
+                "kernel_share": {k: round(v[0] / tot_ms, 4) for k, v in times.items() if v[1]}}
+
+    # end to end through the C ABI with host buffers
+    e2e_s, nbytes = e2e_pass(g, torch, U0, args.steps, cfl)
+    e2e = {"value": world * 3.0 * cells * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "api": "hfv_advance_host"}
+
+    variants = {}
+    if args.variants and rank == 0 and args.workload == "quadrant":
+        for order in (3, 5):
+            for scheme in ("hybrid", "cweno"):
+                for prec in ("fp32", "fp64"):
+                    key = f"order{order}_{scheme}_{prec}"
+                    if (order, scheme, prec) == (args.order, args.scheme, args.precision):
+                        variants[key] = {"value": value / world, "ms_per_step": ms_max / args.steps}
+                        continue
+                    gv = make(order, scheme, prec)
+                    msv, _, _, _ = time_steps(H, torch, gv, U0, args.steps, args.warmup, cfl, dev)
+                    variants[key] = {"value": 3.0 * cells * args.steps / (msv * 1e-3), "ms_per_step": msv / args.steps}
+                    del gv
+
+    cpu = None
+    if args.cpu_baseline and rank == 0 and world == 1:
+        v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 3, 1)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ns} cells (|y - 0.5| < 0.05) of the {cells}-cell mesh, 3 steps x 3 residual "
+                         f"evaluations, FP64, operators built before timing ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if g.fp32 else "f64", "data": "synthetic",
+                "config": _config(args, mesh), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary(), "classes_final": hist,
+                "wall_s_timed": wall, "variants": variants}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * hfv.h -- C ABI of libhfv: the hybrid Linear / CWENOZ / MUSCL finite-volume
+ * residual of Tong & Tsoutsanis (arXiv 2510.25906) for the compressible Euler
+ * equations on unstructured mixed-element meshes, on one NVIDIA GB300 GPU.
+ *
+ * The calls follow the paper's statement of the problem:
+ *   build the mesh and its stencils ............ Sec. 2.1 (stencil selection)
+ *   precompute the reconstruction operators .... Sec. 2.1 (pseudo-inverse,
+ *                                                computed once), Sec. 2.3 (OI)
+ *   compute the residual ....................... Sec. 2 (eq. EulerEquationsDetails)
+ *                                                with the pipeline of Sec. 2.5
+ *   advance a step ............................. Sec. 2.4 (explicit SSP
+ *                                                Runge-Kutta; three-stage here)
+ *
+ * Conventions
+ *   - Every function returns an int status: HFV_OK (0) or a negative HFV_ERR_*
+ *     code.  No C++ exception crosses this interface.  hfv_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the current device.  Streams are cudaStream_t passed
+ *     as void* (NULL = legacy default stream).  Calls marked "async" only
+ *     enqueue work on that stream; calls marked "sync" wait for it.
+ *   - Cell states are conserved variables, structure of arrays:
+ *     U[v * n_cells + c], v = 0..nv-1, nv = dim + 2, order
+ *     (rho, rho u, rho v[, rho w], E).
+ *   - Handles are opaque and owned by the library until *_destroy.
+ *   - Not thread-safe per handle: one host thread drives a given scheme.
+ */
+#ifndef HFV_H
+#define HFV_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HFV_API __attribute__((visibility("default")))
+#else
+#define HFV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define HFV_OK 0
+#define HFV_ERR_ARG (-1)          /* invalid argument (NULL, size, enum) */
+#define HFV_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define HFV_ERR_OOM (-3)          /* device or host allocation failed */
+#define HFV_ERR_MESH (-4)         /* degenerate cell, unmatched or over-shared face */
+#define HFV_ERR_STENCIL (-5)      /* too few cells reachable, or a rank-deficient least-squares system */
+#define HFV_ERR_NONPHYSICAL (-6)  /* a state with rho <= 0, p <= 0 or a non-finite value was seen */
+#define HFV_ERR_TIMEOUT (-7)      /* a bounded device wait gave up */
+#define HFV_ERR_STATE (-8)        /* call not valid for this handle (e.g. wrong precision) */
+
+/* cell types; local vertex order: TRI, QUAD counter-clockwise; HEX v0..v3
+ * bottom face counter-clockwise seen from +z, v4..v7 above them */
+#define HFV_TRI 1
+#define HFV_QUAD 2
+#define HFV_TET 3 /* reserved, not supported */
+#define HFV_HEX 4
+
+/* Riemann solvers at the face quadrature points (Sec. 2.4) */
+#define HFV_RUSANOV 0
+#define HFV_HLLC 1
+#define HFV_HLL 2
+
+/* reconstruction schemes */
+#define HFV_HYBRID 0       /* the paper's detector-driven hybrid (Sec. 2.5) */
+#define HFV_PURE_LINEAR 1  /* every cell linear (still Harten-bounded) */
+#define HFV_PURE_CWENOZ 2  /* every cell CWENOZ (still Harten-bounded) */
+#define HFV_PURE_MUSCL 3   /* every cell MUSCL (still Harten-bounded) */
+
+/* arithmetic of the residual path */
+#define HFV_FP64 0 /* operators, gathers, reconstruction and fluxes in FP64 */
+#define HFV_FP32 1 /* the same in FP32; setup and the Runge-Kutta accumulation stay FP64 */
+
+/* cell classes written by the pipeline (Sec. 2.5; the paper's figures call
+ * them Scheme 0 / 1 / 3 / -1) */
+#define HFV_CLASS_LINEAR 0
+#define HFV_CLASS_CWENOZ 1
+#define HFV_CLASS_MUSCL 2
+#define HFV_CLASS_FIRST 3  /* Harten bound violated: first-order (cell mean) */
+
+typedef struct hfv_mesh hfv_mesh;
+typedef struct hfv_scheme hfv_scheme;
+
+/* Mesh description.  All arrays are host memory owned by the caller and
+ * copied by hfv_mesh_create. */
+typedef struct {
+    int dim;                       /* 2 or 3 */
+    int64_t n_nodes, n_cells;
+    const double* node_xyz;        /* [n_nodes][dim] */
+    const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D), HFV_HEX (3D) */
+    const int64_t* cell_node_ptr;  /* [n_cells + 1] CSR offsets */
+    const int32_t* cell_node_idx;  /* [cell_node_ptr[n_cells]] vertex ids in local order */
+    const double* period;          /* [dim] periodic length per axis, 0 = open (transmissive) */
+} hfv_mesh_desc;
+
+/* Scheme parameters.  hfv_default_params fills the defaults given here. */
+typedef struct {
+    int order;          /* r + 1, 2..5 (default 3); "order" as in Sec. 2.1 */
+    int flux;           /* HFV_RUSANOV / HFV_HLLC / HFV_HLL (default HLLC) */
+    int scheme;         /* HFV_HYBRID (default) or a pure scheme */
+    int nad_vars;       /* detector variables: bit0 density, bit1 pressure,
+                           bit2 the remaining conserved variables (default 3) */
+    int precision;      /* HFV_FP64 (default) or HFV_FP32 */
+    int reserved;
+    double gamma;       /* 1.4 (Sec. 2) */
+    double alpha_m, beta_m, alpha_w, beta_w;  /* detector margins, eqs. marginm and marginw;
+                                                 default 5e-3, 0.5, 0, 0 (Fig. NADMargin (a)) */
+    double kappa, n_exp;   /* deactivation threshold (kappa dx)^n, eq. NADDeactivatedCriteria; default 1, 1 */
+    double lambda1_prime;  /* CWENOZ central weight lambda_1' (Sec. 2.3); default 1e3 */
+    double cweno_eps, cweno_b;          /* 1e-3 and 4 (Sec. 2.3) */
+    double harten_theta, harten_eps;    /* 0.9 and 1e-14 (eq. harten_jump_fix) */
+    double stencil_factor;              /* M = stencil_factor * K(r, d); default 2 (Sec. 2.1) */
+} hfv_scheme_params;
+
+/* Fill *p with the defaults listed above.  Never fails for non-NULL p. */
+HFV_API int hfv_default_params(hfv_scheme_params* p);
+
+/* Build faces, face neighbours, periodic pairing and cell geometry.
+ * Sec. 2 (mixed-element meshes).  sync.  Errors: HFV_ERR_ARG, HFV_ERR_MESH
+ * (bad type/vertex count, zero or negative volume, face shared by more than
+ * two cells, cell that is its own neighbour), HFV_ERR_OOM. */
+HFV_API int hfv_mesh_create(const hfv_mesh_desc* desc, hfv_mesh** out);
+
+/* Sizes of a mesh.  Any output pointer may be NULL. */
+HFV_API int hfv_mesh_info(const hfv_mesh* mesh, int64_t* n_cells, int64_t* n_faces, int* dim);
+
+/* Face neighbours in canonical per-cell form (host outputs, caller-owned):
+ * nbr[c * 6 + f] = cell across local face f of c or -1 on an open boundary,
+ * nbrf[c * 6 + f] = that face's local index inside the neighbour (or -1).
+ * Unused slots (f >= faces of c) are -1.  sync. */
+HFV_API int hfv_mesh_connectivity(const hfv_mesh* mesh, int32_t* nbr, int8_t* nbrf);
+
+/* Build the central and directional stencils (Sec. 2.1, 2.3), then, on the
+ * GPU in FP64, the reference maps, the least-squares matrices, their
+ * Householder-QR pseudo-inverses (computed once, Sec. 2.1), the
+ * oscillation-indicator matrices (Sec. 2.3) and the folded per-cell
+ * operators; allocate the device scratch of the residual.  The mesh must
+ * outlive the scheme.  sync (the setup runs on `stream` and is waited for).
+ * Errors: HFV_ERR_ARG, HFV_ERR_STENCIL (fewer than M cells within 16 face
+ * layers, or a rank-deficient system; hfv_last_error names the cell),
+ * HFV_ERR_CUDA, HFV_ERR_OOM. */
+HFV_API int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* params, void* stream, hfv_scheme** out);
+
+/* Sizes: info[0..7] = N (unknown coefficients, K(r,d)-1), M (central stencil
+ * size), Md (directional / MUSCL stencil size), nq (Gauss points per face
+ * direction), nfp (points per face), nv, Q_total (sum over cells of face
+ * points), precision. */
+HFV_API int hfv_scheme_info(const hfv_scheme* s, int64_t* info);
+
+/* Stencils, for bit-exact checks (host outputs, caller-owned):
+ * central[c * M + m] = m-th cell of c's central stencil, in the order
+ * (face layer, quantised distance, id); dir[(c * 6 + f) * Md + k] = local
+ * index (0..M-1) of the k-th cell of the directional stencil of face f, or
+ * -1 past its size; dir may be NULL.  sync. */
+HFV_API int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* dir);
+
+/* One residual evaluation R(U) = dU/dt (eq. EulerEquationsDetails, inviscid)
+ * with the hybrid pipeline of Sec. 2.5: linear candidate, detector
+ * (eqs. DMP, NADMUSCL, NADCWENOZ, marginm, marginw, NADDeactivatedCriteria),
+ * tagging of the flagged cells' face neighbourhoods, CWENOZ and MUSCL
+ * recomputation, Harten bound (eq. harten_jump_fix), Riemann fluxes.
+ *   U            device, [nv][n_cells], double (HFV_FP64) or float (HFV_FP32)
+ *   R            device, same layout and type; written for every cell
+ *   forced_class device uint8 [n_cells] or NULL.  Non-NULL: skip the
+ *                detector and tagging and use these classes (0..3); the
+ *                Harten bound still applies to classes 0..2.
+ *   class_out    device uint8 [n_cells] or NULL: the final class per cell.
+ * async; allocates nothing; capturable in a CUDA graph.  Errors: HFV_ERR_ARG.
+ * A non-physical state is recorded for hfv_status, not returned here. */
+HFV_API int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced_class, uint8_t* class_out, void* stream);
+
+/* Stable time step dt = cfl * min_c |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|
+ * from the cell averages of U (device, FP64 [nv][n_cells]); result written to
+ * dt_dev (device, one double).  async. */
+HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
+
+/* One three-stage SSP Runge-Kutta step (Shu-Osher form) of U in place:
+ *   U1 = U + dt R(U);  U2 = 3/4 U + 1/4 (U1 + dt R(U1));
+ *   U  = 1/3 U + 2/3 (U2 + dt R(U2)).
+ *   U   device FP64 [nv][n_cells] (the accumulation is FP64 in both precisions;
+ *       in HFV_FP32 each stage's residual is evaluated on an FP32 copy)
+ *   dt  > 0: that step; <= 0: computed from U with `cfl` (hfv_compute_dt)
+ *   dt_used  host double* or NULL; non-NULL makes the call sync.
+ * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG. */
+HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream);
+
+/* End-to-end helper: copy U (host, FP64 [nv][n_cells]) to the device, take
+ * n_steps steps as hfv_step, copy the result back into U.  sync. */
+HFV_API int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double cfl, double dt, void* stream);
+
+/* Class queues of the last residual (host outputs, caller-owned): counts[0]
+ * = CWENOZ cells, counts[1] = MUSCL cells; queues may be NULL or hold
+ * [2][n_cells] int32, each queue in ascending cell order.  sync. */
+HFV_API int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues);
+
+/* Sticky status bits (host output): bit0 = a state with rho <= 0, p <= 0 or
+ * a non-finite value reached hfv_residual.  reset != 0 clears them.  sync.
+ * Returns HFV_ERR_NONPHYSICAL when bit0 is set, HFV_OK otherwise. */
+HFV_API int hfv_status(hfv_scheme* s, int* flags, int reset);
+
+/* Device bytes held by the scheme (operators + scratch). */
+HFV_API int hfv_scheme_device_bytes(const hfv_scheme* s, int64_t* bytes);
+
+/* Per-kernel timer of the hot path (instrumentation for benchmarks).
+ * enable != 0: every kernel the scheme launches afterwards is bracketed by a
+ * pair of CUDA events recorded on its launch stream (at most 512 pending
+ * launches between reads).  enable == 0 switches it off.  sync. */
+HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
+
+/* Fold the pending event pairs into per-kernel totals and read them (host
+ * outputs, 16 entries each): ms[k] total milliseconds and launches[k] count
+ * of kernel k: 0 linear candidate + detector, 1 tagging, 2 block counts,
+ * 3 scan, 4 scatter, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage,
+ * 9 time step, 10 FP32 conversion.  reset != 0 zeroes the totals after
+ * reading.  sync. */
+HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset);
+
+/* Number of kernels launched by this library in this process so far. */
+HFV_API int hfv_launch_count(int64_t* count);
+
+/* Message of the calling thread's last failure ("" if none). */
+HFV_API const char* hfv_last_error(void);
+
+HFV_API void hfv_scheme_destroy(hfv_scheme* s);
+HFV_API void hfv_mesh_destroy(hfv_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFV_H */

@@ -1,0 +1,254 @@
+// api.cu -- the C ABI of libhfv (declared in include/hfv.h): argument checks,
+// object lifetime, and dispatch to the setup and hot-path launchers.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hfv_internal.h"
+
+namespace hfv {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool residual_supported(int d, int r);
+
+}  // namespace hfv
+
+using namespace hfv;
+
+#define API_CUDA(x)                                                                          \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error(std::string("CUDA: ") + cudaGetErrorString(e_) + " at " #x);           \
+            return HFV_ERR_CUDA;                                                             \
+        }                                                                                    \
+    } while (0)
+
+extern "C" const char* hfv_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int hfv_default_params(hfv_scheme_params* p)
+{
+    if (!p) { set_error("hfv_default_params: NULL"); return HFV_ERR_ARG; }
+    std::memset(p, 0, sizeof *p);
+    p->order = 3;
+    p->flux = HFV_HLLC;
+    p->scheme = HFV_HYBRID;
+    p->nad_vars = 3;
+    p->precision = HFV_FP64;
+    p->gamma = 1.4;
+    p->alpha_m = 5e-3;
+    p->beta_m = 0.5;
+    p->alpha_w = 0.0;
+    p->beta_w = 0.0;
+    p->kappa = 1.0;
+    p->n_exp = 1.0;
+    p->lambda1_prime = 1e3;
+    p->cweno_eps = 1e-3;
+    p->cweno_b = 4.0;
+    p->harten_theta = 0.9;
+    p->harten_eps = 1e-14;
+    p->stencil_factor = 2.0;
+    return HFV_OK;
+}
+
+static void timer_free(KernelTimer& t)
+{
+    for (void* e : t.ev) cudaEventDestroy((cudaEvent_t)e);
+    t.ev.clear();
+    t.kid.clear();
+    t.used = 0;
+    t.on = false;
+}
+
+extern "C" void hfv_scheme_destroy(hfv_scheme* s)
+{
+    if (!s) return;
+    timer_free(s->timer);
+    if (s->arena) cudaFree(s->arena);
+    delete s;
+}
+
+extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, void* stream, hfv_scheme** out)
+{
+    if (!mesh || !p || !out) { set_error("hfv_scheme_create: NULL argument"); return HFV_ERR_ARG; }
+    *out = nullptr;
+    const int r = p->order - 1;
+    if (r < 1 || !residual_supported(mesh->dim, r)) {
+        set_error("hfv_scheme_create: order " + std::to_string(p->order) + " is not built for dim " + std::to_string(mesh->dim));
+        return HFV_ERR_ARG;
+    }
+    if (p->stencil_factor != 2.0) { set_error("hfv_scheme_create: only stencil_factor = 2 (M = 2K) is built"); return HFV_ERR_ARG; }
+    if (p->flux < HFV_RUSANOV || p->flux > HFV_HLL || p->scheme < HFV_HYBRID || p->scheme > HFV_PURE_MUSCL ||
+        (p->precision != HFV_FP64 && p->precision != HFV_FP32) || (p->nad_vars & ~7) ||
+        !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0)) {
+        set_error("hfv_scheme_create: parameter out of range");
+        return HFV_ERR_ARG;
+    }
+    hfv_scheme* s = nullptr;
+    try {
+        s = new hfv_scheme();
+    } catch (const std::bad_alloc&) {
+        set_error("hfv_scheme_create: out of host memory");
+        return HFV_ERR_OOM;
+    }
+    s->mesh = mesh;
+    s->p = *p;
+    int rc;
+    try {
+        rc = build_stencils(s);
+    } catch (const std::bad_alloc&) {
+        rc = HFV_ERR_OOM;
+        set_error("hfv_scheme_create: out of host memory");
+    }
+    if (rc == HFV_OK) rc = build_operators(s, stream);
+    if (rc != HFV_OK) {
+        hfv_scheme_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return HFV_OK;
+}
+
+extern "C" int hfv_scheme_info(const hfv_scheme* s, int64_t* info)
+{
+    if (!s || !info) { set_error("hfv_scheme_info: NULL argument"); return HFV_ERR_ARG; }
+    info[0] = s->N; info[1] = s->M; info[2] = s->Md; info[3] = s->nq; info[4] = s->nfp; info[5] = s->nv;
+    info[6] = s->qtot; info[7] = s->p.precision;
+    return HFV_OK;
+}
+
+extern "C" int hfv_scheme_device_bytes(const hfv_scheme* s, int64_t* bytes)
+{
+    if (!s || !bytes) { set_error("hfv_scheme_device_bytes: NULL argument"); return HFV_ERR_ARG; }
+    *bytes = (int64_t)s->arena_bytes;
+    return HFV_OK;
+}
+
+extern "C" int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* dir)
+{
+    if (!s || !central) { set_error("hfv_get_stencils: NULL argument"); return HFV_ERR_ARG; }
+    std::memcpy(central, s->sten.data(), s->sten.size() * sizeof(int32_t));
+    if (dir) {
+        const int64_t nc = s->mesh->nc;
+        for (int64_t c = 0; c < nc; ++c)
+            for (int f = 0; f < kMaxFaces; ++f) {
+                int n = f < type_nfaces(s->mesh->type[c]) ? s->nd[c * kMaxFaces + f] : 0;
+                for (int k = 0; k < s->Md; ++k)
+                    dir[(c * kMaxFaces + f) * s->Md + k] = k < n ? s->dir[(c * kMaxFaces + f) * s->Md + k] : -1;
+            }
+    }
+    return HFV_OK;
+}
+
+extern "C" int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
+{
+    if (!s || !U || !R) { set_error("hfv_residual: NULL argument"); return HFV_ERR_ARG; }
+    return launch_residual(s, U, R, forced, cls_out, stream);
+}
+
+extern "C" int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
+{
+    if (!s || !U || !dt_dev || !(cfl > 0)) { set_error("hfv_compute_dt: bad argument"); return HFV_ERR_ARG; }
+    return launch_dt(s, U, cfl, dt_dev, stream);
+}
+
+extern "C" int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream)
+{
+    if (!s || !U || (!(dt > 0) && !(cfl > 0))) { set_error("hfv_step: bad argument"); return HFV_ERR_ARG; }
+    int rc = launch_step(s, U, cfl, dt, stream);
+    if (rc != HFV_OK) return rc;
+    if (dt_used) {
+        API_CUDA(cudaMemcpyAsync(dt_used, s->a.dt, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        API_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+    return HFV_OK;
+}
+
+extern "C" int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double cfl, double dt, void* stream)
+{
+    if (!s || !U_host || n_steps < 0) { set_error("hfv_advance_host: bad argument"); return HFV_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)s->nv * s->mesh->nc * sizeof(double);
+    double* work = s->a.Uio;   // device state owned by the scheme: no allocation here
+    API_CUDA(cudaMemcpyAsync(work, U_host, bytes, cudaMemcpyHostToDevice, st));
+    int rc = HFV_OK;
+    for (int k = 0; k < n_steps && rc == HFV_OK; ++k) rc = launch_step(s, work, cfl, dt, stream);
+    if (rc == HFV_OK) {
+        API_CUDA(cudaMemcpyAsync(U_host, work, bytes, cudaMemcpyDeviceToHost, st));
+        API_CUDA(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+extern "C" int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues)
+{
+    if (!s || !counts) { set_error("hfv_get_queues: NULL argument"); return HFV_ERR_ARG; }
+    API_CUDA(cudaDeviceSynchronize());
+    API_CUDA(cudaMemcpy(counts, s->a.counts, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (queues) API_CUDA(cudaMemcpy(queues, s->a.queue, 2 * s->mesh->nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return HFV_OK;
+}
+
+extern "C" int hfv_status(hfv_scheme* s, int* flags, int reset)
+{
+    if (!s || !flags) { set_error("hfv_status: NULL argument"); return HFV_ERR_ARG; }
+    API_CUDA(cudaDeviceSynchronize());
+    API_CUDA(cudaMemcpy(flags, s->a.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset) API_CUDA(cudaMemset(s->a.status, 0, sizeof(int)));
+    return (*flags & 1) ? HFV_ERR_NONPHYSICAL : HFV_OK;
+}
+
+extern "C" int hfv_kernel_timer(hfv_scheme* s, int enable)
+{
+    if (!s) { set_error("hfv_kernel_timer: NULL scheme"); return HFV_ERR_ARG; }
+    API_CUDA(cudaDeviceSynchronize());
+    KernelTimer& t = s->timer;
+    if (!enable) { timer_free(t); return HFV_OK; }
+    if (t.ev.empty()) {
+        t.ev.resize(1024, nullptr);
+        t.kid.assign(512, 0);
+        for (auto& e : t.ev) {
+            cudaEvent_t ev;
+            API_CUDA(cudaEventCreate(&ev));
+            e = ev;
+        }
+    }
+    t.used = 0;
+    t.on = true;
+    return HFV_OK;
+}
+
+extern "C" int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset)
+{
+    if (!s || !ms || !launches) { set_error("hfv_kernel_times: NULL argument"); return HFV_ERR_ARG; }
+    KernelTimer& t = s->timer;
+    for (int i = 0; i < t.used; ++i) {
+        API_CUDA(cudaEventSynchronize((cudaEvent_t)t.ev[2 * i + 1]));
+        float f = 0.0f;
+        API_CUDA(cudaEventElapsedTime(&f, (cudaEvent_t)t.ev[2 * i], (cudaEvent_t)t.ev[2 * i + 1]));
+        t.ms[t.kid[i]] += f;
+        t.n[t.kid[i]] += 1;
+    }
+    t.used = 0;
+    for (int k = 0; k < 16; ++k) { ms[k] = t.ms[k]; launches[k] = t.n[k]; }
+    if (reset)
+        for (int k = 0; k < 16; ++k) { t.ms[k] = 0.0; t.n[k] = 0; }
+    return HFV_OK;
+}
+
+extern "C" int hfv_launch_count(int64_t* count)
+{
+    if (!count) { set_error("hfv_launch_count: NULL"); return HFV_ERR_ARG; }
+    *count = g_launches.load();
+    return HFV_OK;
+}

@@ -1,0 +1,131 @@
+// hfv_internal.h -- host-side structures of libhfv shared by its translation
+// units (mesh ingestion, operator setup, hot path, C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hfv.h"
+
+namespace hfv {
+
+constexpr int kMaxFaces = 6;   // hexahedron
+constexpr int kMaxFaceVerts = 4;
+constexpr int kMaxOrder = 5;   // r <= 4
+
+// local face -> local vertices, listed so that the area vector points out of
+// the cell (edges of counter-clockwise polygons; hexahedron faces so that
+// (v2 - v0) x (v3 - v1) is outward)
+int type_nverts(int t);
+int type_nfaces(int t);
+int type_face_nverts(int t);
+int type_face_vertex(int t, int f, int k);
+
+void set_error(const std::string& msg);
+
+}  // namespace hfv
+
+struct hfv_mesh {
+    int dim = 0;
+    int64_t nn = 0, nc = 0, nface = 0;
+    std::vector<double> xyz;        // [nn][3], z = 0 in 2D
+    std::vector<uint8_t> type;      // [nc]
+    std::vector<int64_t> cptr;      // [nc+1]
+    std::vector<int32_t> cidx;
+    double period[3] = {0, 0, 0};
+    // per cell-face, [nc][6]
+    std::vector<int32_t> nbr;       // neighbour or -1
+    std::vector<int8_t> nbrf;       // neighbour's local face or -1
+    std::vector<int8_t> nshift;     // [nc][6][3] periods added to the neighbour's coordinates
+    std::vector<uint8_t> own;       // 1 when this cell owns the face (smaller id, or boundary)
+    std::vector<double> fnorm;      // [nc][6][3] unit normal, outward from this cell (owner's, negated on the other side)
+    std::vector<double> farea;      // [nc][6]
+    // per cell
+    std::vector<double> vol;        // [nc]
+    std::vector<double> vmean;      // [nc][3] vertex mean
+};
+
+// ---------------------------------------------------------------------------
+// device-resident scheme (pointers into one arena), see scheme.cu
+// ---------------------------------------------------------------------------
+struct hfv_dev_arrays {
+    // topology / geometry (always present)
+    int32_t* sten;     // [nc][M]
+    int32_t* nbr;      // [nc][6]
+    int8_t* nbrf;      // [nc][6]
+    uint8_t* nfc;      // [nc] faces per cell
+    int64_t* qoff;     // [nc+1] CSR offsets of face points
+    uint8_t* dir;      // [nc][6][Md] local stencil index of directional cells
+    // per precision (T = double or float), stored as void*
+    void* L;           // [qoff*M]: cell c at M*qoff[c], layout [M][Q_c]
+    void* P;           // [nc][N][M]
+    void* Phil;        // [qoff*d]: cell c at d*qoff[c], layout [Q_c][d]
+    void* OI;          // [nc][N*(N+1)/2] packed upper triangle, row-major
+    void* D;           // [nc][6][d][Md]
+    void* G;           // [nc][d][Md]
+    void* W;           // [qoff]: face point weight * |S|
+    void* nrm;         // [nc][6][3]: outward unit normal (owner's, negated on the other side)
+    void* ivol;        // [nc]: 1/|V|
+    void* dxthr;       // [nc]: deactivation threshold (kappa dx)^n
+    // FP64 extras for the time step
+    double* vol;       // [nc]
+    double* area;      // [nc][6]
+    double* nrm64;     // [nc][6][3]
+    // scratch of the residual
+    void* FS;          // [qoff][nv] face-point states
+    uint8_t* raw;      // [nc] raw class | 0x80 when the linear candidate breaks the Harten bound
+    uint8_t* cls;      // [nc] final class
+    int32_t* queue;    // [2][nc] CWENOZ / MUSCL queues
+    int32_t* counts;   // [2] + block counts
+    int32_t* bcount;   // [2][nblocks]
+    int* status;       // [1]
+    // time stepping scratch
+    double* U1;        // [nv][nc]
+    double* U2;        // [nv][nc]
+    void* Rs;          // [nv][nc] residual of a stage (precision T)
+    float* Uf;         // [nv][nc] FP32 copy of the stage state (HFV_FP32 only)
+    double* dt;        // [1]
+    double* Uio;       // [nv][nc] device state of hfv_advance_host
+};
+
+namespace hfv {
+// hot-path kernel ids for the optional per-kernel timer
+enum KernelId { KID_LINEAR, KID_TAG, KID_COUNT, KID_SCAN, KID_SCATTER, KID_CWENO, KID_MUSCL, KID_FLUX, KID_RK,
+                KID_DT, KID_CVT, KID_COUNT_ALL };
+struct KernelTimer {
+    bool on = false;
+    std::vector<void*> ev;          // cudaEvent_t pairs
+    std::vector<int> kid;           // kernel id of each pending pair
+    int used = 0;
+    double ms[16] = {0};
+    int64_t n[16] = {0};
+};
+void note_launch();
+}  // namespace hfv
+
+struct hfv_scheme {
+    hfv::KernelTimer timer;
+    hfv_mesh* mesh = nullptr;
+    hfv_scheme_params p{};
+    int r = 0, d = 0, nv = 0, N = 0, M = 0, Md = 0, nq = 0, nfp = 0;
+    int64_t qtot = 0;
+    int nblocks = 0;
+    // host copies kept for introspection
+    std::vector<int32_t> sten;      // [nc][M]
+    std::vector<int8_t> sshift;     // [nc][M][3]
+    std::vector<uint8_t> dir;       // [nc][6][Md]
+    std::vector<uint8_t> nd;        // [nc][6]
+    std::vector<int64_t> qoff;      // [nc+1]
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    hfv_dev_arrays a{};
+};
+
+namespace hfv {
+int build_stencils(hfv_scheme* s);       // host, scheme.cpp
+int build_operators(hfv_scheme* s, void* stream);  // device FP64 setup, setup.cu
+int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream);
+int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
+int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream);
+}  // namespace hfv

@@ -1,0 +1,71 @@
+// kernels.cuh -- compile-time configuration of the residual kernels and the
+// parameter block they receive by value.
+#pragma once
+
+#include <cstdint>
+
+#include "physics.cuh"
+
+namespace hfv {
+
+constexpr int cK(int r, int d) { return d == 2 ? (r + 1) * (r + 2) / 2 : (r + 1) * (r + 2) * (r + 3) / 6; }
+
+// sizes fixed by (dimension, polynomial degree): M = 2 K(r, d) central cells,
+// N = K(r, d) - 1 coefficients, Md = 2 K(1, d), nq = ceil((r+1)/2) Gauss
+// points per face direction
+template <int D_, int R_>
+struct Cfg {
+    static constexpr int D = D_;
+    static constexpr int R = R_;
+    static constexpr int NV = D + 2;
+    static constexpr int M = 2 * cK(R, D);
+    static constexpr int N = cK(R, D) - 1;
+    static constexpr int MD = 2 * cK(1, D);
+    static constexpr int NQ = (R + 2) / 2;
+    static constexpr int NFP = D == 2 ? NQ : NQ * NQ;
+    static constexpr int NFMAX = D == 2 ? 4 : 6;
+    static constexpr int QMAX = NFMAX * NFP;
+    static constexpr int NOI = N * (N + 1) / 2;
+};
+
+enum : uint8_t { CLS_LIN = 0, CLS_CW = 1, CLS_MU = 2, CLS_FIRST = 3, HARTEN_FAIL = 0x80 };
+
+template <class T>
+struct KParams {
+    int64_t nc;
+    int scheme;       // HFV_HYBRID / pure
+    int nad_vars;
+    int forced;       // 1 when classes are given
+    const uint8_t* forced_cls;
+    // topology
+    const int32_t* sten;
+    const int32_t* nbr;
+    const int8_t* nbrf;
+    const uint8_t* nfc;
+    const int64_t* qoff;
+    const uint8_t* dir;
+    // operators
+    const T* L;
+    const T* P;
+    const T* Phil;
+    const T* OI;
+    const T* Dd;
+    const T* G;
+    const T* W;
+    const T* nrm;
+    const T* ivol;
+    const T* dxthr;
+    // scratch
+    T* FS;
+    uint8_t* raw;
+    uint8_t* cls;
+    int32_t* queue;
+    int32_t* counts;
+    int32_t* bcount;
+    int nblocks;
+    int* status;
+    // constants
+    T gamma, alpha_m, beta_m, alpha_w, beta_w, lam1, eps_cw, b_cw, h_theta, h_eps;
+};
+
+}  // namespace hfv

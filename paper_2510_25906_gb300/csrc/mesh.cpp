@@ -1,0 +1,321 @@
+// mesh.cpp -- mesh ingestion on the host: face matching (including periodic
+// pairing), face normals and areas, cell volumes and vertex means.
+//
+// The paper's domain is any mix of triangles and quadrilaterals in 2D or
+// hexahedra (among others) in 3D (Sec. 2); each element is one index.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "hfv_internal.h"
+
+namespace hfv {
+
+static const int kTriFaces[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+static const int kQuadFaces[4][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}};
+static const int kHexFaces[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4},
+                                    {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
+
+int type_nverts(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_HEX ? 8 : 0; }
+int type_nfaces(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_HEX ? 6 : 0; }
+int type_face_nverts(int t) { return t == HFV_HEX ? 4 : 2; }
+int type_face_vertex(int t, int f, int k)
+{
+    if (t == HFV_TRI) return kTriFaces[f][k];
+    if (t == HFV_QUAD) return kQuadFaces[f][k];
+    return kHexFaces[f][k];
+}
+
+namespace {
+
+struct Key4 {
+    int64_t v[4];
+    bool operator==(const Key4& o) const { return std::memcmp(v, o.v, sizeof v) == 0; }
+};
+struct Key4Hash {
+    size_t operator()(const Key4& k) const
+    {
+        uint64_t h = 1469598103934665603ull;
+        for (int i = 0; i < 4; ++i) {
+            h ^= (uint64_t)k.v[i] + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+            h *= 1099511628211ull;
+        }
+        return (size_t)h;
+    }
+};
+
+inline const double* node(const hfv_mesh* m, int64_t c, int k) { return &m->xyz[3 * (int64_t)m->cidx[m->cptr[c] + k]]; }
+
+// outward area vector of local face f of cell c, from c's own vertices
+void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
+{
+    int t = m->type[c];
+    if (type_face_nverts(t) == 2) {
+        const double* a = node(m, c, type_face_vertex(t, f, 0));
+        const double* b = node(m, c, type_face_vertex(t, f, 1));
+        A[0] = b[1] - a[1];
+        A[1] = a[0] - b[0];
+        A[2] = 0.0;
+        return;
+    }
+    const double* p0 = node(m, c, type_face_vertex(t, f, 0));
+    const double* p1 = node(m, c, type_face_vertex(t, f, 1));
+    const double* p2 = node(m, c, type_face_vertex(t, f, 2));
+    const double* p3 = node(m, c, type_face_vertex(t, f, 3));
+    double e[3], g[3];
+    for (int k = 0; k < 3; ++k) { e[k] = p2[k] - p0[k]; g[k] = p3[k] - p1[k]; }
+    A[0] = 0.5 * (e[1] * g[2] - e[2] * g[1]);
+    A[1] = 0.5 * (e[2] * g[0] - e[0] * g[2]);
+    A[2] = 0.5 * (e[0] * g[1] - e[1] * g[0]);
+}
+
+// cell measure: triangle cross product, quadrilateral shoelace, hexahedron
+// 2x2x2 Gauss rule on the trilinear map (exact: det J has degree <= 2 per
+// direction)
+double cell_measure(const hfv_mesh* m, int64_t c)
+{
+    int t = m->type[c];
+    if (t == HFV_TRI) {
+        const double *a = node(m, c, 0), *b = node(m, c, 1), *q = node(m, c, 2);
+        return 0.5 * ((b[0] - a[0]) * (q[1] - a[1]) - (b[1] - a[1]) * (q[0] - a[0]));
+    }
+    if (t == HFV_QUAD) {
+        double s = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            const double *a = node(m, c, k), *b = node(m, c, (k + 1) % 4);
+            s += a[0] * b[1] - b[0] * a[1];
+        }
+        return 0.5 * s;
+    }
+    const double g = 0.5 / std::sqrt(3.0);
+    const double pts[2] = {0.5 - g, 0.5 + g};
+    static const int corner[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
+                                     {0, 0, 1}, {1, 0, 1}, {1, 1, 1}, {0, 1, 1}};
+    double vol = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 2; ++k) {
+                double u[3] = {pts[i], pts[j], pts[k]};
+                double J[3][3] = {};
+                for (int a = 0; a < 8; ++a) {
+                    double w[3], dw[3];
+                    for (int q = 0; q < 3; ++q) {
+                        w[q] = corner[a][q] ? u[q] : 1.0 - u[q];
+                        dw[q] = corner[a][q] ? 1.0 : -1.0;
+                    }
+                    double grad[3] = {dw[0] * w[1] * w[2], w[0] * dw[1] * w[2], w[0] * w[1] * dw[2]};
+                    const double* x = node(m, c, a);
+                    for (int r = 0; r < 3; ++r)
+                        for (int q = 0; q < 3; ++q) J[r][q] += x[r] * grad[q];
+                }
+                double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                             J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                             J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                vol += 0.125 * det;
+            }
+    return vol;
+}
+
+}  // namespace
+}  // namespace hfv
+
+using namespace hfv;
+
+extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
+{
+    if (!d || !out || (d->dim != 2 && d->dim != 3) || d->n_cells <= 0 || d->n_nodes <= 0 || !d->node_xyz ||
+        !d->cell_type || !d->cell_node_ptr || !d->cell_node_idx || !d->period || d->n_cells >= (int64_t(1) << 31)) {
+        set_error("hfv_mesh_create: invalid descriptor");
+        return HFV_ERR_ARG;
+    }
+    *out = nullptr;
+    hfv_mesh* m = nullptr;
+    try {
+        m = new hfv_mesh();
+        m->dim = d->dim;
+        m->nn = d->n_nodes;
+        m->nc = d->n_cells;
+        const int64_t nc = m->nc;
+        m->xyz.assign(3 * m->nn, 0.0);
+        for (int64_t i = 0; i < m->nn; ++i)
+            for (int k = 0; k < d->dim; ++k) m->xyz[3 * i + k] = d->node_xyz[d->dim * i + k];
+        m->type.assign(d->cell_type, d->cell_type + nc);
+        m->cptr.assign(d->cell_node_ptr, d->cell_node_ptr + nc + 1);
+        m->cidx.assign(d->cell_node_idx, d->cell_node_idx + m->cptr[nc]);
+        for (int k = 0; k < 3; ++k) m->period[k] = k < d->dim ? d->period[k] : 0.0;
+        for (int64_t c = 0; c < nc; ++c) {
+            int t = m->type[c];
+            bool ok = (d->dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) || (d->dim == 3 && t == HFV_HEX);
+            ok = ok && m->cptr[c + 1] - m->cptr[c] == type_nverts(t);
+            for (int64_t k = m->cptr[c]; ok && k < m->cptr[c + 1]; ++k) ok = m->cidx[k] >= 0 && m->cidx[k] < m->nn;
+            if (!ok) {
+                set_error("hfv_mesh_create: cell " + std::to_string(c) + " has an unsupported type or bad vertices");
+                delete m;
+                return HFV_ERR_MESH;
+            }
+        }
+        m->nbr.assign(nc * kMaxFaces, -1);
+        m->nbrf.assign(nc * kMaxFaces, -1);
+        m->nshift.assign(nc * kMaxFaces * 3, 0);
+        m->own.assign(nc * kMaxFaces, 0);
+        m->fnorm.assign(nc * kMaxFaces * 3, 0.0);
+        m->farea.assign(nc * kMaxFaces, 0.0);
+
+        // topological matching: sorted vertex ids -> first half-face seen
+        std::unordered_map<Key4, int64_t, Key4Hash> open;
+        open.reserve((size_t)(nc * 2));
+        auto link = [&](int64_t c, int f, int64_t c2, int f2) {
+            m->nbr[c * kMaxFaces + f] = (int32_t)c2;
+            m->nbrf[c * kMaxFaces + f] = (int8_t)f2;
+            m->nbr[c2 * kMaxFaces + f2] = (int32_t)c;
+            m->nbrf[c2 * kMaxFaces + f2] = (int8_t)f;
+        };
+        for (int64_t c = 0; c < nc; ++c) {
+            int t = m->type[c];
+            for (int f = 0; f < type_nfaces(t); ++f) {
+                Key4 k{{-1, -1, -1, -1}};
+                int fn = type_face_nverts(t);
+                for (int q = 0; q < fn; ++q) k.v[q] = m->cidx[m->cptr[c] + type_face_vertex(t, f, q)];
+                std::sort(k.v, k.v + fn);
+                auto it = open.find(k);
+                if (it == open.end()) {
+                    open.emplace(k, c * kMaxFaces + f);
+                } else {
+                    int64_t other = it->second;
+                    if (other < 0) {
+                        set_error("hfv_mesh_create: a face is shared by more than two cells");
+                        delete m;
+                        return HFV_ERR_MESH;
+                    }
+                    link(other / kMaxFaces, (int)(other % kMaxFaces), c, f);
+                    it->second = -1;
+                }
+            }
+        }
+        // periodic pairing of still-open faces by their wrapped, quantised centres
+        bool periodic = m->period[0] > 0 || m->period[1] > 0 || m->period[2] > 0;
+        if (periodic) {
+            std::unordered_map<Key4, int64_t, Key4Hash> wrap;
+            for (auto& kv : open) {
+                if (kv.second < 0) continue;
+                int64_t c = kv.second / kMaxFaces;
+                int f = (int)(kv.second % kMaxFaces);
+                int t = m->type[c];
+                double x[3] = {0, 0, 0};
+                for (int q = 0; q < type_face_nverts(t); ++q)
+                    for (int k = 0; k < 3; ++k) x[k] += node(m, c, type_face_vertex(t, f, q))[k];
+                Key4 key{{0, 0, 0, 0}};
+                for (int k = 0; k < 3; ++k) {
+                    double xc = x[k] / type_face_nverts(t);
+                    const int64_t S = int64_t(1) << 30;
+                    if (m->period[k] > 0) {
+                        int64_t q = std::llround(xc / m->period[k] * (double)S) % S;
+                        key.v[k] = q < 0 ? q + S : q;
+                    } else {
+                        key.v[k] = std::llround(xc * (double)S);
+                    }
+                }
+                auto it = wrap.find(key);
+                if (it == wrap.end()) {
+                    wrap.emplace(key, kv.second);
+                } else {
+                    int64_t c2 = it->second / kMaxFaces;
+                    int f2 = (int)(it->second % kMaxFaces);
+                    if (c2 == c) {
+                        set_error("hfv_mesh_create: a cell is its own periodic neighbour (mesh too coarse)");
+                        delete m;
+                        return HFV_ERR_MESH;
+                    }
+                    link(c2, f2, c, f);
+                    double y[3] = {0, 0, 0};
+                    int t2 = m->type[c2];
+                    for (int q = 0; q < type_face_nverts(t2); ++q)
+                        for (int k = 0; k < 3; ++k) y[k] += node(m, c2, type_face_vertex(t2, f2, q))[k];
+                    for (int k = 0; k < 3; ++k) {
+                        // x_c2 + s * period lies next to c  (s integer)
+                        int s = 0;
+                        if (m->period[k] > 0)
+                            s = (int)std::lround((x[k] / type_face_nverts(t) - y[k] / type_face_nverts(t2)) / m->period[k]);
+                        m->nshift[(c * kMaxFaces + f) * 3 + k] = (int8_t)s;
+                        m->nshift[(c2 * kMaxFaces + f2) * 3 + k] = (int8_t)(-s);
+                    }
+                    wrap.erase(it);
+                }
+            }
+        }
+        // ownership, normals, areas, volumes, vertex means
+        m->vol.assign(nc, 0.0);
+        m->vmean.assign(nc * 3, 0.0);
+        int64_t nface = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            int t = m->type[c];
+            for (int f = 0; f < type_nfaces(t); ++f) {
+                int32_t j = m->nbr[c * kMaxFaces + f];
+                if (j == c) {
+                    set_error("hfv_mesh_create: a cell is its own neighbour");
+                    delete m;
+                    return HFV_ERR_MESH;
+                }
+                bool own = j < 0 || j > c;
+                m->own[c * kMaxFaces + f] = own;
+                if (own) {
+                    ++nface;
+                    double A[3];
+                    area_vector(m, c, f, A);
+                    double a = std::sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+                    if (!(a > 0)) {
+                        set_error("hfv_mesh_create: zero-area face on cell " + std::to_string(c));
+                        delete m;
+                        return HFV_ERR_MESH;
+                    }
+                    m->farea[c * kMaxFaces + f] = a;
+                    for (int k = 0; k < 3; ++k) m->fnorm[(c * kMaxFaces + f) * 3 + k] = A[k] / a;
+                    if (j >= 0) {
+                        int f2 = m->nbrf[c * kMaxFaces + f];
+                        m->farea[(int64_t)j * kMaxFaces + f2] = a;
+                        for (int k = 0; k < 3; ++k) m->fnorm[((int64_t)j * kMaxFaces + f2) * 3 + k] = -A[k] / a;
+                    }
+                }
+            }
+            double v = cell_measure(m, c);
+            if (!(v > 0)) {
+                set_error("hfv_mesh_create: cell " + std::to_string(c) + " has non-positive measure (vertex order?)");
+                delete m;
+                return HFV_ERR_MESH;
+            }
+            m->vol[c] = v;
+            int nvx = type_nverts(t);
+            for (int q = 0; q < nvx; ++q)
+                for (int k = 0; k < 3; ++k) m->vmean[3 * c + k] += node(m, c, q)[k];
+            for (int k = 0; k < 3; ++k) m->vmean[3 * c + k] /= nvx;
+        }
+        m->nface = nface;
+    } catch (const std::bad_alloc&) {
+        delete m;
+        set_error("hfv_mesh_create: out of host memory");
+        return HFV_ERR_OOM;
+    }
+    *out = m;
+    return HFV_OK;
+}
+
+extern "C" int hfv_mesh_info(const hfv_mesh* m, int64_t* n_cells, int64_t* n_faces, int* dim)
+{
+    if (!m) { set_error("hfv_mesh_info: NULL mesh"); return HFV_ERR_ARG; }
+    if (n_cells) *n_cells = m->nc;
+    if (n_faces) *n_faces = m->nface;
+    if (dim) *dim = m->dim;
+    return HFV_OK;
+}
+
+extern "C" int hfv_mesh_connectivity(const hfv_mesh* m, int32_t* nbr, int8_t* nbrf)
+{
+    if (!m || !nbr || !nbrf) { set_error("hfv_mesh_connectivity: NULL argument"); return HFV_ERR_ARG; }
+    std::memcpy(nbr, m->nbr.data(), m->nbr.size() * sizeof(int32_t));
+    std::memcpy(nbrf, m->nbrf.data(), m->nbrf.size());
+    return HFV_OK;
+}
+
+extern "C" void hfv_mesh_destroy(hfv_mesh* m) { delete m; }

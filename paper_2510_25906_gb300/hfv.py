@@ -1,0 +1,262 @@
+"""Thin Python binding of libhfv (include/hfv.h): argument marshalling only.
+
+Every step of the residual path runs in the library's CUDA kernels; PyTorch
+supplies device memory and streams.  The binding never falls back to CPU
+arithmetic: if the shared library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhfv.so")
+
+HFV_OK, HFV_ERR_ARG, HFV_ERR_CUDA, HFV_ERR_OOM, HFV_ERR_MESH, HFV_ERR_STENCIL, HFV_ERR_NONPHYSICAL, \
+    HFV_ERR_TIMEOUT, HFV_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+HFV_TRI, HFV_QUAD, HFV_TET, HFV_HEX = 1, 2, 3, 4
+HFV_RUSANOV, HFV_HLLC, HFV_HLL = 0, 1, 2
+HFV_HYBRID, HFV_PURE_LINEAR, HFV_PURE_CWENOZ, HFV_PURE_MUSCL = 0, 1, 2, 3
+HFV_FP64, HFV_FP32 = 0, 1
+HFV_CLASS_LINEAR, HFV_CLASS_CWENOZ, HFV_CLASS_MUSCL, HFV_CLASS_FIRST = 0, 1, 2, 3
+
+KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux", "rk", "dt", "cvt"]
+FLUX = {"rusanov": HFV_RUSANOV, "hllc": HFV_HLLC, "hll": HFV_HLL}
+SCHEME = {"hybrid": HFV_HYBRID, "linear": HFV_PURE_LINEAR, "cweno": HFV_PURE_CWENOZ, "muscl": HFV_PURE_MUSCL}
+PRECISION = {"fp64": HFV_FP64, "fp32": HFV_FP32}
+
+
+class HfvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libhfv error {code}: {msg}")
+        self.code = code
+
+
+class hfv_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int64), ("n_cells", C.c_int64), ("node_xyz", C.c_void_p),
+                ("cell_type", C.c_void_p), ("cell_node_ptr", C.c_void_p), ("cell_node_idx", C.c_void_p),
+                ("period", C.c_void_p)]
+
+
+class hfv_scheme_params(C.Structure):
+    _fields_ = [("order", C.c_int), ("flux", C.c_int), ("scheme", C.c_int), ("nad_vars", C.c_int),
+                ("precision", C.c_int), ("reserved", C.c_int), ("gamma", C.c_double), ("alpha_m", C.c_double),
+                ("beta_m", C.c_double), ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
+                ("n_exp", C.c_double), ("lambda1_prime", C.c_double), ("cweno_eps", C.c_double),
+                ("cweno_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
+                ("stencil_factor", C.c_double)]
+
+
+_lib = None
+
+
+def load():
+    """Load libhfv.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhfv.so not built at {LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, d = C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "hfv_default_params": [vp],
+        "hfv_mesh_create": [vp, vp],
+        "hfv_mesh_info": [vp, vp, vp, vp],
+        "hfv_mesh_connectivity": [vp, vp, vp],
+        "hfv_scheme_create": [vp, vp, vp, vp],
+        "hfv_scheme_info": [vp, vp],
+        "hfv_get_stencils": [vp, vp, vp],
+        "hfv_residual": [vp, vp, vp, vp, vp, vp],
+        "hfv_compute_dt": [vp, vp, d, vp, vp],
+        "hfv_step": [vp, vp, d, d, vp, vp],
+        "hfv_advance_host": [vp, vp, C.c_int, d, d, vp],
+        "hfv_get_queues": [vp, vp, vp],
+        "hfv_status": [vp, vp, C.c_int],
+        "hfv_scheme_device_bytes": [vp, vp],
+        "hfv_kernel_timer": [vp, C.c_int],
+        "hfv_kernel_times": [vp, vp, vp, C.c_int],
+        "hfv_launch_count": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.hfv_last_error.restype = C.c_char_p
+    lib.hfv_last_error.argtypes = []
+    lib.hfv_scheme_destroy.argtypes = [vp]
+    lib.hfv_scheme_destroy.restype = None
+    lib.hfv_mesh_destroy.argtypes = [vp]
+    lib.hfv_mesh_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != HFV_OK:
+        raise HfvError(rc, load().hfv_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def default_params(**kw) -> hfv_scheme_params:
+    p = hfv_scheme_params()
+    _check(load().hfv_default_params(C.byref(p)))
+    for k, v in kw.items():
+        if k == "flux" and isinstance(v, str):
+            v = FLUX[v]
+        elif k == "scheme" and isinstance(v, str):
+            v = SCHEME[v]
+        elif k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(p, k, v)
+    return p
+
+
+class Mesh:
+    """hfv_mesh_create / hfv_mesh_connectivity over an ``inputs.Mesh``."""
+
+    def __init__(self, mesh):
+        lib = load()
+        self.src = mesh
+        self.dim = mesh.dim
+        self.n_cells = mesh.n_cells
+        keep = [np.ascontiguousarray(mesh.nodes, np.float64), np.ascontiguousarray(mesh.cell_type, np.uint8),
+                np.ascontiguousarray(mesh.cell_ptr, np.int64), np.ascontiguousarray(mesh.cell_idx, np.int32),
+                np.ascontiguousarray(mesh.period, np.float64)]
+        desc = hfv_mesh_desc(mesh.dim, mesh.n_nodes, mesh.n_cells, *[k.ctypes.data for k in keep])
+        h = C.c_void_p()
+        _check(lib.hfv_mesh_create(C.byref(desc), C.byref(h)))
+        self.h = h
+        nf = C.c_int64()
+        lib.hfv_mesh_info(self.h, None, C.byref(nf), None)
+        self.n_faces = nf.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hfv_mesh_destroy(self.h)
+            self.h = None
+
+    def connectivity(self):
+        nbr = np.zeros((self.n_cells, 6), np.int32)
+        nbrf = np.zeros((self.n_cells, 6), np.int8)
+        _check(load().hfv_mesh_connectivity(self.h, nbr.ctypes.data, nbrf.ctypes.data))
+        return nbr, nbrf
+
+
+class Scheme:
+    """hfv_scheme_create and the calls on a scheme handle."""
+
+    def __init__(self, mesh: Mesh, stream=None, **kw):
+        lib = load()
+        self.mesh = mesh
+        self.params = default_params(**kw)
+        h = C.c_void_p()
+        _check(lib.hfv_scheme_create(mesh.h, C.byref(self.params), _stream(stream), C.byref(h)))
+        self.h = h
+        info = (C.c_int64 * 8)()
+        _check(lib.hfv_scheme_info(self.h, info))
+        self.N, self.M, self.Md, self.nq, self.nfp, self.nv, self.qtot, prec = list(info)
+        self.fp32 = prec == HFV_FP32
+        self.n_cells = mesh.n_cells
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hfv_scheme_destroy(self.h)
+            self.h = None
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float32 if self.fp32 else torch.float64
+
+    def device_bytes(self) -> int:
+        b = C.c_int64()
+        _check(load().hfv_scheme_device_bytes(self.h, C.byref(b)))
+        return b.value
+
+    def stencils(self):
+        cen = np.zeros((self.n_cells, self.M), np.int32)
+        dr = np.zeros((self.n_cells, 6, self.Md), np.int32)
+        _check(load().hfv_get_stencils(self.h, cen.ctypes.data, dr.ctypes.data))
+        return cen, dr
+
+    def _state(self, U, dtype):
+        import torch
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == dtype and U.is_contiguous()
+                and tuple(U.shape) == (self.nv, self.n_cells)):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor of shape {(self.nv, self.n_cells)}")
+        return C.c_void_p(U.data_ptr())
+
+    def residual(self, U, R=None, forced=None, class_out=None, stream=None):
+        """hfv_residual: returns R (and fills class_out if given)."""
+        import torch
+        u = self._state(U, self.dtype)
+        if R is None:
+            R = torch.empty_like(U)
+        r = self._state(R, self.dtype)
+        f = C.c_void_p(forced.data_ptr()) if forced is not None else None
+        co = C.c_void_p(class_out.data_ptr()) if class_out is not None else None
+        for t in (forced, class_out):
+            if t is not None and not (t.is_cuda and t.dtype == torch.uint8 and t.numel() == self.n_cells):
+                raise ValueError("classes must be CUDA uint8 tensors of n_cells entries")
+        _check(load().hfv_residual(self.h, u, r, f, co, _stream(stream)))
+        return R
+
+    def compute_dt(self, U, cfl: float, dt_out=None, stream=None):
+        import torch
+        u = self._state(U, torch.float64)
+        if dt_out is None:
+            dt_out = torch.empty(1, dtype=torch.float64, device=U.device)
+        _check(load().hfv_compute_dt(self.h, u, cfl, C.c_void_p(dt_out.data_ptr()), _stream(stream)))
+        return dt_out
+
+    def step(self, U, cfl: float = 0.5, dt: float = -1.0, want_dt: bool = False, stream=None):
+        """hfv_step on an FP64 state in place; returns dt when want_dt."""
+        import torch
+        u = self._state(U, torch.float64)
+        out = C.c_double(0.0)
+        _check(load().hfv_step(self.h, u, cfl, dt, C.byref(out) if want_dt else None, _stream(stream)))
+        return out.value if want_dt else None
+
+    def advance_host(self, U: np.ndarray, n_steps: int, cfl: float = 0.5, dt: float = -1.0, stream=None):
+        """hfv_advance_host: U (host FP64 [nv, n]) advanced in place."""
+        if not (U.dtype == np.float64 and U.flags.c_contiguous and U.shape == (self.nv, self.n_cells)):
+            raise ValueError("expected a C-contiguous float64 array [nv, n_cells]")
+        _check(load().hfv_advance_host(self.h, U.ctypes.data, n_steps, cfl, dt, _stream(stream)))
+        return U
+
+    def queues(self):
+        counts = np.zeros(2, np.int32)
+        q = np.zeros((2, self.n_cells), np.int32)
+        _check(load().hfv_get_queues(self.h, counts.ctypes.data, q.ctypes.data))
+        return counts, [q[0, :counts[0]].copy(), q[1, :counts[1]].copy()]
+
+    def kernel_timer(self, enable: bool = True):
+        _check(load().hfv_kernel_timer(self.h, 1 if enable else 0))
+
+    def kernel_times(self, reset: bool = False):
+        ms = np.zeros(16)
+        n = np.zeros(16, np.int64)
+        _check(load().hfv_kernel_times(self.h, ms.ctypes.data, n.ctypes.data, 1 if reset else 0))
+        return {KERNELS[k]: (float(ms[k]), int(n[k])) for k in range(len(KERNELS))}
+
+    def status(self, reset: bool = False):
+        flags = C.c_int(0)
+        rc = load().hfv_status(self.h, C.byref(flags), 1 if reset else 0)
+        if rc not in (HFV_OK, HFV_ERR_NONPHYSICAL):
+            _check(rc)
+        return flags.value
+
+
+def launch_count() -> int:
+    n = C.c_int64()
+    _check(load().hfv_launch_count(C.byref(n)))
+    return n.value

@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (stated with each test):
+  * stencils, connectivity, queues: bit-exact
+  * residual with the oracle's classes forced: <= 1e-12 (FP64), <= 1e-5 (FP32)
+    of max |R| per variable
+  * free-running classes: >= 99.9 % agreement (FP64); mismatches are listed
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_25906_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_25906_gb300 import build as B
+    B.build()
+    import paper_2510_25906_gb300.hfv as H
+    H.load()
+    return H
+
+
+def _hex_contact_state(m):
+    """Seeded solenoidal velocity plus a density jump across x = pi (pressure
+    equilibrium): smooth, weakly non-smooth and discontinuous cells."""
+    U = I.turbulence_state(m, seed=3)
+    x = m.vertex_means()[:, 0]
+    fac = np.where(x < math.pi, 1.0, 0.5)
+    ke = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+    p = (1.4 - 1) * (U[4] - ke)
+    U[0] *= fac
+    U[1:4] *= fac
+    U[4] = p / 0.4 + ke * fac
+    return U
+
+
+def _case(name):
+    if name == "wave_tri32":
+        m = I.structured_tri_mesh(32, periodic=True, jitter=0.2, seed=1)
+        return m, I.density_wave_state(m), dict(order=3, flux="rusanov"), 0
+    if name == "quadrant_r2":
+        m = I.mixed_tri_quad_mesh(24, seed=2)
+        return m, I.quadrant_state(m), dict(order=3, flux="hllc"), 2
+    if name == "quadrant_r4":
+        m = I.mixed_tri_quad_mesh(24, seed=2)
+        return m, I.quadrant_state(m), dict(order=5, flux="hllc"), 2
+    if name == "quadrant_r3_hll":
+        m = I.mixed_tri_quad_mesh(20, seed=11, periodic=True)
+        return m, I.quadrant_state(m), dict(order=4, flux="hll"), 1
+    if name == "hex_r3":
+        m = I.structured_hex_mesh(9, 2 * math.pi, periodic=True)
+        return m, _hex_contact_state(m), dict(order=4, flux="hllc"), 0
+    if name == "hex_r2_open":
+        m = I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.15, seed=5)
+        U = I.turbulence_state(I.structured_hex_mesh(7, 1.0, periodic=True), seed=5)
+        x = m.vertex_means()[:, 1]
+        U[0] *= np.where(x < 0.5, 1.0, 0.7)
+        return m, U, dict(order=3, flux="hllc"), 0
+    raise KeyError(name)
+
+
+CASES = ["wave_tri32", "quadrant_r2", "quadrant_r4", "quadrant_r3_hll", "hex_r3", "hex_r2_open"]
+_cache = {}
+
+
+def _prepared(name):
+    if name not in _cache:
+        m, U, kw, steps = _case(name)
+        om = O.Mesh(m)
+        osch = O.Scheme(om, **kw)
+        for _ in range(steps):
+            U = osch.rk3_step(U, osch.dt(U, 0.5))
+        R, raw, tag, fin = osch.residual(U)
+        _cache[name] = (m, om, osch, U, kw, R, raw, tag, fin)
+    return _cache[name]
+
+
+def _rel(Rg, Ro, mask=None):
+    scale = np.abs(Ro).max(axis=1)
+    scale[scale == 0] = 1.0
+    d = np.abs(Rg - Ro)
+    if mask is not None:
+        d = d[:, mask]
+    return (d.max(axis=1) / scale).max() if d.size else 0.0
+
+
+def _gpu(H, m, kw, precision):
+    gm = H.Mesh(m)
+    return gm, H.Scheme(gm, precision=precision, **kw)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_stencils_bit_exact(H, name):
+    m, om, osch, *_ = _prepared(name)
+    gm, g = _gpu(H, m, _prepared(name)[4], "fp64")
+    cen, dr = g.stencils()
+    for c in range(m.n_cells):
+        st, odir = osch.stencil(c)
+        assert np.array_equal(cen[c], st), c
+        nd = osch.operator(c, "nd").astype(int)
+        for f in range(odir.shape[0]):
+            assert np.array_equal(dr[c, f, :nd[f]], odir[f, :nd[f]]), (c, f)
+            assert (dr[c, f, nd[f]:] == -1).all()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("name", CASES)
+def test_forced_class_residual(H, name, precision, tol):
+    m, om, osch, U, kw, R, raw, tag, fin = _prepared(name)
+    assert len(np.unique(fin)) >= (1 if name == "wave_tri32" else 2)
+    gm, g = _gpu(H, m, kw, precision)
+    dt = g.dtype
+    Ug = torch.tensor(U, dtype=dt, device="cuda")
+    forced = torch.tensor(fin, dtype=torch.uint8, device="cuda")
+    cls = torch.empty(m.n_cells, dtype=torch.uint8, device="cuda")
+    Rg = g.residual(Ug, forced=forced, class_out=cls)
+    torch.cuda.synchronize()
+    cg = cls.cpu().numpy()
+    # the Harten bound still applies on forced classes: it must agree
+    if precision == "fp64":
+        assert np.array_equal(cg, fin)
+    ok = cg == fin
+    err = _rel(Rg.double().cpu().numpy(), R, ok)
+    assert err <= tol, (name, precision, err)
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_free_running_classes_and_queues(H, name):
+    m, om, osch, U, kw, R, raw, tag, fin = _prepared(name)
+    gm, g = _gpu(H, m, kw, "fp64")
+    Ug = torch.tensor(U, device="cuda")
+    cls = torch.empty(m.n_cells, dtype=torch.uint8, device="cuda")
+    Rg = g.residual(Ug, class_out=cls).cpu().numpy()
+    cg = cls.cpu().numpy()
+    agree = (cg == fin).mean()
+    mism = np.nonzero(cg != fin)[0]
+    assert agree >= 0.999, (name, agree, [(int(c), int(cg[c]), int(fin[c])) for c in mism[:20]])
+    # queues: bit-exact ascending lists of the CWENOZ and MUSCL cells of the
+    # pipeline before the Harten bound turns some into first-order cells
+    counts, (qc, qm) = g.queues()
+    assert np.all(np.diff(qc) > 0) and np.all(np.diff(qm) > 0)
+    assert set(qc.tolist()) == set(np.nonzero(tag == O.CW)[0].tolist())
+    assert set(qm.tolist()) == set(np.nonzero(tag == O.MU)[0].tolist())
+    nbr, _ = om.connectivity()
+    good = cg == fin
+    for c in mism:
+        good[nbr[c][nbr[c] >= 0]] = False
+    assert _rel(Rg, R, good) <= 1e-12
+
+
+def test_fp32_free_running_agreement(H):
+    m, om, osch, U, kw, R, raw, tag, fin = _prepared("quadrant_r2")
+    gm, g = _gpu(H, m, kw, "fp32")
+    cls = torch.empty(m.n_cells, dtype=torch.uint8, device="cuda")
+    g.residual(torch.tensor(U, dtype=torch.float32, device="cuda"), class_out=cls)
+    agree = (cls.cpu().numpy() == fin).mean()
+    assert agree >= 0.99, agree
+
+
+def test_dt_and_rk3_step(H):
+    m, om, osch, U, kw, R, raw, tag, fin = _prepared("quadrant_r2")
+    gm, g = _gpu(H, m, kw, "fp64")
+    Ug = torch.tensor(U, device="cuda")
+    dtg = g.compute_dt(Ug, 0.5).item()
+    dto = osch.dt(U, 0.5)
+    assert abs(dtg - dto) <= 1e-14 * dto
+    Uo = osch.rk3_step(U, dto)
+    used = g.step(Ug, dt=dto, want_dt=True)
+    assert used == dto
+    Un = Ug.cpu().numpy()
+    scale = np.abs(Uo).max(axis=1, keepdims=True)
+    assert (np.abs(Un - Uo) / scale).max() <= 1e-12
+    # the CFL path takes the same dt
+    Ug2 = torch.tensor(U, device="cuda")
+    assert g.step(Ug2, cfl=0.5, want_dt=True) == dtg
+
+
+def test_fp32_step_accumulates_in_fp64(H):
+    m, om, osch, U, kw, *_ = _prepared("wave_tri32")
+    gm, g = _gpu(H, m, kw, "fp32")
+    Ug = torch.tensor(U, device="cuda")
+    dto = osch.dt(U, 0.5)
+    Uo = U.copy()
+    for _ in range(3):
+        Uo = osch.rk3_step(Uo, dto)
+        g.step(Ug, dt=dto)
+    err = np.abs(Ug.cpu().numpy() - Uo).max() / np.abs(Uo).max()
+    assert err < 1e-5, err
+
+
+def test_advance_host_matches_device_steps(H):
+    m, om, osch, U, kw, *_ = _prepared("quadrant_r2")
+    gm, g = _gpu(H, m, kw, "fp64")
+    Ud = torch.tensor(U, device="cuda")
+    for _ in range(2):
+        g.step(Ud, cfl=0.5)
+    Uh = np.ascontiguousarray(U.copy())
+    g.advance_host(Uh, 2, cfl=0.5)
+    assert np.array_equal(Uh, Ud.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", ["wave_tri32", "hex_r3"])
+def test_free_stream_and_conservation_on_gpu(H, name):
+    m, om, osch, U, kw, *_ = _prepared(name)
+    gm, g = _gpu(H, m, kw, "fp64")
+    vol, _ = om.geometry()
+    n = m.n_cells
+    Uu = np.tile(np.array([1.2, 0.3, -0.2, 0.1, 3.0][: m.dim + 1] + [3.0])[:, None], (1, n))
+    Rg = g.residual(torch.tensor(Uu, device="cuda")).cpu().numpy()
+    assert np.abs(Rg).max() < 64 * 2.2e-16 * 4 * np.abs(Uu).max() / vol.min() ** (1 / m.dim)
+    Rg = g.residual(torch.tensor(U, device="cuda")).cpu().numpy()
+    assert np.abs((Rg * vol).sum(axis=1)).max() < 1e-12 * (np.abs(Rg) * vol).sum()
+
+
+def test_nonphysical_state_is_reported(H):
+    m, om, osch, U, kw, *_ = _prepared("wave_tri32")
+    gm, g = _gpu(H, m, kw, "fp64")
+    assert g.status(reset=True) == 0
+    Ub = U.copy()
+    Ub[0, 17] = -1.0
+    g.residual(torch.tensor(Ub, device="cuda"))
+    assert g.status() & 1
+    assert H.load().hfv_status(g.h, __import__("ctypes").byref(__import__("ctypes").c_int()), 1) == H.HFV_ERR_NONPHYSICAL
+    g.residual(torch.tensor(U, device="cuda"))
+    assert g.status() == 0
+
+
+def test_argument_errors(H):
+    m = I.mixed_tri_quad_mesh(4, seed=1)
+    gm = H.Mesh(m)
+    with pytest.raises(H.HfvError) as e:
+        H.Scheme(gm, order=9)
+    assert e.value.code == H.HFV_ERR_ARG
+    with pytest.raises(H.HfvError) as e:
+        H.Scheme(gm, order=5)          # 30 neighbours needed, 23 reachable
+    assert e.value.code == H.HFV_ERR_STENCIL
+    with pytest.raises(H.HfvError) as e:
+        H.Scheme(gm, stencil_factor=3.0)
+    assert e.value.code == H.HFV_ERR_ARG
+    g = H.Scheme(gm, order=3)
+    with pytest.raises(ValueError):
+        g.residual(torch.zeros((4, m.n_cells), dtype=torch.float32, device="cuda"))
