@@ -84,7 +84,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     from paper_2510_25906_gb300 import inputs as I
-    mesh, U, dflt = I.workload(args.workload)
+    mesh, U, dflt = I.workload(args.workload, args.scale)
     v, ns, dt = _oracle_steps(mesh, U, args.order, dflt["flux"], args.scheme, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -131,7 +131,7 @@ class Clocks:
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                  "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -238,7 +238,7 @@ def e2e_pass(g, torch, U0, steps, cfl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="quadrant", choices=["quadrant", "turbulence", "density_wave"])
@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--scheme", default="hybrid", choices=["hybrid", "cweno", "linear", "muscl"])
     ap.add_argument("--variants", type=int, default=1, help="also time hybrid/CWENOZ x FP32/FP64 at orders 3, 5")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--scale", type=int, default=None, help="mesh size parameter (small cases for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _env()
@@ -267,7 +268,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    mesh, U0, dflt = I.workload(args.workload)
+    mesh, U0, dflt = I.workload(args.workload, args.scale)
     cfl = dflt["cfl"]
     gm = H.Mesh(mesh)
 
@@ -330,10 +331,10 @@ def main():
 
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
-        v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 3, 1)
+        v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 10, 1, band=0.2)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ns} cells (|y - 0.5| < 0.05) of the {cells}-cell mesh, 3 steps x 3 residual "
-                         f"evaluations, FP64, operators built before timing ({dt:.1f} s)"}
+               "sample": f"{ns} cells (|y - 0.5| < 0.2) of the {cells}-cell mesh, 10 steps x 3 residual "
+                         f"evaluations, FP64, operators built before timing ({dt:.1f} s timed)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

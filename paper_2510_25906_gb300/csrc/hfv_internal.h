@@ -54,11 +54,11 @@ struct hfv_dev_arrays {
     int32_t* sten;     // [nc][M]
     int32_t* nbr;      // [nc][6]
     int8_t* nbrf;      // [nc][6]
-    uint8_t* nfc;      // [nc] faces per cell
+    uint8_t* nfc;      // [nc] faces per cell | (distinct face neighbours << 4)
     int64_t* qoff;     // [nc+1] CSR offsets of face points
     uint8_t* dir;      // [nc][6][Md] local stencil index of directional cells
     // per precision (T = double or float), stored as void*
-    void* L;           // [qoff*M]: cell c at M*qoff[c], layout [M][Q_c]
+    void* L;           // [qoff*M]: cell c at M*qoff[c], layout [Q_c][M]
     void* P;           // [nc][N][M]
     void* Phil;        // [qoff*d]: cell c at d*qoff[c], layout [Q_c][d]
     void* OI;          // [nc][N*(N+1)/2] packed upper triangle, row-major
@@ -116,6 +116,7 @@ struct hfv_scheme {
     std::vector<int8_t> sshift;     // [nc][M][3]
     std::vector<uint8_t> dir;       // [nc][6][Md]
     std::vector<uint8_t> nd;        // [nc][6]
+    std::vector<uint8_t> n1;        // [nc] distinct face neighbours = the stencil's first layer
     std::vector<int64_t> qoff;      // [nc+1]
     void* arena = nullptr;
     size_t arena_bytes = 0;

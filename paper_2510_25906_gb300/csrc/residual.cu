@@ -43,110 +43,198 @@ __device__ __forceinline__ T nad_value(const T* u, int k, T g)
     return u[k - 1];
 }
 
+// ---------------------------------------------------------------------------
+// cell groups: G lanes (a power of two <= 32, inside one warp) own one cell;
+// lane q handles face point q.  Reductions stay inside the group.
+// ---------------------------------------------------------------------------
+template <int G>
+struct Grp {
+    unsigned mask;
+    int lane;
+    __device__ __forceinline__ Grp()
+    {
+        lane = threadIdx.x & (G - 1);
+        const int base = (threadIdx.x & 31) & ~(G - 1);
+        mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << base);
+    }
+    template <class T>
+    __device__ __forceinline__ T max(T v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w > v ? w : v; }
+        return v;
+    }
+    template <class T>
+    __device__ __forceinline__ T min(T v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
+        return v;
+    }
+    template <class T>
+    __device__ __forceinline__ T sum(T v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+        return v;
+    }
+    __device__ __forceinline__ bool any(bool b) const { return (__ballot_sync(mask, b) & mask) != 0u; }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
+
+template <int Q>
+struct GroupSize {
+    static constexpr int value = Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
+};
+
+// contiguous row of M values with the widest aligned vector loads (rows start
+// at (qoff + q) * M elements: 16-byte aligned when M * sizeof(T) % 16 == 0)
+template <class T, int M>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[M])
+{
+    if constexpr (sizeof(T) == 4 && M % 4 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 4) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(p + m));
+            r[m] = v.x; r[m + 1] = v.y; r[m + 2] = v.z; r[m + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && M % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 2) {
+            float2 v = __ldg(reinterpret_cast<const float2*>(p + m));
+            r[m] = v.x; r[m + 1] = v.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 2) {
+            double2 v = __ldg(reinterpret_cast<const double2*>(p + m));
+            r[m] = v.x; r[m + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) r[m] = __ldg(p + m);
+    }
+}
+
+template <class T, int NV>
+__device__ __forceinline__ void store_state(T* __restrict__ p, const T (&w)[NV])
+{
+    if constexpr (sizeof(T) == 4 && NV == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
+    } else if constexpr (sizeof(T) == 8 && NV == 4) {
+        reinterpret_cast<double2*>(p)[0] = make_double2(w[0], w[1]);
+        reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) p[v] = w[v];
+    }
+}
+
+template <class T, int NV>
+__device__ __forceinline__ void load_state(const T* __restrict__ p, T (&w)[NV])
+{
+    if constexpr (sizeof(T) == 4 && NV == 4) {
+        float4 v = *reinterpret_cast<const float4*>(p);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else if constexpr (sizeof(T) == 8 && NV == 4) {
+        double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = p[v];
+    }
+}
+
+// K1: one group per cell.  The group gathers the M stencil states into shared
+// memory; lane q forms the candidate at face point q from its row of L; the
+// detector bounds come from the first stencil layer (the face neighbours).
 template <class C, class T>
 __global__ void __launch_bounds__(128) k_linear(KParams<T> p, const T* __restrict__ U)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
+    __shared__ T sU[CPB][M][NV];
+    const Grp<G> grp;
+    const int gi = threadIdx.x / G, lane = grp.lane;
+    const int64_t c = (int64_t)blockIdx.x * CPB + gi;
     if (c >= p.nc) return;
     const int64_t nc = p.nc;
     T uc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-    {
-        T pc = pressure<T, D>(uc, p.gamma);
-        bool bad = !(uc[0] > T(0)) || !(pc > T(0));
-#pragma unroll
-        for (int v = 0; v < NV; ++v) bad |= !isfinite(uc[v]);
-        if (bad) atomicOr(p.status, 1);
-    }
-    T du[M][NV];
     const int32_t* st = p.sten + c * M;
-#pragma unroll 4
-    for (int m = 0; m < M; ++m) {
-        int64_t j = st[m];
+    for (int m = lane; m < M; m += G) {
+        const int64_t j = st[m];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) du[m][v] = U[v * nc + j] - uc[v];
+        for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j];
     }
-    const int nf = p.nfc[c];
-    const int Q = nf * NFP;
+    const int nfv = p.nfc[c];
+    const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
     const int64_t q0 = p.qoff[c];
-    const T* L = p.L + q0 * M;
-
-    // detector bounds over the cell and its face neighbours
-    const bool detect = !p.forced && p.scheme == HFV_HYBRID;
-    constexpr int KMAX = NV + 1;
-    T mn[KMAX], mx[KMAX], dm[KMAX], dw[KMAX];
-    bool on[KMAX];
-    int nk = 0;
-    int kinds[KMAX];
-    if (detect) {
-        if (p.nad_vars & 1) kinds[nk++] = 0;
-        if (p.nad_vars & 2) kinds[nk++] = 1;
-        if (p.nad_vars & 4)
-            for (int v = 1; v < NV; ++v) kinds[nk++] = v + 1;
+    T w[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) w[v] = uc[v];
+    T lrow[M];
+    if (lane < Q) load_row<T, M>(p.L + (q0 + lane) * M, lrow);
+    grp.sync();
+    if (lane < Q) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[v] += lrow[m] * (sU[gi][m][v] - uc[v]);
+        }
+        store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
+    }
+    if (lane == 0 && !(uc[0] > T(0) && pressure<T, D>(uc, p.gamma) > T(0))) atomicOr(p.status, 1);
+    // Harten test of the linear candidate
+    const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
+    bool fail = false;
+    if (lane < Q) {
+        const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
+        fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
+    }
+    const bool hfail = grp.any(fail);
+    int cl = CLS_LIN;
+    if (!p.forced && p.scheme == HFV_HYBRID) {
         const T thr = p.dxthr[c];
-        for (int a = 0; a < nk; ++a) {
-            T qi = nad_value<T, D>(uc, kinds[a], p.gamma);
-            T lo = qi, hi = qi, dlo = T(0), dhi = T(0);
-            int nn = 0;
-            for (int f = 0; f < nf; ++f) {
-                int64_t j = p.nbr[c * 6 + f];
-                if (j < 0) continue;
+        const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
+        for (int kind = 0; kind < NV + 1; ++kind) {
+            const bool use = kind == 0 ? (p.nad_vars & 1) : kind == 1 ? (p.nad_vars & 2) : (p.nad_vars & 4);
+            if (!use) continue;
+            const T qi = nad_value<T, D>(uc, kind, p.gamma);
+            T qj = qi, dd = T(0);
+            const bool has = lane < n1;
+            if (has) {
                 T uj[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) uj[v] = U[v * nc + j];
-                T qj = nad_value<T, D>(uj, kinds[a], p.gamma);
-                lo = tmin(lo, qj);
-                hi = tmax(hi, qj);
-                T dd = tabs(qj - qi);
-                if (nn == 0) { dlo = dd; dhi = dd; }
-                else { dlo = tmin(dlo, dd); dhi = tmax(dhi, dd); }
-                ++nn;
+                for (int v = 0; v < NV; ++v) uj[v] = sU[gi][lane][v];
+                qj = nad_value<T, D>(uj, kind, p.gamma);
+                dd = tabs(qj - qi);
             }
-            on[a] = nn > 0 && !(dhi - dlo < thr);
-            T range = hi - lo;
-            mn[a] = lo;
-            mx[a] = hi;
-            dm[a] = tmax(p.alpha_m, p.beta_m * range);
-            T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
-            dw[a] = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
-        }
-    }
-    const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-    const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
-    int cl = CLS_LIN;
-    bool hfail = false;
-    T* FS = p.FS + q0 * NV;
-    for (int q = 0; q < Q; ++q) {
-        T w[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) w[v] = uc[v];
-#pragma unroll 4
-        for (int m = 0; m < M; ++m) {
-            T l = L[(int64_t)m * Q + q];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) w[v] += l * du[m][v];
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) FS[q * NV + v] = w[v];
-        for (int a = 0; a < nk; ++a) {
-            if (!on[a]) continue;
-            T x = nad_value<T, D>(w, kinds[a], p.gamma);
-            int k;
-            if (x <= mn[a] - dm[a] || x >= mx[a] + dm[a]) k = CLS_MU;
-            else if (mn[a] - dw[a] < x && x < mx[a] + dw[a]) k = CLS_LIN;
-            else k = CLS_CW;
+            const T lo = grp.min(qj), hi = grp.max(qj);
+            const T dlo = grp.min(has ? dd : T(INFINITY)), dhi = grp.max(has ? dd : T(-INFINITY));
+            if (n1 == 0 || dhi - dlo < thr) continue;   // deactivated: smooth
+            const T range = hi - lo;
+            const T dm = tmax(p.alpha_m, p.beta_m * range);
+            const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
+            int k = CLS_LIN;
+            if (lane < Q) {
+                const T x = nad_value<T, D>(w, kind, p.gamma);
+                if (x <= lo - dm || x >= hi + dm) k = CLS_MU;
+                else if (lo - dw < x && x < hi + dw) k = CLS_LIN;
+                else k = CLS_CW;
+            }
+            k = grp.max(k);
             cl = k > cl ? k : cl;
         }
-        T pw = pressure<T, D>(w, p.gamma);
-        if (!(tabs(w[0] - rb) <= rlim) || !(tabs(pw - pb) <= plim)) hfail = true;
     }
-    uint8_t out;
-    if (p.forced) out = p.forced_cls[c];
-    else if (p.scheme == HFV_HYBRID) out = (uint8_t)cl;
-    else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
-    p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
+    if (lane == 0) {
+        uint8_t out;
+        if (p.forced) out = p.forced_cls[c];
+        else if (p.scheme == HFV_HYBRID) out = (uint8_t)cl;
+        else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
+        p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
+    }
 }
 
 template <class T>
@@ -157,7 +245,7 @@ __global__ void k_tag(KParams<T> p)
     uint8_t r = p.raw[c];
     int t = r & 3;
     if (!p.forced && p.scheme == HFV_HYBRID) {
-        int nf = p.nfc[c];
+        int nf = p.nfc[c] & 15;
         for (int f = 0; f < nf; ++f) {
             int64_t j = p.nbr[c * 6 + f];
             if (j >= 0) {
@@ -239,239 +327,280 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls
     }
 }
 
+// K3: CWENOZ on the CWENOZ queue, one group per queued cell (Sec. 2.3).
+// Lanes share the stencil gather; lane k forms coefficient k of p_opt;
+// lane (f, k) forms the directional degree-1 coefficients; lane v forms the
+// indicators and weights of variable v; lane q writes face point q.
 template <class C, class T>
 __global__ void __launch_bounds__(128) k_cweno(KParams<T> p, const T* __restrict__ U)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, N = C::N, MD = C::MD;
+    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
+    __shared__ T sU[CPB][M][NV];
+    __shared__ T sA[CPB][N][NV];          // p_opt coefficients
+    __shared__ T sS[CPB][6][D][NV];       // directional coefficients
+    __shared__ T sC[CPB][NV][D + 1];      // per variable: omega_1 / lambda_1 and the linear combination
+    const Grp<G> grp;
+    const int gi = threadIdx.x / G, lane = grp.lane;
     const int64_t nc = p.nc;
     const int cnt = p.counts[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
         const int64_t c = p.queue[i];
         T uc[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-        T du[M][NV];
         const int32_t* st = p.sten + c * M;
-        for (int m = 0; m < M; ++m) {
-            int64_t j = st[m];
+        for (int m = lane; m < M; m += G) {
+            const int64_t j = st[m];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) du[m][v] = U[v * nc + j] - uc[v];
+            for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j] - uc[v];
         }
-        const int nf = p.nfc[c];
-        const T lam1 = p.lam1, lams = (T(1) - lam1) / T(nf);
+        grp.sync();
+        const int nf = p.nfc[c] & 15;
+        // p_opt: a_k = sum_m P_km (U_m - U_0)
         const T* P = p.P + c * (int64_t)N * M;
-        const T* OI = p.OI + c * (int64_t)C::NOI;
-        T c1[NV], g[NV][D];
-        for (int v = 0; v < NV; ++v) {
-            T aopt[N];
-            for (int k = 0; k < N; ++k) {
-                T s = T(0);
-                for (int m = 0; m < M; ++m) s += P[k * M + m] * du[m][v];
-                aopt[k] = s;
+        for (int k = lane; k < N; k += G) {
+            T row[M];
+            load_row<T, M>(P + k * M, row);
+            T acc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] = T(0);
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] += row[m] * sU[gi][m][v];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sA[gi][k][v] = acc[v];
+        }
+        // directional degree-1 polynomials
+        for (int t = lane; t < nf * D; t += G) {
+            const int f = t / D, k = t % D;
+            const uint8_t* idx = p.dir + (c * 6 + f) * MD;
+            const T* Dm = p.Dd + ((c * 6 + f) * D + k) * (int64_t)MD;
+            T acc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] = T(0);
+#pragma unroll
+            for (int b = 0; b < MD; ++b) {
+                const T dk = Dm[b];
+                const int m = idx[b];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] += dk * sU[gi][m][v];
             }
-            T as[6][D];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sS[gi][f][k][v] = acc[v];
+        }
+        grp.sync();
+        // indicators and weights, one lane per variable
+        if (lane < NV) {
+            const int v = lane;
+            const T lam1 = p.lam1, lams = (T(1) - lam1) / T(nf);
+            const T* OI = p.OI + c * (int64_t)C::NOI;
             T sumlin[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) sumlin[k] = T(0);
-            for (int f = 0; f < nf; ++f) {
-                const uint8_t* idx = p.dir + (c * 6 + f) * MD;
-                const T* Dm = p.Dd + (c * 6 + f) * (int64_t)D * MD;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    T s = T(0);
-                    for (int b = 0; b < MD; ++b) s += Dm[k * MD + b] * du[idx[b]][v];
-                    as[f][k] = s;
-                    sumlin[k] += s;
-                }
+            for (int k = 0; k < D; ++k) {
+                T s0 = T(0);
+                for (int f = 0; f < nf; ++f) s0 += sS[gi][f][k][v];
+                sumlin[k] = s0;
             }
             // p_1 = (p_opt - sum_s lambda_s p_s) / lambda_1
             T a1[N];
-            for (int k = 0; k < N; ++k) a1[k] = (aopt[k] - (k < D ? lams * sumlin[k] : T(0))) / lam1;
-            // smoothness indicators SI = a^T OI a (packed upper triangle)
+#pragma unroll
+            for (int k = 0; k < N; ++k) a1[k] = (sA[gi][k][v] - (k < D ? lams * sumlin[k < D ? k : 0] : T(0))) / lam1;
             T si1 = T(0);
-            for (int k = 0, o = 0; k < N; ++k) {
-                T s = OI[o++] * a1[k];
-                for (int l = k + 1; l < N; ++l) s += T(2) * OI[o++] * a1[l];
-                si1 += a1[k] * s;
-            }
-            T sis[6];
-            T tsum = T(0);
-            for (int f = 0; f < nf; ++f) {
-                T s = T(0);
-                for (int k = 0; k < D; ++k) {
-                    int o = k * N - k * (k - 1) / 2;
-                    T t = OI[o] * as[f][k];
-                    for (int l = k + 1; l < D; ++l) t += T(2) * OI[o + (l - k)] * as[f][l];
-                    s += as[f][k] * t;
+            {
+                int o = 0;
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    T t = OI[o++] * a1[k];
+#pragma unroll
+                    for (int l = k + 1; l < N; ++l) t += T(2) * OI[o++] * a1[l];
+                    si1 += a1[k] * t;
                 }
-                sis[f] = s;
-                tsum += tabs(s - si1);
+            }
+            T sis[6], tsum = T(0);
+            for (int f = 0; f < nf; ++f) {
+                T s0 = T(0);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const int o = k * N - k * (k - 1) / 2;
+                    T t = OI[o] * sS[gi][f][k][v];
+#pragma unroll
+                    for (int l = k + 1; l < D; ++l) t += T(2) * OI[o + (l - k)] * sS[gi][f][l][v];
+                    s0 += sS[gi][f][k][v] * t;
+                }
+                sis[f] = s0;
+                tsum += tabs(s0 - si1);
             }
             const T tau = tpow(tsum / T(nf), p.b_cw);
-            T w1 = lam1 * (T(1) + tau / (p.eps_cw + si1));
-            T wsum = w1;
-            T ws[6];
+            const T w1 = lam1 * (T(1) + tau / (p.eps_cw + si1));
+            T wsum = w1, ws[6];
             for (int f = 0; f < nf; ++f) {
                 ws[f] = lams * (T(1) + tau / (p.eps_cw + sis[f]));
                 wsum += ws[f];
             }
             const T om1 = w1 / wsum;
-            c1[v] = om1 / lam1;
+            // p_cweno = (omega_1/lambda_1) p_opt + sum_s (omega_s - omega_1 lambda_s / lambda_1) p_s
+            sC[gi][v][0] = om1 / lam1;
 #pragma unroll
-            for (int k = 0; k < D; ++k) g[v][k] = T(0);
-            for (int f = 0; f < nf; ++f) {
-                T cf = ws[f] / wsum - om1 * lams / lam1;
-#pragma unroll
-                for (int k = 0; k < D; ++k) g[v][k] += cf * as[f][k];
+            for (int k = 0; k < D; ++k) {
+                T gk = T(0);
+                for (int f = 0; f < nf; ++f) gk += (ws[f] / wsum - om1 * lams / lam1) * sS[gi][f][k][v];
+                sC[gi][v][1 + k] = gk;
             }
         }
-        // p_cweno = (omega_1/lambda_1) p_opt + sum_s (omega_s - omega_1 lambda_s / lambda_1) p_s
+        grp.sync();
         const int Q = nf * NFP;
         const int64_t q0 = p.qoff[c];
-        T* FS = p.FS + q0 * NV;
-        const T* Phil = p.Phil + q0 * D;
-        const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-        const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
         bool fail = false;
-        for (int q = 0; q < Q; ++q) {
+        if (lane < Q) {
+            T* FS = p.FS + (q0 + lane) * NV;
+            T ph[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
             T w[NV];
+            load_state<T, NV>(FS, w);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                T s = uc[v] + c1[v] * (FS[q * NV + v] - uc[v]);
+                T s0 = uc[v] + sC[gi][v][0] * (w[v] - uc[v]);
 #pragma unroll
-                for (int k = 0; k < D; ++k) s += Phil[q * D + k] * g[v][k];
-                w[v] = s;
+                for (int k = 0; k < D; ++k) s0 += ph[k] * sC[gi][v][1 + k];
+                w[v] = s0;
             }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) FS[q * NV + v] = w[v];
-            T pw = pressure<T, D>(w, p.gamma);
-            if (!(tabs(w[0] - rb) <= rlim) || !(tabs(pw - pb) <= plim)) fail = true;
+            store_state<T, NV>(FS, w);
+            const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
+            const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
+            fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
         }
-        if (fail) p.cls[c] = CLS_FIRST;
+        if (grp.any(fail) && lane == 0) p.cls[c] = CLS_FIRST;
+        grp.sync();
     }
 }
 
+// K4: MUSCL with Barth-Jespersen on the MUSCL queue (Sec. 2.2), one group per
+// queued cell: degree-1 gradient from the first Md stencil cells, limiter
+// bounds from the cell and its face neighbours (the first stencil layer).
 template <class C, class T>
 __global__ void __launch_bounds__(128) k_muscl(KParams<T> p, const T* __restrict__ U)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, MD = C::MD;
+    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
+    __shared__ T sU[CPB][MD][NV];
+    __shared__ T sG[CPB][NV][D];
+    const Grp<G> grp;
+    const int gi = threadIdx.x / G, lane = grp.lane;
     const int64_t nc = p.nc;
     const int cnt = p.counts[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+    for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
         const int64_t c = p.queue[nc + i];
         T uc[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-        const int nf = p.nfc[c];
-        const int Q = nf * NFP;
-        const int64_t q0 = p.qoff[c];
-        const T* Phil = p.Phil + q0 * D;
-        const T* G = p.G + c * (int64_t)D * MD;
         const int32_t* st = p.sten + c * M;
-        T grad[NV][D], theta[NV];
+        for (int m = lane; m < MD; m += G) {
+            const int64_t j = st[m];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j];
+        }
+        grp.sync();
+        const int nfv = p.nfc[c];
+        const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
+        const T* Gm = p.G + c * (int64_t)D * MD;
+        for (int t = lane; t < NV * D; t += G) {
+            const int v = t / D, k = t % D;
+            T acc = T(0);
+#pragma unroll
+            for (int b = 0; b < MD; ++b) acc += Gm[k * MD + b] * (sU[gi][b][v] - uc[v]);
+            sG[gi][v][k] = acc;
+        }
+        grp.sync();
+        const int64_t q0 = p.qoff[c];
+        T ph[D];
+        if (lane < Q)
+#pragma unroll
+            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
+        T w[NV];
+#pragma unroll
         for (int v = 0; v < NV; ++v) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) grad[v][k] = T(0);
-            for (int b = 0; b < MD; ++b) {
-                T dv = U[v * nc + st[b]] - uc[v];
-#pragma unroll
-                for (int k = 0; k < D; ++k) grad[v][k] += G[k * MD + b] * dv;
-            }
             T lo = uc[v], hi = uc[v];
-            for (int f = 0; f < nf; ++f) {
-                int64_t j = p.nbr[c * 6 + f];
-                if (j < 0) continue;
-                T uj = U[v * nc + j];
-                lo = tmin(lo, uj);
-                hi = tmax(hi, uj);
+            for (int m = 0; m < n1; ++m) {
+                lo = tmin(lo, sU[gi][m][v]);
+                hi = tmax(hi, sU[gi][m][v]);
             }
-            T th = T(1);
-            for (int q = 0; q < Q; ++q) {
-                T dl = T(0);
+            T dl = T(0), t = T(1);
+            if (lane < Q) {
 #pragma unroll
-                for (int k = 0; k < D; ++k) dl += Phil[q * D + k] * grad[v][k];
-                T t = T(1);
+                for (int k = 0; k < D; ++k) dl += ph[k] * sG[gi][v][k];
                 if (dl > T(0)) t = tmin(T(1), (hi - uc[v]) / dl);
                 else if (dl < T(0)) t = tmin(T(1), (lo - uc[v]) / dl);
-                th = tmin(th, t);
             }
-            theta[v] = th;
+            const T th = grp.min(t);
+            w[v] = uc[v] + th * dl;
         }
-        T* FS = p.FS + q0 * NV;
-        const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-        const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
         bool fail = false;
-        for (int q = 0; q < Q; ++q) {
-            T w[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                T dl = T(0);
-#pragma unroll
-                for (int k = 0; k < D; ++k) dl += Phil[q * D + k] * grad[v][k];
-                w[v] = uc[v] + theta[v] * dl;
-                FS[q * NV + v] = w[v];
-            }
-            T pw = pressure<T, D>(w, p.gamma);
-            if (!(tabs(w[0] - rb) <= rlim) || !(tabs(pw - pb) <= plim)) fail = true;
+        if (lane < Q) {
+            store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
+            const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
+            const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
+            fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
         }
-        if (fail) p.cls[c] = CLS_FIRST;
+        if (grp.any(fail) && lane == 0) p.cls[c] = CLS_FIRST;
+        grp.sync();
     }
 }
 
+// K6: Riemann fluxes at the face points and the residual, one group per cell,
+// lane q the flux at face point q; the group sums F w |S| in a fixed order.
 template <class C, class T, int KIND>
 __global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict__ U, T* __restrict__ R)
 {
     constexpr int NV = C::NV, D = C::D, NFP = C::NFP;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
+    const Grp<G> grp;
+    const int gi = threadIdx.x / G, lane = grp.lane;
+    const int64_t c = (int64_t)blockIdx.x * CPB + gi;
     if (c >= p.nc) return;
     const int64_t nc = p.nc;
-    T uc[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-    const int cc = p.cls[c];
-    const int nf = p.nfc[c];
+    const int nf = p.nfc[c] & 15, Q = nf * NFP;
     const int64_t q0 = p.qoff[c];
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
-    for (int f = 0; f < nf; ++f) {
+    if (lane < Q) {
+        const int f = lane / NFP, a = lane - f * NFP;
+        const int cc = p.cls[c];
+        T wl[NV], wr[NV], F[NV];
+        if (cc == CLS_FIRST) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) wl[v] = U[v * nc + c];
+        } else {
+            load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
+        }
         const int64_t j = p.nbr[c * 6 + f];
-        const int fj = p.nbrf[c * 6 + f];
+        if (j < 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+        } else if (p.cls[j] == CLS_FIRST) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) wr[v] = U[v * nc + j];
+        } else {
+            load_state<T, NV>(p.FS + (p.qoff[j] + p.nbrf[c * 6 + f] * NFP + a) * NV, wr);
+        }
         const T* n = p.nrm + (c * 6 + f) * 3;
         T nn[3] = {n[0], n[1], n[2]};
-        T uj[NV];
-        int cj = CLS_LIN;
-        if (j >= 0) {
-            cj = p.cls[j];
-            if (cj == CLS_FIRST)
+        riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
+        const T w = p.W[q0 + lane];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) uj[v] = U[v * nc + j];
-        }
-        for (int a = 0; a < NFP; ++a) {
-            const int q = f * NFP + a;
-            T wl[NV], wr[NV], F[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) wl[v] = cc == CLS_FIRST ? uc[v] : p.FS[(q0 + q) * NV + v];
-            if (j < 0) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) wr[v] = wl[v];
-            } else if (cj == CLS_FIRST) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) wr[v] = uj[v];
-            } else {
-                const int64_t qj = p.qoff[j] + fj * NFP + a;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) wr[v] = p.FS[qj * NV + v];
-            }
-            riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
-            const T w = p.W[q0 + q];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] += F[v] * w;
-        }
+        for (int v = 0; v < NV; ++v) acc[v] = F[v] * w;
     }
-    const T iv = p.ivol[c];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) R[v * nc + c] = -acc[v] * iv;
+    for (int v = 0; v < NV; ++v) acc[v] = grp.sum(acc[v]);
+    if (lane < NV) {
+        T val = acc[0];
+#pragma unroll
+        for (int v = 1; v < NV; ++v) val = lane == v ? acc[v] : val;
+        R[lane * nc + c] = -val * p.ivol[c];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -537,21 +666,22 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
 {
     KParams<T> p = make_params<T>(s, forced);
     const int64_t nc = p.nc;
-    const unsigned g128 = (unsigned)((nc + 127) / 128), g256 = (unsigned)((nc + 255) / 256);
-    { Launch l(s, KID_LINEAR, st); k_linear<C, T><<<g128, 128, 0, st>>>(p, U); }
+    constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
+    const unsigned gcell = (unsigned)((nc + CPB - 1) / CPB), g256 = (unsigned)((nc + 255) / 256);
+    { Launch l(s, KID_LINEAR, st); k_linear<C, T><<<gcell, 128, 0, st>>>(p, U); }
     { Launch l(s, KID_TAG, st); k_tag<T><<<g256, 256, 0, st>>>(p); }
     { Launch l(s, KID_COUNT, st); k_count<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks); }
     { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
     { Launch l(s, KID_SCATTER, st); k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue); }
-    const unsigned gq = (unsigned)std::min<int64_t>((nc + 127) / 128, 152 * 8);
+    const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
     { Launch l(s, KID_CWENO, st); k_cweno<C, T><<<gq, 128, 0, st>>>(p, U); }
     { Launch l(s, KID_MUSCL, st); k_muscl<C, T><<<gq, 128, 0, st>>>(p, U); }
     {
         Launch l(s, KID_FLUX, st);
         switch (s->p.flux) {
-        case HFV_RUSANOV: k_flux<C, T, kRusanov><<<g128, 128, 0, st>>>(p, U, R); break;
-        case HFV_HLL: k_flux<C, T, kHLL><<<g128, 128, 0, st>>>(p, U, R); break;
-        default: k_flux<C, T, kHLLC><<<g128, 128, 0, st>>>(p, U, R); break;
+        case HFV_RUSANOV: k_flux<C, T, kRusanov><<<gcell, 128, 0, st>>>(p, U, R); break;
+        case HFV_HLL: k_flux<C, T, kHLL><<<gcell, 128, 0, st>>>(p, U, R); break;
+        default: k_flux<C, T, kHLLC><<<gcell, 128, 0, st>>>(p, U, R); break;
         }
     }
     if (cls_out) HFV_CUDA_CHECK(cudaMemcpyAsync(cls_out, s->a.cls, nc, cudaMemcpyDeviceToDevice, st));
@@ -585,8 +715,11 @@ __global__ void k_set(double* x, double v) { *x = v; }
 
 __global__ void k_dt_init(unsigned long long* x) { *x = 0x7ff0000000000000ull; }
 
-// dt_c = cfl |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|; min over cells (order-free, exact)
-__global__ void __launch_bounds__(256) k_dt(int64_t nc, int d, const double* __restrict__ U, const double* __restrict__ vol,
+// dt_c = cfl |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|; min over cells (order-free,
+// exact).  Evaluated in the residual's precision: FP64, or FP32 from the FP32
+// copy of the state (a stability estimate, not part of the conserved update).
+template <class T>
+__global__ void __launch_bounds__(256) k_dt(int64_t nc, int d, const T* __restrict__ U, const double* __restrict__ vol,
                                             const double* __restrict__ area, const double* __restrict__ nrm,
                                             const uint8_t* __restrict__ nfc, double gamma, double cfl,
                                             unsigned long long* out)
@@ -595,20 +728,23 @@ __global__ void __launch_bounds__(256) k_dt(int64_t nc, int d, const double* __r
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dtc = INFINITY;
     if (c < nc) {
-        double rho = U[c], m2 = 0.0, u[3] = {0, 0, 0};
+        const T g = (T)gamma;
+        T rho = U[c], m2 = T(0), u[3] = {T(0), T(0), T(0)};
         for (int k = 0; k < d; ++k) {
-            u[k] = U[(1 + k) * nc + c] / rho;
-            m2 += U[(1 + k) * nc + c] * U[(1 + k) * nc + c];
+            const T mk = U[(1 + k) * nc + c];
+            u[k] = mk / rho;
+            m2 += mk * mk;
         }
-        double p = (gamma - 1.0) * (U[(d + 1) * nc + c] - 0.5 * m2 / rho);
-        double a = sqrt(gamma * p / rho);
-        double lam = 0.0;
-        for (int f = 0; f < nfc[c]; ++f) {
+        const T p = (g - T(1)) * (U[(d + 1) * nc + c] - T(0.5) * m2 / rho);
+        const T a = tsqrt<T>(g * p / rho);
+        T lam = T(0);
+        const int nf = nfc[c] & 15;
+        for (int f = 0; f < nf; ++f) {
             const double* n = nrm + (c * 6 + f) * 3;
-            double un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
-            lam += (fabs(un) + a) * area[c * 6 + f];
+            const T un = u[0] * (T)n[0] + u[1] * (T)n[1] + u[2] * (T)n[2];
+            lam += (tabs(un) + a) * (T)area[c * 6 + f];
         }
-        dtc = cfl * vol[c] / lam;
+        dtc = (double)((T)cfl * (T)vol[c] / lam);
         if (!(dtc > 0.0)) dtc = 0.0;  // a non-physical state stops the step at dt = 0
     }
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
@@ -654,16 +790,31 @@ int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced
     return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st);
 }
 
-int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
+template <class T>
+static int launch_dt_t(hfv_scheme* s, const T* U, double cfl, double* dt_dev, cudaStream_t st)
 {
-    cudaStream_t st = (cudaStream_t)stream;
     const int64_t nc = s->mesh->nc;
     { Launch l(s, KID_DT, st); k_dt_init<<<1, 1, 0, st>>>((unsigned long long*)dt_dev); }
     {
         Launch l(s, KID_DT, st);
-        k_dt<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, s->d, U, s->a.vol, s->a.area, s->a.nrm64, s->a.nfc,
-                                                             s->p.gamma, cfl, (unsigned long long*)dt_dev);
+        k_dt<T><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, s->d, U, s->a.vol, s->a.area, s->a.nrm64, s->a.nfc,
+                                                                s->p.gamma, cfl, (unsigned long long*)dt_dev);
     }
+    HFV_CUDA_CHECK(cudaGetLastError());
+    return HFV_OK;
+}
+
+int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->p.precision == HFV_FP32) {
+        // the FP32 copy of U drives the estimate
+        const int64_t n = (int64_t)s->nv * s->mesh->nc;
+        { Launch l(s, KID_CVT, st); k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, U, s->a.Uf); }
+        return launch_dt_t<float>(s, s->a.Uf, cfl, dt_dev, st);
+    }
+    int rc = launch_dt_t<double>(s, U, cfl, dt_dev, st);
+    if (rc != HFV_OK) return rc;
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
 }
@@ -674,13 +825,14 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     const int64_t n = (int64_t)s->nv * s->mesh->nc;
     const unsigned g = (unsigned)((n + 255) / 256);
     int rc;
+    const bool f32 = s->p.precision == HFV_FP32;
     if (dt > 0.0) { Launch l(s, KID_DT, st); k_set<<<1, 1, 0, st>>>(s->a.dt, dt); }
-    else if ((rc = launch_dt(s, U, cfl, s->a.dt, stream)) != HFV_OK) return rc;
+    else if ((rc = launch_dt(s, U, cfl, s->a.dt, stream)) != HFV_OK) return rc;   // FP32: also fills Uf
     const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
     double* outs[3] = {s->a.U1, s->a.U2, U};
     const double* ins[3] = {U, s->a.U1, s->a.U2};
-    if (s->p.precision == HFV_FP32) {
-        { Launch l(s, KID_CVT, st); k_to_f32<<<g, 256, 0, st>>>(n, U, s->a.Uf); }
+    if (f32) {
+        if (dt > 0.0) { Launch l(s, KID_CVT, st); k_to_f32<<<g, 256, 0, st>>>(n, U, s->a.Uf); }
         for (int k = 0; k < 3; ++k) {
             if ((rc = launch_residual(s, s->a.Uf, s->a.Rs, nullptr, nullptr, stream)) != HFV_OK) return rc;
             Launch l(s, KID_RK, st);

@@ -70,6 +70,7 @@ int build_stencils(hfv_scheme* s)
     s->sshift.assign(nc * M * 3, 0);
     s->dir.assign(nc * kMaxFaces * Md, 0);
     s->nd.assign(nc * kMaxFaces, 0);
+    s->n1.assign(nc, 0);
 
     std::vector<Cand> visited, layer, next, chosen;
     std::vector<int32_t> mark(nc, -1);   // last cell whose BFS visited this cell
@@ -114,6 +115,9 @@ int build_stencils(hfv_scheme* s)
             return HFV_ERR_STENCIL;
         }
         std::sort(chosen.begin(), chosen.end());
+        int first_layer = 0;
+        for (int a = 0; a < M; ++a) first_layer += chosen[a].layer == 1;
+        s->n1[i] = (uint8_t)first_layer;
         for (int a = 0; a < M; ++a) {
             s->sten[i * M + a] = chosen[a].id;
             for (int k = 0; k < 3; ++k) s->sshift[(i * M + a) * 3 + k] = chosen[a].k[k];

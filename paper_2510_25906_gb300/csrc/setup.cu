@@ -134,7 +134,7 @@ int build_operators(hfv_scheme* s, void* stream)
     std::vector<double> ivol(nc), thr(nc);
     for (int64_t c = 0; c < nc; ++c) {
         int t = m->type[c];
-        nfc[c] = (uint8_t)type_nfaces(t);
+        nfc[c] = (uint8_t)(type_nfaces(t) | (s->n1[c] << 4));
         for (int f = 0; f < type_nfaces(t); ++f) {
             int64_t cf = c * kMaxFaces + f;
             int64_t oc = c;

@@ -10,7 +10,7 @@
 //   3. A_mk = int_{V_m'} phi_k over each (periodically shifted) stencil cell;
 //   4. Householder QR of A, pseudo-inverse A^+ column by column, and
 //      P = A^+ diag(|V_m'|) so that the coefficients are a = P (U_m - U_0);
-//   5. basis values at the cell's face points, L = Phi P (candidate values
+//   5. basis values at the cell's face points, L = Phi P (rows of candidate values
 //      U_0 + L (U_m - U_0)) and the linear block Phi_lin;
 //   6. OI_kq = sum_{1<=|beta|<=r} int_{V_0'} D^beta phi_k D^beta phi_q in
 //      reference coordinates (h_c = 1), from exact moments of the cell;
@@ -59,7 +59,7 @@ struct SetupParams {
 };
 
 struct SetupOut {
-    double* L;      // cell c at M*qoff[c], [M][Q_c]
+    double* L;      // cell c at M*qoff[c], [Q_c][M] (one row per face point)
     double* P;      // [nc][N][M]
     double* Phil;   // [qoff][d]
     double* OI;     // [nc][N(N+1)/2]
@@ -227,7 +227,6 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     const int t = S.type[c];
     const int nf = nfaces(t);
     const int64_t q0 = S.qoff[c];
-    const int Q = (int)(S.qoff[c + 1] - q0);
 
     // 1. reference map of cell c
     double x0[3], J[3][3], Ji[3][3];
@@ -337,7 +336,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
             for (int m = 0; m < M; ++m) {
                 double s = 0.0;
                 for (int kk = 0; kk < N; ++kk) s += phi[kk] * P[kk * M + m];
-                L[(int64_t)m * Q + q] = s;
+                L[(int64_t)q * M + m] = s;
             }
             for (int kk = 0; kk < d; ++kk) O.Phil[(q0 + q) * d + kk] = phi[kk];
             O.W[q0 + q] = wgt;
