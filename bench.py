@@ -169,11 +169,12 @@ class Clocks:
 
 def _k1_bytes(mesh, s, b):
     """Algorithmic bytes of one launch of the linear-candidate + detector
-    kernel: per cell U_i (nv b), stencil ids (4 M), L (Q M b), face-neighbour
-    ids (4 nf), threshold (b), face-point states written (Q nv b), class (1)."""
+    kernel: per cell U_i (nv b), stencil ids (4 M), L (Q M b), threshold (b),
+    face-point states written (Q nv b), face counts + offsets + class (10).
+    Stencil neighbours' states are L2 hits (U is read from DRAM once)."""
     nf = np.where(mesh.cell_type == 4, 6, np.where(mesh.cell_type == 2, 4, 3)).astype(np.int64)
     Q = nf * s.nfp
-    per = s.nv * b + 4 * s.M + Q * s.M * b + 4 * nf + b + Q * s.nv * b + 1
+    per = s.nv * b + 4 * s.M + Q * s.M * b + b + Q * s.nv * b + 10
     return int(per.sum())
 
 
