@@ -211,7 +211,9 @@ def time_steps(H, torch, g, U0, steps, warmup, cfl, dev, with_timer=False):
 
 def kernel_pass(H, torch, g, U0, steps, cfl, dev):
     """Eager steps with the library's per-kernel event timer (events recorded
-    on the launch stream around every kernel), L2 flushed between steps."""
+    on the launch stream around every kernel), L2 flushed between steps; the
+    kernels of a step are queued behind a ~2 ms sleep kernel, so they run
+    back to back as in the graph-timed region."""
     st = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     U = torch.tensor(U0, dtype=torch.float64, device=dev)
@@ -220,6 +222,9 @@ def kernel_pass(H, torch, g, U0, steps, cfl, dev):
     with torch.cuda.stream(st):
         for _ in range(steps):
             flush.zero_()
+            # a bounded sleep kernel keeps the GPU busy while the host enqueues
+            # the step, so no event pair spans a host launch gap
+            torch.cuda._sleep(4_000_000)
             g.step(U, cfl=cfl, stream=st)
             times = g.kernel_times()
     g.kernel_timer(False)

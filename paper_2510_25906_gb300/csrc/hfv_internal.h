@@ -51,16 +51,17 @@ struct hfv_mesh {
 // ---------------------------------------------------------------------------
 struct hfv_dev_arrays {
     // topology / geometry (always present)
-    int32_t* sten;     // [nc][M]
+    int32_t* sten;     // [nc_pad][M] (rows past nc are zero)
     int32_t* nbr;      // [nc][6]
     int8_t* nbrf;      // [nc][6]
     uint8_t* nfc;      // [nc] faces per cell | (distinct face neighbours << 4)
-    int64_t* qoff;     // [nc+1] CSR offsets of face points
+    int64_t* qoff;     // [nc+1] offsets of face points: c * (max faces * points per face)
+    int64_t* loff;     // [nc_pad+1] element offsets of the per-cell L blocks (16-byte padded)
     uint8_t* dir;      // [nc][6][Md] local stencil index of directional cells
     // per precision (T = double or float), stored as void*
-    void* L;           // [qoff*M]: cell c at M*qoff[c], layout [Q_c][M]
+    void* L;           // cell c at loff[c], layout [Q_c][M], blocks padded to 16 bytes
     void* P;           // [nc][N][M]
-    void* Phil;        // [qoff*d]: cell c at d*qoff[c], layout [Q_c][d]
+    void* Phil;        // cell c at d*qoff[c], layout [Q_c][d]
     void* OI;          // [nc][N*(N+1)/2] packed upper triangle, row-major
     void* D;           // [nc][6][d][Md]
     void* G;           // [nc][d][Md]
@@ -110,6 +111,9 @@ struct hfv_scheme {
     hfv_scheme_params p{};
     int r = 0, d = 0, nv = 0, N = 0, M = 0, Md = 0, nq = 0, nfp = 0;
     int64_t qtot = 0;
+    int64_t nc_pad = 0;             // cells rounded up to a multiple of 64 (bulk-copy tiles)
+    int64_t ltot = 0;               // elements of L
+    std::vector<int64_t> loff;      // [nc_pad+1]
     int nblocks = 0;
     // host copies kept for introspection
     std::vector<int32_t> sten;      // [nc][M]

@@ -43,6 +43,7 @@ struct KParams {
     const int8_t* nbrf;
     const uint8_t* nfc;
     const int64_t* qoff;
+    const int64_t* loff;
     const uint8_t* dir;
     // operators
     const T* L;

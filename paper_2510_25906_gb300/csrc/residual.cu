@@ -21,6 +21,7 @@
 
 #include "hfv_internal.h"
 #include "kernels.cuh"
+#include "tma.cuh"
 
 namespace hfv {
 
@@ -88,7 +89,7 @@ struct GroupSize {
 };
 
 // contiguous row of M values with the widest aligned vector loads (rows start
-// at (qoff + q) * M elements: 16-byte aligned when M * sizeof(T) % 16 == 0)
+// at (c * QMAX + q) * M elements: 16-byte aligned when M * sizeof(T) % 16 == 0)
 template <class T, int M>
 __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[M])
 {
@@ -113,6 +114,33 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[M])
     } else {
 #pragma unroll
         for (int m = 0; m < M; ++m) r[m] = __ldg(p + m);
+    }
+}
+
+template <class T, int M>
+__device__ __forceinline__ void load_row_smem(const T* p, T (&r)[M])
+{
+    if constexpr (sizeof(T) == 4 && M % 4 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 4) {
+            float4 v = *reinterpret_cast<const float4*>(p + m);
+            r[m] = v.x; r[m + 1] = v.y; r[m + 2] = v.z; r[m + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && M % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 2) {
+            float2 v = *reinterpret_cast<const float2*>(p + m);
+            r[m] = v.x; r[m + 1] = v.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
+#pragma unroll
+        for (int m = 0; m < M; m += 2) {
+            double2 v = *reinterpret_cast<const double2*>(p + m);
+            r[m] = v.x; r[m + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < M; ++m) r[m] = p[m];
     }
 }
 
@@ -145,95 +173,174 @@ __device__ __forceinline__ void load_state(const T* __restrict__ p, T (&w)[NV])
     }
 }
 
-// K1: one group per cell.  The group gathers the M stencil states into shared
-// memory; lane q forms the candidate at face point q from its row of L; the
-// detector bounds come from the first stencil layer (the face neighbours).
+// K1: persistent, warp-specialised.  Tiles of NG consecutive cells: a
+// producer warp streams each tile's contiguous L blocks and stencil ids into a
+// ring of shared-memory stages with bulk copies (TMA engine, mbarrier
+// completion); eight consumer warps hold NG groups of G lanes, one group per
+// cell.  A group gathers the M stencil states, lane q forms the candidate at
+// face point q from its row of L, and the group runs the detector (bounds
+// from the first stencil layer = the face neighbours) and the Harten test.
 template <class C, class T>
-__global__ void __launch_bounds__(128) k_linear(KParams<T> p, const T* __restrict__ U)
+struct K1Shape {
+    static constexpr int G = GroupSize<C::QMAX>::value;
+    static constexpr int CONSUMERS = 256;                    // 8 warps
+    static constexpr int NG = CONSUMERS / G;                 // cells per tile
+    static constexpr int PER16 = 16 / (int)sizeof(T);
+    static constexpr int LMAX = (C::QMAX * C::M + PER16 - 1) / PER16 * PER16;  // elements per cell block
+    static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
+    static constexpr int SBYTES = NG * C::M * 4;
+    static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
+    static constexpr int STAGES = STAGE * 4 <= 100 * 1024 ? 4 : STAGE * 3 <= 150 * 1024 ? 3 : 2;
+    static constexpr int SU = NG * C::M * C::NV * (int)sizeof(T);
+    static constexpr int SMEM = STAGES * STAGE + (SU + 127) / 128 * 128 + 2 * STAGES * 8;
+    static constexpr int THREADS = CONSUMERS + 32;
+};
+
+template <class C, class T>
+__global__ void __launch_bounds__(288) k_linear(KParams<T> p, const T* __restrict__ U)
 {
-    constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP;
-    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
-    __shared__ T sU[CPB][M][NV];
+    using S = K1Shape<C, T>;
+    constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, G = S::G, NG = S::NG, ST = S::STAGES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    T* sU = reinterpret_cast<T*>(smem + ST * S::STAGE);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + ST * S::STAGE + (S::SU + 127) / 128 * 128);
+    uint64_t* empty = full + ST;
+    const int64_t nc = p.nc;
+    const int64_t ntiles = (nc + NG - 1) / NG;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], S::CONSUMERS / 32);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (threadIdx.x >= S::CONSUMERS) {
+        // ---------------- producer warp ----------------
+        if (threadIdx.x == S::CONSUMERS) {
+            int k = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+                const int s = k % ST;
+                if (k >= ST && !(ok = mbar_wait(&empty[s], ((k / ST) - 1) & 1))) break;
+                const int64_t c0 = tile * NG;
+                const int64_t lb = p.loff[c0], le = p.loff[c0 + NG];
+                const uint32_t lbytes = (uint32_t)((le - lb) * (int64_t)sizeof(T));
+                unsigned char* stage = smem + s * S::STAGE;
+                mbar_arrive_expect_tx(&full[s], lbytes + S::SBYTES);
+                if (lbytes) bulk_g2s(stage, p.L + lb, lbytes, &full[s]);
+                bulk_g2s(stage + S::LBYTES, p.sten + c0 * M, S::SBYTES, &full[s]);
+            }
+            if (!ok) atomicOr(p.status, 4);
+            // every issued copy has landed before the CTA may exit
+            const int issued = k;
+            for (int j = issued - ST > 0 ? issued - ST : 0; j < issued; ++j)
+                if (!mbar_wait(&full[j % ST], (j / ST) & 1)) { atomicOr(p.status, 4); break; }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
-    const int64_t c = (int64_t)blockIdx.x * CPB + gi;
-    if (c >= p.nc) return;
-    const int64_t nc = p.nc;
-    T uc[NV];
+    T* myU = sU + gi * M * NV;
+    int k = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+        const int s = k % ST;
+        const int64_t c0 = tile * NG;
+        const int64_t c = c0 + gi;
+        // independent global loads first, then wait for the stage
+        T uc[NV];
+        int nfv = 0;
+        int64_t lrel = 0;
+        if (c < nc) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-    const int32_t* st = p.sten + c * M;
-    for (int m = lane; m < M; m += G) {
-        const int64_t j = st[m];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j];
-    }
-    const int nfv = p.nfc[c];
-    const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
-    const int64_t q0 = p.qoff[c];
-    T w[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) w[v] = uc[v];
-    T lrow[M];
-    if (lane < Q) load_row<T, M>(p.L + (q0 + lane) * M, lrow);
-    grp.sync();
-    if (lane < Q) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) w[v] += lrow[m] * (sU[gi][m][v] - uc[v]);
+            for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
+            nfv = p.nfc[c];
+            lrel = p.loff[c] - p.loff[c0];
         }
-        store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
-    }
-    if (lane == 0 && !(uc[0] > T(0) && pressure<T, D>(uc, p.gamma) > T(0))) atomicOr(p.status, 1);
-    // Harten test of the linear candidate
-    const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-    bool fail = false;
-    if (lane < Q) {
-        const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
-        fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
-    }
-    const bool hfail = grp.any(fail);
-    int cl = CLS_LIN;
-    if (!p.forced && p.scheme == HFV_HYBRID) {
-        const T thr = p.dxthr[c];
-        const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
-        for (int kind = 0; kind < NV + 1; ++kind) {
-            const bool use = kind == 0 ? (p.nad_vars & 1) : kind == 1 ? (p.nad_vars & 2) : (p.nad_vars & 4);
-            if (!use) continue;
-            const T qi = nad_value<T, D>(uc, kind, p.gamma);
-            T qj = qi, dd = T(0);
-            const bool has = lane < n1;
-            if (has) {
-                T uj[NV];
+        if (!mbar_wait(&full[s], (k / ST) & 1)) {
+            if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
+            break;
+        }
+        const unsigned char* stage = smem + s * S::STAGE;
+        if (c < nc) {
+            const int32_t* st = reinterpret_cast<const int32_t*>(stage + S::LBYTES) + gi * M;
+            for (int m = lane; m < M; m += G) {
+                const int64_t j = st[m];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) uj[v] = sU[gi][lane][v];
-                qj = nad_value<T, D>(uj, kind, p.gamma);
-                dd = tabs(qj - qi);
+                for (int v = 0; v < NV; ++v) myU[m * NV + v] = U[v * nc + j];
             }
-            const T lo = grp.min(qj), hi = grp.max(qj);
-            const T dlo = grp.min(has ? dd : T(INFINITY)), dhi = grp.max(has ? dd : T(-INFINITY));
-            if (n1 == 0 || dhi - dlo < thr) continue;   // deactivated: smooth
-            const T range = hi - lo;
-            const T dm = tmax(p.alpha_m, p.beta_m * range);
-            const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
-            int k = CLS_LIN;
+            const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
+            T w[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) w[v] = uc[v];
+            T lrow[M];
+            if (lane < Q) load_row_smem<T, M>(reinterpret_cast<const T*>(stage) + lrel + lane * M, lrow);
+            grp.sync();
+            const int64_t q0 = c * C::QMAX;
             if (lane < Q) {
-                const T x = nad_value<T, D>(w, kind, p.gamma);
-                if (x <= lo - dm || x >= hi + dm) k = CLS_MU;
-                else if (lo - dw < x && x < hi + dw) k = CLS_LIN;
-                else k = CLS_CW;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) w[v] += lrow[m] * (myU[m * NV + v] - uc[v]);
+                }
+                store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
             }
-            k = grp.max(k);
-            cl = k > cl ? k : cl;
+            if (lane == 0 && !(uc[0] > T(0) && pressure<T, D>(uc, p.gamma) > T(0))) atomicOr(p.status, 1);
+            const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
+            bool fail = false;
+            if (lane < Q) {
+                const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
+                fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
+            }
+            const bool hfail = grp.any(fail);
+            int cl = CLS_LIN;
+            if (!p.forced && p.scheme == HFV_HYBRID) {
+                const T thr = p.dxthr[c];
+                const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
+                for (int kind = 0; kind < NV + 1; ++kind) {
+                    const bool use = kind == 0 ? (p.nad_vars & 1) : kind == 1 ? (p.nad_vars & 2) : (p.nad_vars & 4);
+                    if (!use) continue;
+                    const T qi = nad_value<T, D>(uc, kind, p.gamma);
+                    T qj = qi, dd = T(0);
+                    const bool has = lane < n1;
+                    if (has) {
+                        T uj[NV];
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) uj[v] = myU[lane * NV + v];
+                        qj = nad_value<T, D>(uj, kind, p.gamma);
+                        dd = tabs(qj - qi);
+                    }
+                    const T lo = grp.min(qj), hi = grp.max(qj);
+                    const T dlo = grp.min(has ? dd : T(INFINITY)), dhi = grp.max(has ? dd : T(-INFINITY));
+                    if (n1 == 0 || dhi - dlo < thr) continue;   // deactivated: smooth
+                    const T range = hi - lo;
+                    const T dm = tmax(p.alpha_m, p.beta_m * range);
+                    const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
+                    int kc = CLS_LIN;
+                    if (lane < Q) {
+                        const T x = nad_value<T, D>(w, kind, p.gamma);
+                        if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
+                        else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
+                        else kc = CLS_CW;
+                    }
+                    kc = grp.max(kc);
+                    cl = kc > cl ? kc : cl;
+                }
+            }
+            if (lane == 0) {
+                uint8_t out;
+                if (p.forced) out = p.forced_cls[c];
+                else if (p.scheme == HFV_HYBRID) out = (uint8_t)cl;
+                else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
+                p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
+            }
+            grp.sync();
         }
-    }
-    if (lane == 0) {
-        uint8_t out;
-        if (p.forced) out = p.forced_cls[c];
-        else if (p.scheme == HFV_HYBRID) out = (uint8_t)cl;
-        else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
-        p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -451,7 +558,7 @@ __global__ void __launch_bounds__(128) k_cweno(KParams<T> p, const T* __restrict
         }
         grp.sync();
         const int Q = nf * NFP;
-        const int64_t q0 = p.qoff[c];
+        const int64_t q0 = c * C::QMAX;
         bool fail = false;
         if (lane < Q) {
             T* FS = p.FS + (q0 + lane) * NV;
@@ -514,7 +621,7 @@ __global__ void __launch_bounds__(128) k_muscl(KParams<T> p, const T* __restrict
             sG[gi][v][k] = acc;
         }
         grp.sync();
-        const int64_t q0 = p.qoff[c];
+        const int64_t q0 = c * C::QMAX;
         T ph[D];
         if (lane < Q)
 #pragma unroll
@@ -562,7 +669,7 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict_
     if (c >= p.nc) return;
     const int64_t nc = p.nc;
     const int nf = p.nfc[c] & 15, Q = nf * NFP;
-    const int64_t q0 = p.qoff[c];
+    const int64_t q0 = c * C::QMAX;
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
@@ -584,7 +691,7 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict_
 #pragma unroll
             for (int v = 0; v < NV; ++v) wr[v] = U[v * nc + j];
         } else {
-            load_state<T, NV>(p.FS + (p.qoff[j] + p.nbrf[c * 6 + f] * NFP + a) * NV, wr);
+            load_state<T, NV>(p.FS + (j * C::QMAX + p.nbrf[c * 6 + f] * NFP + a) * NV, wr);
         }
         const T* n = p.nrm + (c * 6 + f) * 3;
         T nn[3] = {n[0], n[1], n[2]};
@@ -647,7 +754,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.nad_vars = s->p.nad_vars;
     p.forced = forced != nullptr;
     p.forced_cls = forced;
-    p.sten = a.sten; p.nbr = a.nbr; p.nbrf = a.nbrf; p.nfc = a.nfc; p.qoff = a.qoff; p.dir = a.dir;
+    p.sten = a.sten; p.nbr = a.nbr; p.nbrf = a.nbrf; p.nfc = a.nfc; p.qoff = a.qoff; p.loff = a.loff; p.dir = a.dir;
     p.L = (const T*)a.L; p.P = (const T*)a.P; p.Phil = (const T*)a.Phil; p.OI = (const T*)a.OI;
     p.Dd = (const T*)a.D; p.G = (const T*)a.G; p.W = (const T*)a.W; p.nrm = (const T*)a.nrm;
     p.ivol = (const T*)a.ivol; p.dxthr = (const T*)a.dxthr;
@@ -668,7 +775,22 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
     const unsigned gcell = (unsigned)((nc + CPB - 1) / CPB), g256 = (unsigned)((nc + 255) / 256);
-    { Launch l(s, KID_LINEAR, st); k_linear<C, T><<<gcell, 128, 0, st>>>(p, U); }
+    {
+        using S1 = K1Shape<C, T>;
+        static int grid1 = 0;   // per instantiation: SMs x resident CTAs
+        if (!grid1) {
+            HFV_CUDA_CHECK(cudaFuncSetAttribute(k_linear<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1::SMEM));
+            int dev = 0, sms = 0, per = 0;
+            HFV_CUDA_CHECK(cudaGetDevice(&dev));
+            HFV_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            HFV_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_linear<C, T>, S1::THREADS, S1::SMEM));
+            grid1 = sms * (per > 0 ? per : 1);
+        }
+        const int64_t ntiles = (nc + S1::NG - 1) / S1::NG;
+        const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, grid1);
+        Launch l(s, KID_LINEAR, st);
+        k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p, U);
+    }
     { Launch l(s, KID_TAG, st); k_tag<T><<<g256, 256, 0, st>>>(p); }
     { Launch l(s, KID_COUNT, st); k_count<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks); }
     { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }

@@ -63,9 +63,23 @@ int build_stencils(hfv_scheme* s)
     }
     const int64_t nc = m->nc;
     const int M = s->M, Md = s->Md;
+    // face-point data live at a fixed stride per cell (the largest face count
+    // of the dimension times the points per face): rows past a cell's own
+    // face points are never read, so the padding costs memory, not traffic
+    const int64_t qs = (int64_t)(d == 2 ? 4 : 6) * s->nfp;
     s->qoff.assign(nc + 1, 0);
-    for (int64_t c = 0; c < nc; ++c) s->qoff[c + 1] = s->qoff[c] + (int64_t)type_nfaces(m->type[c]) * s->nfp;
+    for (int64_t c = 0; c <= nc; ++c) s->qoff[c] = c * qs;
     s->qtot = s->qoff[nc];
+    // L: compact per-cell blocks of Q_c x M values, each padded to 16 bytes so
+    // that a run of consecutive cells is one aligned bulk copy
+    const int per16 = s->p.precision == HFV_FP32 ? 4 : 2;
+    s->nc_pad = (nc + 63) / 64 * 64;
+    s->loff.assign(s->nc_pad + 1, 0);
+    for (int64_t c = 0; c < s->nc_pad; ++c) {
+        int64_t blk = c < nc ? (int64_t)type_nfaces(m->type[c]) * s->nfp * M : 0;
+        s->loff[c + 1] = s->loff[c] + (blk + per16 - 1) / per16 * per16;
+    }
+    s->ltot = s->loff[s->nc_pad];
     s->sten.assign(nc * M, 0);
     s->sshift.assign(nc * M * 3, 0);
     s->dir.assign(nc * kMaxFaces * Md, 0);

@@ -100,9 +100,10 @@ int build_operators(hfv_scheme* s, void* stream)
     // ---- arena layout ----
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
-    size_t o_sten = take(nc * M * 4), o_nbr = take(nc * 6 * 4), o_nbrf = take(nc * 6), o_nfc = take(nc),
-           o_qoff = take((nc + 1) * 8), o_dir = take(nc * 6 * Md);
-    size_t o_L = take(qt * M * b), o_P = take(nc * N * M * b), o_Phil = take(qt * d * b), o_OI = take(nc * NOI * b),
+    const int64_t ncp = s->nc_pad, lt = s->ltot;
+    size_t o_sten = take(ncp * M * 4), o_nbr = take(nc * 6 * 4), o_nbrf = take(nc * 6), o_nfc = take(nc),
+           o_qoff = take((nc + 1) * 8), o_loff = take((ncp + 1) * 8), o_dir = take(nc * 6 * Md);
+    size_t o_L = take(lt * b), o_P = take(nc * N * M * b), o_Phil = take(qt * d * b), o_OI = take(nc * NOI * b),
            o_D = take(nc * 6 * d * Md * b), o_G = take(nc * d * Md * b), o_W = take(qt * b), o_nrm = take(nc * 18 * b),
            o_ivol = take(nc * b), o_thr = take(nc * b);
     size_t o_vol = take(nc * 8), o_area = take(nc * 6 * 8), o_nrm64 = take(nc * 18 * 8);
@@ -116,6 +117,7 @@ int build_operators(hfv_scheme* s, void* stream)
     hfv_dev_arrays& a = s->a;
     a.sten = (int32_t*)(A + o_sten); a.nbr = (int32_t*)(A + o_nbr); a.nbrf = (int8_t*)(A + o_nbrf);
     a.nfc = (uint8_t*)(A + o_nfc); a.qoff = (int64_t*)(A + o_qoff); a.dir = (uint8_t*)(A + o_dir);
+    a.loff = (int64_t*)(A + o_loff);
     a.L = A + o_L; a.P = A + o_P; a.Phil = A + o_Phil; a.OI = A + o_OI; a.D = A + o_D; a.G = A + o_G; a.W = A + o_W;
     a.nrm = A + o_nrm; a.ivol = A + o_ivol; a.dxthr = A + o_thr;
     a.vol = (double*)(A + o_vol); a.area = (double*)(A + o_area); a.nrm64 = (double*)(A + o_nrm64);
@@ -156,6 +158,7 @@ int build_operators(hfv_scheme* s, void* stream)
     SETUP_CHECK(cudaMemcpyAsync(a.nbrf, m->nbrf.data(), nc * 6, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.nfc, nfc.data(), nc, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.qoff, s->qoff.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
+    SETUP_CHECK(cudaMemcpyAsync(a.loff, s->loff.data(), (ncp + 1) * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.dir, s->dir.data(), nc * 6 * Md, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.vol, m->vol.data(), nc * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.area, m->farea.data(), nc * 6 * 8, cudaMemcpyHostToDevice, st));
@@ -170,7 +173,7 @@ int build_operators(hfv_scheme* s, void* stream)
            t_fk = ttake(nc * 18), t_ws = ttake((size_t)chunk * M * N * 8), t_err = ttake(64);
     size_t t_L = 0, t_P = 0, t_Phil = 0, t_OI = 0, t_D = 0, t_G = 0, t_W = 0;
     if (f32) {
-        t_L = ttake(qt * M * 8); t_P = ttake(nc * N * M * 8); t_Phil = ttake(qt * d * 8); t_OI = ttake(nc * NOI * 8);
+        t_L = ttake(lt * 8); t_P = ttake(nc * N * M * 8); t_Phil = ttake(qt * d * 8); t_OI = ttake(nc * NOI * 8);
         t_D = ttake(nc * 6 * d * Md * 8); t_G = ttake(nc * d * Md * 8); t_W = ttake(qt * 8);
     }
     char* T = nullptr;
@@ -191,7 +194,7 @@ int build_operators(hfv_scheme* s, void* stream)
     S.xyz = (const double*)(T + t_xyz); S.cptr = (const int64_t*)(T + t_cptr); S.cidx = (const int32_t*)(T + t_cidx);
     S.type = (const uint8_t*)(T + t_type); S.sten = a.sten; S.sshift = (const int8_t*)(T + t_sshift); S.dir = a.dir;
     S.nd = (const uint8_t*)(T + t_nd); S.fvtx = (const int32_t*)(T + t_fvtx); S.fk = (const int8_t*)(T + t_fk);
-    S.farea = a.area; S.qoff = a.qoff;
+    S.farea = a.area; S.qoff = a.qoff; S.loff = a.loff;
     for (int k = 0; k < 3; ++k) S.period[k] = m->period[k];
     S.d = d; S.r = s->r; S.N = N; S.M = M; S.Md = Md; S.nq = s->nq; S.nfp = s->nfp;
     S.nvq = d == 2 ? s->r + 1 : s->r + 2;
@@ -248,7 +251,7 @@ int build_operators(hfv_scheme* s, void* stream)
     SETUP_CHECK(cudaMemcpyAsync(d_thr, thr.data(), nc * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(d_nrm, nrm.data(), nc * 18 * 8, cudaMemcpyHostToDevice, st));
     if (f32) {
-        convert<float>(O.L, a.L, qt * M, st); convert<float>(O.P, a.P, nc * N * M, st);
+        convert<float>(O.L, a.L, lt, st); convert<float>(O.P, a.P, nc * N * M, st);
         convert<float>(O.Phil, a.Phil, qt * d, st); convert<float>(O.OI, a.OI, nc * NOI, st);
         convert<float>(O.D, a.D, nc * 6 * d * Md, st); convert<float>(O.G, a.G, nc * d * Md, st);
         convert<float>(O.W, a.W, qt, st);

@@ -51,6 +51,7 @@ struct SetupParams {
     const int8_t* fk;        // [nc][6][3] periods added to them for this cell's frame
     const double* farea;     // [nc][6]
     const int64_t* qoff;     // [nc+1]
+    const int64_t* loff;     // [nc+1] offsets of the L blocks
     double period[3];
     int d, r, N, M, Md, nq, nfp, nvq;
     double gfx[kGmax], gfw[kGmax];  // face rule on [0,1]
@@ -59,7 +60,7 @@ struct SetupParams {
 };
 
 struct SetupOut {
-    double* L;      // cell c at M*qoff[c], [Q_c][M] (one row per face point)
+    double* L;      // cell c at loff[c], [Q_c][M] (one row per face point)
     double* P;      // [nc][N][M]
     double* Phil;   // [qoff][d]
     double* OI;     // [nc][N(N+1)/2]
@@ -303,7 +304,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     }
 
     // 5. face points: basis values, L = Phi P, Phi_lin and weights
-    double* L = &O.L[q0 * M];
+    double* L = &O.L[S.loff[c]];
     for (int f = 0; f < nf; ++f) {
         const int32_t* fv = &S.fvtx[(c * 6 + f) * 4];
         const int8_t* k = &S.fk[(c * 6 + f) * 3];
@@ -336,7 +337,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
             for (int m = 0; m < M; ++m) {
                 double s = 0.0;
                 for (int kk = 0; kk < N; ++kk) s += phi[kk] * P[kk * M + m];
-                L[(int64_t)q * M + m] = s;
+                L[(int64_t)q * M + m] = s;   // q < Q_c rows, block padded to 16 bytes
             }
             for (int kk = 0; kk < d; ++kk) O.Phil[(q0 + q) * d + kk] = phi[kk];
             O.W[q0 + q] = wgt;
