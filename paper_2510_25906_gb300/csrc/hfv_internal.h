@@ -85,7 +85,7 @@ struct hfv_dev_arrays {
     double* U1;        // [nv][nc]
     double* U2;        // [nv][nc]
     void* Rs;          // [nv][nc] residual of a stage (precision T)
-    float* Uf;         // [nv][nc] FP32 copy of the stage state (HFV_FP32 only)
+    void* UA;          // [nc][P] cell-major copy of the stage state in the residual precision, P = 4 (2D) / 8 (3D)
     double* dt;        // [1]
     double* Uio;       // [nv][nc] device state of hfv_advance_host
 };

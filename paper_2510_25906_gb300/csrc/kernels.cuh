@@ -56,6 +56,8 @@ struct KParams {
     const T* nrm;
     const T* ivol;
     const T* dxthr;
+    // state of the current stage, cell-major: cell c at UA[c * P], P = 4 (2D) or 8 (3D)
+    const T* UA;
     // scratch
     T* FS;
     uint8_t* raw;

@@ -173,6 +173,26 @@ __device__ __forceinline__ void load_state(const T* __restrict__ p, T (&w)[NV])
     }
 }
 
+// cell-major state rows: P = 4 values (2D) or 8 (3D, 5 used), 16-byte aligned
+template <int NV>
+struct AoSP {
+    static constexpr int P = NV == 4 ? 4 : 8;
+};
+
+template <class T, int NV>
+__device__ __forceinline__ void load_cell(const T* __restrict__ UA, int64_t c, T (&u)[NV])
+{
+    const T* q = UA + c * AoSP<NV>::P;
+    if constexpr (sizeof(T) == 4) {
+        float4 a = __ldg(reinterpret_cast<const float4*>(q));
+        u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+    } else {
+        double2 a = __ldg(reinterpret_cast<const double2*>(q)), b = __ldg(reinterpret_cast<const double2*>(q) + 1);
+        u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y;
+    }
+    if constexpr (NV == 5) u[4] = __ldg(q + 4);
+}
+
 // K1: persistent, warp-specialised.  Tiles of NG consecutive cells: a
 // producer warp streams each tile's contiguous L blocks and stencil ids into a
 // ring of shared-memory stages with bulk copies (TMA engine, mbarrier
@@ -197,7 +217,7 @@ struct K1Shape {
 };
 
 template <class C, class T>
-__global__ void __launch_bounds__(288) k_linear(KParams<T> p, const T* __restrict__ U)
+__global__ void __launch_bounds__(288) k_linear(KParams<T> p)
 {
     using S = K1Shape<C, T>;
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, G = S::G, NG = S::NG, ST = S::STAGES;
@@ -242,36 +262,65 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p, const T* __restric
     }
 
     // ---------------- consumer warps ----------------
+    // Software pipeline: while tile k is computed from shared memory, the
+    // stencil states of tile k+1 are already in flight into registers.
+    constexpr int MI = (M + G - 1) / G;    // stencil cells per lane
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
     T* myU = sU + gi * M * NV;
+    T nu[MI][NV];                          // in-flight stencil states of the next tile
+    T nuc[NV];
+    int nnfv = 0;
+    int64_t nlrel = 0;
+    auto fetch = [&](int64_t tile_f, int stage_f) {
+        const int64_t cf = tile_f * NG + gi;
+        if (cf >= nc) return;
+        const int32_t* st = reinterpret_cast<const int32_t*>(smem + stage_f * S::STAGE + S::LBYTES) + gi * M;
+#pragma unroll
+        for (int i = 0; i < MI; ++i) {
+            const int m = lane + i * G;
+            if (m < M) load_cell<T, NV>(p.UA, st[m], nu[i]);
+        }
+        load_cell<T, NV>(p.UA, cf, nuc);
+        nnfv = p.nfc[cf];
+        nlrel = p.loff[cf] - p.loff[tile_f * NG];
+    };
     int k = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    int64_t tile = blockIdx.x;
+    bool alive = true;
+    if (tile < ntiles) {
+        if (!mbar_wait(&full[0], 0)) { if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4); alive = false; }
+        else fetch(tile, 0);
+    }
+    while (alive && tile < ntiles) {
         const int s = k % ST;
-        const int64_t c0 = tile * NG;
-        const int64_t c = c0 + gi;
-        // independent global loads first, then wait for the stage
+        const int64_t c = tile * NG + gi;
         T uc[NV];
-        int nfv = 0;
-        int64_t lrel = 0;
+        const int nfv = nnfv;
+        const int64_t lrel = nlrel;
         if (c < nc) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
-            nfv = p.nfc[c];
-            lrel = p.loff[c] - p.loff[c0];
+            for (int v = 0; v < NV; ++v) uc[v] = nuc[v];
+#pragma unroll
+            for (int i = 0; i < MI; ++i) {
+                const int m = lane + i * G;
+                if (m < M)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) myU[m * NV + v] = nu[i][v];
+            }
         }
-        if (!mbar_wait(&full[s], (k / ST) & 1)) {
-            if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
-            break;
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) {
+            const int s1 = (k + 1) % ST;
+            if (!mbar_wait(&full[s1], ((k + 1) / ST) & 1)) {
+                if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
+                alive = false;
+            } else {
+                fetch(next, s1);
+            }
         }
         const unsigned char* stage = smem + s * S::STAGE;
         if (c < nc) {
-            const int32_t* st = reinterpret_cast<const int32_t*>(stage + S::LBYTES) + gi * M;
-            for (int m = lane; m < M; m += G) {
-                const int64_t j = st[m];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) myU[m * NV + v] = U[v * nc + j];
-            }
             const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
             T w[NV];
 #pragma unroll
@@ -341,6 +390,8 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p, const T* __restric
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
+        ++k;
+        tile = next;
     }
 }
 
@@ -439,7 +490,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls
 // lane (f, k) forms the directional degree-1 coefficients; lane v forms the
 // indicators and weights of variable v; lane q writes face point q.
 template <class C, class T>
-__global__ void __launch_bounds__(128) k_cweno(KParams<T> p, const T* __restrict__ U)
+__global__ void __launch_bounds__(128) k_cweno(KParams<T> p)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, N = C::N, MD = C::MD;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -454,13 +505,13 @@ __global__ void __launch_bounds__(128) k_cweno(KParams<T> p, const T* __restrict
     for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
         const int64_t c = p.queue[i];
         T uc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
+        load_cell<T, NV>(p.UA, c, uc);
         const int32_t* st = p.sten + c * M;
         for (int m = lane; m < M; m += G) {
-            const int64_t j = st[m];
+            T uj[NV];
+            load_cell<T, NV>(p.UA, st[m], uj);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j] - uc[v];
+            for (int v = 0; v < NV; ++v) sU[gi][m][v] = uj[v] - uc[v];
         }
         grp.sync();
         const int nf = p.nfc[c] & 15;
@@ -588,7 +639,7 @@ __global__ void __launch_bounds__(128) k_cweno(KParams<T> p, const T* __restrict
 // queued cell: degree-1 gradient from the first Md stencil cells, limiter
 // bounds from the cell and its face neighbours (the first stencil layer).
 template <class C, class T>
-__global__ void __launch_bounds__(128) k_muscl(KParams<T> p, const T* __restrict__ U)
+__global__ void __launch_bounds__(128) k_muscl(KParams<T> p)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, MD = C::MD;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -601,13 +652,13 @@ __global__ void __launch_bounds__(128) k_muscl(KParams<T> p, const T* __restrict
     for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
         const int64_t c = p.queue[nc + i];
         T uc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) uc[v] = U[v * nc + c];
+        load_cell<T, NV>(p.UA, c, uc);
         const int32_t* st = p.sten + c * M;
         for (int m = lane; m < MD; m += G) {
-            const int64_t j = st[m];
+            T uj[NV];
+            load_cell<T, NV>(p.UA, st[m], uj);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sU[gi][m][v] = U[v * nc + j];
+            for (int v = 0; v < NV; ++v) sU[gi][m][v] = uj[v];
         }
         grp.sync();
         const int nfv = p.nfc[c];
@@ -659,7 +710,7 @@ __global__ void __launch_bounds__(128) k_muscl(KParams<T> p, const T* __restrict
 // K6: Riemann fluxes at the face points and the residual, one group per cell,
 // lane q the flux at face point q; the group sums F w |S| in a fixed order.
 template <class C, class T, int KIND>
-__global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict__ U, T* __restrict__ R)
+__global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
 {
     constexpr int NV = C::NV, D = C::D, NFP = C::NFP;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -678,8 +729,7 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict_
         const int cc = p.cls[c];
         T wl[NV], wr[NV], F[NV];
         if (cc == CLS_FIRST) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) wl[v] = U[v * nc + c];
+            load_cell<T, NV>(p.UA, c, wl);
         } else {
             load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
         }
@@ -688,8 +738,7 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, const T* __restrict_
 #pragma unroll
             for (int v = 0; v < NV; ++v) wr[v] = wl[v];
         } else if (p.cls[j] == CLS_FIRST) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) wr[v] = U[v * nc + j];
+            load_cell<T, NV>(p.UA, j, wr);
         } else {
             load_state<T, NV>(p.FS + (j * C::QMAX + p.nbrf[c * 6 + f] * NFP + a) * NV, wr);
         }
@@ -758,6 +807,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.L = (const T*)a.L; p.P = (const T*)a.P; p.Phil = (const T*)a.Phil; p.OI = (const T*)a.OI;
     p.Dd = (const T*)a.D; p.G = (const T*)a.G; p.W = (const T*)a.W; p.nrm = (const T*)a.nrm;
     p.ivol = (const T*)a.ivol; p.dxthr = (const T*)a.dxthr;
+    p.UA = (const T*)a.UA;
     p.FS = (T*)a.FS; p.raw = a.raw; p.cls = a.cls; p.queue = a.queue; p.counts = a.counts;
     p.bcount = a.bcount; p.nblocks = s->nblocks; p.status = a.status;
     p.gamma = (T)s->p.gamma; p.alpha_m = (T)s->p.alpha_m; p.beta_m = (T)s->p.beta_m;
@@ -768,13 +818,37 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     return p;
 }
 
+// structure-of-arrays state -> cell-major rows of the stage state
+template <class Tin, class T, int NV>
+__global__ void k_to_aos(int64_t nc, const Tin* __restrict__ U, T* __restrict__ UA)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    constexpr int P = AoSP<NV>::P;
+    T u[P];
+#pragma unroll
+    for (int v = 0; v < P; ++v) u[v] = v < NV ? (T)U[v * nc + c] : T(0);
+    T* q = UA + c * P;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int v = 0; v < P; v += 4) *reinterpret_cast<float4*>(q + v) = make_float4(u[v], u[v + 1], u[v + 2], u[v + 3]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < P; v += 2) *reinterpret_cast<double2*>(q + v) = make_double2(u[v], u[v + 1]);
+    }
+}
+
 template <class C, class T>
-int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t* cls_out, cudaStream_t st)
+int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t* cls_out, cudaStream_t st, bool ua_ready)
 {
     KParams<T> p = make_params<T>(s, forced);
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
     const unsigned gcell = (unsigned)((nc + CPB - 1) / CPB), g256 = (unsigned)((nc + 255) / 256);
+    if (!ua_ready) {
+        Launch l(s, KID_CVT, st);
+        k_to_aos<T, T, C::NV><<<g256, 256, 0, st>>>(nc, U, (T*)s->a.UA);
+    }
     {
         using S1 = K1Shape<C, T>;
         static int grid1 = 0;   // per instantiation: SMs x resident CTAs
@@ -789,21 +863,21 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         const int64_t ntiles = (nc + S1::NG - 1) / S1::NG;
         const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, grid1);
         Launch l(s, KID_LINEAR, st);
-        k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p, U);
+        k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p);
     }
     { Launch l(s, KID_TAG, st); k_tag<T><<<g256, 256, 0, st>>>(p); }
     { Launch l(s, KID_COUNT, st); k_count<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks); }
     { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
     { Launch l(s, KID_SCATTER, st); k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue); }
     const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
-    { Launch l(s, KID_CWENO, st); k_cweno<C, T><<<gq, 128, 0, st>>>(p, U); }
-    { Launch l(s, KID_MUSCL, st); k_muscl<C, T><<<gq, 128, 0, st>>>(p, U); }
+    { Launch l(s, KID_CWENO, st); k_cweno<C, T><<<gq, 128, 0, st>>>(p); }
+    { Launch l(s, KID_MUSCL, st); k_muscl<C, T><<<gq, 128, 0, st>>>(p); }
     {
         Launch l(s, KID_FLUX, st);
         switch (s->p.flux) {
-        case HFV_RUSANOV: k_flux<C, T, kRusanov><<<gcell, 128, 0, st>>>(p, U, R); break;
-        case HFV_HLL: k_flux<C, T, kHLL><<<gcell, 128, 0, st>>>(p, U, R); break;
-        default: k_flux<C, T, kHLLC><<<gcell, 128, 0, st>>>(p, U, R); break;
+        case HFV_RUSANOV: k_flux<C, T, kRusanov><<<gcell, 128, 0, st>>>(p, R); break;
+        case HFV_HLL: k_flux<C, T, kHLL><<<gcell, 128, 0, st>>>(p, R); break;
+        default: k_flux<C, T, kHLLC><<<gcell, 128, 0, st>>>(p, R); break;
         }
     }
     if (cls_out) HFV_CUDA_CHECK(cudaMemcpyAsync(cls_out, s->a.cls, nc, cudaMemcpyDeviceToDevice, st));
@@ -811,26 +885,39 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     return HFV_OK;
 }
 
-
 // ---------------------------------------------------------------------------
 // time stepping (three-stage SSP Runge-Kutta, FP64 accumulation)
 // ---------------------------------------------------------------------------
-template <class T>
-__global__ void k_rk(int64_t n, double a, double b, const double* __restrict__ U0, const double* __restrict__ Us,
-                     const T* __restrict__ R, const double* __restrict__ dt, double* out, float* outf)
+// out = a U0 + b (Us + dt R) per cell (all variables), FP64; the result is
+// also written cell-major in the residual precision for the next stage
+template <class T, int NV>
+__global__ void k_rk(int64_t nc, double a, double b, const double* __restrict__ U0, const double* __restrict__ Us,
+                     const T* __restrict__ R, const double* __restrict__ dt, double* out, T* ua)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double v = b * (Us[i] + dt[0] * (double)R[i]);
-    if (a != 0.0) v += a * U0[i];
-    out[i] = v;
-    if (outf) outf[i] = (float)v;
-}
-
-__global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)in[i];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    constexpr int P = AoSP<NV>::P;
+    const double h = dt[0];
+    T u[P];
+#pragma unroll
+    for (int v = 0; v < P; ++v) u[v] = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double x = b * (Us[v * nc + c] + h * (double)R[v * nc + c]);
+        if (a != 0.0) x += a * U0[v * nc + c];
+        out[v * nc + c] = x;
+        u[v] = (T)x;
+    }
+    if (ua) {
+        T* q = ua + c * P;
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int v = 0; v < P; v += 4) *reinterpret_cast<float4*>(q + v) = make_float4(u[v], u[v + 1], u[v + 2], u[v + 3]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < P; v += 2) *reinterpret_cast<double2*>(q + v) = make_double2(u[v], u[v + 1]);
+        }
+    }
 }
 
 __global__ void k_set(double* x, double v) { *x = v; }
@@ -838,26 +925,30 @@ __global__ void k_set(double* x, double v) { *x = v; }
 __global__ void k_dt_init(unsigned long long* x) { *x = 0x7ff0000000000000ull; }
 
 // dt_c = cfl |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|; min over cells (order-free,
-// exact).  Evaluated in the residual's precision: FP64, or FP32 from the FP32
-// copy of the state (a stability estimate, not part of the conserved update).
-template <class T>
-__global__ void __launch_bounds__(256) k_dt(int64_t nc, int d, const T* __restrict__ U, const double* __restrict__ vol,
+// exact).  Evaluated in the residual's precision from the cell-major stage
+// copy (in FP32 a stability estimate, not part of the conserved update).
+template <class T, int NV>
+__global__ void __launch_bounds__(256) k_dt(int64_t nc, const T* __restrict__ UA, const double* __restrict__ vol,
                                             const double* __restrict__ area, const double* __restrict__ nrm,
                                             const uint8_t* __restrict__ nfc, double gamma, double cfl,
                                             unsigned long long* out)
 {
+    constexpr int D = NV - 2;
     __shared__ double red[8];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dtc = INFINITY;
     if (c < nc) {
         const T g = (T)gamma;
-        T rho = U[c], m2 = T(0), u[3] = {T(0), T(0), T(0)};
-        for (int k = 0; k < d; ++k) {
-            const T mk = U[(1 + k) * nc + c];
-            u[k] = mk / rho;
-            m2 += mk * mk;
+        T uc[NV];
+        load_cell<T, NV>(UA, c, uc);
+        const T rho = uc[0];
+        T m2 = T(0), u[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[k] = uc[1 + k] / rho;
+            m2 += uc[1 + k] * uc[1 + k];
         }
-        const T p = (g - T(1)) * (U[(d + 1) * nc + c] - T(0.5) * m2 / rho);
+        const T p = (g - T(1)) * (uc[D + 1] - T(0.5) * m2 / rho);
         const T a = tsqrt<T>(g * p / rho);
         T lam = T(0);
         const int nf = nfc[c] & 15;
@@ -879,11 +970,9 @@ __global__ void __launch_bounds__(256) k_dt(int64_t nc, int d, const T* __restri
     }
 }
 
-using Res64 = int (*)(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t);
-using Res32 = int (*)(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t);
-
 template <class T>
-static auto pick(int d, int r) -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t)
+static auto pick(int d, int r)
+    -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t, bool)
 {
     if (d == 2) {
         switch (r) {
@@ -904,23 +993,51 @@ static auto pick(int d, int r) -> int (*)(hfv_scheme*, const T*, T*, const uint8
 
 bool residual_supported(int d, int r) { return pick<double>(d, r) != nullptr; }
 
-int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
+static int residual_any(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out,
+                        cudaStream_t st, bool ua_ready)
 {
-    cudaStream_t st = (cudaStream_t)stream;
     if (s->p.precision == HFV_FP32)
-        return pick<float>(s->d, s->r)(s, (const float*)U, (float*)R, forced, cls_out, st);
-    return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st);
+        return pick<float>(s->d, s->r)(s, (const float*)U, (float*)R, forced, cls_out, st, ua_ready);
+    return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st, ua_ready);
 }
 
-template <class T>
-static int launch_dt_t(hfv_scheme* s, const T* U, double cfl, double* dt_dev, cudaStream_t st)
+int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
+{
+    return residual_any(s, U, R, forced, cls_out, (cudaStream_t)stream, false);
+}
+
+// FP64 structure-of-arrays state -> cell-major stage copy in the residual precision
+static void stage_from(hfv_scheme* s, const double* U, cudaStream_t st)
 {
     const int64_t nc = s->mesh->nc;
+    const unsigned g = (unsigned)((nc + 255) / 256);
+    Launch l(s, KID_CVT, st);
+    const bool f32 = s->p.precision == HFV_FP32;
+    if (s->nv == 4) {
+        if (f32) k_to_aos<double, float, 4><<<g, 256, 0, st>>>(nc, U, (float*)s->a.UA);
+        else k_to_aos<double, double, 4><<<g, 256, 0, st>>>(nc, U, (double*)s->a.UA);
+    } else {
+        if (f32) k_to_aos<double, float, 5><<<g, 256, 0, st>>>(nc, U, (float*)s->a.UA);
+        else k_to_aos<double, double, 5><<<g, 256, 0, st>>>(nc, U, (double*)s->a.UA);
+    }
+}
+
+// dt from the stage copy already in UA
+static int dt_from_stage(hfv_scheme* s, double cfl, double* dt_dev, cudaStream_t st)
+{
+    const int64_t nc = s->mesh->nc;
+    const unsigned g = (unsigned)((nc + 255) / 256);
+    const bool f32 = s->p.precision == HFV_FP32;
     { Launch l(s, KID_DT, st); k_dt_init<<<1, 1, 0, st>>>((unsigned long long*)dt_dev); }
-    {
-        Launch l(s, KID_DT, st);
-        k_dt<T><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, s->d, U, s->a.vol, s->a.area, s->a.nrm64, s->a.nfc,
-                                                                s->p.gamma, cfl, (unsigned long long*)dt_dev);
+    Launch l(s, KID_DT, st);
+    auto* out = (unsigned long long*)dt_dev;
+    const hfv_dev_arrays& a = s->a;
+    if (s->nv == 4) {
+        if (f32) k_dt<float, 4><<<g, 256, 0, st>>>(nc, (const float*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
+        else k_dt<double, 4><<<g, 256, 0, st>>>(nc, (const double*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
+    } else {
+        if (f32) k_dt<float, 5><<<g, 256, 0, st>>>(nc, (const float*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
+        else k_dt<double, 5><<<g, 256, 0, st>>>(nc, (const double*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
@@ -929,43 +1046,38 @@ static int launch_dt_t(hfv_scheme* s, const T* U, double cfl, double* dt_dev, cu
 int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    if (s->p.precision == HFV_FP32) {
-        // the FP32 copy of U drives the estimate
-        const int64_t n = (int64_t)s->nv * s->mesh->nc;
-        { Launch l(s, KID_CVT, st); k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, U, s->a.Uf); }
-        return launch_dt_t<float>(s, s->a.Uf, cfl, dt_dev, st);
-    }
-    int rc = launch_dt_t<double>(s, U, cfl, dt_dev, st);
-    if (rc != HFV_OK) return rc;
-    HFV_CUDA_CHECK(cudaGetLastError());
-    return HFV_OK;
+    stage_from(s, U, st);
+    return dt_from_stage(s, cfl, dt_dev, st);
+}
+
+template <class T, int NV>
+static void rk_launch(hfv_scheme* s, int k, double* U, const double* in, double* out, cudaStream_t st)
+{
+    const int64_t nc = s->mesh->nc;
+    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+    Launch l(s, KID_RK, st);
+    k_rk<T, NV><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, A[k], B[k], U, in, (const T*)s->a.Rs, s->a.dt, out,
+                                                                k < 2 ? (T*)s->a.UA : nullptr);
 }
 
 int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = (int64_t)s->nv * s->mesh->nc;
-    const unsigned g = (unsigned)((n + 255) / 256);
     int rc;
-    const bool f32 = s->p.precision == HFV_FP32;
+    stage_from(s, U, st);
     if (dt > 0.0) { Launch l(s, KID_DT, st); k_set<<<1, 1, 0, st>>>(s->a.dt, dt); }
-    else if ((rc = launch_dt(s, U, cfl, s->a.dt, stream)) != HFV_OK) return rc;   // FP32: also fills Uf
-    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+    else if ((rc = dt_from_stage(s, cfl, s->a.dt, st)) != HFV_OK) return rc;
     double* outs[3] = {s->a.U1, s->a.U2, U};
     const double* ins[3] = {U, s->a.U1, s->a.U2};
-    if (f32) {
-        if (dt > 0.0) { Launch l(s, KID_CVT, st); k_to_f32<<<g, 256, 0, st>>>(n, U, s->a.Uf); }
-        for (int k = 0; k < 3; ++k) {
-            if ((rc = launch_residual(s, s->a.Uf, s->a.Rs, nullptr, nullptr, stream)) != HFV_OK) return rc;
-            Launch l(s, KID_RK, st);
-            k_rk<float><<<g, 256, 0, st>>>(n, A[k], B[k], U, ins[k], (const float*)s->a.Rs, s->a.dt, outs[k],
-                                           k < 2 ? s->a.Uf : nullptr);
-        }
-    } else {
-        for (int k = 0; k < 3; ++k) {
-            if ((rc = launch_residual(s, ins[k], s->a.Rs, nullptr, nullptr, stream)) != HFV_OK) return rc;
-            Launch l(s, KID_RK, st);
-            k_rk<double><<<g, 256, 0, st>>>(n, A[k], B[k], U, ins[k], (const double*)s->a.Rs, s->a.dt, outs[k], nullptr);
+    const bool f32 = s->p.precision == HFV_FP32;
+    for (int k = 0; k < 3; ++k) {
+        if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, true)) != HFV_OK) return rc;
+        if (s->nv == 4) {
+            if (f32) rk_launch<float, 4>(s, k, U, ins[k], outs[k], st);
+            else rk_launch<double, 4>(s, k, U, ins[k], outs[k], st);
+        } else {
+            if (f32) rk_launch<float, 5>(s, k, U, ins[k], outs[k], st);
+            else rk_launch<double, 5>(s, k, U, ins[k], outs[k], st);
         }
     }
     HFV_CUDA_CHECK(cudaGetLastError());

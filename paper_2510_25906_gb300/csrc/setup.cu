@@ -109,7 +109,7 @@ int build_operators(hfv_scheme* s, void* stream)
     size_t o_vol = take(nc * 8), o_area = take(nc * 6 * 8), o_nrm64 = take(nc * 18 * 8);
     size_t o_FS = take(qt * nv * b), o_raw = take(nc), o_cls = take(nc), o_queue = take(2 * nc * 4), o_counts = take(64),
            o_bcount = take(2 * (size_t)s->nblocks * 4), o_status = take(64);
-    size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_Uf = take(f32 ? nv * nc * 4 : 0),
+    size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b),
            o_dt = take(64), o_Uio = take(nv * nc * 8);
     s->arena_bytes = off;
     SETUP_CHECK(cudaMalloc(&s->arena, off));
@@ -123,7 +123,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.vol = (double*)(A + o_vol); a.area = (double*)(A + o_area); a.nrm64 = (double*)(A + o_nrm64);
     a.FS = A + o_FS; a.raw = (uint8_t*)(A + o_raw); a.cls = (uint8_t*)(A + o_cls); a.queue = (int32_t*)(A + o_queue);
     a.counts = (int32_t*)(A + o_counts); a.bcount = (int32_t*)(A + o_bcount); a.status = (int*)(A + o_status);
-    a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.Uf = f32 ? (float*)(A + o_Uf) : nullptr;
+    a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA;
     a.dt = (double*)(A + o_dt);
     a.Uio = (double*)(A + o_Uio);
     SETUP_CHECK(cudaMemsetAsync(s->arena, 0, off, st));
