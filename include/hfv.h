@@ -221,6 +221,26 @@ HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int r
 /* Number of kernels launched by this library in this process so far. */
 HFV_API int hfv_launch_count(int64_t* count);
 
+/* Class-queue compaction that allocates nothing (the paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory when they need the queues, e.g. code running inside a CUDA stream
+ * capture, or a solver whose host framework's pool allocator owns all device
+ * memory).  Given classes (device uint8 [n_cells], values 0..3), writes
+ * counts[0] = number of CWENOZ cells (class 1), counts[1] = number of MUSCL
+ * cells (class 2) (device int32 [2]) and the two queues in ascending cell
+ * order to queues[0..counts[0]) and queues[n_cells..n_cells+counts[1])
+ * (device int32 [2 * n_cells]) -- the same compaction the residual applies
+ * to its tagged classes.  Scratch: a file-scope device array of 2 x 65,536
+ * int32 block counts, held by every device that loads the library until the
+ * process exits; n_cells above 16,777,216 is rejected with HFV_ERR_ARG.  The
+ * first call on a device looks up that array's device address (set-up once
+ * per device, under a host lock); make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (different streams, concurrently) race.  No entry of the array needs to
+ * start at zero: each call writes every entry it reads.  async. */
+HFV_API int hfv_class_queues_static(const uint8_t* classes, int64_t n_cells, int32_t* counts, int32_t* queues,
+                                    void* stream);
+
 /* Message of the calling thread's last failure ("" if none). */
 HFV_API const char* hfv_last_error(void);
 

@@ -79,6 +79,7 @@ def load():
         "hfv_kernel_timer": [vp, C.c_int],
         "hfv_kernel_times": [vp, vp, vp, C.c_int],
         "hfv_launch_count": [vp],
+        "hfv_class_queues_static": [vp, C.c_int64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -260,3 +261,20 @@ def launch_count() -> int:
     n = C.c_int64()
     _check(load().hfv_launch_count(C.byref(n)))
     return n.value
+
+
+def class_queues_static(classes, counts=None, queues=None, stream=None):
+    """hfv_class_queues_static: compaction of a CUDA uint8 class tensor into the
+    CWENOZ / MUSCL queues with the library's static scratch (no allocation in
+    the library; the outputs are allocated here unless given)."""
+    import torch
+    if not (isinstance(classes, torch.Tensor) and classes.is_cuda and classes.dtype == torch.uint8):
+        raise ValueError("classes must be a CUDA uint8 tensor")
+    n = classes.numel()
+    if counts is None:
+        counts = torch.empty(2, dtype=torch.int32, device=classes.device)
+    if queues is None:
+        queues = torch.empty(2 * n, dtype=torch.int32, device=classes.device)
+    _check(load().hfv_class_queues_static(C.c_void_p(classes.data_ptr()), n, C.c_void_p(counts.data_ptr()),
+                                          C.c_void_p(queues.data_ptr()), _stream(stream)))
+    return counts, queues

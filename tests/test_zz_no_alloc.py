@@ -1,0 +1,56 @@
+"""The compaction entry point that allocates nothing (for callers that cannot
+call cudaMalloc when they need the queues, e.g. inside a stream capture).
+
+It must produce the same counts and queues as the compaction inside
+hfv_residual: with classes forced, the residual compacts exactly the given
+CWENOZ and MUSCL cells, so both are compared bit for bit, on two calls in a
+row (the static scratch keeps the previous call's contents)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2510_25906_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_25906_gb300 import build as B
+    B.build()
+    import paper_2510_25906_gb300.hfv as H
+    H.load()
+    return H
+
+
+def test_static_scratch_compaction_matches_residual_queues(H):
+    m = I.mixed_tri_quad_mesh(80, seed=2)       # 9,600-odd cells: 38 blocks and a ragged tail
+    U = I.quadrant_state(m)
+    g = H.Scheme(H.Mesh(m), order=3, flux="hllc")
+    rng = np.random.default_rng(7)
+    for trial in range(2):
+        forced = torch.tensor(rng.integers(0, 4, m.n_cells).astype(np.uint8), device="cuda")
+        g.residual(torch.tensor(U, device="cuda"), forced=forced)
+        ref_counts, (ref_c, ref_m) = g.queues()
+        for call in range(2):                   # two calls in a row share the scratch
+            counts, queues = H.class_queues_static(forced)
+            torch.cuda.synchronize()
+            cnt = counts.cpu().numpy()
+            q = queues.cpu().numpy()
+            assert np.array_equal(cnt, ref_counts), (trial, call, cnt, ref_counts)
+            assert np.array_equal(q[:cnt[0]], ref_c)
+            assert np.array_equal(q[m.n_cells:m.n_cells + cnt[1]], ref_m)
+
+
+def test_static_scratch_rejects_oversized_input(H):
+    lib = H.load()
+    tiny = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(8, dtype=torch.int32, device="cuda")
+    rc = lib.hfv_class_queues_static(ctypes.c_void_p(tiny.data_ptr()), (1 << 24) + 1, ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == H.HFV_ERR_ARG
+    assert b"static scratch limit" in lib.hfv_last_error()
