@@ -8,7 +8,7 @@
 //   K2 k_tag      class of a cell = max over itself and its face neighbours
 //                 (tagging of the flagged cells' neighbourhood); linear cells
 //                 that fail the Harten bound become first-order
-//      k_count / k_scan / k_scatter: warp-ballot compaction of the CWENOZ and
+//      (k_tag also counts) k_scan / k_scatter: warp-ballot compaction of the CWENOZ and
 //                 MUSCL cells into two queues in ascending cell order
 //   K3 k_cweno    CWENOZ on the CWENOZ queue (Sec. 2.3)
 //   K4 k_muscl    MUSCL + Barth-Jespersen on the MUSCL queue (Sec. 2.2)
@@ -72,6 +72,20 @@ struct Grp {
         for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
         return v;
     }
+    // 32-bit values reduce in one REDUX instruction; floats through an
+    // order-preserving integer image (exact, so the result is the same value)
+    __device__ __forceinline__ int max(int v) const { return __reduce_max_sync(mask, v); }
+    __device__ __forceinline__ static unsigned ord(float x)
+    {
+        const unsigned u = __float_as_uint(x);
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    }
+    __device__ __forceinline__ static float unord(unsigned u)
+    {
+        return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+    }
+    __device__ __forceinline__ float min(float v) const { return unord(__reduce_min_sync(mask, ord(v))); }
+    __device__ __forceinline__ float max(float v) const { return unord(__reduce_max_sync(mask, ord(v))); }
     template <class T>
     __device__ __forceinline__ T sum(T v) const
     {
@@ -211,7 +225,7 @@ struct K1Shape {
     static constexpr int SBYTES = NG * C::M * 4;
     static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
     static constexpr int STAGES = STAGE * 4 <= 100 * 1024 ? 4 : STAGE * 3 <= 150 * 1024 ? 3 : 2;
-    static constexpr int SU = NG * C::M * C::NV * (int)sizeof(T);
+    static constexpr int SU = NG * C::M * AoSP<C::NV>::P * (int)sizeof(T);   // U_m - U_0 rows
     static constexpr int SMEM = STAGES * STAGE + (SU + 127) / 128 * 128 + 2 * STAGES * 8;
     static constexpr int THREADS = CONSUMERS + 32;
 };
@@ -265,9 +279,10 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
     // Software pipeline: while tile k is computed from shared memory, the
     // stencil states of tile k+1 are already in flight into registers.
     constexpr int MI = (M + G - 1) / G;    // stencil cells per lane
+    constexpr int P = AoSP<NV>::P;
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
-    T* myU = sU + gi * M * NV;
+    T* myU = sU + gi * M * P;              // rows of U_m - U_0
     T nu[MI][NV];                          // in-flight stencil states of the next tile
     T nuc[NV];
     int nnfv = 0;
@@ -295,18 +310,29 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
     while (alive && tile < ntiles) {
         const int s = k % ST;
         const int64_t c = tile * NG + gi;
-        T uc[NV];
+        T uc[NV], face[NV];                // the cell's state; lane < n1: its face neighbour's state
         const int nfv = nnfv;
         const int64_t lrel = nlrel;
         if (c < nc) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) uc[v] = nuc[v];
+            for (int v = 0; v < NV; ++v) { uc[v] = nuc[v]; face[v] = nu[0][v]; }
 #pragma unroll
             for (int i = 0; i < MI; ++i) {
                 const int m = lane + i * G;
-                if (m < M)
+                if (m < M) {
+                    T row[P];
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) myU[m * NV + v] = nu[i][v];
+                    for (int v = 0; v < P; ++v) row[v] = v < NV ? nu[i][v] - uc[v] : T(0);
+                    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                        for (int v = 0; v < P; v += 4)
+                            *reinterpret_cast<float4*>(myU + m * P + v) = make_float4(row[v], row[v + 1], row[v + 2], row[v + 3]);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < P; v += 2)
+                            *reinterpret_cast<double2*>(myU + m * P + v) = make_double2(row[v], row[v + 1]);
+                    }
+                }
             }
         }
         const int64_t next = tile + gridDim.x;
@@ -330,10 +356,24 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
             grp.sync();
             const int64_t q0 = c * C::QMAX;
             if (lane < Q) {
+                if constexpr (sizeof(T) == 4) {
+                    // packed FP32x2 FMAs: one instruction per two variables
+                    float2 w01 = make_float2(w[0], w[1]), w23 = make_float2(w[2], w[3]);
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
+                    for (int m = 0; m < M; ++m) {
+                        const float4 d = *reinterpret_cast<const float4*>(myU + m * P);
+                        const float2 l2 = make_float2(lrow[m], lrow[m]);
+                        w01 = __ffma2_rn(l2, make_float2(d.x, d.y), w01);
+                        w23 = __ffma2_rn(l2, make_float2(d.z, d.w), w23);
+                        if constexpr (NV == 5) w[4] = fmaf(lrow[m], myU[m * P + 4], w[4]);
+                    }
+                    w[0] = w01.x; w[1] = w01.y; w[2] = w23.x; w[3] = w23.y;
+                } else {
 #pragma unroll
-                    for (int v = 0; v < NV; ++v) w[v] += lrow[m] * (myU[m * NV + v] - uc[v]);
+                    for (int m = 0; m < M; ++m) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) w[v] = fma(lrow[m], myU[m * P + v], w[v]);
+                    }
                 }
                 store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
             }
@@ -356,10 +396,7 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
                     T qj = qi, dd = T(0);
                     const bool has = lane < n1;
                     if (has) {
-                        T uj[NV];
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) uj[v] = myU[lane * NV + v];
-                        qj = nad_value<T, D>(uj, kind, p.gamma);
+                        qj = nad_value<T, D>(face, kind, p.gamma);
                         dd = tabs(qj - qi);
                     }
                     const T lo = grp.min(qj), hi = grp.max(qj);
@@ -395,70 +432,81 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
     }
 }
 
+// K2a: tagging of the flagged cells' face neighbourhood (class = max over the
+// cell and its face neighbours), first-order for linear cells that broke the
+// Harten bound, and the per-block counts of the CWENOZ / MUSCL queues
+// (blocks of 256 cells, warp ballots)
 template <class T>
-__global__ void k_tag(KParams<T> p)
+__global__ void __launch_bounds__(256) k_tag(KParams<T> p)
 {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.nc) return;
-    uint8_t r = p.raw[c];
-    int t = r & 3;
-    if (!p.forced && p.scheme == HFV_HYBRID) {
-        int nf = p.nfc[c] & 15;
-        for (int f = 0; f < nf; ++f) {
-            int64_t j = p.nbr[c * 6 + f];
-            if (j >= 0) {
-                int tj = p.raw[j] & 3;
-                t = tj > t ? tj : t;
+    __shared__ int sc[2][8];
+    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    int t = 255;
+    if (c < p.nc) {
+        const uint8_t r = p.raw[c];
+        t = r & 3;
+        if (!p.forced && p.scheme == HFV_HYBRID) {
+            const int nf = p.nfc[c] & 15;
+            for (int f = 0; f < nf; ++f) {
+                const int64_t j = p.nbr[c * 6 + f];
+                if (j >= 0) {
+                    const int tj = p.raw[j] & 3;
+                    t = tj > t ? tj : t;
+                }
             }
         }
+        if (t == CLS_LIN && (r & HARTEN_FAIL)) t = CLS_FIRST;
+        p.cls[c] = (uint8_t)t;
     }
-    if (t == CLS_LIN && (r & HARTEN_FAIL)) t = CLS_FIRST;
-    p.cls[c] = (uint8_t)t;
-}
-
-// per-block counts of CWENOZ / MUSCL cells (blocks of 256 cells)
-__global__ void __launch_bounds__(256) k_count(const uint8_t* __restrict__ cls, int64_t nc, int32_t* bcount, int nblocks)
-{
-    __shared__ int s[2][8];
-    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    int t = c < nc ? cls[c] : 255;
-    unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
-    unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { s[0][w] = __popc(b1); s[1][w] = __popc(b2); }
+    const unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
+    const unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sc[0][w] = __popc(b1); sc[1][w] = __popc(b2); }
     __syncthreads();
     if (threadIdx.x < 2) {
         int sum = 0;
-        for (int k = 0; k < 8; ++k) sum += s[threadIdx.x][k];
-        bcount[threadIdx.x * nblocks + blockIdx.x] = sum;
+        for (int k = 0; k < 8; ++k) sum += sc[threadIdx.x][k];
+        p.bcount[threadIdx.x * p.nblocks + blockIdx.x] = sum;
     }
 }
 
-// exclusive scan of the block counts (one block of 1024 threads); totals to counts[0..1]
+// exclusive scan of the block counts (one block of 1024 threads, warp
+// shuffles); totals to counts[0..1]
 __global__ void __launch_bounds__(1024) k_scan(int32_t* bcount, int nblocks, int32_t* counts)
 {
-    __shared__ int part[1024];
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = 0; q < 2; ++q) {
         int32_t* b = bcount + q * nblocks;
-        int per = (nblocks + 1023) / 1024;
-        int lo = threadIdx.x * per, hi = min(lo + per, nblocks);
-        int sum = 0;
-        for (int i = lo; i < hi; ++i) sum += b[i];
-        part[threadIdx.x] = sum;
+        const int per = (nblocks + 1023) / 1024;
+        const int lo = threadIdx.x * per, hi = min(lo + per, nblocks);
+        int v = 0;
+        for (int i = lo; i < hi; ++i) v += b[i];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
         __syncthreads();
-        for (int off = 1; off < 1024; off <<= 1) {    // Hillis-Steele inclusive scan
-            int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-            __syncthreads();
-            part[threadIdx.x] += v;
-            __syncthreads();
+        if (w == 0) {
+            int z = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            wsum[lane] = z;
         }
-        int run = part[threadIdx.x] - sum;              // exclusive prefix of this thread's chunk
+        __syncthreads();
+        int run = x - v + (w > 0 ? wsum[w - 1] : 0);
         for (int i = lo; i < hi; ++i) {
-            int v = b[i];
+            const int e = b[i];
             b[i] = run;
-            run += v;
+            run += e;
         }
-        if (threadIdx.x == 1023) counts[q] = part[1023];
+        if (threadIdx.x == 0) counts[q] = wsum[31];
         __syncthreads();
     }
 }
@@ -865,8 +913,7 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         Launch l(s, KID_LINEAR, st);
         k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p);
     }
-    { Launch l(s, KID_TAG, st); k_tag<T><<<g256, 256, 0, st>>>(p); }
-    { Launch l(s, KID_COUNT, st); k_count<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks); }
+    { Launch l(s, KID_TAG, st); k_tag<T><<<s->nblocks, 256, 0, st>>>(p); }
     { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
     { Launch l(s, KID_SCATTER, st); k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue); }
     const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
