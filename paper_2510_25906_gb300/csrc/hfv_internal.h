@@ -86,6 +86,8 @@ struct hfv_dev_arrays {
     double* U2;        // [nv][nc]
     void* Rs;          // [nv][nc] residual of a stage (precision T)
     void* UA;          // [nc][P] cell-major copy of the stage state in the residual precision, P = 4 (2D) / 8 (3D)
+    void* UB;          // second stage copy: stages alternate UA / UB
+    void* areaT;       // [nc][6] face areas in the residual precision
     double* dt;        // [1]
     double* Uio;       // [nv][nc] device state of hfv_advance_host
 };

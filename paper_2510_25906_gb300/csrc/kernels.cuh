@@ -67,6 +67,15 @@ struct KParams {
     int32_t* bcount;
     int nblocks;
     int* status;
+    // Runge-Kutta stage fused into the flux kernel (rk_b != 0): for every
+    // variable, out = rk_a U0 + rk_b (Us + dt R) in FP64, and the next stage's
+    // cell-major copy into ua_next (may be null)
+    double rk_a, rk_b;
+    const double* U0;
+    const double* Us;
+    const double* dt;
+    double* out;
+    T* ua_next;
     // constants
     T gamma, alpha_m, beta_m, alpha_w, beta_w, lam1, eps_cw, b_cw, h_theta, h_eps;
 };

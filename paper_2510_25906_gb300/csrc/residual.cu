@@ -72,20 +72,7 @@ struct Grp {
         for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
         return v;
     }
-    // 32-bit values reduce in one REDUX instruction; floats through an
-    // order-preserving integer image (exact, so the result is the same value)
-    __device__ __forceinline__ int max(int v) const { return __reduce_max_sync(mask, v); }
-    __device__ __forceinline__ static unsigned ord(float x)
-    {
-        const unsigned u = __float_as_uint(x);
-        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    }
-    __device__ __forceinline__ static float unord(unsigned u)
-    {
-        return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-    }
-    __device__ __forceinline__ float min(float v) const { return unord(__reduce_min_sync(mask, ord(v))); }
-    __device__ __forceinline__ float max(float v) const { return unord(__reduce_max_sync(mask, ord(v))); }
+
     template <class T>
     __device__ __forceinline__ T sum(T v) const
     {
@@ -511,22 +498,47 @@ __global__ void __launch_bounds__(1024) k_scan(int32_t* bcount, int nblocks, int
     }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls, int64_t nc, const int32_t* bcount,
-                                                 int nblocks, int32_t* queue)
+// K2c: scatter into the queues.  With fold != 0 (few blocks) every block
+// first sums the counts of the blocks before it, replacing the separate
+// scan, and the last block writes the totals.
+__global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls, int64_t nc, int32_t* bcount,
+                                                 int nblocks, int32_t* queue, int32_t* counts, int fold)
 {
     __shared__ int s[2][8];
+    __shared__ int base[2];
+    __shared__ int red[2][8];
     const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    int t = c < nc ? cls[c] : 255;
-    unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
-    unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = c < nc ? cls[c] : 255;
+    const unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
+    const unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { s[0][w] = __popc(b1); s[1][w] = __popc(b2); }
+    if (fold) {
+        // exclusive prefix of this block: sum of the earlier blocks' counts
+        int p0 = 0, p1 = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += 256) { p0 += bcount[i]; p1 += bcount[nblocks + i]; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+        }
+        if (lane == 0) { red[0][w] = p0; red[1][w] = p1; }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            int sum = 0;
+            for (int k = 0; k < 8; ++k) sum += red[threadIdx.x][k];
+            base[threadIdx.x] = sum;
+            if (blockIdx.x == (unsigned)nblocks - 1) counts[threadIdx.x] = sum + bcount[threadIdx.x * nblocks + blockIdx.x];
+        }
+    } else if (threadIdx.x < 2) {
+        base[threadIdx.x] = bcount[threadIdx.x * nblocks + blockIdx.x];
+    }
     __syncthreads();
-    unsigned lt = (1u << lane) - 1u;
+    const unsigned lt = (1u << lane) - 1u;
     if (t == CLS_CW || t == CLS_MU) {
-        int q = t == CLS_CW ? 0 : 1;
-        unsigned b = q == 0 ? b1 : b2;
-        int off = bcount[q * nblocks + blockIdx.x];
+        const int q = t == CLS_CW ? 0 : 1;
+        const unsigned b = q == 0 ? b1 : b2;
+        int off = base[q];
         for (int k = 0; k < w; ++k) off += s[q][k];
         off += __popc(b & lt);
         queue[q * nc + off] = (int32_t)c;
@@ -538,7 +550,21 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls
 // lane (f, k) forms the directional degree-1 coefficients; lane v forms the
 // indicators and weights of variable v; lane q writes face point q.
 template <class C, class T>
-__global__ void __launch_bounds__(128) k_cweno(KParams<T> p)
+__device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, unsigned nbl);
+template <class C, class T>
+__device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, unsigned nbl);
+
+// K3 + K4 in one launch: the first `split` blocks work through the CWENOZ
+// queue, the others through the MUSCL queue (no divergence between them)
+template <class C, class T>
+__global__ void __launch_bounds__(128) k_nonlinear(KParams<T> p, unsigned split)
+{
+    if (blockIdx.x < split) cweno_part<C, T>(p, blockIdx.x, split);
+    else muscl_part<C, T>(p, blockIdx.x - split, gridDim.x - split);
+}
+
+template <class C, class T>
+__device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, unsigned nbl)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, N = C::N, MD = C::MD;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -550,7 +576,7 @@ __global__ void __launch_bounds__(128) k_cweno(KParams<T> p)
     const int gi = threadIdx.x / G, lane = grp.lane;
     const int64_t nc = p.nc;
     const int cnt = p.counts[0];
-    for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
+    for (int64_t i = (int64_t)bid * CPB + gi; i < cnt; i += (int64_t)nbl * CPB) {
         const int64_t c = p.queue[i];
         T uc[NV];
         load_cell<T, NV>(p.UA, c, uc);
@@ -687,7 +713,7 @@ __global__ void __launch_bounds__(128) k_cweno(KParams<T> p)
 // queued cell: degree-1 gradient from the first Md stencil cells, limiter
 // bounds from the cell and its face neighbours (the first stencil layer).
 template <class C, class T>
-__global__ void __launch_bounds__(128) k_muscl(KParams<T> p)
+__device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, unsigned nbl)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, MD = C::MD;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -697,7 +723,7 @@ __global__ void __launch_bounds__(128) k_muscl(KParams<T> p)
     const int gi = threadIdx.x / G, lane = grp.lane;
     const int64_t nc = p.nc;
     const int cnt = p.counts[1];
-    for (int64_t i = (int64_t)blockIdx.x * CPB + gi; i < cnt; i += (int64_t)gridDim.x * CPB) {
+    for (int64_t i = (int64_t)bid * CPB + gi; i < cnt; i += (int64_t)nbl * CPB) {
         const int64_t c = p.queue[nc + i];
         T uc[NV];
         load_cell<T, NV>(p.UA, c, uc);
@@ -803,7 +829,17 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
         T val = acc[0];
 #pragma unroll
         for (int v = 1; v < NV; ++v) val = lane == v ? acc[v] : val;
-        R[lane * nc + c] = -val * p.ivol[c];
+        const T r = -val * p.ivol[c];
+        if (p.rk_b == 0.0) {
+            R[lane * nc + c] = r;
+        } else {
+            // Runge-Kutta stage update of variable `lane` of cell c (FP64)
+            const int64_t e = lane * nc + c;
+            double x = p.rk_b * (p.Us[e] + p.dt[0] * (double)r);
+            if (p.rk_a != 0.0) x += p.rk_a * p.U0[e];
+            p.out[e] = x;
+            if (p.ua_next) p.ua_next[c * AoSP<NV>::P + lane] = (T)x;
+        }
     }
 }
 
@@ -886,16 +922,34 @@ __global__ void k_to_aos(int64_t nc, const Tin* __restrict__ U, T* __restrict__ 
     }
 }
 
+// fused Runge-Kutta stage applied in the flux kernel's epilogue (see KParams)
+struct StageRK {
+    double a = 0.0, b = 0.0;
+    const double* U0 = nullptr;
+    const double* Us = nullptr;
+    double* out = nullptr;
+    void* ua_next = nullptr;
+};
+
 template <class C, class T>
-int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t* cls_out, cudaStream_t st, bool ua_ready)
+int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t* cls_out, cudaStream_t st,
+                 const T* ua, const StageRK* rk)
 {
     KParams<T> p = make_params<T>(s, forced);
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
     const unsigned gcell = (unsigned)((nc + CPB - 1) / CPB), g256 = (unsigned)((nc + 255) / 256);
-    if (!ua_ready) {
+    if (!ua) {
         Launch l(s, KID_CVT, st);
         k_to_aos<T, T, C::NV><<<g256, 256, 0, st>>>(nc, U, (T*)s->a.UA);
+        ua = (const T*)s->a.UA;
+    }
+    p.UA = ua;
+    if (rk) {
+        p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.dt = s->a.dt; p.out = rk->out;
+        p.ua_next = (T*)rk->ua_next;
+    } else {
+        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr; p.out = nullptr; p.ua_next = nullptr;
     }
     {
         using S1 = K1Shape<C, T>;
@@ -914,11 +968,19 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p);
     }
     { Launch l(s, KID_TAG, st); k_tag<T><<<s->nblocks, 256, 0, st>>>(p); }
-    { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
-    { Launch l(s, KID_SCATTER, st); k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue); }
-    const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
-    { Launch l(s, KID_CWENO, st); k_cweno<C, T><<<gq, 128, 0, st>>>(p); }
-    { Launch l(s, KID_MUSCL, st); k_muscl<C, T><<<gq, 128, 0, st>>>(p); }
+    const int fold = s->nblocks <= 1024;
+    if (!fold) { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
+    {
+        Launch l(s, KID_SCATTER, st);
+        k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue, s->a.counts, fold);
+    }
+    {
+        // CWENOZ cells cost several times a MUSCL cell: 3/4 of the blocks
+        const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
+        const unsigned split = gq - gq / 4;
+        Launch l(s, KID_CWENO, st);
+        k_nonlinear<C, T><<<gq, 128, 0, st>>>(p, split);
+    }
     {
         Launch l(s, KID_FLUX, st);
         switch (s->p.flux) {
@@ -935,28 +997,31 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
 // ---------------------------------------------------------------------------
 // time stepping (three-stage SSP Runge-Kutta, FP64 accumulation)
 // ---------------------------------------------------------------------------
-// out = a U0 + b (Us + dt R) per cell (all variables), FP64; the result is
-// also written cell-major in the residual precision for the next stage
+__global__ void k_set(double* x, double v) { *x = v; }
+
+__global__ void k_dt_init(unsigned long long* x) { *x = 0x7ff0000000000000ull; }
+
+// FP64 state (structure of arrays) -> the first stage's cell-major copy, and,
+// when dt_out is given, the stable step
+//   dt = cfl min_c |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|
+// from the copy (FP64 with FP64 geometry, or FP32 with FP32 geometry: then a
+// stability estimate, not part of the conserved update).  The min is
+// order-free and exact.
 template <class T, int NV>
-__global__ void k_rk(int64_t nc, double a, double b, const double* __restrict__ U0, const double* __restrict__ Us,
-                     const T* __restrict__ R, const double* __restrict__ dt, double* out, T* ua)
+__global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __restrict__ U, T* __restrict__ UA,
+                                                  const T* __restrict__ ivol, const T* __restrict__ area,
+                                                  const T* __restrict__ nrm, const uint8_t* __restrict__ nfc,
+                                                  double gamma, double cfl, unsigned long long* dt_out)
 {
+    constexpr int D = NV - 2, P = AoSP<NV>::P;
+    __shared__ double red[8];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    constexpr int P = AoSP<NV>::P;
-    const double h = dt[0];
-    T u[P];
+    double dtc = INFINITY;
+    if (c < nc) {
+        T u[P];
 #pragma unroll
-    for (int v = 0; v < P; ++v) u[v] = T(0);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        double x = b * (Us[v * nc + c] + h * (double)R[v * nc + c]);
-        if (a != 0.0) x += a * U0[v * nc + c];
-        out[v * nc + c] = x;
-        u[v] = (T)x;
-    }
-    if (ua) {
-        T* q = ua + c * P;
+        for (int v = 0; v < P; ++v) u[v] = v < NV ? (T)U[v * nc + c] : T(0);
+        T* q = UA + c * P;
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int v = 0; v < P; v += 4) *reinterpret_cast<float4*>(q + v) = make_float4(u[v], u[v + 1], u[v + 2], u[v + 3]);
@@ -964,62 +1029,42 @@ __global__ void k_rk(int64_t nc, double a, double b, const double* __restrict__ 
 #pragma unroll
             for (int v = 0; v < P; v += 2) *reinterpret_cast<double2*>(q + v) = make_double2(u[v], u[v + 1]);
         }
-    }
-}
-
-__global__ void k_set(double* x, double v) { *x = v; }
-
-__global__ void k_dt_init(unsigned long long* x) { *x = 0x7ff0000000000000ull; }
-
-// dt_c = cfl |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|; min over cells (order-free,
-// exact).  Evaluated in the residual's precision from the cell-major stage
-// copy (in FP32 a stability estimate, not part of the conserved update).
-template <class T, int NV>
-__global__ void __launch_bounds__(256) k_dt(int64_t nc, const T* __restrict__ UA, const double* __restrict__ vol,
-                                            const double* __restrict__ area, const double* __restrict__ nrm,
-                                            const uint8_t* __restrict__ nfc, double gamma, double cfl,
-                                            unsigned long long* out)
-{
-    constexpr int D = NV - 2;
-    __shared__ double red[8];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double dtc = INFINITY;
-    if (c < nc) {
-        const T g = (T)gamma;
-        T uc[NV];
-        load_cell<T, NV>(UA, c, uc);
-        const T rho = uc[0];
-        T m2 = T(0), u[3] = {T(0), T(0), T(0)};
+        if (dt_out) {
+            const T g = (T)gamma, rho = u[0];
+            T m2 = T(0), vel[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            u[k] = uc[1 + k] / rho;
-            m2 += uc[1 + k] * uc[1 + k];
+            for (int k = 0; k < D; ++k) {
+                vel[k] = u[1 + k] / rho;
+                m2 += u[1 + k] * u[1 + k];
+            }
+            const T pr = (g - T(1)) * (u[D + 1] - T(0.5) * m2 / rho);
+            const T a = tsqrt<T>(g * pr / rho);
+            T lam = T(0);
+            const int nf = nfc[c] & 15;
+            for (int f = 0; f < nf; ++f) {
+                const T* n = nrm + (c * 6 + f) * 3;
+                const T un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
+                lam += (tabs(un) + a) * area[c * 6 + f];
+            }
+            dtc = (double)((T)cfl * (T(1) / ivol[c]) / lam);
+            if (sizeof(T) == 8) dtc = (double)((T)cfl / (ivol[c] * lam));
+            if (!(dtc > 0.0)) dtc = 0.0;  // a non-physical state stops the step at dt = 0
         }
-        const T p = (g - T(1)) * (uc[D + 1] - T(0.5) * m2 / rho);
-        const T a = tsqrt<T>(g * p / rho);
-        T lam = T(0);
-        const int nf = nfc[c] & 15;
-        for (int f = 0; f < nf; ++f) {
-            const double* n = nrm + (c * 6 + f) * 3;
-            const T un = u[0] * (T)n[0] + u[1] * (T)n[1] + u[2] * (T)n[2];
-            lam += (tabs(un) + a) * (T)area[c * 6 + f];
-        }
-        dtc = (double)((T)cfl * (T)vol[c] / lam);
-        if (!(dtc > 0.0)) dtc = 0.0;  // a non-physical state stops the step at dt = 0
     }
+    if (!dt_out) return;
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dtc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = red[0];
         for (int k = 1; k < 8; ++k) m = fmin(m, red[k]);
-        atomicMin(out, (unsigned long long)__double_as_longlong(m));
+        atomicMin(dt_out, (unsigned long long)__double_as_longlong(m));
     }
 }
 
 template <class T>
 static auto pick(int d, int r)
-    -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t, bool)
+    -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t, const T*, const StageRK*)
 {
     if (d == 2) {
         switch (r) {
@@ -1041,50 +1086,34 @@ static auto pick(int d, int r)
 bool residual_supported(int d, int r) { return pick<double>(d, r) != nullptr; }
 
 static int residual_any(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out,
-                        cudaStream_t st, bool ua_ready)
+                        cudaStream_t st, const void* ua, const StageRK* rk)
 {
     if (s->p.precision == HFV_FP32)
-        return pick<float>(s->d, s->r)(s, (const float*)U, (float*)R, forced, cls_out, st, ua_ready);
-    return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st, ua_ready);
+        return pick<float>(s->d, s->r)(s, (const float*)U, (float*)R, forced, cls_out, st, (const float*)ua, rk);
+    return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st, (const double*)ua, rk);
 }
 
 int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
 {
-    return residual_any(s, U, R, forced, cls_out, (cudaStream_t)stream, false);
+    return residual_any(s, U, R, forced, cls_out, (cudaStream_t)stream, nullptr, nullptr);
 }
 
-// FP64 structure-of-arrays state -> cell-major stage copy in the residual precision
-static void stage_from(hfv_scheme* s, const double* U, cudaStream_t st)
+// FP64 state -> cell-major copy in UA (and the step into dt_dev when given)
+static int stage_in(hfv_scheme* s, const double* U, double cfl, double* dt_dev, cudaStream_t st)
 {
     const int64_t nc = s->mesh->nc;
     const unsigned g = (unsigned)((nc + 255) / 256);
+    const hfv_dev_arrays& a = s->a;
+    auto* out = (unsigned long long*)dt_dev;
+    if (dt_dev) { Launch l(s, KID_DT, st); k_dt_init<<<1, 1, 0, st>>>(out); }
     Launch l(s, KID_CVT, st);
     const bool f32 = s->p.precision == HFV_FP32;
     if (s->nv == 4) {
-        if (f32) k_to_aos<double, float, 4><<<g, 256, 0, st>>>(nc, U, (float*)s->a.UA);
-        else k_to_aos<double, double, 4><<<g, 256, 0, st>>>(nc, U, (double*)s->a.UA);
+        if (f32) k_stage_in<float, 4><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, s->p.gamma, cfl, out);
+        else k_stage_in<double, 4><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, s->p.gamma, cfl, out);
     } else {
-        if (f32) k_to_aos<double, float, 5><<<g, 256, 0, st>>>(nc, U, (float*)s->a.UA);
-        else k_to_aos<double, double, 5><<<g, 256, 0, st>>>(nc, U, (double*)s->a.UA);
-    }
-}
-
-// dt from the stage copy already in UA
-static int dt_from_stage(hfv_scheme* s, double cfl, double* dt_dev, cudaStream_t st)
-{
-    const int64_t nc = s->mesh->nc;
-    const unsigned g = (unsigned)((nc + 255) / 256);
-    const bool f32 = s->p.precision == HFV_FP32;
-    { Launch l(s, KID_DT, st); k_dt_init<<<1, 1, 0, st>>>((unsigned long long*)dt_dev); }
-    Launch l(s, KID_DT, st);
-    auto* out = (unsigned long long*)dt_dev;
-    const hfv_dev_arrays& a = s->a;
-    if (s->nv == 4) {
-        if (f32) k_dt<float, 4><<<g, 256, 0, st>>>(nc, (const float*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
-        else k_dt<double, 4><<<g, 256, 0, st>>>(nc, (const double*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
-    } else {
-        if (f32) k_dt<float, 5><<<g, 256, 0, st>>>(nc, (const float*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
-        else k_dt<double, 5><<<g, 256, 0, st>>>(nc, (const double*)a.UA, a.vol, a.area, a.nrm64, a.nfc, s->p.gamma, cfl, out);
+        if (f32) k_stage_in<float, 5><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, s->p.gamma, cfl, out);
+        else k_stage_in<double, 5><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, s->p.gamma, cfl, out);
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
@@ -1092,40 +1121,33 @@ static int dt_from_stage(hfv_scheme* s, double cfl, double* dt_dev, cudaStream_t
 
 int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
 {
-    cudaStream_t st = (cudaStream_t)stream;
-    stage_from(s, U, st);
-    return dt_from_stage(s, cfl, dt_dev, st);
-}
-
-template <class T, int NV>
-static void rk_launch(hfv_scheme* s, int k, double* U, const double* in, double* out, cudaStream_t st)
-{
-    const int64_t nc = s->mesh->nc;
-    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
-    Launch l(s, KID_RK, st);
-    k_rk<T, NV><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(nc, A[k], B[k], U, in, (const T*)s->a.Rs, s->a.dt, out,
-                                                                k < 2 ? (T*)s->a.UA : nullptr);
+    return stage_in(s, U, cfl, dt_dev, (cudaStream_t)stream);
 }
 
 int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
-    stage_from(s, U, st);
-    if (dt > 0.0) { Launch l(s, KID_DT, st); k_set<<<1, 1, 0, st>>>(s->a.dt, dt); }
-    else if ((rc = dt_from_stage(s, cfl, s->a.dt, st)) != HFV_OK) return rc;
+    if (dt > 0.0) {
+        { Launch l(s, KID_DT, st); k_set<<<1, 1, 0, st>>>(s->a.dt, dt); }
+        if ((rc = stage_in(s, U, cfl, nullptr, st)) != HFV_OK) return rc;
+    } else if ((rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
+        return rc;
+    }
+    // stages read UA, UB, UA; each stage's flux kernel writes the next copy
+    void* ua[3] = {s->a.UA, s->a.UB, s->a.UA};
     double* outs[3] = {s->a.U1, s->a.U2, U};
     const double* ins[3] = {U, s->a.U1, s->a.U2};
-    const bool f32 = s->p.precision == HFV_FP32;
+    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int k = 0; k < 3; ++k) {
-        if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, true)) != HFV_OK) return rc;
-        if (s->nv == 4) {
-            if (f32) rk_launch<float, 4>(s, k, U, ins[k], outs[k], st);
-            else rk_launch<double, 4>(s, k, U, ins[k], outs[k], st);
-        } else {
-            if (f32) rk_launch<float, 5>(s, k, U, ins[k], outs[k], st);
-            else rk_launch<double, 5>(s, k, U, ins[k], outs[k], st);
-        }
+        StageRK rk;
+        rk.a = A[k];
+        rk.b = B[k];
+        rk.U0 = U;
+        rk.Us = ins[k];
+        rk.out = outs[k];
+        rk.ua_next = k < 2 ? ua[k + 1] : nullptr;
+        if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, ua[k], &rk)) != HFV_OK) return rc;
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;

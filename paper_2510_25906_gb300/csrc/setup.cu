@@ -109,7 +109,8 @@ int build_operators(hfv_scheme* s, void* stream)
     size_t o_vol = take(nc * 8), o_area = take(nc * 6 * 8), o_nrm64 = take(nc * 18 * 8);
     size_t o_FS = take(qt * nv * b), o_raw = take(nc), o_cls = take(nc), o_queue = take(2 * nc * 4), o_counts = take(64),
            o_bcount = take(2 * (size_t)s->nblocks * 4), o_status = take(64);
-    size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b),
+    size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b), o_UB = take(nc * (nv == 4 ? 4 : 8) * b),
+           o_areaT = take(nc * 6 * b),
            o_dt = take(64), o_Uio = take(nv * nc * 8);
     s->arena_bytes = off;
     SETUP_CHECK(cudaMalloc(&s->arena, off));
@@ -123,7 +124,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.vol = (double*)(A + o_vol); a.area = (double*)(A + o_area); a.nrm64 = (double*)(A + o_nrm64);
     a.FS = A + o_FS; a.raw = (uint8_t*)(A + o_raw); a.cls = (uint8_t*)(A + o_cls); a.queue = (int32_t*)(A + o_queue);
     a.counts = (int32_t*)(A + o_counts); a.bcount = (int32_t*)(A + o_bcount); a.status = (int*)(A + o_status);
-    a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA;
+    a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA; a.UB = A + o_UB; a.areaT = A + o_areaT;
     a.dt = (double*)(A + o_dt);
     a.Uio = (double*)(A + o_Uio);
     SETUP_CHECK(cudaMemsetAsync(s->arena, 0, off, st));
@@ -256,10 +257,12 @@ int build_operators(hfv_scheme* s, void* stream)
         convert<float>(O.D, a.D, nc * 6 * d * Md, st); convert<float>(O.G, a.G, nc * d * Md, st);
         convert<float>(O.W, a.W, qt, st);
         convert<float>(d_ivol, a.ivol, nc, st); convert<float>(d_thr, a.dxthr, nc, st); convert<float>(d_nrm, a.nrm, nc * 18, st);
+        convert<float>(a.area, a.areaT, nc * 6, st);
     } else {
         SETUP_CHECK(cudaMemcpyAsync(a.ivol, d_ivol, nc * 8, cudaMemcpyDeviceToDevice, st));
         SETUP_CHECK(cudaMemcpyAsync(a.dxthr, d_thr, nc * 8, cudaMemcpyDeviceToDevice, st));
         SETUP_CHECK(cudaMemcpyAsync(a.nrm, d_nrm, nc * 18 * 8, cudaMemcpyDeviceToDevice, st));
+        SETUP_CHECK(cudaMemcpyAsync(a.areaT, a.area, nc * 6 * 8, cudaMemcpyDeviceToDevice, st));
     }
     SETUP_CHECK(cudaGetLastError());
     SETUP_CHECK(cudaStreamSynchronize(st));
