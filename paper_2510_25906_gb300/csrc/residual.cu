@@ -419,6 +419,18 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
     }
 }
 
+// a first-order cell's face points all carry its cell mean
+template <class T>
+__device__ __forceinline__ void write_mean(const KParams<T>& p, int64_t c)
+{
+    const int nv = p.nv, P = nv == 4 ? 4 : 8, nfp = p.nfp;
+    const int Q = (p.nfc[c] & 15) * nfp;
+    const T* u = p.UA + c * P;
+    T* fs = p.FS + c * (int64_t)p.qmax * nv;
+    for (int q = 0; q < Q; ++q)
+        for (int v = 0; v < nv; ++v) fs[q * nv + v] = u[v];
+}
+
 // K2a: tagging of the flagged cells' face neighbourhood (class = max over the
 // cell and its face neighbours), first-order for linear cells that broke the
 // Harten bound, and the per-block counts of the CWENOZ / MUSCL queues
@@ -444,6 +456,7 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
         }
         if (t == CLS_LIN && (r & HARTEN_FAIL)) t = CLS_FIRST;
         p.cls[c] = (uint8_t)t;
+        if (t == CLS_FIRST) write_mean<T>(p, c);
     }
     const unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
     const unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
@@ -685,12 +698,12 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
         const int Q = nf * NFP;
         const int64_t q0 = c * C::QMAX;
         bool fail = false;
+        T w[NV];
         if (lane < Q) {
             T* FS = p.FS + (q0 + lane) * NV;
             T ph[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
-            T w[NV];
             load_state<T, NV>(FS, w);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -699,12 +712,14 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
                 for (int k = 0; k < D; ++k) s0 += ph[k] * sC[gi][v][1 + k];
                 w[v] = s0;
             }
-            store_state<T, NV>(FS, w);
             const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
             const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
             fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
         }
-        if (grp.any(fail) && lane == 0) p.cls[c] = CLS_FIRST;
+        // a cell failing the Harten bound falls back to its mean at every point
+        const bool anyf = grp.any(fail);
+        if (lane < Q) store_state<T, NV>(p.FS + (q0 + lane) * NV, anyf ? uc : w);
+        if (anyf && lane == 0) p.cls[c] = CLS_FIRST;
         grp.sync();
     }
 }
@@ -771,18 +786,23 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
         }
         bool fail = false;
         if (lane < Q) {
-            store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
             const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
             const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
             fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
         }
-        if (grp.any(fail) && lane == 0) p.cls[c] = CLS_FIRST;
+        // a cell failing the Harten bound falls back to its mean at every point
+        const bool anyf = grp.any(fail);
+        if (lane < Q) store_state<T, NV>(p.FS + (q0 + lane) * NV, anyf ? uc : w);
+        if (anyf && lane == 0) p.cls[c] = CLS_FIRST;
         grp.sync();
     }
 }
 
 // K6: Riemann fluxes at the face points and the residual, one group per cell,
 // lane q the flux at face point q; the group sums F w |S| in a fixed order.
+// Both sides' states come from FS (a first-order cell carries its mean
+// there); the neighbour's point is at a precomputed offset.  With a fused
+// Runge-Kutta stage, lane v < nv updates variable v of the cell.
 template <class C, class T, int KIND>
 __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
 {
@@ -793,6 +813,13 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
     const int64_t c = (int64_t)blockIdx.x * CPB + gi;
     if (c >= p.nc) return;
     const int64_t nc = p.nc;
+    // the Runge-Kutta operands do not depend on the fluxes: load them first
+    double u0 = 0.0, us = 0.0;
+    const int64_t e = (int64_t)(lane < NV ? lane : 0) * nc + c;
+    if (p.rk_b != 0.0 && lane < NV) {
+        us = p.Us[e];
+        if (p.rk_a != 0.0) u0 = p.U0[e];
+    }
     const int nf = p.nfc[c] & 15, Q = nf * NFP;
     const int64_t q0 = c * C::QMAX;
     T acc[NV];
@@ -800,21 +827,14 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
     if (lane < Q) {
         const int f = lane / NFP, a = lane - f * NFP;
-        const int cc = p.cls[c];
+        const int32_t nb = p.nfs[c * 6 + f];
         T wl[NV], wr[NV], F[NV];
-        if (cc == CLS_FIRST) {
-            load_cell<T, NV>(p.UA, c, wl);
-        } else {
-            load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
-        }
-        const int64_t j = p.nbr[c * 6 + f];
-        if (j < 0) {
+        load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
+        if (nb < 0) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) wr[v] = wl[v];
-        } else if (p.cls[j] == CLS_FIRST) {
-            load_cell<T, NV>(p.UA, j, wr);
         } else {
-            load_state<T, NV>(p.FS + (j * C::QMAX + p.nbrf[c * 6 + f] * NFP + a) * NV, wr);
+            load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
         }
         const T* n = p.nrm + (c * 6 + f) * 3;
         T nn[3] = {n[0], n[1], n[2]};
@@ -834,9 +854,8 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
             R[lane * nc + c] = r;
         } else {
             // Runge-Kutta stage update of variable `lane` of cell c (FP64)
-            const int64_t e = lane * nc + c;
-            double x = p.rk_b * (p.Us[e] + p.dt[0] * (double)r);
-            if (p.rk_a != 0.0) x += p.rk_a * p.U0[e];
+            double x = p.rk_b * (us + p.dt[0] * (double)r);
+            if (p.rk_a != 0.0) x += p.rk_a * u0;
             p.out[e] = x;
             if (p.ua_next) p.ua_next[c * AoSP<NV>::P + lane] = (T)x;
         }
@@ -892,6 +911,10 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.Dd = (const T*)a.D; p.G = (const T*)a.G; p.W = (const T*)a.W; p.nrm = (const T*)a.nrm;
     p.ivol = (const T*)a.ivol; p.dxthr = (const T*)a.dxthr;
     p.UA = (const T*)a.UA;
+    p.nfs = a.nfs;
+    p.nv = s->nv;
+    p.nfp = s->nfp;
+    p.qmax = (s->d == 2 ? 4 : 6) * s->nfp;
     p.FS = (T*)a.FS; p.raw = a.raw; p.cls = a.cls; p.queue = a.queue; p.counts = a.counts;
     p.bcount = a.bcount; p.nblocks = s->nblocks; p.status = a.status;
     p.gamma = (T)s->p.gamma; p.alpha_m = (T)s->p.alpha_m; p.beta_m = (T)s->p.beta_m;

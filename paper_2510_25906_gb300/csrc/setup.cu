@@ -101,6 +101,7 @@ int build_operators(hfv_scheme* s, void* stream)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
     const int64_t ncp = s->nc_pad, lt = s->ltot;
+    size_t o_nfs = take(nc * 6 * 4);
     size_t o_sten = take(ncp * M * 4), o_nbr = take(nc * 6 * 4), o_nbrf = take(nc * 6), o_nfc = take(nc),
            o_qoff = take((nc + 1) * 8), o_loff = take((ncp + 1) * 8), o_dir = take(nc * 6 * Md);
     size_t o_L = take(lt * b), o_P = take(nc * N * M * b), o_Phil = take(qt * d * b), o_OI = take(nc * NOI * b),
@@ -119,6 +120,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.sten = (int32_t*)(A + o_sten); a.nbr = (int32_t*)(A + o_nbr); a.nbrf = (int8_t*)(A + o_nbrf);
     a.nfc = (uint8_t*)(A + o_nfc); a.qoff = (int64_t*)(A + o_qoff); a.dir = (uint8_t*)(A + o_dir);
     a.loff = (int64_t*)(A + o_loff);
+    a.nfs = (int32_t*)(A + o_nfs);
     a.L = A + o_L; a.P = A + o_P; a.Phil = A + o_Phil; a.OI = A + o_OI; a.D = A + o_D; a.G = A + o_G; a.W = A + o_W;
     a.nrm = A + o_nrm; a.ivol = A + o_ivol; a.dxthr = A + o_thr;
     a.vol = (double*)(A + o_vol); a.area = (double*)(A + o_area); a.nrm64 = (double*)(A + o_nrm64);
@@ -131,6 +133,19 @@ int build_operators(hfv_scheme* s, void* stream)
 
     // ---- host-side per-cell data ----
     std::vector<int32_t> nbr(m->nbr.begin(), m->nbr.end());
+    std::vector<int32_t> nfs(nc * 6, -1);
+    {
+        const int64_t qs = (int64_t)(d == 2 ? 4 : 6) * s->nfp;
+        if (nc * qs >= (int64_t(1) << 31)) {
+            set_error("hfv_scheme_create: mesh too large for 32-bit face-point offsets");
+            return HFV_ERR_ARG;
+        }
+        for (int64_t c = 0; c < nc; ++c)
+            for (int f = 0; f < 6; ++f) {
+                const int32_t j = m->nbr[c * kMaxFaces + f];
+                if (j >= 0) nfs[c * 6 + f] = (int32_t)(j * qs + m->nbrf[c * kMaxFaces + f] * s->nfp);
+            }
+    }
     std::vector<uint8_t> nfc(nc);
     std::vector<int32_t> fvtx(nc * 24, 0);
     std::vector<int8_t> fk(nc * 18, 0);
@@ -156,6 +171,7 @@ int build_operators(hfv_scheme* s, void* stream)
     }
     SETUP_CHECK(cudaMemcpyAsync(a.sten, s->sten.data(), nc * M * 4, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.nbr, nbr.data(), nc * 6 * 4, cudaMemcpyHostToDevice, st));
+    SETUP_CHECK(cudaMemcpyAsync(a.nfs, nfs.data(), nc * 6 * 4, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.nbrf, m->nbrf.data(), nc * 6, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.nfc, nfc.data(), nc, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.qoff, s->qoff.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
