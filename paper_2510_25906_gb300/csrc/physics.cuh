@@ -48,14 +48,62 @@ HDI float tsqrt<float>(float x) { return sqrtf(x); }
 template <>
 HDI double tsqrt<double>(double x) { return sqrt(x); }
 
+// reciprocal and square root: IEEE in FP64; in FP32 the hardware
+// approximations (about 2 ulp), far inside the FP32 path's 1e-5 bar
+template <class T>
+HDI T trcp(T x);
+template <>
+HDI double trcp<double>(double x) { return 1.0 / x; }
+template <>
+HDI float trcp<float>(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(1.0f, x);
+#else
+    return 1.0f / x;
+#endif
+}
+template <class T>
+HDI T fsqrt(T x);
+template <>
+HDI double fsqrt<double>(double x) { return sqrt(x); }
+template <>
+HDI float fsqrt<float>(float x)
+{
+#ifdef __CUDA_ARCH__
+    return x > 0.0f ? x * rsqrtf(x) : 0.0f;
+#else
+    return sqrtf(x);
+#endif
+}
+
 template <class T, int D, int KIND>
 HDI void riemann(const T* UL, const T* UR, const T* n, T g, T* F)
 {
     constexpr int NV = D + 2;
-    T FL[NV], FR[NV], unl, unr, pl, pr;
-    normal_flux<T, D>(UL, n, g, FL, unl, pl);
-    normal_flux<T, D>(UR, n, g, FR, unr, pr);
-    T cl = tsqrt<T>(g * pl / UL[0]), cr = tsqrt<T>(g * pr / UR[0]);
+    const T il = trcp<T>(UL[0]), ir = trcp<T>(UR[0]);
+    T ml2 = T(0), mr2 = T(0), mnl = T(0), mnr = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        ml2 += UL[1 + k] * UL[1 + k];
+        mr2 += UR[1 + k] * UR[1 + k];
+        mnl += UL[1 + k] * n[k];
+        mnr += UR[1 + k] * n[k];
+    }
+    const T unl = mnl * il, unr = mnr * ir;
+    const T pl = (g - T(1)) * (UL[D + 1] - T(0.5) * ml2 * il);
+    const T pr = (g - T(1)) * (UR[D + 1] - T(0.5) * mr2 * ir);
+    T FL[NV], FR[NV];
+    FL[0] = mnl;
+    FR[0] = mnr;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        FL[1 + k] = UL[1 + k] * unl + pl * n[k];
+        FR[1 + k] = UR[1 + k] * unr + pr * n[k];
+    }
+    FL[D + 1] = (UL[D + 1] + pl) * unl;
+    FR[D + 1] = (UR[D + 1] + pr) * unr;
+    const T cl = fsqrt<T>(g * pl * il), cr = fsqrt<T>(g * pr * ir);
     if (KIND == kRusanov) {
         T al = (unl < T(0) ? -unl : unl) + cl, ar = (unr < T(0) ? -unr : unr) + cr;
         T s = al > ar ? al : ar;
@@ -78,28 +126,24 @@ HDI void riemann(const T* UL, const T* UR, const T* n, T g, T* F)
         return;
     }
     if (KIND == kHLL) {
-        T inv = T(1) / (SR - SL);
+        const T inv = trcp<T>(SR - SL);
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] = (SR * FL[v] - SL * FR[v] + SL * SR * (UR[v] - UL[v])) * inv;
         return;
     }
-    // contact wave speed
-    T ml = UL[0] * (SL - unl), mr = UR[0] * (SR - unr);
-    T Ss = (pr - pl + ml * unl - mr * unr) / (ml - mr);
+    // contact wave speed and the star state on its upwind side
+    const T ml = UL[0] * (SL - unl), mr = UR[0] * (SR - unr);
+    const T Ss = (pr - pl + ml * unl - mr * unr) * trcp<T>(ml - mr);
     const bool left = Ss >= T(0);
     const T* UK = left ? UL : UR;
     const T* FK = left ? FL : FR;
-    T SK = left ? SL : SR, unk = left ? unl : unr, pk = left ? pl : pr, mk = left ? ml : mr;
-    T rk = UK[0];
-    T fac = mk / (SK - Ss);   // rho*
-    T dS = Ss - unk;
+    const T SK = left ? SL : SR, unk = left ? unl : unr, pk = left ? pl : pr, mk = left ? ml : mr, ik = left ? il : ir;
+    const T fac = mk * trcp<T>(SK - Ss);   // rho*
+    const T dS = Ss - unk;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        T us = fac * (UK[1 + k] / rk + dS * n[k]);
-        F[1 + k] = FK[1 + k] + SK * (us - UK[1 + k]);
-    }
+    for (int k = 0; k < D; ++k) F[1 + k] = FK[1 + k] + SK * (fac * (UK[1 + k] * ik + dS * n[k]) - UK[1 + k]);
     F[0] = FK[0] + SK * (fac - UK[0]);
-    T Es = fac * (UK[D + 1] / rk + dS * (Ss + pk / mk));
+    const T Es = fac * (UK[D + 1] * ik + dS * (Ss + pk * trcp<T>(mk)));
     F[D + 1] = FK[D + 1] + SK * (Es - UK[D + 1]);
 }
 
