@@ -241,6 +241,48 @@ def e2e_pass(g, torch, U0, steps, cfl):
     return time.perf_counter() - t0, Uh.nbytes
 
 
+def turbulence_variants(H, I, torch, dev, args):
+    """The 3D workload: 128^3 periodic hexahedra, order 4, HLLC.  The seeded
+    initial field is first advanced `pre` steps (hybrid, FP32; untimed input
+    preparation) so that compressible structures have formed; every variant
+    then times `steps` steps from that same state, L2 flushed between steps."""
+    mesh, U0, d = I.workload("turbulence", args.turbulence_scale)
+    gm = H.Mesh(mesh)
+    cells, cfl, steps = mesh.n_cells, d["cfl"], args.turbulence_steps
+    out = {"workload": f"3D decaying turbulence, periodic [0,2pi]^3, {cells} hexahedra, order 4, HLLC, SSP-RK3",
+           "pre_steps": args.turbulence_pre, "steps": steps}
+    g = H.Scheme(gm, order=4, flux="hllc", scheme="hybrid", precision="fp32")
+    U = torch.tensor(U0, device=dev)
+    for _ in range(args.turbulence_pre):
+        g.step(U, cfl=cfl)
+    torch.cuda.synchronize(dev)
+    Upre = U.cpu().numpy()
+    cls = torch.empty(cells, dtype=torch.uint8, device=dev)
+    g.residual(U.float().contiguous(), class_out=cls)
+    out["classes_at_start"] = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+    for scheme in ("hybrid", "cweno"):
+        for prec in ("fp32", "fp64"):
+            gv = g if (scheme, prec) == ("hybrid", "fp32") else H.Scheme(gm, order=4, flux="hllc", scheme=scheme,
+                                                                           precision=prec)
+            ms, _, _, _ = time_steps(H, torch, gv, Upre, steps, 2, cfl, dev)
+            entry = {"value": 3.0 * cells * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+            if (scheme, prec) == ("hybrid", "fp32"):
+                times = kernel_pass(H, torch, gv, Upre, steps, cfl, dev)
+                k_ms, k_n = times["linear"]
+                kb = _k1_bytes(mesh, gv, 4)
+                ach = kb / (k_ms / k_n * 1e-3) / 1e9
+                peak, _ = _peaks()
+                entry["k_linear"] = {"achieved_GBs": ach, "frac": ach / peak, "avg_launch_us": 1e3 * k_ms / k_n,
+                                     "algorithmic_bytes_per_launch": kb}
+                entry["kernel_share"] = {k: round(v[0] / sum(x[0] for x in times.values()), 4)
+                                         for k, v in times.items() if v[1]}
+            out[f"{scheme}_{prec}"] = entry
+            if gv is not g:
+                del gv
+                torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +296,10 @@ def main():
     ap.add_argument("--variants", type=int, default=1, help="also time hybrid/CWENOZ x FP32/FP64 at orders 3, 5")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--scale", type=int, default=None, help="mesh size parameter (small cases for profiling)")
+    ap.add_argument("--turbulence", type=int, default=1, help="also time the 3D workload (rank 0)")
+    ap.add_argument("--turbulence-scale", type=int, default=None)
+    ap.add_argument("--turbulence-pre", type=int, default=100)
+    ap.add_argument("--turbulence-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _env()
@@ -334,6 +380,9 @@ def main():
                     msv, _, _, _ = time_steps(H, torch, gv, U0, args.steps, args.warmup, cfl, dev)
                     variants[key] = {"value": 3.0 * cells * args.steps / (msv * 1e-3), "ms_per_step": msv / args.steps}
                     del gv
+    turbulence = None
+    if args.turbulence and rank == 0:
+        turbulence = turbulence_variants(H, I, torch, dev, args)
 
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -348,7 +397,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if g.fp32 else "f64", "data": "synthetic",
                 "config": _config(args, mesh), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "classes_final": hist,
-                "wall_s_timed": wall, "variants": variants}
+                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
