@@ -211,14 +211,18 @@ struct K1Shape {
     static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
     static constexpr int SBYTES = NG * C::M * 4;
     static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
-    static constexpr int STAGES = STAGE * 4 <= 100 * 1024 ? 4 : STAGE * 3 <= 150 * 1024 ? 3 : 2;
     static constexpr int SU = NG * C::M * AoSP<C::NV>::P * (int)sizeof(T);   // U_m - U_0 rows
+    // resident CTAs per SM aimed for (register and shared-memory budget)
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : (C::D == 2 && C::R <= 2) ? 4 : 2;
+    static constexpr int BUDGET = 227 * 1024 / MINB - (SU + 127) / 128 * 128 - 1024;
+    static constexpr int FIT = BUDGET / STAGE;
+    static constexpr int STAGES = FIT >= 4 ? 4 : FIT >= 3 ? 3 : 2;
     static constexpr int SMEM = STAGES * STAGE + (SU + 127) / 128 * 128 + 2 * STAGES * 8;
     static constexpr int THREADS = CONSUMERS + 32;
 };
 
 template <class C, class T>
-__global__ void __launch_bounds__(288) k_linear(KParams<T> p)
+__global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
 {
     using S = K1Shape<C, T>;
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, G = S::G, NG = S::NG, ST = S::STAGES;
@@ -338,28 +342,44 @@ __global__ void __launch_bounds__(288) k_linear(KParams<T> p)
             T w[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) w[v] = uc[v];
-            T lrow[M];
-            if (lane < Q) load_row_smem<T, M>(reinterpret_cast<const T*>(stage) + lrel + lane * M, lrow);
             grp.sync();
             const int64_t q0 = c * C::QMAX;
             if (lane < Q) {
+                // the row of L is read from the stage as the products need it
+                const T* lr = reinterpret_cast<const T*>(stage) + lrel + lane * M;
                 if constexpr (sizeof(T) == 4) {
                     // packed FP32x2 FMAs: one instruction per two variables
                     float2 w01 = make_float2(w[0], w[1]), w23 = make_float2(w[2], w[3]);
+                    constexpr int VW = M % 4 == 0 ? 4 : 2;
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
-                        const float4 d = *reinterpret_cast<const float4*>(myU + m * P);
-                        const float2 l2 = make_float2(lrow[m], lrow[m]);
-                        w01 = __ffma2_rn(l2, make_float2(d.x, d.y), w01);
-                        w23 = __ffma2_rn(l2, make_float2(d.z, d.w), w23);
-                        if constexpr (NV == 5) w[4] = fmaf(lrow[m], myU[m * P + 4], w[4]);
+                    for (int m0 = 0; m0 < M; m0 += VW) {
+                        float lv[VW];
+                        if constexpr (VW == 4) {
+                            const float4 t = *reinterpret_cast<const float4*>(lr + m0);
+                            lv[0] = t.x; lv[1] = t.y; lv[2] = t.z; lv[3] = t.w;
+                        } else {
+                            const float2 t = *reinterpret_cast<const float2*>(lr + m0);
+                            lv[0] = t.x; lv[1] = t.y;
+                        }
+#pragma unroll
+                        for (int j = 0; j < VW; ++j) {
+                            const int m = m0 + j;
+                            const float4 d = *reinterpret_cast<const float4*>(myU + m * P);
+                            const float2 l2 = make_float2(lv[j], lv[j]);
+                            w01 = __ffma2_rn(l2, make_float2(d.x, d.y), w01);
+                            w23 = __ffma2_rn(l2, make_float2(d.z, d.w), w23);
+                            if constexpr (NV == 5) w[4] = fmaf(lv[j], myU[m * P + 4], w[4]);
+                        }
                     }
                     w[0] = w01.x; w[1] = w01.y; w[2] = w23.x; w[3] = w23.y;
                 } else {
 #pragma unroll
-                    for (int m = 0; m < M; ++m) {
+                    for (int m0 = 0; m0 < M; m0 += 2) {
+                        const double2 t = *reinterpret_cast<const double2*>(lr + m0);
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) w[v] = fma(lrow[m], myU[m * P + v], w[v]);
+                        for (int v = 0; v < NV; ++v) w[v] = fma(t.x, myU[m0 * P + v], w[v]);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) w[v] = fma(t.y, myU[(m0 + 1) * P + v], w[v]);
                     }
                 }
                 store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
