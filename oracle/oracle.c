@@ -155,7 +155,8 @@ static int cell_rule(int type, const double* v, int n, double* px, double* pw)
                         double dN[3] = {df[0] * f[1] * f[2], f[0] * df[1] * f[2], f[0] * f[1] * df[2]};
                         for (int d = 0; d < 3; ++d) {
                             X[d] += Nv * v[3 * a + d];
-                            for (int e = 0; e < 3; ++e) Jm[d][e] += v[3 * a + d] * dN[e];
+                            /* differences to v0: the shape-function gradients sum to zero */
+                            for (int e = 0; e < 3; ++e) Jm[d][e] += (v[3 * a + d] - v[d]) * dN[e];
                         }
                     }
                     double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1])

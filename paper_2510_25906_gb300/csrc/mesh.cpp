@@ -82,10 +82,13 @@ double cell_measure(const hfv_mesh* m, int64_t c)
         return 0.5 * ((b[0] - a[0]) * (q[1] - a[1]) - (b[1] - a[1]) * (q[0] - a[0]));
     }
     if (t == HFV_QUAD) {
+        // shoelace on coordinates relative to v0 (absolute coordinates would
+        // cancel catastrophically for small cells far from the origin)
+        const double* o = node(m, c, 0);
         double s = 0.0;
-        for (int k = 0; k < 4; ++k) {
-            const double *a = node(m, c, k), *b = node(m, c, (k + 1) % 4);
-            s += a[0] * b[1] - b[0] * a[1];
+        for (int k = 1; k < 3; ++k) {
+            const double *a = node(m, c, k), *b = node(m, c, k + 1);
+            s += (a[0] - o[0]) * (b[1] - o[1]) - (b[0] - o[0]) * (a[1] - o[1]);
         }
         return 0.5 * s;
     }
@@ -107,8 +110,9 @@ double cell_measure(const hfv_mesh* m, int64_t c)
                     }
                     double grad[3] = {dw[0] * w[1] * w[2], w[0] * dw[1] * w[2], w[0] * w[1] * dw[2]};
                     const double* x = node(m, c, a);
+                    const double* x0 = node(m, c, 0);
                     for (int r = 0; r < 3; ++r)
-                        for (int q = 0; q < 3; ++q) J[r][q] += x[r] * grad[q];
+                        for (int q = 0; q < 3; ++q) J[r][q] += (x[r] - x0[r]) * grad[q];   // the gradients sum to 0
                 }
                 double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
                              J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +

@@ -66,9 +66,11 @@ def _check(H, mesh, U, kw, precision, near, n_near, n_rand, tol, seed, key):
     good = np.array([cg[c] == fin[c] and all(cg[j] == fin[j] for j in nbr[c] if j >= 0 and fin[j] != 255)
                      for c in smp])
     scale = np.abs(Ro[:, smp]).max(axis=1)
-    err = (np.abs(Rg[:, smp] - Ro[:, smp])[:, good].max(axis=1) / scale).max()
+    per_var = np.abs(Rg[:, smp] - Ro[:, smp])[:, good].max(axis=1) / scale
+    err = per_var.max()
     print(f"{mesh.name} {kw} {precision}: {smp.size} sampled cells, classes {np.bincount(fin[smp], minlength=4)}, "
-          f"agreement {agree:.4f}, max rel err {err:.2e}")
+          f"agreement {agree:.4f}, max rel err {err:.2e} per variable {np.array2string(per_var, precision=2)} "
+          f"max|R| {np.array2string(scale, precision=3)}")
     assert err <= tol, err
     assert len(np.unique(fin[smp])) >= 2
 
