@@ -37,6 +37,32 @@ UNIT = "cell-residuals/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
+# DRAM traffic of k_linear per cell, from one ncu capture of the kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its cells; the
+# kernel reads per-cell data only, so traffic scales with the cells).  A figure
+# holds only while the kernel sources are those the capture ran: their hash is
+# stored beside it, and a mismatch reports null.
+KERNEL_SOURCES = ("residual.cu", "kernels.cuh", "tma.cuh", "physics.cuh")
+TRAFFIC = {}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2510_25906_gb300", "csrc")
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload, order, precision, scheme, cells):
+    t = TRAFFIC.get((workload, order, precision, scheme))
+    if not t or t["sources"] != kernel_source_hash():
+        return None
+    return int(round(t["bytes_per_cell"] * cells))
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -357,7 +383,8 @@ def main():
     tot_ms = sum(v[0] for v in times.values())
     roofline = {"kernel": "k_linear (gather + linear candidate + detector + Harten test)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": _traffic(args.workload, args.order, args.precision, args.scheme, cells),
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
                 "algorithmic_bytes_per_launch": kbytes, "avg_launch_us": 1e3 * k_ms / max(k_n, 1),
                 "kernel_share": {k: round(v[0] / tot_ms, 4) for k, v in times.items() if v[1]}}

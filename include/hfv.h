@@ -197,8 +197,11 @@ HFV_API int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double 
 HFV_API int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues);
 
 /* Sticky status bits (host output): bit0 = a state with rho <= 0, p <= 0 or
- * a non-finite value reached hfv_residual.  reset != 0 clears them.  sync.
- * Returns HFV_ERR_NONPHYSICAL when bit0 is set, HFV_OK otherwise. */
+ * a non-finite value reached hfv_residual; bit2 = a bounded wait on a bulk
+ * copy inside the candidate kernel gave up (the kernel skipped the rest of
+ * its cells and returned; the residual of that launch is incomplete).
+ * reset != 0 clears them.  sync.  Returns HFV_ERR_TIMEOUT when bit2 is set,
+ * else HFV_ERR_NONPHYSICAL when bit0 is set, else HFV_OK. */
 HFV_API int hfv_status(hfv_scheme* s, int* flags, int reset);
 
 /* Device bytes held by the scheme (operators + scratch). */

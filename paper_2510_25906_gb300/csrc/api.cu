@@ -205,6 +205,10 @@ extern "C" int hfv_status(hfv_scheme* s, int* flags, int reset)
     API_CUDA(cudaDeviceSynchronize());
     API_CUDA(cudaMemcpy(flags, s->a.status, sizeof(int), cudaMemcpyDeviceToHost));
     if (reset) API_CUDA(cudaMemset(s->a.status, 0, sizeof(int)));
+    if (*flags & 4) {
+        set_error("hfv_status: a bounded device wait gave up");
+        return HFV_ERR_TIMEOUT;
+    }
     return (*flags & 1) ? HFV_ERR_NONPHYSICAL : HFV_OK;
 }
 

@@ -54,7 +54,8 @@ struct hfv_dev_arrays {
     int32_t* sten;     // [nc_pad][M] (rows past nc are zero)
     int32_t* nbr;      // [nc][6]
     int8_t* nbrf;      // [nc][6]
-    int32_t* nfs;      // [nc][6] FS point offset of the neighbour's matching face, -1 on open boundaries
+    int32_t* nfs;      // [nc][6] FS point offset of the neighbour's matching face, -1 on open boundaries,
+                       // -2 past the cell's last face
     uint8_t* nfc;      // [nc] faces per cell | (distinct face neighbours << 4)
     int64_t* qoff;     // [nc+1] offsets of face points: c * (max faces * points per face)
     int64_t* loff;     // [nc_pad+1] element offsets of the per-cell L blocks (16-byte padded)

@@ -44,7 +44,8 @@ struct KParams {
     const uint8_t* nfc;
     const int64_t* qoff;
     const int64_t* loff;
-    const int32_t* nfs;   // [nc][6] FS point offset of the neighbour's matching face (-1: open boundary)
+    const int32_t* nfs;   // [nc][6] FS point offset of the neighbour's matching face (-1: open boundary,
+                          // -2: no such face)
     int nv, nfp, qmax;
     const uint8_t* dir;
     // operators

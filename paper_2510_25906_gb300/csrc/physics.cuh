@@ -16,31 +16,6 @@ namespace hfv {
 
 enum { kRusanov = 0, kHLLC = 1, kHLL = 2 };
 
-template <class T, int D>
-HDI T pressure(const T* U, T g)
-{
-    T m2 = T(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) m2 += U[1 + k] * U[1 + k];
-    return (g - T(1)) * (U[D + 1] - T(0.5) * m2 / U[0]);
-}
-
-// normal flux F(U).n and the normal velocity / pressure it used
-template <class T, int D>
-HDI void normal_flux(const T* U, const T* n, T g, T* F, T& un, T& p)
-{
-    T inv = T(1) / U[0];
-    un = T(0);
-#pragma unroll
-    for (int k = 0; k < D; ++k) un += U[1 + k] * n[k];
-    un *= inv;
-    p = pressure<T, D>(U, g);
-    F[0] = U[0] * un;
-#pragma unroll
-    for (int k = 0; k < D; ++k) F[1 + k] = U[1 + k] * un + p * n[k];
-    F[D + 1] = (U[D + 1] + p) * un;
-}
-
 template <class T>
 HDI T tsqrt(T x);
 template <>
@@ -75,6 +50,31 @@ HDI float fsqrt<float>(float x)
 #else
     return sqrtf(x);
 #endif
+}
+
+template <class T, int D>
+HDI T pressure(const T* U, T g)
+{
+    T m2 = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) m2 += U[1 + k] * U[1 + k];
+    return (g - T(1)) * (U[D + 1] - T(0.5) * m2 * trcp<T>(U[0]));
+}
+
+// normal flux F(U).n and the normal velocity / pressure it used
+template <class T, int D>
+HDI void normal_flux(const T* U, const T* n, T g, T* F, T& un, T& p)
+{
+    T inv = T(1) / U[0];
+    un = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) un += U[1 + k] * n[k];
+    un *= inv;
+    p = pressure<T, D>(U, g);
+    F[0] = U[0] * un;
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] = U[1 + k] * un + p * n[k];
+    F[D + 1] = (U[D + 1] + p) * un;
 }
 
 template <class T, int D, int KIND>

@@ -198,12 +198,26 @@ __device__ __forceinline__ void load_cell(const T* __restrict__ UA, int64_t c, T
 // producer warp streams each tile's contiguous L blocks and stencil ids into a
 // ring of shared-memory stages with bulk copies (TMA engine, mbarrier
 // completion); eight consumer warps hold NG groups of G lanes, one group per
-// cell.  A group gathers the M stencil states, lane q forms the candidate at
-// face point q from its row of L, and the group runs the detector (bounds
-// from the first stencil layer = the face neighbours) and the Harten test.
+// cell.  A group gathers the M stencil states into rows of U_m - U_0, lane l
+// forms the candidate at face points l, l + G, ... (PPL of them) from their
+// rows of L, and the group runs the detector (bounds from the first stencil
+// layer = the face neighbours) and the Harten test.
+//
+// L block of a cell with Q face points: columns in chunks of W = 16 bytes /
+// sizeof(T); chunk j holds [Q][W] (the W values of every row for columns
+// jW .. jW+W-1), a last partial chunk of width M mod W holds [Q][M mod W].
+// One 16-byte load gives a lane W columns of its row, and the eight lanes of
+// a group read 128 contiguous bytes.
 template <class C, class T>
 struct K1Shape {
-    static constexpr int G = GroupSize<C::QMAX>::value;
+    // one face point per lane: more points per lane would need more cells
+    // per tile than a ring of 16-byte aligned stages of L holds (3.8 KB of L
+    // per hexahedron at order 4)
+    static constexpr int PPL = 1;
+    static constexpr int G = GroupSize<(C::QMAX + PPL - 1) / PPL>::value;   // lanes per cell
+    static constexpr int SLOT = C::NFMAX <= 4 ? 4 : 8;       // lanes of one face-neighbour reduction
+    // lanes past the first SLOT take the bounds from the group's first lane
+    static constexpr bool NB_BCAST = G > SLOT;
     static constexpr int CONSUMERS = 256;                    // 8 warps
     static constexpr int NG = CONSUMERS / G;                 // cells per tile
     static constexpr int PER16 = 16 / (int)sizeof(T);
@@ -211,23 +225,48 @@ struct K1Shape {
     static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
     static constexpr int SBYTES = NG * C::M * 4;
     static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
-    static constexpr int SU = NG * C::M * AoSP<C::NV>::P * (int)sizeof(T);   // U_m - U_0 rows
+    // rows of U_m - U_0 per cell: [M][4] and, with five variables, [M] of the
+    // fifth; cells 16 bytes apart modulo 128 so that the four cells of a warp
+    // read different banks
+    static constexpr int DU4 = C::M * 4 * (int)sizeof(T);
+    static constexpr int DU5 = C::NV == 5 ? (C::M * (int)sizeof(T) + 15) / 16 * 16 : 0;
+    static constexpr int CSTRIDE = (DU4 + DU5 + 127) / 128 * 128 + 16;
+    static constexpr int SU = NG * CSTRIDE;
     // resident CTAs per SM aimed for (register and shared-memory budget)
-    static constexpr int MINB = sizeof(T) == 8 ? 1 : (C::D == 2 && C::R <= 2) ? 4 : 2;
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : (C::D == 2 && C::R <= 2) ? 3 : 2;
     static constexpr int BUDGET = 227 * 1024 / MINB - (SU + 127) / 128 * 128 - 1024;
     static constexpr int FIT = BUDGET / STAGE;
     static constexpr int STAGES = FIT >= 4 ? 4 : FIT >= 3 ? 3 : 2;
     static constexpr int SMEM = STAGES * STAGE + (SU + 127) / 128 * 128 + 2 * STAGES * 8;
     static constexpr int THREADS = CONSUMERS + 32;
+    static_assert(SMEM <= 227 * 1024, "staging ring exceeds shared memory");
 };
+
+// min / max over the SLOT aligned lanes of a segment (xor offsets below SLOT
+// stay inside it)
+template <int SLOT, class T>
+__device__ __forceinline__ T seg_min(unsigned mask, T v)
+{
+#pragma unroll
+    for (int o = SLOT / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
+    return v;
+}
+template <int SLOT, class T>
+__device__ __forceinline__ T seg_max(unsigned mask, T v)
+{
+#pragma unroll
+    for (int o = SLOT / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w > v ? w : v; }
+    return v;
+}
 
 template <class C, class T>
 __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
 {
     using S = K1Shape<C, T>;
-    constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, G = S::G, NG = S::NG, ST = S::STAGES;
+    constexpr int M = C::M, NV = C::NV, D = C::D, G = S::G, NG = S::NG, ST = S::STAGES, PPL = S::PPL;
+    constexpr int SLOT = S::SLOT, W = S::PER16, M4 = M / W * W, TW = M - M4;
     extern __shared__ __align__(128) unsigned char smem[];
-    T* sU = reinterpret_cast<T*>(smem + ST * S::STAGE);
+    unsigned char* sU = smem + ST * S::STAGE;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + ST * S::STAGE + (S::SU + 127) / 128 * 128);
     uint64_t* empty = full + ST;
     const int64_t nc = p.nc;
@@ -270,14 +309,15 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     // Software pipeline: while tile k is computed from shared memory, the
     // stencil states of tile k+1 are already in flight into registers.
     constexpr int MI = (M + G - 1) / G;    // stencil cells per lane
-    constexpr int P = AoSP<NV>::P;
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
-    T* myU = sU + gi * M * P;              // rows of U_m - U_0
+    T* dU4 = reinterpret_cast<T*>(sU + gi * S::CSTRIDE);          // [M][4]
+    T* dU5 = reinterpret_cast<T*>(sU + gi * S::CSTRIDE + S::DU4); // [M] (five variables)
     T nu[MI][NV];                          // in-flight stencil states of the next tile
-    T nuc[NV];
+    T nuc[NV];                             // the cell
     int nnfv = 0;
     int64_t nlrel = 0;
+    T nthr = T(0);
     auto fetch = [&](int64_t tile_f, int stage_f) {
         const int64_t cf = tile_f * NG + gi;
         if (cf >= nc) return;
@@ -289,6 +329,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
         }
         load_cell<T, NV>(p.UA, cf, nuc);
         nnfv = p.nfc[cf];
+        nthr = p.dxthr[cf];
         nlrel = p.loff[cf] - p.loff[tile_f * NG];
     };
     int k = 0;
@@ -301,28 +342,30 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     while (alive && tile < ntiles) {
         const int s = k % ST;
         const int64_t c = tile * NG + gi;
-        T uc[NV], face[NV];                // the cell's state; lane < n1: its face neighbour's state
+        T uc[NV], nb[NV];                  // the cell's state; face neighbour `lane` (lane < SLOT)
         const int nfv = nnfv;
         const int64_t lrel = nlrel;
+        const T thr = nthr;
         if (c < nc) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) { uc[v] = nuc[v]; face[v] = nu[0][v]; }
+            for (int v = 0; v < NV; ++v) {
+                uc[v] = nuc[v];
+                nb[v] = lane < M ? nu[0][v] : uc[v];
+            }
 #pragma unroll
             for (int i = 0; i < MI; ++i) {
                 const int m = lane + i * G;
                 if (m < M) {
-                    T row[P];
+                    T row[NV];
 #pragma unroll
-                    for (int v = 0; v < P; ++v) row[v] = v < NV ? nu[i][v] - uc[v] : T(0);
+                    for (int v = 0; v < NV; ++v) row[v] = nu[i][v] - uc[v];
                     if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                        for (int v = 0; v < P; v += 4)
-                            *reinterpret_cast<float4*>(myU + m * P + v) = make_float4(row[v], row[v + 1], row[v + 2], row[v + 3]);
+                        *reinterpret_cast<float4*>(dU4 + m * 4) = make_float4(row[0], row[1], row[2], row[3]);
                     } else {
-#pragma unroll
-                        for (int v = 0; v < P; v += 2)
-                            *reinterpret_cast<double2*>(myU + m * P + v) = make_double2(row[v], row[v + 1]);
+                        *reinterpret_cast<double2*>(dU4 + m * 4) = make_double2(row[0], row[1]);
+                        *reinterpret_cast<double2*>(dU4 + m * 4 + 2) = make_double2(row[2], row[3]);
                     }
+                    if constexpr (NV == 5) dU5[m] = row[4];
                 }
             }
         }
@@ -338,95 +381,171 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
         }
         const unsigned char* stage = smem + s * S::STAGE;
         if (c < nc) {
-            const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
-            T w[NV];
+            const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * C::NFP;
+            T w[PPL][NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) w[v] = uc[v];
+            for (int j = 0; j < PPL; ++j)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) w[j][v] = uc[v];
             grp.sync();
-            const int64_t q0 = c * C::QMAX;
-            if (lane < Q) {
-                // the row of L is read from the stage as the products need it
-                const T* lr = reinterpret_cast<const T*>(stage) + lrel + lane * M;
-                if constexpr (sizeof(T) == 4) {
-                    // packed FP32x2 FMAs: one instruction per two variables
-                    float2 w01 = make_float2(w[0], w[1]), w23 = make_float2(w[2], w[3]);
-                    constexpr int VW = M % 4 == 0 ? 4 : 2;
+            const T* lb = reinterpret_cast<const T*>(stage) + lrel;
+            // candidate: w = U_0 + sum_m L_qm (U_m - U_0), one chunk of W
+            // columns of L per 16-byte load
+            if constexpr (sizeof(T) == 4) {
+                float2 w01[PPL], w23[PPL];
 #pragma unroll
-                    for (int m0 = 0; m0 < M; m0 += VW) {
-                        float lv[VW];
-                        if constexpr (VW == 4) {
-                            const float4 t = *reinterpret_cast<const float4*>(lr + m0);
-                            lv[0] = t.x; lv[1] = t.y; lv[2] = t.z; lv[3] = t.w;
+                for (int j = 0; j < PPL; ++j) { w01[j] = make_float2(w[j][0], w[j][1]); w23[j] = make_float2(w[j][2], w[j][3]); }
+#pragma unroll
+                for (int m0 = 0; m0 < M4; m0 += 4) {
+                    float lv[PPL][4];
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int q = lane + j * G;
+                        if (q < Q) {
+                            const float4 t = *reinterpret_cast<const float4*>(lb + m0 * Q + q * 4);
+                            lv[j][0] = t.x; lv[j][1] = t.y; lv[j][2] = t.z; lv[j][3] = t.w;
                         } else {
-                            const float2 t = *reinterpret_cast<const float2*>(lr + m0);
-                            lv[0] = t.x; lv[1] = t.y;
-                        }
-#pragma unroll
-                        for (int j = 0; j < VW; ++j) {
-                            const int m = m0 + j;
-                            const float4 d = *reinterpret_cast<const float4*>(myU + m * P);
-                            const float2 l2 = make_float2(lv[j], lv[j]);
-                            w01 = __ffma2_rn(l2, make_float2(d.x, d.y), w01);
-                            w23 = __ffma2_rn(l2, make_float2(d.z, d.w), w23);
-                            if constexpr (NV == 5) w[4] = fmaf(lv[j], myU[m * P + 4], w[4]);
+                            lv[j][0] = lv[j][1] = lv[j][2] = lv[j][3] = 0.0f;
                         }
                     }
-                    w[0] = w01.x; w[1] = w01.y; w[2] = w23.x; w[3] = w23.y;
-                } else {
+                    float4 e5 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if constexpr (NV == 5) e5 = *reinterpret_cast<const float4*>(dU5 + m0);
+                    const float e5a[4] = {e5.x, e5.y, e5.z, e5.w};
 #pragma unroll
-                    for (int m0 = 0; m0 < M; m0 += 2) {
-                        const double2 t = *reinterpret_cast<const double2*>(lr + m0);
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 d = *reinterpret_cast<const float4*>(dU4 + (m0 + i) * 4);
+                        const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
 #pragma unroll
-                        for (int v = 0; v < NV; ++v) w[v] = fma(t.x, myU[m0 * P + v], w[v]);
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) w[v] = fma(t.y, myU[(m0 + 1) * P + v], w[v]);
+                        for (int j = 0; j < PPL; ++j) {
+                            const float2 l2 = make_float2(lv[j][i], lv[j][i]);
+                            w01[j] = __ffma2_rn(l2, d01, w01[j]);
+                            w23[j] = __ffma2_rn(l2, d23, w23[j]);
+                            if constexpr (NV == 5) w[j][4] = fmaf(lv[j][i], e5a[i], w[j][4]);
+                        }
                     }
                 }
-                store_state<T, NV>(p.FS + (q0 + lane) * NV, w);
+                if constexpr (TW == 2) {
+                    float lt[PPL][2];
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int q = lane + j * G;
+                        if (q < Q) {
+                            const float2 t = *reinterpret_cast<const float2*>(lb + M4 * Q + q * 2);
+                            lt[j][0] = t.x; lt[j][1] = t.y;
+                        } else {
+                            lt[j][0] = lt[j][1] = 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const float4 d = *reinterpret_cast<const float4*>(dU4 + (M4 + i) * 4);
+                        const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
+#pragma unroll
+                        for (int j = 0; j < PPL; ++j) {
+                            const float2 l2 = make_float2(lt[j][i], lt[j][i]);
+                            w01[j] = __ffma2_rn(l2, d01, w01[j]);
+                            w23[j] = __ffma2_rn(l2, d23, w23[j]);
+                            if constexpr (NV == 5) w[j][4] = fmaf(lt[j][i], dU5[M4 + i], w[j][4]);
+                        }
+                    }
+                }
+                static_assert(TW == 0 || TW == 2, "FP32 stencil sizes are even");
+#pragma unroll
+                for (int j = 0; j < PPL; ++j) { w[j][0] = w01[j].x; w[j][1] = w01[j].y; w[j][2] = w23[j].x; w[j][3] = w23[j].y; }
+            } else {
+                static_assert(sizeof(T) == 4 || TW == 0, "FP64 stencil sizes are even");
+#pragma unroll 2
+                for (int m0 = 0; m0 < M; m0 += 2) {
+                    double lv[PPL][2];
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int q = lane + j * G;
+                        if (q < Q) {
+                            const double2 t = *reinterpret_cast<const double2*>(lb + m0 * Q + q * 2);
+                            lv[j][0] = t.x; lv[j][1] = t.y;
+                        } else {
+                            lv[j][0] = lv[j][1] = 0.0;
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const double2 a = *reinterpret_cast<const double2*>(dU4 + (m0 + i) * 4);
+                        const double2 b = *reinterpret_cast<const double2*>(dU4 + (m0 + i) * 4 + 2);
+                        const double d[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+                        for (int j = 0; j < PPL; ++j) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) w[j][v] = fma(lv[j][i], d[v], w[j][v]);
+                            if constexpr (NV == 5) w[j][4] = fma(lv[j][i], dU5[m0 + i], w[j][4]);
+                        }
+                    }
+                }
             }
-            if (lane == 0 && !(uc[0] > T(0) && pressure<T, D>(uc, p.gamma) > T(0))) atomicOr(p.status, 1);
+            const int64_t q0 = c * C::QMAX;
             const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
+            if (lane == 0 && !(rb > T(0) && pb > T(0))) atomicOr(p.status, 1);
+            // Harten test of the candidate at the lane's points
+            const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
+            T pw[PPL];
             bool fail = false;
-            if (lane < Q) {
-                const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
-                fail = !(tabs(w[0] - rb) <= rlim) || !(tabs(pressure<T, D>(w, p.gamma) - pb) <= plim);
+#pragma unroll
+            for (int j = 0; j < PPL; ++j) {
+                const int q = lane + j * G;
+                pw[j] = pressure<T, D>(w[j], p.gamma);
+                if (q < Q) {
+                    store_state<T, NV>(p.FS + (q0 + q) * NV, w[j]);
+                    fail = fail || !(tabs(w[j][0] - rb) <= rlim) || !(tabs(pw[j] - pb) <= plim);
+                }
             }
-            const bool hfail = grp.any(fail);
             int cl = CLS_LIN;
             if (!p.forced && p.scheme == HFV_HYBRID) {
-                const T thr = p.dxthr[c];
+                // detector: lane l < SLOT takes face neighbour l for the
+                // bounds, every lane its own face points for the classification
+                const bool has = lane < n1;
+                const int src = (threadIdx.x & 31) & ~(G - 1);   // the group's first lane
+                const T pn = pressure<T, D>(nb, p.gamma);
                 const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
+#pragma unroll
                 for (int kind = 0; kind < NV + 1; ++kind) {
                     const bool use = kind == 0 ? (p.nad_vars & 1) : kind == 1 ? (p.nad_vars & 2) : (p.nad_vars & 4);
                     if (!use) continue;
-                    const T qi = nad_value<T, D>(uc, kind, p.gamma);
-                    T qj = qi, dd = T(0);
-                    const bool has = lane < n1;
-                    if (has) {
-                        qj = nad_value<T, D>(face, kind, p.gamma);
-                        dd = tabs(qj - qi);
+                    const T qi = kind == 0 ? rb : kind == 1 ? pb : uc[kind - 1];
+                    const T qn = kind == 0 ? nb[0] : kind == 1 ? pn : nb[kind - 1];
+                    const T qj = has ? qn : qi;
+                    const T dd = tabs(qj - qi);
+                    T lo = seg_min<SLOT>(grp.mask, qj), hi = seg_max<SLOT>(grp.mask, qj);
+                    T dlo = seg_min<SLOT>(grp.mask, has ? dd : T(INFINITY));
+                    T dhi = seg_max<SLOT>(grp.mask, has ? dd : T(-INFINITY));
+                    if constexpr (S::NB_BCAST) {
+                        lo = __shfl_sync(grp.mask, lo, src);
+                        hi = __shfl_sync(grp.mask, hi, src);
+                        dlo = __shfl_sync(grp.mask, dlo, src);
+                        dhi = __shfl_sync(grp.mask, dhi, src);
                     }
-                    const T lo = grp.min(qj), hi = grp.max(qj);
-                    const T dlo = grp.min(has ? dd : T(INFINITY)), dhi = grp.max(has ? dd : T(-INFINITY));
                     if (n1 == 0 || dhi - dlo < thr) continue;   // deactivated: smooth
                     const T range = hi - lo;
                     const T dm = tmax(p.alpha_m, p.beta_m * range);
                     const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
-                    int kc = CLS_LIN;
-                    if (lane < Q) {
-                        const T x = nad_value<T, D>(w, kind, p.gamma);
-                        if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
-                        else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
-                        else kc = CLS_CW;
+#pragma unroll
+                    for (int j = 0; j < PPL; ++j) {
+                        const int q = lane + j * G;
+                        if (q < Q) {
+                            const T x = kind == 0 ? w[j][0] : kind == 1 ? pw[j] : w[j][kind - 1];
+                            int kc;
+                            if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
+                            else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
+                            else kc = CLS_CW;
+                            cl = kc > cl ? kc : cl;
+                        }
                     }
-                    kc = grp.max(kc);
-                    cl = kc > cl ? kc : cl;
                 }
             }
+            const bool hfail = grp.any(fail);
+            const bool any_mu = grp.any(cl == CLS_MU), any_cw = grp.any(cl == CLS_CW);
             if (lane == 0) {
                 uint8_t out;
                 if (p.forced) out = p.forced_cls[c];
-                else if (p.scheme == HFV_HYBRID) out = (uint8_t)cl;
+                else if (p.scheme == HFV_HYBRID) out = any_mu ? CLS_MU : any_cw ? CLS_CW : CLS_LIN;
                 else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
                 p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
             }
@@ -823,8 +942,15 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
 // Both sides' states come from FS (a first-order cell carries its mean
 // there); the neighbour's point is at a precomputed offset.  With a fused
 // Runge-Kutta stage, lane v < nv updates variable v of the cell.
+// resident blocks per SM aimed for: 12 (40 registers) for the FP32 3D
+// kernels, where the occupancy gain outweighs a few spilled registers
+template <class C, class T>
+struct FluxShape {
+    static constexpr int MINB = (C::D == 3 && sizeof(T) == 4) ? 12 : 1;
+};
+
 template <class C, class T, int KIND>
-__global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
+__global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> p, T* __restrict__ R)
 {
     constexpr int NV = C::NV, D = C::D, NFP = C::NFP;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
@@ -833,21 +959,31 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
     const int64_t c = (int64_t)blockIdx.x * CPB + gi;
     if (c >= p.nc) return;
     const int64_t nc = p.nc;
-    // the Runge-Kutta operands do not depend on the fluxes: load them first
-    double u0 = 0.0, us = 0.0;
+    // geometry and connectivity first: none of it depends on the fluxes
+    const T ivol = lane < NV ? p.ivol[c] : T(0);
+    const int64_t q0 = c * C::QMAX;
+    const bool inq = lane < C::QMAX;
+    const int f = inq ? lane / NFP : 0, a = lane - f * NFP;
+    int32_t nb = -2;
+    T wq = T(0), nn[3] = {T(0), T(0), T(0)};
+    if (inq) {
+        nb = p.nfs[c * 6 + f];
+        wq = p.W[q0 + lane];
+        const T* n = p.nrm + (c * 6 + f) * 3;
+        nn[0] = n[0]; nn[1] = n[1]; nn[2] = n[2];
+    }
+    // the Runge-Kutta operands do not depend on the fluxes either
+    double u0 = 0.0, us = 0.0, dt = 0.0;
     const int64_t e = (int64_t)(lane < NV ? lane : 0) * nc + c;
     if (p.rk_b != 0.0 && lane < NV) {
         us = p.Us[e];
+        dt = p.dt[0];
         if (p.rk_a != 0.0) u0 = p.U0[e];
     }
-    const int nf = p.nfc[c] & 15, Q = nf * NFP;
-    const int64_t q0 = c * C::QMAX;
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
-    if (lane < Q) {
-        const int f = lane / NFP, a = lane - f * NFP;
-        const int32_t nb = p.nfs[c * 6 + f];
+    if (nb != -2) {
         T wl[NV], wr[NV], F[NV];
         load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
         if (nb < 0) {
@@ -856,12 +992,9 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
         } else {
             load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
         }
-        const T* n = p.nrm + (c * 6 + f) * 3;
-        T nn[3] = {n[0], n[1], n[2]};
         riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
-        const T w = p.W[q0 + lane];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = F[v] * w;
+        for (int v = 0; v < NV; ++v) acc[v] = F[v] * wq;
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = grp.sum(acc[v]);
@@ -869,12 +1002,12 @@ __global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
         T val = acc[0];
 #pragma unroll
         for (int v = 1; v < NV; ++v) val = lane == v ? acc[v] : val;
-        const T r = -val * p.ivol[c];
+        const T r = -val * ivol;
         if (p.rk_b == 0.0) {
             R[lane * nc + c] = r;
         } else {
             // Runge-Kutta stage update of variable `lane` of cell c (FP64)
-            double x = p.rk_b * (us + p.dt[0] * (double)r);
+            double x = p.rk_b * (us + dt * (double)r);
             if (p.rk_a != 0.0) x += p.rk_a * u0;
             p.out[e] = x;
             if (p.ua_next) p.ua_next[c * AoSP<NV>::P + lane] = (T)x;

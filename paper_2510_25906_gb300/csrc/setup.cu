@@ -143,7 +143,8 @@ int build_operators(hfv_scheme* s, void* stream)
         for (int64_t c = 0; c < nc; ++c)
             for (int f = 0; f < 6; ++f) {
                 const int32_t j = m->nbr[c * kMaxFaces + f];
-                if (j >= 0) nfs[c * 6 + f] = (int32_t)(j * qs + m->nbrf[c * kMaxFaces + f] * s->nfp);
+                if (f >= type_nfaces(m->type[c])) nfs[c * 6 + f] = -2;
+                else if (j >= 0) nfs[c * 6 + f] = (int32_t)(j * qs + m->nbrf[c * kMaxFaces + f] * s->nfp);
             }
     }
     std::vector<uint8_t> nfc(nc);
@@ -215,6 +216,7 @@ int build_operators(hfv_scheme* s, void* stream)
     for (int k = 0; k < 3; ++k) S.period[k] = m->period[k];
     S.d = d; S.r = s->r; S.N = N; S.M = M; S.Md = Md; S.nq = s->nq; S.nfp = s->nfp;
     S.nvq = d == 2 ? s->r + 1 : s->r + 2;
+    S.lcw = f32 ? 4 : 2;
     gauss01(s->nq, S.gfx, S.gfw);
     gauss01(S.nvq, S.gvx, S.gvw);
     {

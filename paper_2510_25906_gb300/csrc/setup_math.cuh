@@ -54,13 +54,14 @@ struct SetupParams {
     const int64_t* loff;     // [nc+1] offsets of the L blocks
     double period[3];
     int d, r, N, M, Md, nq, nfp, nvq;
+    int lcw;                 // column chunk of the L blocks: 16 bytes of the kernel precision
     double gfx[kGmax], gfw[kGmax];  // face rule on [0,1]
     double gvx[kGmax], gvw[kGmax];  // volume rule on [0,1]
     int8_t ex[kNmax][3];            // monomial exponents
 };
 
 struct SetupOut {
-    double* L;      // cell c at loff[c], [Q_c][M] (one row per face point)
+    double* L;      // cell c at loff[c]: Q_c rows x M columns, columns in chunks of lcw (l_index)
     double* P;      // [nc][N][M]
     double* Phil;   // [qoff][d]
     double* OI;     // [nc][N(N+1)/2]
@@ -69,6 +70,16 @@ struct SetupOut {
     double* W;      // [qoff]
     int* err;       // first failing cell + 1 (0 = none)
 };
+
+// position of L_qm inside a cell's block of Q rows and M columns: column
+// chunks of width W (the values of 16 bytes), chunk j = [Q][W]; the last
+// partial chunk of width M mod W = [Q][M mod W]
+HD inline int64_t l_index(int q, int m, int Q, int M, int W)
+{
+    const int M4 = M / W * W;
+    if (m < M4) return (int64_t)(m / W) * Q * W + q * W + m % W;
+    return (int64_t)M4 * Q + q * (M - M4) + (m - M4);
+}
 
 // workspace of one thread: A [M][N], stride-interleaved between threads
 struct SetupWork {
@@ -337,7 +348,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
             for (int m = 0; m < M; ++m) {
                 double s = 0.0;
                 for (int kk = 0; kk < N; ++kk) s += phi[kk] * P[kk * M + m];
-                L[(int64_t)q * M + m] = s;   // q < Q_c rows, block padded to 16 bytes
+                L[l_index(q, m, nf * S.nfp, M, S.lcw)] = s;   // block padded to 16 bytes
             }
             for (int kk = 0; kk < d; ++kk) O.Phil[(q0 + q) * d + kk] = phi[kk];
             O.W[q0 + q] = wgt;
