@@ -309,6 +309,83 @@ def turbulence_variants(H, I, torch, dev, args):
     return out
 
 
+def batched_variants(H, I, torch, dev, args):
+    """Independent open 2D problems of uneven size and order (the batched
+    workload): one batched mesh and scheme per order, all advanced by one
+    hfv_step_many per step (one stream per order, one CUDA graph), against
+    one scheme per problem stepped one after another (also graph-captured).
+    Cell-residuals/s of the whole batch, FP32, CFL 0.5, each problem with
+    its own CFL step."""
+    t0 = time.perf_counter()
+    P = I.batched_problems(args.batched, seed=5)
+    t_gen = time.perf_counter() - t0
+    cells = sum(p["mesh"].n_cells for p in P)
+    groups = {}
+    for k, p in enumerate(P):
+        groups.setdefault(p["order"], []).append(k)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    st = torch.cuda.Stream(device=dev)
+
+    def timed(step_fn, steps, warmup):
+        with torch.cuda.stream(st):
+            for _ in range(warmup):
+                step_fn(st)
+            torch.cuda.synchronize(dev)
+            n0 = H.launch_count()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=st):
+                step_fn(st)
+            launches = H.launch_count() - n0
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(st)
+                graph.replay()
+                ev[k][1].record(st)
+            torch.cuda.synchronize(dev)
+        return sum(a.elapsed_time(b) for a, b in ev), launches
+
+    t0 = time.perf_counter()
+    schemes, states = [], []
+    for order, ks in sorted(groups.items()):
+        gm = H.Mesh.batch([P[k]["mesh"] for k in ks])
+        schemes.append(H.Scheme(gm, order=order, flux="hllc", precision="fp32"))
+        states.append(torch.tensor(np.concatenate([P[k]["U"] for k in ks], axis=1), device=dev))
+    t_setup = time.perf_counter() - t0
+    ms_b, l_b = timed(lambda s: H.step_many(schemes, states, cfl=0.5, stream=s), args.batched_steps, 3)
+    hist = np.zeros(4, np.int64)
+    for g, U in zip(schemes, states):
+        cls = torch.empty(g.n_cells, dtype=torch.uint8, device=dev)
+        g.residual(U.float().contiguous(), class_out=cls)
+        hist += np.bincount(cls.cpu().numpy(), minlength=4)
+    del schemes, states
+    torch.cuda.empty_cache()
+
+    t0 = time.perf_counter()
+    single = []
+    for p in P:
+        g = H.Scheme(H.Mesh(p["mesh"]), order=p["order"], flux="hllc", precision="fp32")
+        single.append((g, torch.tensor(p["U"], device=dev)))
+    t_setup1 = time.perf_counter() - t0
+
+    def each(s):
+        for g, U in single:
+            g.step(U, cfl=0.5, stream=s)
+    ms_1, l_1 = timed(each, args.batched_steps, 3)
+    del single
+    torch.cuda.empty_cache()
+    K = args.batched_steps
+    return {"workload": f"{len(P)} independent open 2D problems, jittered triangle meshes of 1k-200k cells "
+                        f"(log-uniform), orders {sorted(groups)} uniform, sine waves and rotated Sod tubes, HLLC, FP32",
+            "problems": len(P), "cells": int(cells), "per_order": {int(o): len(ks) for o, ks in sorted(groups.items())},
+            "classes": hist.tolist(), "steps": K,
+            "batched": {"value": 3.0 * cells * K / (ms_b * 1e-3), "ms_per_step": ms_b / K,
+                        "launches_per_step": l_b, "form": "one batched mesh per order, hfv_step_many, one graph"},
+            "per_problem": {"value": 3.0 * cells * K / (ms_1 * 1e-3), "ms_per_step": ms_1 / K,
+                            "launches_per_step": l_1, "form": "one scheme per problem, hfv_step each, one graph"},
+            "speedup": ms_1 / ms_b, "setup_s": {"inputs": t_gen, "batched": t_setup, "per_problem": t_setup1}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,6 +403,8 @@ def main():
     ap.add_argument("--turbulence-scale", type=int, default=None)
     ap.add_argument("--turbulence-pre", type=int, default=100)
     ap.add_argument("--turbulence-steps", type=int, default=10)
+    ap.add_argument("--batched", type=int, default=256, help="problems of the batched workload (0: skip)")
+    ap.add_argument("--batched-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _env()
@@ -410,6 +489,9 @@ def main():
     turbulence = None
     if args.turbulence and rank == 0:
         turbulence = turbulence_variants(H, I, torch, dev, args)
+    batched = None
+    if args.batched and rank == 0:
+        batched = batched_variants(H, I, torch, dev, args)
 
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -424,7 +506,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if g.fp32 else "f64", "data": "synthetic",
                 "config": _config(args, mesh), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "classes_final": hist,
-                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence}
+                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence, "batched": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

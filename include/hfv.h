@@ -124,6 +124,24 @@ HFV_API int hfv_default_params(hfv_scheme_params* p);
  * two cells, cell that is its own neighbour), HFV_ERR_OOM. */
 HFV_API int hfv_mesh_create(const hfv_mesh_desc* desc, hfv_mesh** out);
 
+/* A batch of independent problems as one mesh (the batched workload of many
+ * 2D problems of uneven size): the meshes are concatenated, node and cell ids
+ * offset per mesh, and problem k becomes the cells
+ * cell_offsets[k] .. cell_offsets[k+1] - 1 (hfv_mesh_segments), in the given
+ * order.  No face is shared between problems, so stencils (Sec. 2.1),
+ * detector bounds (Sec. 2.5) and fluxes never couple them, and a residual of
+ * the batch equals, cell by cell, the residuals of the problems alone.
+ * hfv_step and hfv_compute_dt take one time step per problem.  The paper
+ * solves one problem at a time; batching is a property of this library.
+ * All meshes must have the same dim and be open (period 0).  Errors:
+ * HFV_ERR_ARG (bad descriptor, periodic mesh), HFV_ERR_MESH, HFV_ERR_OOM. */
+HFV_API int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, hfv_mesh** out);
+
+/* Problems of a mesh (1 for hfv_mesh_create): *n_segments, and when
+ * cell_offsets (host, n_segments + 1 int64) is non-NULL their first cells
+ * and the total.  sync. */
+HFV_API int hfv_mesh_segments(const hfv_mesh* mesh, int* n_segments, int64_t* cell_offsets);
+
 /* Sizes of a mesh.  Any output pointer may be NULL. */
 HFV_API int hfv_mesh_info(const hfv_mesh* mesh, int64_t* n_cells, int64_t* n_faces, int* dim);
 
@@ -173,8 +191,9 @@ HFV_API int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* dir
 HFV_API int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced_class, uint8_t* class_out, void* stream);
 
 /* Stable time step dt = cfl * min_c |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|
- * from the cell averages of U (device, FP64 [nv][n_cells]); result written to
- * dt_dev (device, one double).  async. */
+ * from the cell averages of U (device, FP64 [nv][n_cells]), the minimum taken
+ * over each problem's cells; result written to dt_dev (device, one double per
+ * problem of the mesh, hfv_mesh_segments).  async. */
 HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
 
 /* One three-stage SSP Runge-Kutta step (Shu-Osher form) of U in place:
@@ -182,10 +201,20 @@ HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* d
  *   U  = 1/3 U + 2/3 (U2 + dt R(U2)).
  *   U   device FP64 [nv][n_cells] (the accumulation is FP64 in both precisions;
  *       in HFV_FP32 each stage's residual is evaluated on an FP32 copy)
- *   dt  > 0: that step; <= 0: computed from U with `cfl` (hfv_compute_dt)
- *   dt_used  host double* or NULL; non-NULL makes the call sync.
+ *   dt  > 0: that step for every problem; <= 0: each problem's own step
+ *       computed from U with `cfl` (hfv_compute_dt)
+ *   dt_used  host double* (one per problem of the mesh) or NULL; non-NULL
+ *       makes the call sync.
  * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG. */
 HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream);
+
+/* hfv_step on several schemes at once, each on its own stream forked from
+ * `stream` and joined back into it (so their kernels may run concurrently,
+ * and a stream capture records one graph with one branch per scheme): the
+ * form a batch of problems of different orders takes, one batched mesh per
+ * order.  U[k] is scheme k's state; cfl and dt as for hfv_step.  Schemes
+ * must be distinct.  async; allocates nothing.  Errors: HFV_ERR_ARG. */
+HFV_API int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n, double cfl, double dt, void* stream);
 
 /* End-to-end helper: copy U (host, FP64 [nv][n_cells]) to the device, take
  * n_steps steps as hfv_step, copy the result back into U.  sync. */

@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     objs = [os.path.join(BUILD, u + ".o") for u in UNITS]
     if force or jobs or not os.path.exists(OUT):
         tmp = OUT + f".{os.getpid()}.tmp"
-        run([nvcc, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart"])
+        run([nvcc, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart", "-lpthread"])
         os.replace(tmp, OUT)
     return OUT
 

@@ -74,6 +74,9 @@ extern "C" void hfv_scheme_destroy(hfv_scheme* s)
 {
     if (!s) return;
     timer_free(s->timer);
+    if (s->side) cudaStreamDestroy((cudaStream_t)s->side);
+    if (s->ev_fork) cudaEventDestroy((cudaEvent_t)s->ev_fork);
+    if (s->ev_join) cudaEventDestroy((cudaEvent_t)s->ev_join);
     if (s->arena) cudaFree(s->arena);
     delete s;
 }
@@ -111,6 +114,20 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
         set_error("hfv_scheme_create: out of host memory");
     }
     if (rc == HFV_OK) rc = build_operators(s, stream);
+    if (rc == HFV_OK) {
+        cudaStream_t side;
+        cudaEvent_t e1, e2;
+        if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess) {
+            rc = HFV_ERR_CUDA;
+        } else {
+            s->side = side;
+            if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) rc = HFV_ERR_CUDA;
+            else s->ev_fork = e1;
+            if (rc == HFV_OK && cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) rc = HFV_ERR_CUDA;
+            else if (rc == HFV_OK) s->ev_join = e2;
+        }
+        if (rc != HFV_OK) set_error("hfv_scheme_create: stream or event creation failed");
+    }
     if (rc != HFV_OK) {
         hfv_scheme_destroy(s);
         return rc;
@@ -168,9 +185,35 @@ extern "C" int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double*
     int rc = launch_step(s, U, cfl, dt, stream);
     if (rc != HFV_OK) return rc;
     if (dt_used) {
-        API_CUDA(cudaMemcpyAsync(dt_used, s->a.dt, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+        API_CUDA(cudaMemcpyAsync(dt_used, s->a.dt, s->nseg * sizeof(double), cudaMemcpyDeviceToHost,
+                                 (cudaStream_t)stream));
         API_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     }
+    return HFV_OK;
+}
+
+extern "C" int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n, double cfl, double dt, void* stream)
+{
+    if (!schemes || !U || n <= 0 || (!(dt > 0) && !(cfl > 0))) {
+        set_error("hfv_step_many: bad argument");
+        return HFV_ERR_ARG;
+    }
+    for (int k = 0; k < n; ++k)
+        if (!schemes[k] || !U[k]) { set_error("hfv_step_many: NULL scheme or state"); return HFV_ERR_ARG; }
+    // fork: every scheme's side stream waits for the caller's stream; each
+    // step runs on its own side stream; join: the caller's stream waits for
+    // all of them.  Under stream capture this records one graph with a
+    // branch per scheme.
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < n; ++k) {
+        hfv_scheme* s = schemes[k];
+        API_CUDA(cudaEventRecord((cudaEvent_t)s->ev_fork, st));
+        API_CUDA(cudaStreamWaitEvent((cudaStream_t)s->side, (cudaEvent_t)s->ev_fork, 0));
+        const int rc = launch_step(s, U[k], cfl, dt, s->side);
+        if (rc != HFV_OK) return rc;
+        API_CUDA(cudaEventRecord((cudaEvent_t)s->ev_join, (cudaStream_t)s->side));
+    }
+    for (int k = 0; k < n; ++k) API_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)schemes[k]->ev_join, 0));
     return HFV_OK;
 }
 

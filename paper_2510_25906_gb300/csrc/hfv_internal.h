@@ -44,6 +44,9 @@ struct hfv_mesh {
     // per cell
     std::vector<double> vol;        // [nc]
     std::vector<double> vmean;      // [nc][3] vertex mean
+    // independent problems of a batch: cells seg_off[k] .. seg_off[k+1] - 1
+    // form problem k (one segment for a single mesh)
+    std::vector<int64_t> seg_off;
 };
 
 // ---------------------------------------------------------------------------
@@ -90,7 +93,8 @@ struct hfv_dev_arrays {
     void* UA;          // [nc][P] cell-major copy of the stage state in the residual precision, P = 4 (2D) / 8 (3D)
     void* UB;          // second stage copy: stages alternate UA / UB
     void* areaT;       // [nc][6] face areas in the residual precision
-    double* dt;        // [1]
+    double* dt;        // [nseg] time step per problem
+    int32_t* seg;      // [nc] problem of each cell (batched meshes; null for one problem)
     double* Uio;       // [nv][nc] device state of hfv_advance_host
 };
 
@@ -119,6 +123,7 @@ struct hfv_scheme {
     int64_t ltot = 0;               // elements of L
     std::vector<int64_t> loff;      // [nc_pad+1]
     int nblocks = 0;
+    int nseg = 1;                   // independent problems in the mesh
     // host copies kept for introspection
     std::vector<int32_t> sten;      // [nc][M]
     std::vector<int8_t> sshift;     // [nc][M][3]
@@ -128,6 +133,10 @@ struct hfv_scheme {
     std::vector<int64_t> qoff;      // [nc+1]
     void* arena = nullptr;
     size_t arena_bytes = 0;
+    // side stream and fork / join events of hfv_step_many
+    void* side = nullptr;
+    void* ev_fork = nullptr;
+    void* ev_join = nullptr;
     hfv_dev_arrays a{};
 };
 

@@ -76,7 +76,8 @@ struct KParams {
     double rk_a, rk_b;
     const double* U0;
     const double* Us;
-    const double* dt;
+    const double* dt;     // [problems]
+    const int32_t* seg;   // problem of each cell, or null (one problem)
     double* out;
     T* ua_next;
     // constants

@@ -296,12 +296,102 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
             for (int k = 0; k < 3; ++k) m->vmean[3 * c + k] /= nvx;
         }
         m->nface = nface;
+        m->seg_off = {0, nc};
     } catch (const std::bad_alloc&) {
         delete m;
         set_error("hfv_mesh_create: out of host memory");
         return HFV_ERR_OOM;
     }
     *out = m;
+    return HFV_OK;
+}
+
+extern "C" int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, hfv_mesh** out)
+{
+    if (!descs || !out || n_meshes <= 0) {
+        set_error("hfv_mesh_create_batch: invalid arguments");
+        return HFV_ERR_ARG;
+    }
+    *out = nullptr;
+    // one descriptor holding every mesh, node and cell ids offset per mesh:
+    // no face is shared between meshes, so stencils and fluxes never couple them
+    int64_t nn = 0, nc = 0, nidx = 0;
+    const int dim = descs[0].dim;
+    for (int k = 0; k < n_meshes; ++k) {
+        const hfv_mesh_desc& d = descs[k];
+        if (d.dim != dim || d.n_cells <= 0 || d.n_nodes <= 0 || !d.node_xyz || !d.cell_type || !d.cell_node_ptr ||
+            !d.cell_node_idx || !d.period) {
+            set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " is invalid or of another dimension");
+            return HFV_ERR_ARG;
+        }
+        for (int a = 0; a < dim; ++a)
+            if (d.period[a] != 0.0) {
+                set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " is periodic; batched meshes are open");
+                return HFV_ERR_ARG;
+            }
+        nn += d.n_nodes;
+        nc += d.n_cells;
+        nidx += d.cell_node_ptr[d.n_cells];
+    }
+    if (nn >= (int64_t(1) << 31) || nc >= (int64_t(1) << 31)) {
+        set_error("hfv_mesh_create_batch: more than 2^31 nodes or cells");
+        return HFV_ERR_ARG;
+    }
+    std::vector<int64_t> seg(n_meshes + 1, 0);
+    std::vector<double> xyz, period(dim, 0.0);
+    std::vector<uint8_t> type;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> idx;
+    try {
+        xyz.reserve(nn * dim);
+        type.reserve(nc);
+        ptr.reserve(nc + 1);
+        idx.reserve(nidx);
+        ptr.push_back(0);
+        int64_t node0 = 0;
+        for (int k = 0; k < n_meshes; ++k) {
+            const hfv_mesh_desc& d = descs[k];
+            xyz.insert(xyz.end(), d.node_xyz, d.node_xyz + d.n_nodes * dim);
+            type.insert(type.end(), d.cell_type, d.cell_type + d.n_cells);
+            const int64_t base = ptr.back();
+            for (int64_t c = 0; c < d.n_cells; ++c) ptr.push_back(base + d.cell_node_ptr[c + 1] - d.cell_node_ptr[0]);
+            for (int64_t i = d.cell_node_ptr[0]; i < d.cell_node_ptr[d.n_cells]; ++i) {
+                const int32_t v = d.cell_node_idx[i];
+                if (v < 0 || v >= d.n_nodes) {
+                    set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " has a vertex id out of range");
+                    return HFV_ERR_MESH;
+                }
+                idx.push_back((int32_t)(v + node0));
+            }
+            node0 += d.n_nodes;
+            seg[k + 1] = seg[k] + d.n_cells;
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("hfv_mesh_create_batch: out of host memory");
+        return HFV_ERR_OOM;
+    }
+    hfv_mesh_desc all;
+    all.dim = dim;
+    all.n_nodes = nn;
+    all.n_cells = nc;
+    all.node_xyz = xyz.data();
+    all.cell_type = type.data();
+    all.cell_node_ptr = ptr.data();
+    all.cell_node_idx = idx.data();
+    all.period = period.data();
+    hfv_mesh* m = nullptr;
+    int rc = hfv_mesh_create(&all, &m);
+    if (rc != HFV_OK) return rc;
+    m->seg_off = seg;
+    *out = m;
+    return HFV_OK;
+}
+
+extern "C" int hfv_mesh_segments(const hfv_mesh* m, int* n_segments, int64_t* cell_offsets)
+{
+    if (!m || !n_segments) { set_error("hfv_mesh_segments: NULL argument"); return HFV_ERR_ARG; }
+    *n_segments = (int)m->seg_off.size() - 1;
+    if (cell_offsets) std::memcpy(cell_offsets, m->seg_off.data(), m->seg_off.size() * sizeof(int64_t));
     return HFV_OK;
 }
 

@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
     const int64_t e = (int64_t)(lane < NV ? lane : 0) * nc + c;
     if (p.rk_b != 0.0 && lane < NV) {
         us = p.Us[e];
-        dt = p.dt[0];
+        dt = p.dt[p.seg ? p.seg[c] : 0];
         if (p.rk_a != 0.0) u0 = p.U0[e];
     }
     T acc[NV];
@@ -1122,10 +1122,11 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     }
     p.UA = ua;
     if (rk) {
-        p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.dt = s->a.dt; p.out = rk->out;
+        p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.dt = s->a.dt; p.seg = s->a.seg; p.out = rk->out;
         p.ua_next = (T*)rk->ua_next;
     } else {
-        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr; p.out = nullptr; p.ua_next = nullptr;
+        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr; p.seg = nullptr; p.out = nullptr;
+        p.ua_next = nullptr;
     }
     {
         using S1 = K1Shape<C, T>;
@@ -1173,21 +1174,31 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
 // ---------------------------------------------------------------------------
 // time stepping (three-stage SSP Runge-Kutta, FP64 accumulation)
 // ---------------------------------------------------------------------------
-__global__ void k_set(double* x, double v) { *x = v; }
+__global__ void k_set(double* x, double v, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
 
-__global__ void k_dt_init(unsigned long long* x) { *x = 0x7ff0000000000000ull; }
+__global__ void k_dt_init(unsigned long long* x, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 0x7ff0000000000000ull;
+}
 
 // FP64 state (structure of arrays) -> the first stage's cell-major copy, and,
 // when dt_out is given, the stable step
 //   dt = cfl min_c |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|
 // from the copy (FP64 with FP64 geometry, or FP32 with FP32 geometry: then a
-// stability estimate, not part of the conserved update).  The min is
+// stability estimate, not part of the conserved update), one minimum per
+// problem (seg: the problem of each cell, null for one problem).  The min is
 // order-free and exact.
 template <class T, int NV>
 __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __restrict__ U, T* __restrict__ UA,
                                                   const T* __restrict__ ivol, const T* __restrict__ area,
                                                   const T* __restrict__ nrm, const uint8_t* __restrict__ nfc,
-                                                  double gamma, double cfl, unsigned long long* dt_out)
+                                                  const int32_t* __restrict__ seg, double gamma, double cfl,
+                                                  unsigned long long* dt_out)
 {
     constexpr int D = NV - 2, P = AoSP<NV>::P;
     __shared__ double red[8];
@@ -1228,13 +1239,25 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
         }
     }
     if (!dt_out) return;
+    // problems are runs of consecutive cells: a block inside one problem
+    // reduces first, a block across a boundary takes one atomic per cell
+    int k0 = 0;
+    if (seg) {
+        const int64_t c0 = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t c1 = min(c0 + (int64_t)blockDim.x, nc) - 1;
+        k0 = seg[c0];
+        if (seg[c1] != k0) {
+            if (c < nc) atomicMin(dt_out + seg[c], (unsigned long long)__double_as_longlong(dtc));
+            return;
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dtc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = red[0];
         for (int k = 1; k < 8; ++k) m = fmin(m, red[k]);
-        atomicMin(dt_out, (unsigned long long)__double_as_longlong(m));
+        atomicMin(dt_out + k0, (unsigned long long)__double_as_longlong(m));
     }
 }
 
@@ -1281,15 +1304,15 @@ static int stage_in(hfv_scheme* s, const double* U, double cfl, double* dt_dev, 
     const unsigned g = (unsigned)((nc + 255) / 256);
     const hfv_dev_arrays& a = s->a;
     auto* out = (unsigned long long*)dt_dev;
-    if (dt_dev) { Launch l(s, KID_DT, st); k_dt_init<<<1, 1, 0, st>>>(out); }
+    if (dt_dev) { Launch l(s, KID_DT, st); k_dt_init<<<(s->nseg + 255) / 256, 256, 0, st>>>(out, s->nseg); }
     Launch l(s, KID_CVT, st);
     const bool f32 = s->p.precision == HFV_FP32;
     if (s->nv == 4) {
-        if (f32) k_stage_in<float, 4><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, s->p.gamma, cfl, out);
-        else k_stage_in<double, 4><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, s->p.gamma, cfl, out);
+        if (f32) k_stage_in<float, 4><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        else k_stage_in<double, 4><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
     } else {
-        if (f32) k_stage_in<float, 5><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, s->p.gamma, cfl, out);
-        else k_stage_in<double, 5><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, s->p.gamma, cfl, out);
+        if (f32) k_stage_in<float, 5><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        else k_stage_in<double, 5><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
@@ -1305,7 +1328,7 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
     if (dt > 0.0) {
-        { Launch l(s, KID_DT, st); k_set<<<1, 1, 0, st>>>(s->a.dt, dt); }
+        { Launch l(s, KID_DT, st); k_set<<<(s->nseg + 255) / 256, 256, 0, st>>>(s->a.dt, dt, s->nseg); }
         if ((rc = stage_in(s, U, cfl, nullptr, st)) != HFV_OK) return rc;
     } else if ((rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
         return rc;

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
+#include <vector>
 
 #include "hfv_internal.h"
 
@@ -86,9 +88,18 @@ int build_stencils(hfv_scheme* s)
     s->nd.assign(nc * kMaxFaces, 0);
     s->n1.assign(nc, 0);
 
-    std::vector<Cand> visited, layer, next, chosen;
-    std::vector<int32_t> mark(nc, -1);   // last cell whose BFS visited this cell
-    for (int64_t i = 0; i < nc; ++i) {
+    // cells are independent: contiguous ranges on host threads, each with
+    // its own BFS marks; the first failing cell (in cell order) is reported
+    struct Work {
+        std::vector<Cand> layer, next, chosen;
+        std::vector<int32_t> mark;   // last cell whose BFS visited this cell
+        int64_t fail = -1;
+    };
+    auto one = [&](int64_t i, Work& w) -> bool {
+        std::vector<Cand>& layer = w.layer;
+        std::vector<Cand>& next = w.next;
+        std::vector<Cand>& chosen = w.chosen;
+        std::vector<int32_t>& mark = w.mark;
         const double* xi = &m->vmean[3 * i];
         double h2 = d == 2 ? m->vol[i] : std::cbrt(m->vol[i]) * std::cbrt(m->vol[i]);
         layer.clear();
@@ -123,11 +134,7 @@ int build_stencils(hfv_scheme* s)
             chosen.insert(chosen.end(), next.begin(), next.begin() + take);
             layer.swap(next);
         }
-        if ((int)chosen.size() < M) {
-            set_error("hfv_scheme_create: cell " + std::to_string(i) + " reaches fewer than M = " + std::to_string(M) +
-                      " cells within 16 face layers");
-            return HFV_ERR_STENCIL;
-        }
+        if ((int)chosen.size() < M) return false;
         std::sort(chosen.begin(), chosen.end());
         int first_layer = 0;
         for (int a = 0; a < M; ++a) first_layer += chosen[a].layer == 1;
@@ -157,7 +164,31 @@ int build_stencils(hfv_scheme* s)
             for (int a = cnt; a < Md; ++a) out[a] = 0;
             s->nd[i * kMaxFaces + f] = (uint8_t)cnt;
         }
+        return true;
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)(hw ? hw : 1), 16, nc / 4096}));
+    std::vector<Work> work(nt);
+    auto range = [&](int t) {
+        Work& w = work[t];
+        w.mark.assign(nc, -1);
+        const int64_t lo = nc * t / nt, hi = nc * (t + 1) / nt;
+        for (int64_t i = lo; i < hi; ++i)
+            if (!one(i, w)) { w.fail = i; return; }
+    };
+    if (nt == 1) {
+        range(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t) th.emplace_back(range, t);
+        for (auto& x : th) x.join();
     }
+    for (const Work& w : work)
+        if (w.fail >= 0) {
+            set_error("hfv_scheme_create: cell " + std::to_string(w.fail) + " reaches fewer than M = " +
+                      std::to_string(M) + " cells within 16 face layers");
+            return HFV_ERR_STENCIL;
+        }
     return HFV_OK;
 }
 

@@ -96,6 +96,7 @@ int build_operators(hfv_scheme* s, void* stream)
     const bool f32 = s->p.precision == HFV_FP32;
     const size_t b = f32 ? 4 : 8;
     s->nblocks = (int)((nc + 255) / 256);
+    s->nseg = (int)m->seg_off.size() - 1;
 
     // ---- arena layout ----
     size_t off = 0;
@@ -112,7 +113,8 @@ int build_operators(hfv_scheme* s, void* stream)
            o_bcount = take(2 * (size_t)s->nblocks * 4), o_status = take(64);
     size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b), o_UB = take(nc * (nv == 4 ? 4 : 8) * b),
            o_areaT = take(nc * 6 * b),
-           o_dt = take(64), o_Uio = take(nv * nc * 8);
+           o_dt = take(std::max<int64_t>(64, 8 * (int64_t)s->nseg)), o_Uio = take(nv * nc * 8),
+           o_seg = take(s->nseg > 1 ? nc * 4 : 0);
     s->arena_bytes = off;
     SETUP_CHECK(cudaMalloc(&s->arena, off));
     char* A = (char*)s->arena;
@@ -128,6 +130,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.counts = (int32_t*)(A + o_counts); a.bcount = (int32_t*)(A + o_bcount); a.status = (int*)(A + o_status);
     a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA; a.UB = A + o_UB; a.areaT = A + o_areaT;
     a.dt = (double*)(A + o_dt);
+    a.seg = s->nseg > 1 ? (int32_t*)(A + o_seg) : nullptr;
     a.Uio = (double*)(A + o_Uio);
     SETUP_CHECK(cudaMemsetAsync(s->arena, 0, off, st));
 
@@ -177,6 +180,13 @@ int build_operators(hfv_scheme* s, void* stream)
     SETUP_CHECK(cudaMemcpyAsync(a.nfc, nfc.data(), nc, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.qoff, s->qoff.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.loff, s->loff.data(), (ncp + 1) * 8, cudaMemcpyHostToDevice, st));
+    std::vector<int32_t> seg;
+    if (a.seg) {
+        seg.resize(nc);
+        for (int k = 0; k < s->nseg; ++k)
+            for (int64_t c = m->seg_off[k]; c < m->seg_off[k + 1]; ++c) seg[c] = k;
+        SETUP_CHECK(cudaMemcpyAsync(a.seg, seg.data(), nc * 4, cudaMemcpyHostToDevice, st));
+    }
     SETUP_CHECK(cudaMemcpyAsync(a.dir, s->dir.data(), nc * 6 * Md, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.vol, m->vol.data(), nc * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(a.area, m->farea.data(), nc * 6 * 8, cudaMemcpyHostToDevice, st));

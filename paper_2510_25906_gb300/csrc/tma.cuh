@@ -1,14 +1,23 @@
 // tma.cuh -- Blackwell bulk-copy (TMA engine) and mbarrier helpers, inline PTX.
 //
-// Every wait is bounded: after kWaitLimit unsuccessful polls the caller gets
-// `false` and must record an error instead of spinning on.
+// Every wait is bounded: after kWaitNs nanoseconds of unsuccessful polls
+// (global timer) the caller gets `false` and must record an error instead of
+// spinning on.
 #pragma once
 
 #include <cstdint>
 
 namespace hfv {
 
-constexpr uint32_t kWaitLimit = 1u << 24;  // polls of try_wait (each suspends ~ up to its time hint)
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
+constexpr uint32_t kSuspendNs = 20000;         // try_wait suspends the thread up to this long
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -38,22 +47,27 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-// wait for the phase with the given parity to complete; false on timeout
+// wait for the phase with the given parity to complete; false on timeout.
+// A waiting thread is suspended inside try_wait (woken when the phase
+// completes), so a stalled warp takes no issue slots.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint64_t t0 = 0;
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
+        const uint64_t t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > kWaitNs) return false;
     }
-    return false;
 }
 
 // bulk global -> shared copy completing `bytes` transactions on `bar`

@@ -64,6 +64,8 @@ def load():
     sig = {
         "hfv_default_params": [vp],
         "hfv_mesh_create": [vp, vp],
+        "hfv_mesh_create_batch": [vp, C.c_int, vp],
+        "hfv_mesh_segments": [vp, vp, vp],
         "hfv_mesh_info": [vp, vp, vp, vp],
         "hfv_mesh_connectivity": [vp, vp, vp],
         "hfv_scheme_create": [vp, vp, vp, vp],
@@ -72,6 +74,7 @@ def load():
         "hfv_residual": [vp, vp, vp, vp, vp, vp],
         "hfv_compute_dt": [vp, vp, d, vp, vp],
         "hfv_step": [vp, vp, d, d, vp, vp],
+        "hfv_step_many": [vp, vp, C.c_int, d, d, vp],
         "hfv_advance_host": [vp, vp, C.c_int, d, d, vp],
         "hfv_get_queues": [vp, vp, vp],
         "hfv_status": [vp, vp, C.c_int],
@@ -121,24 +124,46 @@ def default_params(**kw) -> hfv_scheme_params:
     return p
 
 
-class Mesh:
-    """hfv_mesh_create / hfv_mesh_connectivity over an ``inputs.Mesh``."""
+def _desc(mesh):
+    keep = [np.ascontiguousarray(mesh.nodes, np.float64), np.ascontiguousarray(mesh.cell_type, np.uint8),
+            np.ascontiguousarray(mesh.cell_ptr, np.int64), np.ascontiguousarray(mesh.cell_idx, np.int32),
+            np.ascontiguousarray(mesh.period, np.float64)]
+    return hfv_mesh_desc(mesh.dim, mesh.n_nodes, mesh.n_cells, *[k.ctypes.data for k in keep]), keep
 
-    def __init__(self, mesh):
+
+class Mesh:
+    """hfv_mesh_create / hfv_mesh_connectivity over an ``inputs.Mesh``;
+    ``Mesh.batch`` = hfv_mesh_create_batch over a list of them."""
+
+    def __init__(self, mesh, _batch=None):
         lib = load()
         self.src = mesh
-        self.dim = mesh.dim
-        self.n_cells = mesh.n_cells
-        keep = [np.ascontiguousarray(mesh.nodes, np.float64), np.ascontiguousarray(mesh.cell_type, np.uint8),
-                np.ascontiguousarray(mesh.cell_ptr, np.int64), np.ascontiguousarray(mesh.cell_idx, np.int32),
-                np.ascontiguousarray(mesh.period, np.float64)]
-        desc = hfv_mesh_desc(mesh.dim, mesh.n_nodes, mesh.n_cells, *[k.ctypes.data for k in keep])
         h = C.c_void_p()
-        _check(lib.hfv_mesh_create(C.byref(desc), C.byref(h)))
+        if _batch is None:
+            desc, keep = _desc(mesh)
+            _check(lib.hfv_mesh_create(C.byref(desc), C.byref(h)))
+        else:
+            pairs = [_desc(m) for m in _batch]
+            arr = (hfv_mesh_desc * len(pairs))(*[d for d, _ in pairs])
+            _check(lib.hfv_mesh_create_batch(arr, len(pairs), C.byref(h)))
         self.h = h
-        nf = C.c_int64()
-        lib.hfv_mesh_info(self.h, None, C.byref(nf), None)
-        self.n_faces = nf.value
+        nc, nf, dim = C.c_int64(), C.c_int64(), C.c_int()
+        lib.hfv_mesh_info(self.h, C.byref(nc), C.byref(nf), C.byref(dim))
+        self.n_cells, self.n_faces, self.dim = nc.value, nf.value, dim.value
+        ns = C.c_int()
+        _check(lib.hfv_mesh_segments(self.h, C.byref(ns), None))
+        self.segments = np.zeros(ns.value + 1, np.int64)
+        _check(lib.hfv_mesh_segments(self.h, C.byref(ns), self.segments.ctypes.data))
+
+    @classmethod
+    def batch(cls, meshes):
+        """Independent open problems as one mesh, problem k = cells
+        segments[k] .. segments[k+1] - 1."""
+        return cls(None, _batch=list(meshes))
+
+    @property
+    def n_segments(self) -> int:
+        return self.segments.size - 1
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -215,17 +240,20 @@ class Scheme:
         import torch
         u = self._state(U, torch.float64)
         if dt_out is None:
-            dt_out = torch.empty(1, dtype=torch.float64, device=U.device)
+            dt_out = torch.empty(self.mesh.n_segments, dtype=torch.float64, device=U.device)
         _check(load().hfv_compute_dt(self.h, u, cfl, C.c_void_p(dt_out.data_ptr()), _stream(stream)))
         return dt_out
 
     def step(self, U, cfl: float = 0.5, dt: float = -1.0, want_dt: bool = False, stream=None):
-        """hfv_step on an FP64 state in place; returns dt when want_dt."""
+        """hfv_step on an FP64 state in place; returns dt when want_dt (a
+        float, or one per problem of a batched mesh)."""
         import torch
         u = self._state(U, torch.float64)
-        out = C.c_double(0.0)
-        _check(load().hfv_step(self.h, u, cfl, dt, C.byref(out) if want_dt else None, _stream(stream)))
-        return out.value if want_dt else None
+        out = np.zeros(self.mesh.n_segments)
+        _check(load().hfv_step(self.h, u, cfl, dt, out.ctypes.data if want_dt else None, _stream(stream)))
+        if not want_dt:
+            return None
+        return float(out[0]) if out.size == 1 else out
 
     def advance_host(self, U: np.ndarray, n_steps: int, cfl: float = 0.5, dt: float = -1.0, stream=None):
         """hfv_advance_host: U (host FP64 [nv, n]) advanced in place."""
@@ -255,6 +283,17 @@ class Scheme:
         if rc not in (HFV_OK, HFV_ERR_NONPHYSICAL):
             _check(rc)
         return flags.value
+
+
+def step_many(schemes, states, cfl: float = 0.5, dt: float = -1.0, stream=None):
+    """hfv_step_many: one step of every (scheme, FP64 state) pair, the schemes
+    on their own streams forked from and joined into ``stream``."""
+    import torch
+    if len(schemes) != len(states) or not schemes:
+        raise ValueError("one state per scheme")
+    hs = (C.c_void_p * len(schemes))(*[s.h.value for s in schemes])
+    us = (C.c_void_p * len(states))(*[s._state(U, torch.float64).value for s, U in zip(schemes, states)])
+    _check(load().hfv_step_many(hs, us, len(schemes), cfl, dt, _stream(stream)))
 
 
 def launch_count() -> int:

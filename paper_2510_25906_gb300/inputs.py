@@ -109,15 +109,14 @@ def structured_tri_mesh(n: int, periodic: bool = True, jitter: float = 0.2, seed
     """n x n quads, each cut along its (i,j)->(i+1,j+1) diagonal: 2 n^2 triangles."""
     rng = np.random.default_rng(seed)
     nodes = _grid_nodes_2d(n, lx, ly, jitter, rng)
-    nid = lambda i, j: j * (n + 1) + i
-    conn = []
-    for j in range(n):
-        for i in range(n):
-            a, b, c, d = nid(i, j), nid(i + 1, j), nid(i + 1, j + 1), nid(i, j + 1)
-            conn.append((a, b, c))
-            conn.append((a, c, d))
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    a = (j * (n + 1) + i).ravel()
+    b, c, d = a + 1, a + n + 2, a + n + 1
+    conn = np.stack([np.stack([a, b, c], 1), np.stack([a, c, d], 1)], 1).reshape(-1, 3).astype(np.int32)
     period = [lx, ly] if periodic else [0.0, 0.0]
-    return _finish(2, nodes, [TRI] * len(conn), conn, period, f"tri{n}", n=n, seed=seed)
+    ptr = np.arange(0, 3 * conn.shape[0] + 1, 3, dtype=np.int64)
+    return Mesh(2, np.ascontiguousarray(nodes, dtype=np.float64), np.full(conn.shape[0], TRI, np.uint8), ptr,
+                conn.ravel(), np.asarray(period, dtype=np.float64), f"tri{n}", dict(n=n, seed=seed))
 
 
 def structured_quad_mesh(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0, periodic=(False, False),
@@ -312,6 +311,56 @@ def turbulence_state(mesh: Mesh, seed: int = 3, k0: float = 4.0, mach_t: float =
 # ---------------------------------------------------------------------------
 # Named workloads (sizes as the paper's workloads; small variants for tests)
 # ---------------------------------------------------------------------------
+
+SOD_STATES = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1))   # (rho, u, v, p) left / right of the membrane
+
+
+def batched_problems(count: int = 256, seed: int = 5, min_cells: int = 1000, max_cells: int = 200000,
+                     orders=(2, 3, 4, 5)):
+    """Independent open 2D problems of uneven size: jittered triangle meshes of
+    the unit square with 2 n^2 cells, n^2 log-uniform between min_cells / 2
+    and max_cells / 2; the order drawn uniformly from ``orders``; the state
+    either a smooth density wave  rho = 1 + 0.2 sin(2 pi k (x cos a + y sin a)),
+    (u, v) = 0.5 (cos a, sin a), p = 1, or a Sod shock tube whose membrane
+    passes through the centre with normal (cos a, sin a); the angle a uniform.
+    Wave averages by a 4 x 4 collapsed Gauss rule, Sod states at the vertex
+    mean.  Returns a list of dicts with keys mesh, U, order, kind, angle."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        cells = math.exp(rng.uniform(math.log(min_cells), math.log(max_cells)))
+        n = max(4, int(round(math.sqrt(cells / 2.0))))
+        order = int(rng.choice(orders))
+        ang = float(rng.uniform(0.0, 2.0 * math.pi))
+        sine = bool(rng.random() < 0.5)
+        m = structured_tri_mesh(n, periodic=False, jitter=0.2, seed=seed * 100003 + k)
+        ca, sa = math.cos(ang), math.sin(ang)
+        if sine:
+            kw = int(rng.integers(1, 4))
+            rb = cell_average_2d(m, lambda x, y: 1.0 + 0.2 * np.sin(2.0 * np.pi * kw * (x * ca + y * sa)), npts=4)
+            U = np.stack([rb, 0.5 * ca * rb, 0.5 * sa * rb, 1.0 / (GAMMA - 1.0) + 0.125 * rb])
+        else:
+            c = m.vertex_means()
+            left = (c[:, 0] - 0.5) * ca + (c[:, 1] - 0.5) * sa < 0.0
+            prim = np.where(left[:, None], np.array(SOD_STATES[0]), np.array(SOD_STATES[1]))
+            U = conserved_2d(prim[:, 0], prim[:, 1], prim[:, 2], prim[:, 3])
+        out.append({"mesh": m, "U": np.ascontiguousarray(U), "order": order, "kind": "sine" if sine else "sod",
+                    "angle": ang})
+    return out
+
+
+def concat_meshes(meshes) -> Mesh:
+    """Disjoint union of open meshes (node and cell ids offset per mesh), in
+    order: the layout a batch of problems has as one mesh."""
+    nodes = np.concatenate([m.nodes for m in meshes])
+    types = np.concatenate([m.cell_type for m in meshes])
+    noff = np.cumsum([0] + [m.n_nodes for m in meshes])
+    idx = np.concatenate([m.cell_idx.astype(np.int64) + noff[k] for k, m in enumerate(meshes)]).astype(np.int32)
+    counts = np.concatenate([np.diff(m.cell_ptr) for m in meshes])
+    ptr = np.zeros(types.size + 1, np.int64)
+    np.cumsum(counts, out=ptr[1:])
+    return Mesh(meshes[0].dim, nodes, types, ptr, idx, np.zeros(meshes[0].dim), "batch", {"count": len(meshes)})
+
 
 def workload(name: str, scale: int | None = None):
     """Return (mesh, U0, defaults) for a named workload.
