@@ -352,6 +352,12 @@ def batched_variants(H, I, torch, dev, args):
         schemes.append(H.Scheme(gm, order=order, flux="hllc", precision="fp32"))
         states.append(torch.tensor(np.concatenate([P[k]["U"] for k in ks], axis=1), device=dev))
     t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    shapes = {}
+    if args.batched_autotune:
+        for (order, _), g, U in zip(sorted(groups.items()), schemes, states):
+            shapes[int(order)] = g.autotune(U.float().contiguous(), reps=3)
+    t_tune = time.perf_counter() - t0
     ms_b, l_b = timed(lambda s: H.step_many(schemes, states, cfl=0.5, stream=s), args.batched_steps, 3)
     hist = np.zeros(4, np.int64)
     for g, U in zip(schemes, states):
@@ -383,7 +389,8 @@ def batched_variants(H, I, torch, dev, args):
                         "launches_per_step": l_b, "form": "one batched mesh per order, hfv_step_many, one graph"},
             "per_problem": {"value": 3.0 * cells * K / (ms_1 * 1e-3), "ms_per_step": ms_1 / K,
                             "launches_per_step": l_1, "form": "one scheme per problem, hfv_step each, one graph"},
-            "speedup": ms_1 / ms_b, "setup_s": {"inputs": t_gen, "batched": t_setup, "per_problem": t_setup1}}
+            "speedup": ms_1 / ms_b, "autotuned_shapes": shapes,
+            "setup_s": {"inputs": t_gen, "batched": t_setup, "autotune": t_tune, "per_problem": t_setup1}}
 
 
 def main():
@@ -405,6 +412,7 @@ def main():
     ap.add_argument("--turbulence-steps", type=int, default=10)
     ap.add_argument("--batched", type=int, default=256, help="problems of the batched workload (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--batched-autotune", type=int, default=1)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _env()

@@ -208,6 +208,17 @@ HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* d
  * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG. */
 HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream);
 
+/* Autotuner of the residual's launch shape for this scheme and state: the
+ * persistent candidate kernel's resident CTAs per SM, and the CWENOZ / MUSCL
+ * kernel's blocks per SM and the share of them given to the CWENOZ queue.
+ * Coordinate descent over candidate values, each timed with CUDA events over
+ * `reps` residuals of U (device, the scheme's precision, [nv][n_cells]) on
+ * `stream`; the fastest shape is kept for every later call on the scheme.
+ * shape (host, 3 ints, may be NULL) receives it.  The results of the
+ * residual do not depend on the shape.  sync.  Errors: HFV_ERR_ARG,
+ * HFV_ERR_CUDA. */
+HFV_API int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, int* shape);
+
 /* hfv_step on several schemes at once, each on its own stream forked from
  * `stream` and joined back into it (so their kernels may run concurrently,
  * and a stream capture records one graph with one branch per scheme): the

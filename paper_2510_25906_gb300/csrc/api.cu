@@ -192,6 +192,70 @@ extern "C" int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double*
     return HFV_OK;
 }
 
+extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, int* shape)
+{
+    if (!s || !U || reps <= 0) { set_error("hfv_autotune: bad argument"); return HFV_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    API_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        set_error("hfv_autotune: event creation failed");
+        return HFV_ERR_CUDA;
+    }
+    int rc = HFV_OK;
+    // time `reps` residuals of U with the scheme's current shape (after one untimed)
+    auto measure = [&](float* ms) -> int {
+        int r = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);
+        if (r != HFV_OK) return r;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return HFV_ERR_CUDA;
+        for (int k = 0; k < reps && r == HFV_OK; ++k) r = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);
+        if (r != HFV_OK) return r;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+            return HFV_ERR_CUDA;
+        return HFV_OK;
+    };
+    // coordinate descent over the three knobs, each from its current value
+    auto tune = [&](int* knob, const int* cand, int n) -> int {
+        int best = *knob;
+        float tbest = 0.0f;
+        int r = measure(&tbest);
+        for (int i = 0; i < n && r == HFV_OK; ++i) {
+            if (cand[i] == best) continue;
+            const int keep = *knob;
+            *knob = cand[i];
+            float t = 0.0f;
+            r = measure(&t);
+            if (r == HFV_OK && t < tbest) { tbest = t; best = cand[i]; }
+            else *knob = keep;
+        }
+        *knob = best;
+        return r;
+    };
+    if (rc == HFV_OK) rc = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);   // fills sms and the occupancy bound
+    if (rc == HFV_OK) API_CUDA(cudaStreamSynchronize(st));
+    if (rc == HFV_OK) {
+        int per[8], n = 0;
+        for (int k = 1; k <= s->linear_per_sm_max && n < 8; ++k) per[n++] = k;
+        if (s->tune_linear_per_sm <= 0) s->tune_linear_per_sm = s->linear_per_sm_max;
+        rc = tune(&s->tune_linear_per_sm, per, n);
+    }
+    static const int nl[] = {2, 4, 8, 16, 32};
+    static const int pct[] = {50, 67, 75, 85, 95};
+    if (rc == HFV_OK) rc = tune(&s->tune_nl_per_sm, nl, 5);
+    if (rc == HFV_OK) rc = tune(&s->tune_nl_cweno_pct, pct, 5);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != HFV_OK) return rc;
+    if (shape) {
+        shape[0] = s->tune_linear_per_sm;
+        shape[1] = s->tune_nl_per_sm;
+        shape[2] = s->tune_nl_cweno_pct;
+    }
+    return HFV_OK;
+}
+
 extern "C" int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n, double cfl, double dt, void* stream)
 {
     if (!schemes || !U || n <= 0 || (!(dt > 0) && !(cfl > 0))) {

@@ -124,6 +124,13 @@ struct hfv_scheme {
     std::vector<int64_t> loff;      // [nc_pad+1]
     int nblocks = 0;
     int nseg = 1;                   // independent problems in the mesh
+    // launch shape of the residual's kernels (hfv_autotune): resident CTAs per
+    // SM of the candidate kernel (0 = as many as fit), blocks per SM of the
+    // CWENOZ / MUSCL kernel and the percentage of them on the CWENOZ queue
+    int tune_linear_per_sm = 0;
+    int tune_nl_per_sm = 16;
+    int tune_nl_cweno_pct = 75;
+    int sms = 152, linear_per_sm_max = 1;   // filled at the first residual
     // host copies kept for introspection
     std::vector<int32_t> sten;      // [nc][M]
     std::vector<int8_t> sshift;     // [nc][M][3]

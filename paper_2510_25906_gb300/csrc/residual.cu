@@ -1130,17 +1130,21 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     }
     {
         using S1 = K1Shape<C, T>;
-        static int grid1 = 0;   // per instantiation: SMs x resident CTAs
-        if (!grid1) {
+        static int sms = 0, per_max = 0;   // per instantiation: SMs and resident CTAs per SM
+        if (!sms) {
             HFV_CUDA_CHECK(cudaFuncSetAttribute(k_linear<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1::SMEM));
-            int dev = 0, sms = 0, per = 0;
+            int dev = 0, n = 0, per = 0;
             HFV_CUDA_CHECK(cudaGetDevice(&dev));
-            HFV_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            HFV_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
             HFV_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_linear<C, T>, S1::THREADS, S1::SMEM));
-            grid1 = sms * (per > 0 ? per : 1);
+            per_max = per > 0 ? per : 1;
+            sms = n;
         }
+        s->sms = sms;
+        s->linear_per_sm_max = per_max;
+        const int per = s->tune_linear_per_sm > 0 ? std::min(s->tune_linear_per_sm, per_max) : per_max;
         const int64_t ntiles = (nc + S1::NG - 1) / S1::NG;
-        const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, grid1);
+        const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per);
         Launch l(s, KID_LINEAR, st);
         k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p);
     }
@@ -1152,9 +1156,11 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue, s->a.counts, fold);
     }
     {
-        // CWENOZ cells cost several times a MUSCL cell: 3/4 of the blocks
-        const unsigned gq = (unsigned)std::min<int64_t>((nc + CPB - 1) / CPB, 152 * 16);
-        const unsigned split = gq - gq / 4;
+        // CWENOZ cells cost several times a MUSCL cell: by default 3/4 of the
+        // blocks take the CWENOZ queue
+        const unsigned gq = (unsigned)std::max<int64_t>(
+            2, std::min<int64_t>((nc + CPB - 1) / CPB, (int64_t)s->sms * s->tune_nl_per_sm));
+        const unsigned split = std::min<unsigned>(gq - 1, std::max<unsigned>(1, gq * s->tune_nl_cweno_pct / 100));
         Launch l(s, KID_CWENO, st);
         k_nonlinear<C, T><<<gq, 128, 0, st>>>(p, split);
     }

@@ -75,6 +75,7 @@ def load():
         "hfv_compute_dt": [vp, vp, d, vp, vp],
         "hfv_step": [vp, vp, d, d, vp, vp],
         "hfv_step_many": [vp, vp, C.c_int, d, d, vp],
+        "hfv_autotune": [vp, vp, C.c_int, vp, vp],
         "hfv_advance_host": [vp, vp, C.c_int, d, d, vp],
         "hfv_get_queues": [vp, vp, vp],
         "hfv_status": [vp, vp, C.c_int],
@@ -243,6 +244,14 @@ class Scheme:
             dt_out = torch.empty(self.mesh.n_segments, dtype=torch.float64, device=U.device)
         _check(load().hfv_compute_dt(self.h, u, cfl, C.c_void_p(dt_out.data_ptr()), _stream(stream)))
         return dt_out
+
+    def autotune(self, U, reps: int = 5, stream=None):
+        """hfv_autotune on a state in the scheme's precision; returns the shape
+        (candidate-kernel CTAs per SM, nonlinear blocks per SM, CWENOZ share %)."""
+        u = self._state(U, self.dtype)
+        shape = (C.c_int * 3)()
+        _check(load().hfv_autotune(self.h, u, reps, _stream(stream), shape))
+        return tuple(shape)
 
     def step(self, U, cfl: float = 0.5, dt: float = -1.0, want_dt: bool = False, stream=None):
         """hfv_step on an FP64 state in place; returns dt when want_dt (a

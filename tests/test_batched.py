@@ -188,3 +188,18 @@ def test_batched_against_oracle(H):
     agree = (cls.cpu().numpy() == fin).mean()
     assert agree >= 0.999, agree
     assert len(np.unique(fin)) >= 2
+
+
+@pytest.mark.gpu
+def test_autotune_keeps_results(H):
+    """hfv_autotune changes launch shapes only: the residual is bit-identical
+    before and after, and the chosen shape is within the candidate ranges."""
+    P = I.batched_problems(8, seed=51, min_cells=2000, max_cells=20000, orders=(3,))
+    gm = H.Mesh.batch([p["mesh"] for p in P])
+    g = H.Scheme(gm, order=3, flux="hllc", precision="fp32")
+    U = torch.tensor(np.concatenate([p["U"] for p in P], axis=1), dtype=torch.float32, device="cuda")
+    R0 = g.residual(U).cpu().numpy()
+    shape = g.autotune(U, reps=2)
+    assert 1 <= shape[0] <= 8 and shape[1] in (2, 4, 8, 16, 32) and shape[2] in (50, 67, 75, 85, 95), shape
+    R1 = g.residual(U).cpu().numpy()
+    assert np.array_equal(R0, R1)
