@@ -393,6 +393,54 @@ def batched_variants(H, I, torch, dev, args):
             "setup_s": {"inputs": t_gen, "batched": t_setup, "autotune": t_tune, "per_problem": t_setup1}}
 
 
+def adjoint_variants(H, I, torch, dev, args):
+    """The adjoint workload: dJ/dU0 of J = sum |V| rho^2 after K checkpointed
+    SSP-RK3 steps (FP64, order 3 hybrid, HLLC, classes frozen along the
+    forward trajectory) on an open unit cube of n^3 jittered hexahedra with a
+    Gaussian density pulse ahead of a planar Mach 2 shock.  Reports the time
+    of the forward sweep and of the backward sweep (stage recomputation and
+    three residual VJPs per step) and the VJP rate."""
+    from paper_2510_25906_gb300 import adjoint as A
+    n = args.adjoint_n
+    m, U0 = I.adjoint_problem(n)
+    gm = H.Mesh(m)
+    g = H.Scheme(gm, order=3, flux="hllc", precision="fp64")
+    U = torch.tensor(U0, device=dev)
+    J = A.density_square_integral(gm.volumes())
+    # one warm call of each kernel family
+    A.rk3_gradient(g, U, 1, J, cfl=0.5)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    Jv, dJ, UN, dts = A.rk3_gradient(g, U, args.adjoint_steps, J, cfl=0.5)
+    torch.cuda.synchronize(dev)
+    total = time.perf_counter() - t0
+    # the backward sweep alone: forward once more, then time a VJP burst
+    cls = torch.empty(m.n_cells, dtype=torch.uint8, device=dev)
+    g.residual(U, class_out=cls)
+    lam = torch.ones_like(U)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        g.residual_vjp(U, cls, lam)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    vjp_ms = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        g.residual(U, forced=cls)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    res_ms = e0.elapsed_time(e1) / reps
+    hist = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+    return {"workload": f"open unit cube, {n}^3 jittered hexahedra ({m.n_cells} cells), Gaussian density pulse ahead "
+                        f"of a planar Mach 2 shock, order 3 hybrid, HLLC, FP64, classes frozen",
+            "cells": int(m.n_cells), "steps": args.adjoint_steps, "objective": "sum |V| rho^2 after the steps",
+            "J": Jv, "grad_norm": float(dJ.norm().item()), "classes_at_start": hist,
+            "forward_plus_backward_s": total, "vjp_ms": vjp_ms, "residual_ms": res_ms,
+            "vjp_cells_per_s": m.n_cells / (vjp_ms * 1e-3), "checkpoint_bytes": int(args.adjoint_steps * U.numel() * 8)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,6 +461,9 @@ def main():
     ap.add_argument("--batched", type=int, default=256, help="problems of the batched workload (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-autotune", type=int, default=1)
+    ap.add_argument("--adjoint", type=int, default=1, help="also time the checkpointed adjoint (rank 0)")
+    ap.add_argument("--adjoint-n", type=int, default=100)
+    ap.add_argument("--adjoint-steps", type=int, default=50)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = _env()
@@ -500,6 +551,9 @@ def main():
     batched = None
     if args.batched and rank == 0:
         batched = batched_variants(H, I, torch, dev, args)
+    adjoint = None
+    if args.adjoint and rank == 0:
+        adjoint = adjoint_variants(H, I, torch, dev, args)
 
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -514,7 +568,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if g.fp32 else "f64", "data": "synthetic",
                 "config": _config(args, mesh), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "classes_final": hist,
-                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence, "batched": batched}
+                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -142,6 +142,10 @@ HFV_API int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, hfv_
  * and the total.  sync. */
 HFV_API int hfv_mesh_segments(const hfv_mesh* mesh, int* n_segments, int64_t* cell_offsets);
 
+/* Cell measures |V_c| (host output, caller-owned, n_cells doubles): areas
+ * in 2D, volumes in 3D, as the scheme uses them (Sec. 2).  sync. */
+HFV_API int hfv_mesh_volumes(const hfv_mesh* mesh, double* vol);
+
 /* Sizes of a mesh.  Any output pointer may be NULL. */
 HFV_API int hfv_mesh_info(const hfv_mesh* mesh, int64_t* n_cells, int64_t* n_faces, int* dim);
 
@@ -207,6 +211,26 @@ HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* d
  *       makes the call sync.
  * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG. */
 HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream);
+
+/* Vector-Jacobian product of the residual: g = lam^T dR/dU at U, with the
+ * cell classes frozen (the detector, tagging and Harten decisions of
+ * Sec. 2.5) and every branch inside the reconstructions and the Riemann
+ * solver (limiter bounds and minimum, |x|, HLLC wave pattern) taken as in
+ * the evaluation at U; the derivative of that branch.
+ *   U    device FP64 [nv][n_cells]
+ *   cls  device uint8 [n_cells], classes as hfv_residual's class_out (a
+ *        forced LINEAR or CWENOZ cell that breaks the Harten bound at U falls
+ *        back to FIRST as in hfv_residual)
+ *   lam  device FP64 [nv][n_cells], the adjoint of R
+ *   g    device FP64 [nv][n_cells], output
+ * FP64 schemes only.  The first call allocates the adjoint's scratch
+ * (face-point adjoints, per-stencil-entry contributions and the inverse
+ * stencil map, about (Q_max + M + 1) nv 8 + 12 M bytes per cell), kept until
+ * hfv_scheme_destroy.  The paper states no adjoint; this is the
+ * differentiation of its residual.  async.  Errors: HFV_ERR_ARG,
+ * HFV_ERR_OOM, HFV_ERR_CUDA. */
+HFV_API int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g,
+                             void* stream);
 
 /* Autotuner of the residual's launch shape for this scheme and state: the
  * persistent candidate kernel's resident CTAs per SM, and the CWENOZ / MUSCL

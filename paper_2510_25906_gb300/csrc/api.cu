@@ -77,6 +77,7 @@ extern "C" void hfv_scheme_destroy(hfv_scheme* s)
     if (s->side) cudaStreamDestroy((cudaStream_t)s->side);
     if (s->ev_fork) cudaEventDestroy((cudaEvent_t)s->ev_fork);
     if (s->ev_join) cudaEventDestroy((cudaEvent_t)s->ev_join);
+    adjoint_free(s);
     if (s->arena) cudaFree(s->arena);
     delete s;
 }
@@ -190,6 +191,14 @@ extern "C" int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double*
         API_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     }
     return HFV_OK;
+}
+
+extern "C" int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g,
+                                void* stream)
+{
+    if (!s || !U || !cls || !lam || !g) { set_error("hfv_residual_vjp: NULL argument"); return HFV_ERR_ARG; }
+    if (s->p.precision != HFV_FP64) { set_error("hfv_residual_vjp: FP64 schemes only"); return HFV_ERR_ARG; }
+    return launch_vjp(s, U, cls, lam, g, stream);
 }
 
 extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, int* shape)

@@ -113,6 +113,17 @@ struct KernelTimer {
 void note_launch();
 }  // namespace hfv
 
+// scratch of the residual's vector-Jacobian product (adjoint.cu), allocated
+// on its first use
+struct hfv_adjoint_arrays {
+    void* base = nullptr;
+    double* MU = nullptr;       // [qtot][nv] adjoint of the face-point states
+    double* A = nullptr;        // [nc][M][nv] contributions to the stencil cells
+    double* S0 = nullptr;       // [nc][nv] contributions to the cell itself
+    int64_t* inv_ptr = nullptr; // [nc+1] inverse stencil map (CSR, ascending (c, m))
+    int32_t* inv_idx = nullptr; // [nc*M] entries c * M + m
+};
+
 struct hfv_scheme {
     hfv::KernelTimer timer;
     hfv_mesh* mesh = nullptr;
@@ -145,6 +156,7 @@ struct hfv_scheme {
     void* ev_fork = nullptr;
     void* ev_join = nullptr;
     hfv_dev_arrays a{};
+    hfv_adjoint_arrays adj{};
 };
 
 namespace hfv {
@@ -153,4 +165,6 @@ int build_operators(hfv_scheme* s, void* stream);  // device FP64 setup, setup.c
 int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream);
 int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
 int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream);
+int launch_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g, void* stream);
+void adjoint_free(hfv_scheme* s);
 }  // namespace hfv

@@ -28,6 +28,12 @@ struct Cfg {
     static constexpr int NOI = N * (N + 1) / 2;
 };
 
+// lanes of the group that owns one cell: the face points rounded up to 8, 16 or 32
+template <int Q>
+struct GroupSize {
+    static constexpr int value = Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
+};
+
 enum : uint8_t { CLS_LIN = 0, CLS_CW = 1, CLS_MU = 2, CLS_FIRST = 3, HARTEN_FAIL = 0x80 };
 
 template <class T>

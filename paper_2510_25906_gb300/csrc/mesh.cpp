@@ -395,6 +395,13 @@ extern "C" int hfv_mesh_segments(const hfv_mesh* m, int* n_segments, int64_t* ce
     return HFV_OK;
 }
 
+extern "C" int hfv_mesh_volumes(const hfv_mesh* m, double* vol)
+{
+    if (!m || !vol) { set_error("hfv_mesh_volumes: NULL argument"); return HFV_ERR_ARG; }
+    std::memcpy(vol, m->vol.data(), m->vol.size() * sizeof(double));
+    return HFV_OK;
+}
+
 extern "C" int hfv_mesh_info(const hfv_mesh* m, int64_t* n_cells, int64_t* n_faces, int* dim)
 {
     if (!m) { set_error("hfv_mesh_info: NULL mesh"); return HFV_ERR_ARG; }

@@ -16,17 +16,18 @@ namespace hfv {
 
 enum { kRusanov = 0, kHLLC = 1, kHLL = 2 };
 
+// generic forms (used by the dual numbers of the adjoint); FP32 and FP64 below
 template <class T>
-HDI T tsqrt(T x);
+HDI T tsqrt(T x) { return sqrt(x); }
 template <>
-HDI float tsqrt<float>(float x) { return sqrtf(x); }
+HDI float tsqrt<float>(float x) { return ::sqrtf(x); }
 template <>
-HDI double tsqrt<double>(double x) { return sqrt(x); }
+HDI double tsqrt<double>(double x) { return ::sqrt(x); }
 
 // reciprocal and square root: IEEE in FP64; in FP32 the hardware
 // approximations (about 2 ulp), far inside the FP32 path's 1e-5 bar
 template <class T>
-HDI T trcp(T x);
+HDI T trcp(T x) { return T(1) / x; }
 template <>
 HDI double trcp<double>(double x) { return 1.0 / x; }
 template <>
@@ -39,9 +40,9 @@ HDI float trcp<float>(float x)
 #endif
 }
 template <class T>
-HDI T fsqrt(T x);
+HDI T fsqrt(T x) { return x > T(0) ? sqrt(x) : T(0); }
 template <>
-HDI double fsqrt<double>(double x) { return sqrt(x); }
+HDI double fsqrt<double>(double x) { return ::sqrt(x); }
 template <>
 HDI float fsqrt<float>(float x)
 {

@@ -84,11 +84,6 @@ struct Grp {
     __device__ __forceinline__ void sync() const { __syncwarp(mask); }
 };
 
-template <int Q>
-struct GroupSize {
-    static constexpr int value = Q <= 8 ? 8 : Q <= 16 ? 16 : 32;
-};
-
 // contiguous row of M values with the widest aligned vector loads (rows start
 // at (c * QMAX + q) * M elements: 16-byte aligned when M * sizeof(T) % 16 == 0)
 template <class T, int M>

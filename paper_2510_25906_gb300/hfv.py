@@ -76,6 +76,8 @@ def load():
         "hfv_step": [vp, vp, d, d, vp, vp],
         "hfv_step_many": [vp, vp, C.c_int, d, d, vp],
         "hfv_autotune": [vp, vp, C.c_int, vp, vp],
+        "hfv_residual_vjp": [vp, vp, vp, vp, vp, vp],
+        "hfv_mesh_volumes": [vp, vp],
         "hfv_advance_host": [vp, vp, C.c_int, d, d, vp],
         "hfv_get_queues": [vp, vp, vp],
         "hfv_status": [vp, vp, C.c_int],
@@ -155,6 +157,12 @@ class Mesh:
         _check(lib.hfv_mesh_segments(self.h, C.byref(ns), None))
         self.segments = np.zeros(ns.value + 1, np.int64)
         _check(lib.hfv_mesh_segments(self.h, C.byref(ns), self.segments.ctypes.data))
+
+    def volumes(self) -> np.ndarray:
+        """hfv_mesh_volumes: |V_c| per cell."""
+        v = np.zeros(self.n_cells)
+        _check(load().hfv_mesh_volumes(self.h, v.ctypes.data))
+        return v
 
     @classmethod
     def batch(cls, meshes):
@@ -244,6 +252,19 @@ class Scheme:
             dt_out = torch.empty(self.mesh.n_segments, dtype=torch.float64, device=U.device)
         _check(load().hfv_compute_dt(self.h, u, cfl, C.c_void_p(dt_out.data_ptr()), _stream(stream)))
         return dt_out
+
+    def residual_vjp(self, U, cls, lam, g=None, stream=None):
+        """hfv_residual_vjp: g = lam^T dR/dU at U (FP64) with the classes cls frozen."""
+        import torch
+        u = self._state(U, torch.float64)
+        l = self._state(lam, torch.float64)
+        if not (isinstance(cls, torch.Tensor) and cls.is_cuda and cls.dtype == torch.uint8 and cls.numel() == self.n_cells):
+            raise ValueError("classes must be a CUDA uint8 tensor of n_cells entries")
+        if g is None:
+            g = torch.empty_like(lam)
+        _check(load().hfv_residual_vjp(self.h, u, C.c_void_p(cls.data_ptr()), l, self._state(g, torch.float64),
+                                       _stream(stream)))
+        return g
 
     def autotune(self, U, reps: int = 5, stream=None):
         """hfv_autotune on a state in the scheme's precision; returns the shape

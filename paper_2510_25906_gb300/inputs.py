@@ -362,6 +362,35 @@ def concat_meshes(meshes) -> Mesh:
     return Mesh(meshes[0].dim, nodes, types, ptr, idx, np.zeros(meshes[0].dim), "batch", {"count": len(meshes)})
 
 
+def mach2_shock_states(gamma: float = GAMMA, mach: float = 2.0):
+    """Pre- and post-shock primitive states (rho, u, v, w, p) of a normal shock
+    of Mach number `mach` running along +x into gas at rest with rho = p = 1
+    (Rankine-Hugoniot relations)."""
+    m2 = mach * mach
+    r = (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    pr = 1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0)
+    s = mach * math.sqrt(gamma)
+    return (r, s * (1.0 - 1.0 / r), 0.0, 0.0, pr), (1.0, 0.0, 0.0, 0.0, 1.0)
+
+
+def adjoint_problem(n: int = 100, seed: int = 4, gamma: float = GAMMA):
+    """Open unit cube of n^3 jittered hexahedra (the adjoint workload's
+    stand-in for its tetrahedral mesh): a Gaussian density pulse
+    rho = 1 + 0.5 exp(-|x - (0.75, 0.5, 0.5)|^2 / (2 0.08^2)) in gas at rest
+    (p = 1) ahead of a planar Mach 2 shock at x = 0.4 moving along +x.
+    Cell values at the vertex means."""
+    m = structured_hex_mesh(n, 1.0, periodic=False, jitter=0.15, seed=seed)
+    c = m.vertex_means()
+    post, pre = mach2_shock_states(gamma)
+    behind = c[:, 0] < 0.4
+    prim = np.where(behind[:, None], np.array(post), np.array(pre))
+    r2 = ((c - np.array([0.75, 0.5, 0.5])) ** 2).sum(1)
+    prim[:, 0] = np.where(behind, prim[:, 0], 1.0 + 0.5 * np.exp(-r2 / (2 * 0.08 ** 2)))
+    rho, u, v, w, p = prim.T
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return m, np.ascontiguousarray(np.stack([rho, rho * u, rho * v, rho * w, E]))
+
+
 def workload(name: str, scale: int | None = None):
     """Return (mesh, U0, defaults) for a named workload.
 
