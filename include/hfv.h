@@ -56,7 +56,7 @@ extern "C" {
  * bottom face counter-clockwise seen from +z, v4..v7 above them */
 #define HFV_TRI 1
 #define HFV_QUAD 2
-#define HFV_TET 3 /* reserved, not supported */
+#define HFV_TET 3 /* positive volume v0 v1 v2 v3; orders 2 and 3 */
 #define HFV_HEX 4
 
 /* Riemann solvers at the face quadrature points (Sec. 2.4) */
@@ -74,6 +74,12 @@ extern "C" {
 #define HFV_FP64 0 /* operators, gathers, reconstruction and fluxes in FP64 */
 #define HFV_FP32 1 /* the same in FP32; setup and the Runge-Kutta accumulation stay FP64 */
 
+/* time integration and MUSCL limiter (hfv_scheme_params) */
+#define HFV_SSPRK3 0
+#define HFV_SSPRK54 1
+#define HFV_BARTH_JESPERSEN 0
+#define HFV_VENKATAKRISHNAN 1
+
 /* cell classes written by the pipeline (Sec. 2.5; the paper's figures call
  * them Scheme 0 / 1 / 3 / -1) */
 #define HFV_CLASS_LINEAR 0
@@ -90,7 +96,7 @@ typedef struct {
     int dim;                       /* 2 or 3 */
     int64_t n_nodes, n_cells;
     const double* node_xyz;        /* [n_nodes][dim] */
-    const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D), HFV_HEX (3D) */
+    const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D); all HFV_HEX or all HFV_TET (3D) */
     const int64_t* cell_node_ptr;  /* [n_cells + 1] CSR offsets */
     const int32_t* cell_node_idx;  /* [cell_node_ptr[n_cells]] vertex ids in local order */
     const double* period;          /* [dim] periodic length per axis, 0 = open (transmissive) */
@@ -104,7 +110,9 @@ typedef struct {
     int nad_vars;       /* detector variables: bit0 density, bit1 pressure,
                            bit2 the remaining conserved variables (default 3) */
     int precision;      /* HFV_FP64 (default) or HFV_FP32 */
-    int reserved;
+    int time_scheme;    /* hfv_step: HFV_SSPRK3 (default, three-stage SSP) or HFV_SSPRK54
+                           (the five-stage, fourth-order SSP method of Spiteri and Ruuth the
+                           paper integrates with, Sec. 2) */
     double gamma;       /* 1.4 (Sec. 2) */
     double alpha_m, beta_m, alpha_w, beta_w;  /* detector margins, eqs. marginm and marginw;
                                                  default 5e-3, 0.5, 0, 0 (Fig. NADMargin (a)) */
@@ -113,6 +121,10 @@ typedef struct {
     double cweno_eps, cweno_b;          /* 1e-3 and 4 (Sec. 2.3) */
     double harten_theta, harten_eps;    /* 0.9 and 1e-14 (eq. harten_jump_fix) */
     double stencil_factor;              /* M = stencil_factor * K(r, d); default 2 (Sec. 2.1) */
+    int limiter;        /* MUSCL limiter: HFV_BARTH_JESPERSEN (default, Sec. 2.2) or
+                           HFV_VENKATAKRISHNAN (the smooth limiter the paper runs with K = 5) */
+    int reserved;
+    double venkat_k;    /* Venkatakrishnan threshold eps^2 = (K dx)^3, dx = |V|^(1/d); default 5 */
 } hfv_scheme_params;
 
 /* Fill *p with the defaults listed above.  Never fails for non-NULL p. */
@@ -200,9 +212,12 @@ HFV_API int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* f
  * problem of the mesh, hfv_mesh_segments).  async. */
 HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
 
-/* One three-stage SSP Runge-Kutta step (Shu-Osher form) of U in place:
+/* One SSP Runge-Kutta step of U in place, Shu-Osher form.  time_scheme
+ * HFV_SSPRK3 (three stages):
  *   U1 = U + dt R(U);  U2 = 3/4 U + 1/4 (U1 + dt R(U1));
- *   U  = 1/3 U + 2/3 (U2 + dt R(U2)).
+ *   U  = 1/3 U + 2/3 (U2 + dt R(U2));
+ * HFV_SSPRK54: the five-stage, fourth-order method of Spiteri and Ruuth
+ *   u_i = sum_j alpha_ij u_j + beta_ij dt R(u_j), u_0 = U, U = u_5.
  *   U   device FP64 [nv][n_cells] (the accumulation is FP64 in both precisions;
  *       in HFV_FP32 each stage's residual is evaluated on an FP32 copy)
  *   dt  > 0: that step for every problem; <= 0: each problem's own step

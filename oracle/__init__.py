@@ -22,6 +22,7 @@ _lib = None
 
 FLUX = {"rusanov": 0, "hllc": 1, "hll": 2}
 SCHEME = {"hybrid": 0, "linear": 1, "cweno": 2, "muscl": 3}
+LIMITER = {"barth": 0, "venkatakrishnan": 1}
 LIN, CW, MU, FIRST = 0, 1, 2, 3
 
 
@@ -41,7 +42,7 @@ class Params(C.Structure):
                 ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1p", C.c_double), ("cw_eps", C.c_double),
                 ("cw_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("pad", C.c_int), ("venkat_k", C.c_double)]
 
 
 def default_params(**kw) -> dict:
@@ -50,7 +51,7 @@ def default_params(**kw) -> dict:
     Harten theta = 0.9, eps = 1e-14, deactivation (kappa dx)^n with kappa = 1, n = 1."""
     p = dict(order=3, flux="rusanov", scheme="hybrid", nad_vars=3, gamma=1.4, alpha_m=5e-3, beta_m=0.5,
              alpha_w=0.0, beta_w=0.0, kappa=1.0, n_exp=1.0, lambda1p=1e3, cw_eps=1e-3, cw_b=4.0,
-             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0)
+             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0, limiter="barth", pad=0, venkat_k=5.0)
     p.update(kw)
     return p
 
@@ -82,6 +83,7 @@ def _load():
         lib.or_stencil.argtypes = [C.c_void_p, I64, I32, I32]
         lib.or_cell_operator.argtypes = [C.c_void_p, I64, C.c_int, P]
         lib.or_cell_face_points.argtypes = [C.c_void_p, I64, P]
+        lib.or_cell_face_weights.argtypes = [C.c_void_p, I64, P]
         lib.or_cell_refmap.argtypes = [C.c_void_p, I64, P, P]
         lib.or_reconstruct.argtypes = [C.c_void_p, P, I64, C.c_int, P]
         lib.or_harten_ok.argtypes = [C.c_void_p, P, I64, P]
@@ -94,6 +96,9 @@ def _load():
         lib.or_rk3_step.argtypes = [C.c_void_p, P, D]
         lib.RHS = C.CFUNCTYPE(None, C.c_void_p, P, P)
         lib.or_rk3_generic.argtypes = [I64, P, D, lib.RHS, C.c_void_p]
+        lib.or_rk54_step.argtypes = [C.c_void_p, P, D]
+        lib.or_rk54_generic.argtypes = [I64, P, D, lib.RHS, C.c_void_p]
+        lib.or_rk54_table.argtypes = [P, P]
         lib.or_ops_built.restype = I64
         lib.or_ops_built.argtypes = [C.c_void_p]
         _lib = lib
@@ -106,6 +111,29 @@ def _p(a, ct=C.c_double):
 
 def _err(lib):
     return lib.or_last_error().decode()
+
+
+def rk54_table():
+    """The Shu-Osher coefficients (alpha, beta) [6][5] of the SSP-RK(5,4) step."""
+    lib = _load()
+    a, b = np.zeros(30), np.zeros(30)
+    lib.or_rk54_table(_p(a), _p(b))
+    return a.reshape(6, 5), b.reshape(6, 5)
+
+
+def rk54_generic(U: np.ndarray, dt: float, rhs) -> np.ndarray:
+    """One SSP-RK(5,4) step of u' = rhs(u) for a flat FP64 vector (pins)."""
+    lib = _load()
+    U = np.ascontiguousarray(U, np.float64).copy()
+    n = U.size
+
+    def cb(ctx, u, r):
+        uu = np.ctypeslib.as_array(u, shape=(n,))
+        rr = np.ctypeslib.as_array(r, shape=(n,))
+        rr[:] = rhs(uu.copy())
+    f = lib.RHS(cb)
+    lib.or_rk54_generic(n, _p(U), dt, f, None)
+    return U
 
 
 def gauss_legendre(n: int):
@@ -198,6 +226,8 @@ class Scheme:
                 v = FLUX[v] if isinstance(v, str) else v
             if k == "scheme":
                 v = SCHEME[v] if isinstance(v, str) else v
+            if k == "limiter":
+                v = LIMITER[v] if isinstance(v, str) else v
             setattr(cp, k, v)
         self._cp = cp
         self.h = self.lib.or_scheme_create(mesh.h, C.byref(cp))
@@ -207,7 +237,7 @@ class Scheme:
         self.lib.or_scheme_sizes(self.h, sz)
         self.N, self.M, self.Md, self.nq, self.nfp, self.nv = list(sz)
         self.dim = mesh.dim
-        nf_of = {1: 3, 2: 4, 4: 6}
+        nf_of = {1: 3, 2: 4, 3: 4, 4: 6}
         self.nf = np.array([nf_of[int(t)] for t in mesh.src.cell_type], np.int32) if mesh.n_cells < 300000 else None
 
     def __del__(self):
@@ -216,7 +246,7 @@ class Scheme:
             self.h = None
 
     def _nf(self, c):
-        return {1: 3, 2: 4, 4: 6}[int(self.mesh.src.cell_type[c])]
+        return {1: 3, 2: 4, 3: 4, 4: 6}[int(self.mesh.src.cell_type[c])]
 
     def Q(self, c):
         return self._nf(c) * self.nfp
@@ -241,6 +271,12 @@ class Scheme:
     def face_points(self, c: int) -> np.ndarray:
         out = np.zeros((self.Q(c), 3))
         self.lib.or_cell_face_points(self.h, c, _p(out))
+        return out
+
+    def face_weights(self, c: int) -> np.ndarray:
+        """Quadrature weight times |S| of each face point of cell c."""
+        out = np.zeros(self.Q(c))
+        self.lib.or_cell_face_weights(self.h, c, _p(out))
         return out
 
     def refmap(self, c: int):
@@ -298,6 +334,14 @@ class Scheme:
     def dt(self, U: np.ndarray, cfl: float) -> float:
         U = np.ascontiguousarray(U, np.float64)
         return float(self.lib.or_dt(self.h, _p(U), cfl))
+
+    def rk54_step(self, U: np.ndarray, dt: float) -> np.ndarray:
+        """One step of the five-stage, fourth-order SSP Runge-Kutta method of
+        Spiteri and Ruuth (the paper's integrator)."""
+        U = np.ascontiguousarray(U, np.float64).copy()
+        if self.lib.or_rk54_step(self.h, _p(U), dt) != 0:
+            raise RuntimeError("oracle step: " + _err(self.lib))
+        return U
 
     def rk3_step(self, U: np.ndarray, dt: float) -> np.ndarray:
         U = np.ascontiguousarray(U, np.float64).copy()

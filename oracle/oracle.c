@@ -66,10 +66,17 @@ static const int QUAD_F[4][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}};
 static const int HEX_F[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4},
                                 {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
 
-static int t_nverts(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_HEX ? 8 : 0; }
-static int t_nfaces(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_HEX ? 6 : 0; }
-static int t_fnv(int t) { return t == OR_HEX ? 4 : 2; }
-static int t_fv(int t, int f, int k) { return t == OR_TRI ? TRI_F[f][k] : t == OR_QUAD ? QUAD_F[f][k] : HEX_F[f][k]; }
+/* tetrahedron (positively oriented v0 v1 v2 v3) faces, each listed so that
+ * (b-a) x (c-a) points outward: the face opposite vertex k is face k */
+static const int TET_F[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+
+static int t_nverts(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_TET ? 4 : t == OR_HEX ? 8 : 0; }
+static int t_nfaces(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_TET ? 4 : t == OR_HEX ? 6 : 0; }
+static int t_fnv(int t) { return t == OR_HEX ? 4 : t == OR_TET ? 3 : 2; }
+static int t_fv(int t, int f, int k)
+{
+    return t == OR_TRI ? TRI_F[f][k] : t == OR_QUAD ? QUAD_F[f][k] : t == OR_TET ? TET_F[f][k] : HEX_F[f][k];
+}
 
 /* ------------------------------------------------------------------------ */
 /* Gauss-Legendre on [0,1] by Newton iteration on P_n                         */
@@ -136,6 +143,20 @@ static int cell_rule(int type, const double* v, int n, double* px, double* pw)
                 px[3 * np + 2] = 0.0;
                 pw[np++] = gw[i] * gw[j] * fabs(xs[0] * xt[1] - xs[1] * xt[0]);
             }
+    } else if (type == OR_TET) {
+        /* collapsed map x = p0 + s a + s t b + s t u c with a = p1-p0,
+         * b = p2-p1, c = p3-p2: |J| = s^2 t |det(a, b, c)| */
+        double a[3], b[3], cc[3];
+        for (int d = 0; d < 3; ++d) { a[d] = v[3 + d] - v[d]; b[d] = v[6 + d] - v[3 + d]; cc[d] = v[9 + d] - v[6 + d]; }
+        double det = fabs(a[0] * (b[1] * cc[2] - b[2] * cc[1]) - a[1] * (b[0] * cc[2] - b[2] * cc[0])
+                          + a[2] * (b[0] * cc[1] - b[1] * cc[0]));
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    double s1 = gx[i], t = gx[j], u = gx[k];
+                    for (int d = 0; d < 3; ++d) px[3 * np + d] = v[d] + s1 * a[d] + s1 * t * b[d] + s1 * t * u * cc[d];
+                    pw[np++] = gw[i] * gw[j] * gw[k] * s1 * s1 * t * det;
+                }
     } else if (type == OR_HEX) {
         /* trilinear map over the unit cube; vertex k sits at corner (sx,sy,sz) */
         static const int cs[8][3] = {{0, 0, 0}, {1, 0, 0}, {1, 1, 0}, {0, 1, 0},
@@ -243,6 +264,12 @@ static void face_areavec(const or_mesh* m, int64_t c, int f, double* A)
     if (t_fnv(t) == 2) {
         /* counter-clockwise cell: outward normal of edge a->b is (dy, -dx) */
         A[0] = P[1][1] - P[0][1]; A[1] = -(P[1][0] - P[0][0]); A[2] = 0.0;
+    } else if (t_fnv(t) == 3) {
+        double u[3], w[3];
+        for (int d = 0; d < 3; ++d) { u[d] = P[1][d] - P[0][d]; w[d] = P[2][d] - P[0][d]; }
+        A[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
+        A[1] = 0.5 * (u[2] * w[0] - u[0] * w[2]);
+        A[2] = 0.5 * (u[0] * w[1] - u[1] * w[0]);
     } else {
         double u[3], w[3];
         for (int d = 0; d < 3; ++d) { u[d] = P[2][d] - P[0][d]; w[d] = P[3][d] - P[1][d]; }
@@ -281,7 +308,8 @@ or_mesh* or_mesh_create(int dim, int64_t nn, int64_t nc, const double* xyz, cons
     for (int d = 0; d < 3; ++d) m->period[d] = d < dim ? period[d] : 0.0;
     for (int64_t c = 0; c < nc; ++c) {
         int t = type[c];
-        if ((dim == 2 && t != OR_TRI && t != OR_QUAD) || (dim == 3 && t != OR_HEX) ||
+        if ((dim == 2 && t != OR_TRI && t != OR_QUAD) || (dim == 3 && t != OR_HEX && t != OR_TET) ||
+            (dim == 3 && t != type[0]) ||
             cptr[c + 1] - cptr[c] != t_nverts(t)) { fail("unsupported cell type or vertex count"); or_mesh_free(m); return NULL; }
     }
 
@@ -466,6 +494,9 @@ typedef struct {
     int nad_vars;    /* bit0 density, bit1 pressure, bit2 the other conserved variables */
     double gamma, alpha_m, beta_m, alpha_w, beta_w, kappa, n_exp, lambda1p, cw_eps, cw_b, harten_theta, harten_eps;
     double stencil_factor;   /* M = stencil_factor * K(r,d) */
+    int limiter;             /* MUSCL limiter: 0 Barth-Jespersen, 1 Venkatakrishnan */
+    int pad;
+    double venkat_k;         /* Venkatakrishnan threshold eps^2 = (K dx)^3 */
 } or_params;
 
 typedef struct {
@@ -526,7 +557,11 @@ or_scheme* or_scheme_create(or_mesh* m, const or_params* p)
     s->M = (int)llround(p->stencil_factor * K_of(r, s->d));
     s->Md = 2 * K_of(1, s->d);
     if (s->M < s->N || s->M < s->Md) { free(s); fail("stencil too small"); return NULL; }
-    s->nq = (r + 2) / 2;             /* ceil((r+1)/2) Gauss points: exact to degree >= r */
+    /* Gauss points per face direction, exact to degree >= r: ceil((r+1)/2) on
+     * edges and quadrilaterals; ceil((r+2)/2) per direction of the collapsed
+     * rule on triangles (a tetrahedron's faces), exact to degree 2 nq - 2 */
+    const int tet = s->d == 3 && m->type[0] == OR_TET;
+    s->nq = tet ? (r + 3) / 2 : (r + 2) / 2;
     s->nfp = s->d == 2 ? s->nq : s->nq * s->nq;
     /* monomial exponents by total degree, then descending powers of xi, eta */
     int k = 0;
@@ -554,6 +589,18 @@ or_scheme* or_scheme_create(or_mesh* m, const or_params* p)
                 for (int dd = 0; dd < 3; ++dd) s->fqx[(g * s->nfp + a) * 3 + dd] = P[0][dd] + gx[a] * (P[1][dd] - P[0][dd]);
                 s->fqw[g * s->nfp + a] = gw[a] * m->farea[g];
             }
+        } else if (tet) {
+            /* collapsed rule on the face triangle P0 P1 P2: x = P0 + u (P1-P0)
+             * + u v (P2-P1), weight w_i w_j 2 u |S| (the map's Jacobian is
+             * 2 |S| u) */
+            for (int j = 0; j < s->nq; ++j)
+                for (int i = 0; i < s->nq; ++i) {
+                    double u = gx[i], v = gx[j];
+                    int a = i + s->nq * j;
+                    for (int dd = 0; dd < 3; ++dd)
+                        s->fqx[(g * s->nfp + a) * 3 + dd] = P[0][dd] + u * (P[1][dd] - P[0][dd]) + u * v * (P[2][dd] - P[1][dd]);
+                    s->fqw[g * s->nfp + a] = gw[i] * gw[j] * 2.0 * u * m->farea[g];
+                }
         } else {
             for (int j = 0; j < s->nq; ++j)
                 for (int i = 0; i < s->nq; ++i) {
@@ -702,7 +749,8 @@ static int pinv_qr(const double* A, int M, int N, double* X)
 static double ipow(double x, int e) { double r = 1.0; for (int i = 0; i < e; ++i) r *= x; return r; }
 
 /* reference map of cell i: xi = Jinv (x - v0), from its corner simplex
- * (triangle v0 v1 v2; quadrilateral v0 v1 v3; hexahedron v0 v1 v3 v4),
+ * (triangle v0 v1 v2; quadrilateral v0 v1 v3; tetrahedron v0 v1 v2 v3;
+ * hexahedron v0 v1 v3 v4),
  * the reading taken for the paper's transformation (Sec. 2.1) */
 static void ref_map(const or_scheme* s, int64_t i, double* x0, double Jinv[3][3], double* detJ)
 {
@@ -710,7 +758,7 @@ static void ref_map(const or_scheme* s, int64_t i, double* x0, double Jinv[3][3]
     double v[3 * MAXV];
     cell_verts(m, i, v);
     int t = m->type[i];
-    int c1 = 1, c2 = (t == OR_TRI) ? 2 : 3, c3 = 4;
+    int c1 = 1, c2 = (t == OR_TRI || t == OR_TET) ? 2 : 3, c3 = t == OR_TET ? 3 : 4;
     double J[3][3] = {{0}};
     for (int d = 0; d < 3; ++d) {
         x0[d] = v[d];
@@ -1054,13 +1102,28 @@ static void rec_cweno(or_scheme* s, or_ops* o, const double* U, int64_t i, const
     }
 }
 
-/* MUSCL with Barth-Jespersen (Sec. 2.2): degree-1 polynomial, one limiter
- * value per variable from the min / max over the cell and its face
- * neighbours */
+/* Venkatakrishnan's smooth limiter value at one face point: the unlimited
+ * increment d2 = grad U . (x_q - x_c), the bound's distance d1 = U_max - U_c
+ * (d2 > 0) or U_min - U_c (d2 < 0), eps2 = (K dx)^3:
+ *   phi = [(d1^2 + eps2) d2 + 2 d2^2 d1] / (d2 [d1^2 + 2 d2^2 + d1 d2 + eps2]),
+ * capped at 1; phi = 1 where d2 = 0 */
+static double venkat_phi(double d1, double d2, double eps2)
+{
+    if (d2 == 0.0) return 1.0;
+    double num = (d1 * d1 + eps2) * d2 + 2.0 * d2 * d2 * d1;
+    double den = d2 * (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+    return fmin(1.0, num / den);
+}
+
+/* MUSCL (Sec. 2.2): degree-1 polynomial, one limiter value per variable from
+ * the min / max over the cell and its face neighbours; Barth-Jespersen by
+ * default, Venkatakrishnan's limiter with limiter = 1 */
 static void rec_muscl(or_scheme* s, or_ops* o, const double* U, int64_t i, double* V)
 {
     const or_mesh* m = s->m;
     int N = s->N, d = s->d, Md = s->Md, nv = s->nv, nf = n_faces_of(s, i), Q = Q_of(s, i);
+    const double dx = d == 2 ? sqrt(m->vol[i]) : cbrt(m->vol[i]);
+    const double eps2 = pow(s->p.venkat_k * dx, 3.0);
     for (int v = 0; v < nv; ++v) {
         double u0 = U[(int64_t)v * m->nc + i];
         double ac[3];
@@ -1083,8 +1146,13 @@ static void rec_muscl(or_scheme* s, or_ops* o, const double* U, int64_t i, doubl
             for (int k = 0; k < d; ++k) sum += o->Phi[q * N + k] * ac[k];
             del[q] = sum;
             double t = 1.0;
-            if (sum > 0.0) t = fmin(1.0, (mx - u0) / sum);
-            else if (sum < 0.0) t = fmin(1.0, (mn - u0) / sum);
+            if (s->p.limiter == 1) {
+                if (sum > 0.0) t = venkat_phi(mx - u0, sum, eps2);
+                else if (sum < 0.0) t = venkat_phi(mn - u0, sum, eps2);
+            } else {
+                if (sum > 0.0) t = fmin(1.0, (mx - u0) / sum);
+                else if (sum < 0.0) t = fmin(1.0, (mn - u0) / sum);
+            }
             if (t < theta) theta = t;
         }
         for (int q = 0; q < Q; ++q) V[q * nv + v] = u0 + theta * del[q];
@@ -1308,6 +1376,52 @@ void or_rk3_generic(int64_t n, double* U, double dt, or_rhs_fn rhs, void* ctx)
     free(U1); free(R);
 }
 
+/* The five-stage, fourth-order SSP Runge-Kutta method of Spiteri and Ruuth
+ * (the paper's time integrator), Shu-Osher form
+ *   u_i = sum_j alpha_ij u_j + beta_ij dt L(u_j),  u_0 = u^n,  u^{n+1} = u_5 */
+static const double RK54_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269},
+};
+static const double RK54_B[6][5] = {
+    {0, 0, 0, 0, 0},
+    {0.391752226571890, 0, 0, 0, 0},
+    {0, 0.368410593050371, 0, 0, 0},
+    {0, 0, 0.251891774271694, 0, 0},
+    {0, 0, 0, 0.544974750228521, 0},
+    {0, 0, 0, 0.063692468666290, 0.226007483236906},
+};
+
+void or_rk54_table(double* alpha, double* beta)
+{
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 5; ++j) { alpha[i * 5 + j] = RK54_A[i][j]; beta[i * 5 + j] = RK54_B[i][j]; }
+}
+
+void or_rk54_generic(int64_t n, double* U, double dt, or_rhs_fn rhs, void* ctx)
+{
+    double* u[6];
+    double* L[5];
+    u[0] = U;
+    for (int i = 1; i < 6; ++i) u[i] = (double*)malloc(n * sizeof(double));
+    for (int j = 0; j < 5; ++j) L[j] = (double*)malloc(n * sizeof(double));
+    for (int i = 1; i < 6; ++i) {
+        rhs(ctx, u[i - 1], L[i - 1]);
+        for (int64_t k = 0; k < n; ++k) {
+            double x = 0.0;
+            for (int j = 0; j < i; ++j) x += RK54_A[i][j] * u[j][k] + RK54_B[i][j] * dt * L[j][k];
+            u[i][k] = x;
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) U[k] = u[5][k];
+    for (int i = 1; i < 6; ++i) free(u[i]);
+    for (int j = 0; j < 5; ++j) free(L[j]);
+}
+
 static int g_rk_err;
 static void scheme_rhs(void* ctx, const double* U, double* R)
 {
@@ -1317,6 +1431,12 @@ int or_rk3_step(or_scheme* s, double* U, double dt)
 {
     g_rk_err = 0;
     or_rk3_generic((int64_t)s->nv * s->m->nc, U, dt, scheme_rhs, s);
+    return g_rk_err ? -1 : 0;
+}
+int or_rk54_step(or_scheme* s, double* U, double dt)
+{
+    g_rk_err = 0;
+    or_rk54_generic((int64_t)s->nv * s->m->nc, U, dt, scheme_rhs, s);
     return g_rk_err ? -1 : 0;
 }
 
@@ -1361,6 +1481,16 @@ int or_cell_face_points(or_scheme* s, int64_t c, double* out)
 {
     double nrm[3];
     for (int f = 0; f < n_faces_of(s, c); ++f) cell_face_points(s, c, f, &out[3 * f * s->nfp], nrm);
+    return 0;
+}
+/* face-point weights w |S| of one cell, in its face-point order */
+int or_cell_face_weights(or_scheme* s, int64_t c, double* out)
+{
+    const or_mesh* m = s->m;
+    for (int f = 0; f < n_faces_of(s, c); ++f) {
+        int64_t g = m->cface[c * MAXNF + f];
+        for (int a = 0; a < s->nfp; ++a) out[f * s->nfp + a] = s->fqw[g * s->nfp + a];
+    }
     return 0;
 }
 /* reference map of cell c: x0 [3], Jinv [3][3] */

@@ -69,6 +69,8 @@ struct AdjParams {
     const int32_t* inv_idx;
     double* g;           // [nv][nc]
     double gamma, lam1, eps_cw, b_cw;
+    int limiter;
+    double venk_k;
 };
 
 template <int NV>
@@ -328,6 +330,12 @@ __device__ void muscl_var(const AdjParams& p, int64_t c, int nf, int n1, const S
         lo = dmin(lo, um[m]);
         hi = dmax(hi, um[m]);
     }
+    double eps2 = 0.0;
+    if (p.limiter == 1) {
+        const double vol = 1.0 / p.ivol[c];
+        const double kd = p.venk_k * (D == 2 ? ::sqrt(vol) : ::cbrt(vol));
+        eps2 = kd * kd * kd;
+    }
     const int Q = nf * NFP;
     S th(1.0);
     S dl[C::QMAX];
@@ -336,8 +344,17 @@ __device__ void muscl_var(const AdjParams& p, int64_t c, int nf, int n1, const S
         for (int k = 0; k < D; ++k) d0 += p.Phil[(c * C::QMAX + q) * D + k] * gr[k];
         dl[q] = d0;
         S t(1.0);
-        if (d0 > 0.0) t = dmin(S(1.0), (hi - u0) / d0);
-        else if (d0 < 0.0) t = dmin(S(1.0), (lo - u0) / d0);
+        if (p.limiter == 1) {
+            if (d0 > 0.0 || d0 < 0.0) {
+                const S d1 = (d0 > 0.0 ? hi : lo) - u0;
+                const S num = (d1 * d1 + eps2) * d0 + 2.0 * d0 * d0 * d1;
+                const S den = d0 * (d1 * d1 + 2.0 * d0 * d0 + d1 * d0 + eps2);
+                t = dmin(S(1.0), num / den);
+            }
+        } else {
+            if (d0 > 0.0) t = dmin(S(1.0), (hi - u0) / d0);
+            else if (d0 < 0.0) t = dmin(S(1.0), (lo - u0) / d0);
+        }
         th = dmin(th, t);
     }
     for (int q = 0; q < Q; ++q) w[q] = u0 + th * dl[q];
@@ -419,6 +436,7 @@ int run_vjp(hfv_scheme* s, const double* lam, double* g, cudaStream_t st)
     p.queue = a.queue; p.counts = a.counts; p.lam = lam;
     p.MU = s->adj.MU; p.A = s->adj.A; p.S0 = s->adj.S0; p.inv_ptr = s->adj.inv_ptr; p.inv_idx = s->adj.inv_idx; p.g = g;
     p.gamma = s->p.gamma; p.lam1 = 1.0 - 1.0 / s->p.lambda1_prime; p.eps_cw = s->p.cweno_eps; p.b_cw = s->p.cweno_b;
+    p.limiter = s->p.limiter; p.venk_k = s->p.venkat_k;
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
     const unsigned gf = (unsigned)((nc + CPB - 1) / CPB);
@@ -452,7 +470,7 @@ int adjoint_prepare(hfv_scheme* s, cudaStream_t st)
 {
     if (s->adj.base) return HFV_OK;
     const int64_t nc = s->mesh->nc, M = s->M, nv = s->nv;
-    const int64_t qtot = nc * (s->d == 2 ? 4 : 6) * s->nfp;
+    const int64_t qtot = nc * (s->d == 2 || s->tet ? 4 : 6) * s->nfp;
     std::vector<int64_t> ptr(nc + 1, 0);
     std::vector<int32_t> idx(nc * M);
     for (int64_t e = 0; e < nc * M; ++e) ++ptr[s->sten[e] + 1];
@@ -503,6 +521,11 @@ int launch_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double*
         case 2: return run_vjp<Cfg<2, 2>>(s, lam, g, st);
         case 3: return run_vjp<Cfg<2, 3>>(s, lam, g, st);
         case 4: return run_vjp<Cfg<2, 4>>(s, lam, g, st);
+        }
+    } else if (s->tet) {
+        switch (s->r) {
+        case 1: return run_vjp<Cfg<3, 1, 1>>(s, lam, g, st);
+        case 2: return run_vjp<Cfg<3, 2, 1>>(s, lam, g, st);
         }
     } else {
         switch (s->r) {

@@ -19,7 +19,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-bool residual_supported(int d, int r);
+bool residual_supported(int d, int r, int tet);
 
 }  // namespace hfv
 
@@ -55,6 +55,9 @@ extern "C" int hfv_default_params(hfv_scheme_params* p)
     p->lambda1_prime = 1e3;
     p->cweno_eps = 1e-3;
     p->cweno_b = 4.0;
+    p->time_scheme = HFV_SSPRK3;
+    p->limiter = HFV_BARTH_JESPERSEN;
+    p->venkat_k = 5.0;
     p->harten_theta = 0.9;
     p->harten_eps = 1e-14;
     p->stencil_factor = 2.0;
@@ -87,13 +90,17 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
     if (!mesh || !p || !out) { set_error("hfv_scheme_create: NULL argument"); return HFV_ERR_ARG; }
     *out = nullptr;
     const int r = p->order - 1;
-    if (r < 1 || !residual_supported(mesh->dim, r)) {
-        set_error("hfv_scheme_create: order " + std::to_string(p->order) + " is not built for dim " + std::to_string(mesh->dim));
+    const int tet = mesh->dim == 3 && mesh->type[0] == HFV_TET;
+    if (r < 1 || !residual_supported(mesh->dim, r, tet)) {
+        set_error("hfv_scheme_create: order " + std::to_string(p->order) + " is not built for dim " +
+                  std::to_string(mesh->dim) + (tet ? " tetrahedra" : ""));
         return HFV_ERR_ARG;
     }
     if (p->stencil_factor != 2.0) { set_error("hfv_scheme_create: only stencil_factor = 2 (M = 2K) is built"); return HFV_ERR_ARG; }
     if (p->flux < HFV_RUSANOV || p->flux > HFV_HLL || p->scheme < HFV_HYBRID || p->scheme > HFV_PURE_MUSCL ||
         (p->precision != HFV_FP64 && p->precision != HFV_FP32) || (p->nad_vars & ~7) ||
+        (p->time_scheme != HFV_SSPRK3 && p->time_scheme != HFV_SSPRK54) ||
+        (p->limiter != HFV_BARTH_JESPERSEN && p->limiter != HFV_VENKATAKRISHNAN) || !(p->venkat_k >= 0.0) ||
         !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0)) {
         set_error("hfv_scheme_create: parameter out of range");
         return HFV_ERR_ARG;

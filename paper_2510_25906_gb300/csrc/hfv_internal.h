@@ -93,7 +93,11 @@ struct hfv_dev_arrays {
     void* UA;          // [nc][P] cell-major copy of the stage state in the residual precision, P = 4 (2D) / 8 (3D)
     void* UB;          // second stage copy: stages alternate UA / UB
     void* areaT;       // [nc][6] face areas in the residual precision
+    double* U3;        // SSP-RK(5,4) stages u_3, u_4 and the partial sum of u_5 (else null)
+    double* U4;
+    double* U5;
     double* dt;        // [nseg] time step per problem
+    double* dtc;       // [6][nseg] stage step sizes of the step: factor times dt
     int32_t* seg;      // [nc] problem of each cell (batched meshes; null for one problem)
     double* Uio;       // [nv][nc] device state of hfv_advance_host
 };
@@ -129,6 +133,7 @@ struct hfv_scheme {
     hfv_mesh* mesh = nullptr;
     hfv_scheme_params p{};
     int r = 0, d = 0, nv = 0, N = 0, M = 0, Md = 0, nq = 0, nfp = 0;
+    int tet = 0;                    // 3D mesh of tetrahedra (else hexahedra)
     int64_t qtot = 0;
     int64_t nc_pad = 0;             // cells rounded up to a multiple of 64 (bulk-copy tiles)
     int64_t ltot = 0;               // elements of L

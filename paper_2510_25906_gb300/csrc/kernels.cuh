@@ -10,20 +10,23 @@ namespace hfv {
 
 constexpr int cK(int r, int d) { return d == 2 ? (r + 1) * (r + 2) / 2 : (r + 1) * (r + 2) * (r + 3) / 6; }
 
-// sizes fixed by (dimension, polynomial degree): M = 2 K(r, d) central cells,
-// N = K(r, d) - 1 coefficients, Md = 2 K(1, d), nq = ceil((r+1)/2) Gauss
-// points per face direction
-template <int D_, int R_>
+// sizes fixed by (dimension, polynomial degree, tetrahedra or not): M =
+// 2 K(r, d) central cells, N = K(r, d) - 1 coefficients, Md = 2 K(1, d),
+// nq Gauss points per face direction: ceil((r+1)/2) on edges and
+// quadrilaterals, ceil((r+2)/2) per direction of the collapsed rule on the
+// triangles of tetrahedra
+template <int D_, int R_, int TET_ = 0>
 struct Cfg {
     static constexpr int D = D_;
     static constexpr int R = R_;
+    static constexpr int TET = TET_;
     static constexpr int NV = D + 2;
     static constexpr int M = 2 * cK(R, D);
     static constexpr int N = cK(R, D) - 1;
     static constexpr int MD = 2 * cK(1, D);
-    static constexpr int NQ = (R + 2) / 2;
+    static constexpr int NQ = TET ? (R + 3) / 2 : (R + 2) / 2;
     static constexpr int NFP = D == 2 ? NQ : NQ * NQ;
-    static constexpr int NFMAX = D == 2 ? 4 : 6;
+    static constexpr int NFMAX = D == 2 ? 4 : TET ? 4 : 6;
     static constexpr int QMAX = NFMAX * NFP;
     static constexpr int NOI = N * (N + 1) / 2;
 };
@@ -77,17 +80,21 @@ struct KParams {
     int nblocks;
     int* status;
     // Runge-Kutta stage fused into the flux kernel (rk_b != 0): for every
-    // variable, out = rk_a U0 + rk_b (Us + dt R) in FP64, and the next stage's
-    // cell-major copy into ua_next (may be null)
+    // variable, out = rk_a U0 + rk_b (Us + c R) in FP64 with the stage's step
+    // c = f dt (per problem, in dtc), and the next stage's cell-major copy
+    // into ua_next (may be null); R itself also into Rcopy when non-null
     double rk_a, rk_b;
+    T* Rcopy;
     const double* U0;
     const double* Us;
-    const double* dt;     // [problems]
+    const double* dtc;    // [problems]
     const int32_t* seg;   // problem of each cell, or null (one problem)
     double* out;
     T* ua_next;
     // constants
     T gamma, alpha_m, beta_m, alpha_w, beta_w, lam1, eps_cw, b_cw, h_theta, h_eps;
+    int limiter;          // MUSCL: 0 Barth-Jespersen, 1 Venkatakrishnan
+    T venk_k;
 };
 
 }  // namespace hfv

@@ -17,14 +17,18 @@ static const int kTriFaces[3][2] = {{0, 1}, {1, 2}, {2, 0}};
 static const int kQuadFaces[4][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 0}};
 static const int kHexFaces[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4},
                                     {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
+// tetrahedron v0 v1 v2 v3 of positive volume: face k is opposite vertex k,
+// listed so that (p1 - p0) x (p2 - p0) points outward
+static const int kTetFaces[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
 
-int type_nverts(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_HEX ? 8 : 0; }
-int type_nfaces(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_HEX ? 6 : 0; }
-int type_face_nverts(int t) { return t == HFV_HEX ? 4 : 2; }
+int type_nverts(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 8 : 0; }
+int type_nfaces(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 6 : 0; }
+int type_face_nverts(int t) { return t == HFV_HEX ? 4 : t == HFV_TET ? 3 : 2; }
 int type_face_vertex(int t, int f, int k)
 {
     if (t == HFV_TRI) return kTriFaces[f][k];
     if (t == HFV_QUAD) return kQuadFaces[f][k];
+    if (t == HFV_TET) return kTetFaces[f][k];
     return kHexFaces[f][k];
 }
 
@@ -63,6 +67,14 @@ void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
     const double* p0 = node(m, c, type_face_vertex(t, f, 0));
     const double* p1 = node(m, c, type_face_vertex(t, f, 1));
     const double* p2 = node(m, c, type_face_vertex(t, f, 2));
+    if (type_face_nverts(t) == 3) {
+        double e[3], g[3];
+        for (int k = 0; k < 3; ++k) { e[k] = p1[k] - p0[k]; g[k] = p2[k] - p0[k]; }
+        A[0] = 0.5 * (e[1] * g[2] - e[2] * g[1]);
+        A[1] = 0.5 * (e[2] * g[0] - e[0] * g[2]);
+        A[2] = 0.5 * (e[0] * g[1] - e[1] * g[0]);
+        return;
+    }
     const double* p3 = node(m, c, type_face_vertex(t, f, 3));
     double e[3], g[3];
     for (int k = 0; k < 3; ++k) { e[k] = p2[k] - p0[k]; g[k] = p3[k] - p1[k]; }
@@ -71,12 +83,23 @@ void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
     A[2] = 0.5 * (e[0] * g[1] - e[1] * g[0]);
 }
 
-// cell measure: triangle cross product, quadrilateral shoelace, hexahedron
-// 2x2x2 Gauss rule on the trilinear map (exact: det J has degree <= 2 per
-// direction)
+// cell measure: triangle cross product, quadrilateral shoelace, tetrahedron
+// triple product, hexahedron 2x2x2 Gauss rule on the trilinear map (exact:
+// det J has degree <= 2 per direction)
 double cell_measure(const hfv_mesh* m, int64_t c)
 {
     int t = m->type[c];
+    if (t == HFV_TET) {
+        const double* o = node(m, c, 0);
+        double a[3], b[3], q[3];
+        for (int k = 0; k < 3; ++k) {
+            a[k] = node(m, c, 1)[k] - o[k];
+            b[k] = node(m, c, 2)[k] - o[k];
+            q[k] = node(m, c, 3)[k] - o[k];
+        }
+        return (a[0] * (b[1] * q[2] - b[2] * q[1]) - a[1] * (b[0] * q[2] - b[2] * q[0]) +
+                a[2] * (b[0] * q[1] - b[1] * q[0])) / 6.0;
+    }
     if (t == HFV_TRI) {
         const double *a = node(m, c, 0), *b = node(m, c, 1), *q = node(m, c, 2);
         return 0.5 * ((b[0] - a[0]) * (q[1] - a[1]) - (b[1] - a[1]) * (q[0] - a[0]));
@@ -151,7 +174,9 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
         for (int k = 0; k < 3; ++k) m->period[k] = k < d->dim ? d->period[k] : 0.0;
         for (int64_t c = 0; c < nc; ++c) {
             int t = m->type[c];
-            bool ok = (d->dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) || (d->dim == 3 && t == HFV_HEX);
+            // 3D meshes are all hexahedra or all tetrahedra
+            bool ok = (d->dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) ||
+                      (d->dim == 3 && (t == HFV_HEX || t == HFV_TET) && t == m->type[0]);
             ok = ok && m->cptr[c + 1] - m->cptr[c] == type_nverts(t);
             for (int64_t k = m->cptr[c]; ok && k < m->cptr[c + 1]; ++k) ok = m->cidx[k] >= 0 && m->cidx[k] < m->nn;
             if (!ok) {

@@ -205,11 +205,15 @@ __device__ __forceinline__ void load_cell(const T* __restrict__ UA, int64_t c, T
 // a group read 128 contiguous bytes.
 template <class C, class T>
 struct K1Shape {
-    // one face point per lane: more points per lane would need more cells
-    // per tile than a ring of 16-byte aligned stages of L holds (3.8 KB of L
-    // per hexahedron at order 4)
-    static constexpr int PPL = 1;
-    static constexpr int G = GroupSize<(C::QMAX + PPL - 1) / PPL>::value;   // lanes per cell
+    // 2D orders 2-4: four lanes per cell (one per face neighbour) with up to
+    // two face points each, so that the per-cell work of the detector and of
+    // the Harten test is shared by eight cells per warp instruction; one
+    // face point per lane elsewhere (more points per lane in 3D would need
+    // more cells per tile than a ring of stages of L holds: 3.8 KB of L per
+    // hexahedron at order 4)
+    static constexpr bool SMALL = C::D == 2 && C::QMAX <= 8;
+    static constexpr int PPL = SMALL ? C::QMAX / 4 : 1;
+    static constexpr int G = SMALL ? 4 : GroupSize<C::QMAX>::value;   // lanes per cell
     static constexpr int SLOT = C::NFMAX <= 4 ? 4 : 8;       // lanes of one face-neighbour reduction
     // lanes past the first SLOT take the bounds from the group's first lane
     static constexpr bool NB_BCAST = G > SLOT;
@@ -228,7 +232,7 @@ struct K1Shape {
     static constexpr int CSTRIDE = (DU4 + DU5 + 127) / 128 * 128 + 16;
     static constexpr int SU = NG * CSTRIDE;
     // resident CTAs per SM aimed for (register and shared-memory budget)
-    static constexpr int MINB = sizeof(T) == 8 ? 1 : (C::D == 2 && C::R <= 2) ? 3 : 2;
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : 2;
     static constexpr int BUDGET = 227 * 1024 / MINB - (SU + 127) / 128 * 128 - 1024;
     static constexpr int FIT = BUDGET / STAGE;
     static constexpr int STAGES = FIT >= 4 ? 4 : FIT >= 3 ? 3 : 2;
@@ -238,19 +242,25 @@ struct K1Shape {
 };
 
 // min / max over the SLOT aligned lanes of a segment (xor offsets below SLOT
-// stay inside it)
+// stay inside it).  The whole warp takes part (full mask): callers keep the
+// control flow warp-uniform.  Operands are finite or +-inf.
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+
 template <int SLOT, class T>
-__device__ __forceinline__ T seg_min(unsigned mask, T v)
+__device__ __forceinline__ T seg_min(T v)
 {
 #pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
+    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 template <int SLOT, class T>
-__device__ __forceinline__ T seg_max(unsigned mask, T v)
+__device__ __forceinline__ T seg_max(T v)
 {
 #pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w > v ? w : v; }
+    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -315,7 +325,24 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     T nthr = T(0);
     auto fetch = [&](int64_t tile_f, int stage_f) {
         const int64_t cf = tile_f * NG + gi;
-        if (cf >= nc) return;
+        if (cf >= nc) {
+            // with several cells per warp, a group past the last cell runs on
+            // a quiet dummy cell with no faces (Q = n1 = 0) and stores
+            // nothing: the warp stays converged (a whole warp past the last
+            // cell skips the tile)
+            if constexpr (G < 32) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    nuc[v] = v == 0 ? T(1) : v == NV - 1 ? T(2.5) : T(0);
+#pragma unroll
+                    for (int i = 0; i < MI; ++i) nu[i][v] = nuc[v];
+                }
+                nnfv = 0;
+                nthr = T(0);
+                nlrel = 0;
+            }
+            return;
+        }
         const int32_t* st = reinterpret_cast<const int32_t*>(smem + stage_f * S::STAGE + S::LBYTES) + gi * M;
 #pragma unroll
         for (int i = 0; i < MI; ++i) {
@@ -331,8 +358,12 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     int64_t tile = blockIdx.x;
     bool alive = true;
     if (tile < ntiles) {
-        if (!mbar_wait(&full[0], 0)) { if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4); alive = false; }
-        else fetch(tile, 0);
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[0], 0))) {
+            if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
+            alive = false;
+        } else {
+            fetch(tile, 0);
+        }
     }
     while (alive && tile < ntiles) {
         const int s = k % ST;
@@ -341,7 +372,9 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
         const int nfv = nnfv;
         const int64_t lrel = nlrel;
         const T thr = nthr;
-        if (c < nc) {
+        const bool valid = c < nc;
+        const bool run = G < 32 || valid;   // warp-uniform
+        if (run) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 uc[v] = nuc[v];
@@ -367,7 +400,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) {
             const int s1 = (k + 1) % ST;
-            if (!mbar_wait(&full[s1], ((k + 1) / ST) & 1)) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s1], ((k + 1) / ST) & 1))) {
                 if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
                 alive = false;
             } else {
@@ -375,14 +408,14 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
             }
         }
         const unsigned char* stage = smem + s * S::STAGE;
-        if (c < nc) {
+        if (run) {
             const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * C::NFP;
             T w[PPL][NV];
 #pragma unroll
             for (int j = 0; j < PPL; ++j)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) w[j][v] = uc[v];
-            grp.sync();
+            __syncwarp();
             const T* lb = reinterpret_cast<const T*>(stage) + lrel;
             // candidate: w = U_0 + sum_m L_qm (U_m - U_0), one chunk of W
             // columns of L per 16-byte load
@@ -478,7 +511,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
             }
             const int64_t q0 = c * C::QMAX;
             const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-            if (lane == 0 && !(rb > T(0) && pb > T(0))) atomicOr(p.status, 1);
+            if (valid && lane == 0 && !(rb > T(0) && pb > T(0))) atomicOr(p.status, 1);
             // Harten test of the candidate at the lane's points
             const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
             T pw[PPL];
@@ -498,6 +531,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
                 // bounds, every lane its own face points for the classification
                 const bool has = lane < n1;
                 const int src = (threadIdx.x & 31) & ~(G - 1);   // the group's first lane
+                const bool det = n1 > 0;
                 const T pn = pressure<T, D>(nb, p.gamma);
                 const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
 #pragma unroll
@@ -508,43 +542,46 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
                     const T qn = kind == 0 ? nb[0] : kind == 1 ? pn : nb[kind - 1];
                     const T qj = has ? qn : qi;
                     const T dd = tabs(qj - qi);
-                    T lo = seg_min<SLOT>(grp.mask, qj), hi = seg_max<SLOT>(grp.mask, qj);
-                    T dlo = seg_min<SLOT>(grp.mask, has ? dd : T(INFINITY));
-                    T dhi = seg_max<SLOT>(grp.mask, has ? dd : T(-INFINITY));
+                    T lo = seg_min<SLOT>(qj), hi = seg_max<SLOT>(qj);
+                    T dlo = seg_min<SLOT>(has ? dd : T(INFINITY));
+                    T dhi = seg_max<SLOT>(has ? dd : T(-INFINITY));
                     if constexpr (S::NB_BCAST) {
-                        lo = __shfl_sync(grp.mask, lo, src);
-                        hi = __shfl_sync(grp.mask, hi, src);
-                        dlo = __shfl_sync(grp.mask, dlo, src);
-                        dhi = __shfl_sync(grp.mask, dhi, src);
+                        lo = __shfl_sync(0xffffffffu, lo, src);
+                        hi = __shfl_sync(0xffffffffu, hi, src);
+                        dlo = __shfl_sync(0xffffffffu, dlo, src);
+                        dhi = __shfl_sync(0xffffffffu, dhi, src);
                     }
-                    if (n1 == 0 || dhi - dlo < thr) continue;   // deactivated: smooth
-                    const T range = hi - lo;
-                    const T dm = tmax(p.alpha_m, p.beta_m * range);
-                    const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
+                    // deactivated (smooth) unless the neighbour differences spread by thr
+                    if (det && !(dhi - dlo < thr)) {
+                        const T range = hi - lo;
+                        const T dm = tmax(p.alpha_m, p.beta_m * range);
+                        const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
 #pragma unroll
-                    for (int j = 0; j < PPL; ++j) {
-                        const int q = lane + j * G;
-                        if (q < Q) {
-                            const T x = kind == 0 ? w[j][0] : kind == 1 ? pw[j] : w[j][kind - 1];
-                            int kc;
-                            if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
-                            else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
-                            else kc = CLS_CW;
-                            cl = kc > cl ? kc : cl;
+                        for (int j = 0; j < PPL; ++j) {
+                            const int q = lane + j * G;
+                            if (q < Q) {
+                                const T x = kind == 0 ? w[j][0] : kind == 1 ? pw[j] : w[j][kind - 1];
+                                int kc;
+                                if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
+                                else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
+                                else kc = CLS_CW;
+                                cl = kc > cl ? kc : cl;
+                            }
                         }
                     }
                 }
             }
-            const bool hfail = grp.any(fail);
-            const bool any_mu = grp.any(cl == CLS_MU), any_cw = grp.any(cl == CLS_CW);
-            if (lane == 0) {
+            const unsigned gbits = grp.mask;
+            const bool hfail = (__ballot_sync(0xffffffffu, fail) & gbits) != 0u;
+            const bool any_mu = (__ballot_sync(0xffffffffu, cl == CLS_MU) & gbits) != 0u;
+            const bool any_cw = (__ballot_sync(0xffffffffu, cl == CLS_CW) & gbits) != 0u;
+            if (valid && lane == 0) {
                 uint8_t out;
                 if (p.forced) out = p.forced_cls[c];
                 else if (p.scheme == HFV_HYBRID) out = any_mu ? CLS_MU : any_cw ? CLS_CW : CLS_LIN;
                 else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
                 p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
             }
-            grp.sync();
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
@@ -579,11 +616,15 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
         const uint8_t r = p.raw[c];
         t = r & 3;
         if (!p.forced && p.scheme == HFV_HYBRID) {
-            const int nf = p.nfc[c] & 15;
-            for (int f = 0; f < nf; ++f) {
-                const int64_t j = p.nbr[c * 6 + f];
-                if (j >= 0) {
-                    const int tj = p.raw[j] & 3;
+            // the six neighbour slots in three 8-byte loads (slots past the
+            // cell's faces hold -1), then the neighbours' classes together
+            const int2* nb2 = reinterpret_cast<const int2*>(p.nbr + c * 6);
+            const int2 a = nb2[0], b = nb2[1], d = nb2[2];
+            const int32_t nbj[6] = {a.x, a.y, b.x, b.y, d.x, d.y};
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                if (nbj[f] >= 0) {
+                    const int tj = p.raw[nbj[f]] & 3;
                     t = tj > t ? tj : t;
                 }
             }
@@ -858,9 +899,23 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
     }
 }
 
-// K4: MUSCL with Barth-Jespersen on the MUSCL queue (Sec. 2.2), one group per
-// queued cell: degree-1 gradient from the first Md stencil cells, limiter
-// bounds from the cell and its face neighbours (the first stencil layer).
+// Venkatakrishnan's smooth limiter value at one face point (d2 != 0 the
+// unlimited increment, d1 the distance to the bound on its side,
+// eps2 = (K dx)^3), capped at 1
+template <class T>
+__device__ __forceinline__ T venk_phi(T d1, T d2, T eps2)
+{
+    const T num = (d1 * d1 + eps2) * d2 + T(2) * d2 * d2 * d1;
+    const T den = d2 * (d1 * d1 + T(2) * d2 * d2 + d1 * d2 + eps2);
+    return tmin(T(1), num / den);
+}
+__device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
+
+// K4: MUSCL on the MUSCL queue (Sec. 2.2), one group per queued cell:
+// degree-1 gradient from the first Md stencil cells, limiter bounds from the
+// cell and its face neighbours (the first stencil layer); Barth-Jespersen, or
+// Venkatakrishnan's limiter with its threshold (K dx)^3.
 template <class C, class T>
 __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, unsigned nbl)
 {
@@ -901,6 +956,13 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
 #pragma unroll
             for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
         T w[NV];
+        T eps2 = T(0);
+        if (p.limiter == 1) {
+            const T vol = T(1) / p.ivol[c];
+            const T dx = D == 2 ? tsqrt<T>(vol) : tcbrt(vol);
+            const T kd = p.venk_k * dx;
+            eps2 = kd * kd * kd;
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             T lo = uc[v], hi = uc[v];
@@ -912,8 +974,13 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
             if (lane < Q) {
 #pragma unroll
                 for (int k = 0; k < D; ++k) dl += ph[k] * sG[gi][v][k];
-                if (dl > T(0)) t = tmin(T(1), (hi - uc[v]) / dl);
-                else if (dl < T(0)) t = tmin(T(1), (lo - uc[v]) / dl);
+                if (p.limiter == 1) {
+                    if (dl > T(0)) t = venk_phi(hi - uc[v], dl, eps2);
+                    else if (dl < T(0)) t = venk_phi(lo - uc[v], dl, eps2);
+                } else {
+                    if (dl > T(0)) t = tmin(T(1), (hi - uc[v]) / dl);
+                    else if (dl < T(0)) t = tmin(T(1), (lo - uc[v]) / dl);
+                }
             }
             const T th = grp.min(t);
             w[v] = uc[v] + th * dl;
@@ -968,11 +1035,12 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
         nn[0] = n[0]; nn[1] = n[1]; nn[2] = n[2];
     }
     // the Runge-Kutta operands do not depend on the fluxes either
-    double u0 = 0.0, us = 0.0, dt = 0.0;
+    double u0 = 0.0, us = 0.0, cdt = 0.0;
     const int64_t e = (int64_t)(lane < NV ? lane : 0) * nc + c;
+    const int sg = p.seg ? p.seg[c] : 0;
     if (p.rk_b != 0.0 && lane < NV) {
         us = p.Us[e];
-        dt = p.dt[p.seg ? p.seg[c] : 0];
+        cdt = p.dtc[sg];
         if (p.rk_a != 0.0) u0 = p.U0[e];
     }
     T acc[NV];
@@ -1002,8 +1070,9 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
             R[lane * nc + c] = r;
         } else {
             // Runge-Kutta stage update of variable `lane` of cell c (FP64)
-            double x = p.rk_b * (us + dt * (double)r);
+            double x = p.rk_b * (us + cdt * (double)r);
             if (p.rk_a != 0.0) x += p.rk_a * u0;
+            if (p.Rcopy) p.Rcopy[lane * nc + c] = r;
             p.out[e] = x;
             if (p.ua_next) p.ua_next[c * AoSP<NV>::P + lane] = (T)x;
         }
@@ -1062,7 +1131,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.nfs = a.nfs;
     p.nv = s->nv;
     p.nfp = s->nfp;
-    p.qmax = (s->d == 2 ? 4 : 6) * s->nfp;
+    p.qmax = (s->d == 2 || s->tet ? 4 : 6) * s->nfp;
     p.FS = (T*)a.FS; p.raw = a.raw; p.cls = a.cls; p.queue = a.queue; p.counts = a.counts;
     p.bcount = a.bcount; p.nblocks = s->nblocks; p.status = a.status;
     p.gamma = (T)s->p.gamma; p.alpha_m = (T)s->p.alpha_m; p.beta_m = (T)s->p.beta_m;
@@ -1070,6 +1139,8 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.lam1 = (T)(1.0 - 1.0 / s->p.lambda1_prime);
     p.eps_cw = (T)s->p.cweno_eps; p.b_cw = (T)s->p.cweno_b;
     p.h_theta = (T)s->p.harten_theta; p.h_eps = (T)s->p.harten_eps;
+    p.limiter = s->p.limiter;
+    p.venk_k = (T)s->p.venkat_k;
     return p;
 }
 
@@ -1096,10 +1167,12 @@ __global__ void k_to_aos(int64_t nc, const Tin* __restrict__ U, T* __restrict__ 
 // fused Runge-Kutta stage applied in the flux kernel's epilogue (see KParams)
 struct StageRK {
     double a = 0.0, b = 0.0;
+    int coef = 0;             // row of the step's step-size table c = f dt (k_rk_coef)
     const double* U0 = nullptr;
     const double* Us = nullptr;
     double* out = nullptr;
     void* ua_next = nullptr;
+    bool keep_R = false;      // also store R (into Rs)
 };
 
 template <class C, class T>
@@ -1117,11 +1190,13 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     }
     p.UA = ua;
     if (rk) {
-        p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.dt = s->a.dt; p.seg = s->a.seg; p.out = rk->out;
-        p.ua_next = (T*)rk->ua_next;
+        p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.seg = s->a.seg;
+        p.dtc = s->a.dtc + (int64_t)rk->coef * s->nseg;
+        p.out = rk->out; p.ua_next = (T*)rk->ua_next;
+        p.Rcopy = rk->keep_R ? (T*)s->a.Rs : nullptr;
     } else {
-        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr; p.seg = nullptr; p.out = nullptr;
-        p.ua_next = nullptr;
+        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dtc = nullptr;
+        p.seg = nullptr; p.out = nullptr; p.ua_next = nullptr; p.Rcopy = nullptr;
     }
     {
         using S1 = K1Shape<C, T>;
@@ -1185,6 +1260,33 @@ __global__ void k_dt_init(unsigned long long* x, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = 0x7ff0000000000000ull;
+}
+
+// the step's stage step sizes c_k = w_k dt per problem (row k of dtc)
+struct RkWeights {
+    double w[8];
+    int n;
+};
+__global__ void k_rk_coef(const double* __restrict__ dt, int nseg, RkWeights w, double* __restrict__ dtc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    const double h = dt[i];
+    for (int k = 0; k < w.n; ++k) dtc[k * nseg + i] = w.w[k] * h;
+}
+
+// SSP-RK(5,4): the part of the last stage known after stage 4,
+//   P = a52 u2 + a53 (u3 + c R(u3)),  c = (beta_53 / alpha_53) dt
+template <class T>
+__global__ void __launch_bounds__(256) k_rk_partial(int64_t n, int64_t nc, const double* __restrict__ u2,
+                                                   const double* __restrict__ u3, const T* __restrict__ R3,
+                                                   const double* __restrict__ c, const int32_t* __restrict__ seg,
+                                                   double a52, double a53, double* __restrict__ P)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cell = i % nc;
+    P[i] = a52 * u2[i] + a53 * (u3[i] + c[seg ? seg[cell] : 0] * (double)R3[i]);
 }
 
 // FP64 state (structure of arrays) -> the first stage's cell-major copy, and,
@@ -1263,7 +1365,7 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
 }
 
 template <class T>
-static auto pick(int d, int r)
+static auto pick(int d, int r, int tet)
     -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t, const T*, const StageRK*)
 {
     if (d == 2) {
@@ -1272,6 +1374,11 @@ static auto pick(int d, int r)
         case 2: return run_residual<Cfg<2, 2>, T>;
         case 3: return run_residual<Cfg<2, 3>, T>;
         case 4: return run_residual<Cfg<2, 4>, T>;
+        }
+    } else if (tet) {
+        switch (r) {
+        case 1: return run_residual<Cfg<3, 1, 1>, T>;
+        case 2: return run_residual<Cfg<3, 2, 1>, T>;
         }
     } else {
         switch (r) {
@@ -1283,14 +1390,14 @@ static auto pick(int d, int r)
     return nullptr;
 }
 
-bool residual_supported(int d, int r) { return pick<double>(d, r) != nullptr; }
+bool residual_supported(int d, int r, int tet) { return pick<double>(d, r, tet) != nullptr; }
 
 static int residual_any(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out,
                         cudaStream_t st, const void* ua, const StageRK* rk)
 {
     if (s->p.precision == HFV_FP32)
-        return pick<float>(s->d, s->r)(s, (const float*)U, (float*)R, forced, cls_out, st, (const float*)ua, rk);
-    return pick<double>(s->d, s->r)(s, (const double*)U, (double*)R, forced, cls_out, st, (const double*)ua, rk);
+        return pick<float>(s->d, s->r, s->tet)(s, (const float*)U, (float*)R, forced, cls_out, st, (const float*)ua, rk);
+    return pick<double>(s->d, s->r, s->tet)(s, (const double*)U, (double*)R, forced, cls_out, st, (const double*)ua, rk);
 }
 
 int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
@@ -1334,20 +1441,79 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     } else if ((rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
         return rc;
     }
-    // stages read UA, UB, UA; each stage's flux kernel writes the next copy
-    void* ua[3] = {s->a.UA, s->a.UB, s->a.UA};
+    // stages alternate the cell-major copies UA, UB, UA, ...; each stage's
+    // flux kernel writes the next one
+    void* uab[2] = {s->a.UA, s->a.UB};
+    auto coefs = [&](const double* w, int n) -> int {
+        RkWeights rw;
+        rw.n = n;
+        for (int k = 0; k < n; ++k) rw.w[k] = w[k];
+        Launch l(s, KID_DT, st);
+        k_rk_coef<<<(s->nseg + 255) / 256, 256, 0, st>>>(s->a.dt, s->nseg, rw, s->a.dtc);
+        HFV_CUDA_CHECK(cudaGetLastError());
+        return HFV_OK;
+    };
+    if (s->p.time_scheme == HFV_SSPRK54) {
+        // u_i = sum_j alpha_ij u_j + beta_ij dt L(u_j) (Spiteri and Ruuth's
+        // SSP-RK(5,4), Shu-Osher form): stage i reads u_{i-1} and writes
+        //   u_i = alpha_i0 u_0 + alpha_i,i-1 (u_{i-1} + (beta_i,i-1 / alpha_i,i-1) dt L(u_{i-1}));
+        // after stage 4, P = alpha_52 u_2 + alpha_53 (u_3 + (beta_53 / alpha_53) dt L(u_3))
+        // from the kept L(u_3), and stage 5 writes
+        //   u_5 = P + alpha_54 (u_4 + (beta_54 / alpha_54) dt L(u_4))
+        static const double a10 = 1.0, b10 = 0.391752226571890;
+        static const double a20 = 0.444370493651235, a21 = 0.555629506348765, b21 = 0.368410593050371;
+        static const double a30 = 0.620101851488403, a32 = 0.379898148511597, b32 = 0.251891774271694;
+        static const double a40 = 0.178079954393132, a43 = 0.821920045606868, b43 = 0.544974750228521;
+        static const double a52 = 0.517231671970585, a53 = 0.096059710526147, b53 = 0.063692468666290;
+        static const double a54 = 0.386708617503269, b54 = 0.226007483236906;
+        double* u[5] = {U, s->a.U1, s->a.U2, s->a.U3, s->a.U4};
+        const double A0[5] = {0.0, a20, a30, a40, 1.0};
+        const double Bk[5] = {a10, a21, a32, a43, a54};
+        // c_k = (beta_k,k-1 / alpha_k,k-1) dt; row 5 (beta_53 / alpha_53) dt for P
+        const double W[6] = {b10 / a10, b21 / a21, b32 / a32, b43 / a43, b54 / a54, b53 / a53};
+        if ((rc = coefs(W, 6)) != HFV_OK) return rc;
+        const int64_t nvc = (int64_t)s->nv * s->mesh->nc;
+        for (int k = 0; k < 5; ++k) {
+            StageRK rk;
+            rk.a = A0[k];
+            rk.b = Bk[k];
+            rk.coef = k;
+            rk.U0 = k == 4 ? s->a.U5 : U;
+            rk.Us = u[k];
+            rk.out = k == 4 ? U : u[k + 1];
+            rk.ua_next = k < 4 ? uab[(k + 1) & 1] : nullptr;
+            rk.keep_R = k == 3;
+            if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, uab[k & 1], &rk)) != HFV_OK) return rc;
+            if (k == 3) {
+                Launch l(s, KID_RK, st);
+                const unsigned g = (unsigned)((nvc + 255) / 256);
+                const double* c5 = s->a.dtc + 5 * (int64_t)s->nseg;
+                if (s->p.precision == HFV_FP32)
+                    k_rk_partial<float><<<g, 256, 0, st>>>(nvc, s->mesh->nc, s->a.U2, s->a.U3, (const float*)s->a.Rs, c5,
+                                                          s->a.seg, a52, a53, s->a.U5);
+                else
+                    k_rk_partial<double><<<g, 256, 0, st>>>(nvc, s->mesh->nc, s->a.U2, s->a.U3, (const double*)s->a.Rs,
+                                                           c5, s->a.seg, a52, a53, s->a.U5);
+            }
+        }
+        HFV_CUDA_CHECK(cudaGetLastError());
+        return HFV_OK;
+    }
     double* outs[3] = {s->a.U1, s->a.U2, U};
     const double* ins[3] = {U, s->a.U1, s->a.U2};
     const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double ones[3] = {1.0, 1.0, 1.0};
+    if ((rc = coefs(ones, 3)) != HFV_OK) return rc;
     for (int k = 0; k < 3; ++k) {
         StageRK rk;
         rk.a = A[k];
         rk.b = B[k];
+        rk.coef = k;
         rk.U0 = U;
         rk.Us = ins[k];
         rk.out = outs[k];
-        rk.ua_next = k < 2 ? ua[k + 1] : nullptr;
-        if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, ua[k], &rk)) != HFV_OK) return rc;
+        rk.ua_next = k < 2 ? uab[(k + 1) & 1] : nullptr;
+        if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, uab[k & 1], &rk)) != HFV_OK) return rc;
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;

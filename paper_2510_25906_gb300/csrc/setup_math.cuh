@@ -90,8 +90,8 @@ struct SetupWork {
 
 namespace setup_detail {
 
-HD inline int nverts(int t) { return t == 1 ? 3 : t == 2 ? 4 : 8; }
-HD inline int nfaces(int t) { return t == 1 ? 3 : t == 2 ? 4 : 6; }
+HD inline int nverts(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : 8; }
+HD inline int nfaces(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : 6; }
 
 HD inline double ipow(double x, int e)
 {
@@ -154,6 +154,23 @@ HD inline void cell_rule(const SetupParams& S, int t, const double v[8][3], F&& 
                     f(x, S.gvw[i] * S.gvw[j] * u * det);
                 }
         }
+        return;
+    }
+    if (t == 3) {
+        // tetrahedron: collapsed cube x = v0 + s a + s w b + s w z c with
+        // a = v1 - v0, b = v2 - v1, c = v3 - v2, |J| = s^2 w |det(a, b, c)|
+        double a[3], b[3], cc[3];
+        for (int q = 0; q < 3; ++q) { a[q] = v[1][q] - v[0][q]; b[q] = v[2][q] - v[1][q]; cc[q] = v[3][q] - v[2][q]; }
+        double det = fabs(a[0] * (b[1] * cc[2] - b[2] * cc[1]) - a[1] * (b[0] * cc[2] - b[2] * cc[0]) +
+                          a[2] * (b[0] * cc[1] - b[1] * cc[0]));
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    double s1 = S.gvx[i], w = S.gvx[j], z = S.gvx[k];
+                    double x[3];
+                    for (int q = 0; q < 3; ++q) x[q] = v[0][q] + s1 * a[q] + s1 * w * b[q] + s1 * w * z * cc[q];
+                    f(x, S.gvw[i] * S.gvw[j] * S.gvw[k] * s1 * s1 * w * det);
+                }
         return;
     }
     // hexahedron: trilinear map of the unit cube
@@ -244,7 +261,9 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     double x0[3], J[3][3], Ji[3][3];
     {
         const double* p0 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c]]];
-        int c1 = 1, c2 = t == 1 ? 2 : 3, c3 = 4;
+        // corner simplex: triangle v0 v1 v2, quadrilateral v0 v1 v3,
+        // tetrahedron v0 v1 v2 v3, hexahedron v0 v1 v3 v4
+        int c1 = 1, c2 = (t == 1 || t == 3) ? 2 : 3, c3 = t == 3 ? 3 : 4;
         const double* p1 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c] + c1]];
         const double* p2 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c] + c2]];
         for (int q = 0; q < 3; ++q) {
@@ -320,7 +339,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
         const int32_t* fv = &S.fvtx[(c * 6 + f) * 4];
         const int8_t* k = &S.fk[(c * 6 + f) * 3];
         double pv[4][3];
-        int nfv = d == 2 ? 2 : 4;
+        int nfv = d == 2 ? 2 : t == 3 ? 3 : 4;
         for (int a = 0; a < nfv; ++a)
             for (int q = 0; q < 3; ++q) pv[a][q] = S.xyz[3 * (int64_t)fv[a] + q] + k[q] * S.period[q];
         const double area = S.farea[c * 6 + f];
@@ -330,6 +349,13 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
                 double s = S.gfx[al];
                 for (int q = 0; q < 3; ++q) xp[q] = pv[0][q] + s * (pv[1][q] - pv[0][q]);
                 wgt = S.gfw[al] * area;
+            } else if (t == 3) {
+                // triangle face: collapsed rule x = p0 + s (p1 - p0) + s u (p2 - p1),
+                // weight w_i w_j 2 s |S|
+                int i = al % S.nq, jj = al / S.nq;
+                double s = S.gfx[i], u = S.gfx[jj];
+                for (int q = 0; q < 3; ++q) xp[q] = pv[0][q] + s * (pv[1][q] - pv[0][q]) + s * u * (pv[2][q] - pv[1][q]);
+                wgt = S.gfw[i] * S.gfw[jj] * 2.0 * s * area;
             } else {
                 int i = al % S.nq, jj = al / S.nq;
                 double s = S.gfx[i], u = S.gfx[jj];

@@ -26,6 +26,8 @@ KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux"
 FLUX = {"rusanov": HFV_RUSANOV, "hllc": HFV_HLLC, "hll": HFV_HLL}
 SCHEME = {"hybrid": HFV_HYBRID, "linear": HFV_PURE_LINEAR, "cweno": HFV_PURE_CWENOZ, "muscl": HFV_PURE_MUSCL}
 PRECISION = {"fp64": HFV_FP64, "fp32": HFV_FP32}
+TIME_SCHEME = {"ssprk3": 0, "ssprk54": 1}
+LIMITER = {"barth": 0, "venkatakrishnan": 1}
 
 
 class HfvError(RuntimeError):
@@ -42,11 +44,11 @@ class hfv_mesh_desc(C.Structure):
 
 class hfv_scheme_params(C.Structure):
     _fields_ = [("order", C.c_int), ("flux", C.c_int), ("scheme", C.c_int), ("nad_vars", C.c_int),
-                ("precision", C.c_int), ("reserved", C.c_int), ("gamma", C.c_double), ("alpha_m", C.c_double),
+                ("precision", C.c_int), ("time_scheme", C.c_int), ("gamma", C.c_double), ("alpha_m", C.c_double),
                 ("beta_m", C.c_double), ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1_prime", C.c_double), ("cweno_eps", C.c_double),
                 ("cweno_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("reserved", C.c_int), ("venkat_k", C.c_double)]
 
 
 _lib = None
@@ -123,6 +125,10 @@ def default_params(**kw) -> hfv_scheme_params:
             v = SCHEME[v]
         elif k == "precision" and isinstance(v, str):
             v = PRECISION[v]
+        elif k == "time_scheme" and isinstance(v, str):
+            v = TIME_SCHEME[v]
+        elif k == "limiter" and isinstance(v, str):
+            v = LIMITER[v]
         setattr(p, k, v)
     return p
 

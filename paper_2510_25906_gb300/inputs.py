@@ -194,6 +194,41 @@ def structured_hex_mesh(n: int, length: float = 2.0 * math.pi, periodic: bool = 
                 np.asarray(period, np.float64), f"hex{n}", {"n": n, "seed": seed})
 
 
+def structured_tet_mesh(n: int, length: float = 1.0, periodic: bool = False, jitter: float = 0.0,
+                        seed: int = 4) -> Mesh:
+    """n^3 hexahedra of [0,L]^3 each cut into six tetrahedra along its
+    (0,0,0)-(1,1,1) diagonal (one per ordering of the axes: the path
+    000 -> e_a -> e_a + e_b -> 111), conforming across the grid; 6 n^3 cells,
+    vertices of each tetrahedron ordered to positive volume.  Interior nodes
+    jittered by up to `jitter` h per coordinate."""
+    hx = structured_hex_mesh(n, length, periodic=periodic, jitter=jitter, seed=seed)
+    corner = {(0, 0, 0): 0, (1, 0, 0): 1, (1, 1, 0): 2, (0, 1, 0): 3, (0, 0, 1): 4, (1, 0, 1): 5, (1, 1, 1): 6,
+              (0, 1, 1): 7}
+    tets = []
+    for perm in ((0, 1, 2), (1, 2, 0), (2, 0, 1), (0, 2, 1), (2, 1, 0), (1, 0, 2)):
+        b = [0, 0, 0]
+        path = [corner[tuple(b)]]
+        for ax in perm:
+            b[ax] = 1
+            path.append(corner[tuple(b)])
+        tets.append(path)
+    hc = hx.cell_idx.reshape(-1, 8)
+    conn = np.concatenate([hc[:, t] for t in tets], axis=0)          # [6 n^3, 4], grouped by pattern
+    order = np.arange(conn.shape[0]).reshape(6, -1).T.ravel()       # the six of each hexahedron together
+    conn = np.ascontiguousarray(conn[order]).astype(np.int32)
+    x = hx.nodes[conn]
+    det = np.einsum("ij,ij->i", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
+    flip = det < 0
+    conn[flip, 1], conn[flip, 2] = conn[flip, 2].copy(), conn[flip, 1].copy()
+    x = hx.nodes[conn]
+    det = np.einsum("ij,ij->i", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))
+    if not (det > 0).all():
+        raise ValueError("jitter too large: inverted tetrahedra")
+    ncell = conn.shape[0]
+    return Mesh(3, hx.nodes, np.full(ncell, TET, np.uint8), np.arange(ncell + 1, dtype=np.int64) * 4, conn.ravel(),
+                hx.period, f"tet{n}", {"n": n, "seed": seed})
+
+
 # ---------------------------------------------------------------------------
 # Initial states
 # ---------------------------------------------------------------------------
@@ -312,6 +347,37 @@ def turbulence_state(mesh: Mesh, seed: int = 3, k0: float = 4.0, mach_t: float =
 # Named workloads (sizes as the paper's workloads; small variants for tests)
 # ---------------------------------------------------------------------------
 
+def isentropic_vortex_state(mesh: Mesh, t: float = 0.0, eps: float = 5.0, L: float = 10.0,
+                            gamma: float = GAMMA, npts: int = 8) -> np.ndarray:
+    """Cell averages of the isentropic vortex of the paper's 2D accuracy test
+    (Sec. 3.1): strength eps centred at (L/2, L/2) at t = 0, carried by the
+    free stream (u, v) = (1, 1) on the periodic square [0, L]^2:
+      du = -eps/(2 pi) e^((1-r^2)/2) (y - yc),  dv = eps/(2 pi) e^((1-r^2)/2) (x - xc),
+      T = 1 - (gamma-1) eps^2/(8 gamma pi^2) e^(1-r^2),  rho = T^(1/(gamma-1)),  p = rho T,
+    the centre at (L/2 + t, L/2 + t) wrapped into the square."""
+    xc = (0.5 * L + t) % L
+    yc = (0.5 * L + t) % L
+
+    def prim(x, y):
+        dx = (x - xc + 0.5 * L) % L - 0.5 * L
+        dy = (y - yc + 0.5 * L) % L - 0.5 * L
+        r2 = dx * dx + dy * dy
+        e = np.exp(0.5 * (1.0 - r2))
+        u = 1.0 - eps / (2 * math.pi) * e * dy
+        v = 1.0 + eps / (2 * math.pi) * e * dx
+        T = 1.0 - (gamma - 1.0) * eps * eps / (8.0 * gamma * math.pi ** 2) * e * e
+        rho = T ** (1.0 / (gamma - 1.0))
+        return rho, u, v, rho * T
+
+    comps = []
+    for k in range(4):
+        def f(x, y, k=k):
+            rho, u, v, p = prim(x, y)
+            return (rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v))[k]
+        comps.append(cell_average_2d(mesh, f, npts=npts))
+    return np.stack(comps)
+
+
 SOD_STATES = ((1.0, 0.0, 0.0, 1.0), (0.125, 0.0, 0.0, 0.1))   # (rho, u, v, p) left / right of the membrane
 
 
@@ -373,13 +439,13 @@ def mach2_shock_states(gamma: float = GAMMA, mach: float = 2.0):
     return (r, s * (1.0 - 1.0 / r), 0.0, 0.0, pr), (1.0, 0.0, 0.0, 0.0, 1.0)
 
 
-def adjoint_problem(n: int = 100, seed: int = 4, gamma: float = GAMMA):
-    """Open unit cube of n^3 jittered hexahedra (the adjoint workload's
-    stand-in for its tetrahedral mesh): a Gaussian density pulse
+def adjoint_problem(n: int = 55, seed: int = 4, gamma: float = GAMMA):
+    """Open unit cube of n^3 hexahedra cut into 6 n^3 jittered tetrahedra
+    (55^3 * 6 = 998,250 cells by default): a Gaussian density pulse
     rho = 1 + 0.5 exp(-|x - (0.75, 0.5, 0.5)|^2 / (2 0.08^2)) in gas at rest
     (p = 1) ahead of a planar Mach 2 shock at x = 0.4 moving along +x.
     Cell values at the vertex means."""
-    m = structured_hex_mesh(n, 1.0, periodic=False, jitter=0.15, seed=seed)
+    m = structured_tet_mesh(n, 1.0, periodic=False, jitter=0.1, seed=seed)
     c = m.vertex_means()
     post, pre = mach2_shock_states(gamma)
     behind = c[:, 0] < 0.4

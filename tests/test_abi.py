@@ -50,6 +50,8 @@ def test_default_params(H):
     lambda: I.mixed_tri_quad_mesh(20, seed=9, periodic=True),
     lambda: I.structured_hex_mesh(10, 2 * math.pi, periodic=True),
     lambda: I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.2, seed=3),
+    lambda: I.structured_tet_mesh(5, 1.0, periodic=False, jitter=0.1, seed=3),
+    lambda: I.structured_tet_mesh(4, 1.0, periodic=True),
 ])
 def test_connectivity_bit_exact_with_oracle(H, maker):
     m = maker()

@@ -71,6 +71,8 @@ CASES = {
                     dict(order=3, flux="hllc")),
     "hex_r3_hllc": (lambda: I.structured_hex_mesh(6, 1.0, periodic=False, jitter=0.1, seed=7), _hex_state,
                     dict(order=4, flux="hllc")),
+    "tet_r2_hllc": (lambda: I.structured_tet_mesh(4, 1.0, periodic=False, jitter=0.1, seed=8), _hex_state,
+                    dict(order=3, flux="hllc")),
 }
 
 
@@ -102,13 +104,17 @@ def test_vjp_against_central_differences(H, name):
         assert abs(fd - an) <= 1e-6 * scale, (fd, an, scale)
 
 
-@pytest.mark.parametrize("name", ["mixed_r2_hllc", "hex_r2_hllc"])
+@pytest.mark.parametrize("name", ["mixed_r2_hllc", "hex_r2_hllc", "tet_r2_hllc"])
 def test_vjp_against_oracle_gradient(H, name):
     """The oracle's gradient: central differences of the oracle's FP64
     residual (classes forced), one input at a time."""
     mk, st, kw = CASES[name]
-    m = I.mixed_tri_quad_mesh(5, seed=4) if m_is_2d(name) else I.structured_hex_mesh(3, 1.0, periodic=False,
-                                                                                      jitter=0.15, seed=5)
+    if name.startswith("mixed"):
+        m = I.mixed_tri_quad_mesh(5, seed=4)
+    elif name.startswith("hex"):
+        m = I.structured_hex_mesh(3, 1.0, periodic=False, jitter=0.15, seed=5)
+    else:
+        m = I.structured_tet_mesh(2, 1.0, periodic=False, jitter=0.1, seed=5)
     U = st(m, 3)
     cls_np = _classes(m.n_cells, 7)
     g = H.Scheme(H.Mesh(m), precision="fp64", **kw)
@@ -131,10 +137,6 @@ def test_vjp_against_oracle_gradient(H, name):
     err = np.abs(grad - ref).max() / np.abs(ref).max()
     print(f"{name}: {m.n_cells} cells, classes {np.bincount(fin_np, minlength=4)}, max rel err {err:.2e}")
     assert err <= 1e-6, err
-
-
-def m_is_2d(name):
-    return name.startswith("mixed")
 
 
 @pytest.mark.parametrize("name", ["mixed_r2_hllc", "hex_r2_hllc"])

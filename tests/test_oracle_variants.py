@@ -1,0 +1,118 @@
+"""Pins of the oracle's paper variants (CPU): the SSP-RK(5,4) time step of
+Spiteri and Ruuth (the paper's integrator, Sec. 2) and Venkatakrishnan's
+limiter for the MUSCL reconstruction (the paper's parameter K = 5).
+
+  * SSP-RK(5,4): its Shu-Osher table satisfies the eight order conditions of
+    a fourth-order Runge-Kutta method (Butcher form), every coefficient is
+    non-negative and every stage is a convex combination; on u' = lambda u
+    the error of one step against exp(z) falls as z^5; a step of the Euler
+    residual is that same method applied to the residual.
+  * Venkatakrishnan: with eps = 0 its limiter value never exceeds
+    Barth-Jespersen's at any face point (phi(y) <= min(1, y)), so the face
+    values stay inside the neighbour bounds and the cell's limiter is at most
+    Barth-Jespersen's; with a large K it does not limit (a plane is
+    reproduced exactly); at a jump with the paper's K = 5 it limits (one
+    theta in (0, 1) scales every point's increment).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_25906_gb300 import inputs as I
+
+
+def _butcher(al, be):
+    A = np.zeros((6, 5))
+    for i in range(1, 6):
+        for j in range(i):
+            A[i] += al[i, j] * A[j]
+            A[i, j] += be[i, j]
+    return A[:5, :5], A[5]
+
+
+def test_rk54_order_conditions_and_ssp_form():
+    al, be = O.rk54_table()
+    assert np.allclose(al[1:].sum(axis=1), 1.0, atol=1e-14)
+    assert (al >= 0).all() and (be >= 0).all()
+    A, b = _butcher(al, be)
+    c = A.sum(axis=1)
+    conds = [b.sum() - 1, b @ c - 1 / 2, b @ c ** 2 - 1 / 3, b @ A @ c - 1 / 6, b @ c ** 3 - 1 / 4,
+             b @ (c * (A @ c)) - 1 / 8, b @ A @ c ** 2 - 1 / 12, b @ A @ A @ c - 1 / 24]
+    assert np.abs(conds).max() < 1e-14, conds
+    # not fifth order: some fifth-order condition fails
+    assert abs(b @ c ** 4 - 1 / 5) > 1e-6 or abs(b @ A @ A @ A @ c - 1 / 120) > 1e-6
+
+
+def test_rk54_linear_error_is_fifth_power():
+    lam = -1.0
+    errs = []
+    for dt in (0.2, 0.1, 0.05):
+        u = O.rk54_generic(np.array([1.0]), dt, lambda x: lam * x)
+        errs.append(abs(u[0] - np.exp(lam * dt)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 28 < r1 < 36 and 29 < r2 < 35, (errs, r1, r2)
+
+
+def test_rk54_step_is_the_method_on_the_residual():
+    m = I.mixed_tri_quad_mesh(10, seed=2, periodic=True)
+    s = O.Scheme(O.Mesh(m), order=3, flux="hllc")
+    U = I.quadrant_state(m)
+    dt = 0.5 * s.dt(U, 0.5)
+    got = s.rk54_step(U, dt)
+    shape = U.shape
+    ref = O.rk54_generic(U.ravel(), dt, lambda x: s.residual(x.reshape(shape))[0].ravel()).reshape(shape)
+    assert np.array_equal(got, ref)
+
+
+def _random_state(m, seed):
+    rng = np.random.default_rng(seed)
+    n = m.n_cells
+    return np.stack([1 + rng.random(n), rng.standard_normal(n), rng.standard_normal(n), 5 + rng.random(n)])
+
+
+def test_venkatakrishnan_without_threshold_is_inside_barth_jespersen():
+    m = I.mixed_tri_quad_mesh(14, seed=6)
+    sv = O.Scheme(O.Mesh(m), order=3, limiter="venkatakrishnan", venkat_k=0.0)
+    sb = O.Scheme(O.Mesh(m), order=3)
+    nbr, _ = sv.mesh.connectivity()
+    U = _random_state(m, 1)
+    strict = 0
+    for c in range(0, m.n_cells, 7):
+        Vv = sv.reconstruct(U, c, O.MU)
+        Vb = sb.reconstruct(U, c, O.MU)
+        nb = [j for j in nbr[c] if j >= 0] + [c]
+        lo, hi = U[:, nb].min(axis=1), U[:, nb].max(axis=1)
+        assert (Vv >= lo - 1e-14).all() and (Vv <= hi + 1e-14).all()
+        # same gradient, smaller or equal limiter: |V - u0| shrinks point by point
+        dv, db = np.abs(Vv - U[:, c]), np.abs(Vb - U[:, c])
+        assert (dv <= db + 1e-14).all()
+        strict += int((dv < db - 1e-12).any())
+    assert strict > 0
+
+
+def test_venkatakrishnan_large_threshold_reproduces_a_plane():
+    m = I.mixed_tri_quad_mesh(14, seed=6)
+    s = O.Scheme(O.Mesh(m), order=3, limiter="venkatakrishnan", venkat_k=1e6)
+    rho = I.cell_average_2d(m, lambda x, y: 2.0 + 0.3 * (x - 2 * y))
+    U = np.stack([rho, rho, rho, rho + 3])
+    for c in (40, 150, 260):
+        V = s.reconstruct(U, c, O.MU)
+        P = s.face_points(c)
+        ex = 2.0 + 0.3 * (P[:, 0] - 2 * P[:, 1])
+        assert np.abs(V[:, 0] - ex).max() < 1e-12
+
+
+def test_venkatakrishnan_limits_at_a_jump():
+    m = I.structured_quad_mesh(16, 16, jitter=0.1, seed=3)
+    s = O.Scheme(O.Mesh(m), order=3, limiter="venkatakrishnan", venkat_k=5.0)
+    vm = m.vertex_means()
+    rho = np.where(vm[:, 0] < 0.5, 1.0, 0.2)
+    U = np.stack([rho, 0 * rho, 0 * rho, 2.5 + 0 * rho])
+    free = O.Scheme(O.Mesh(m), order=3, limiter="venkatakrishnan", venkat_k=1e6)
+    for c in (7 * 16 + 7, 7 * 16 + 8):   # the two cells on either side of the jump
+        V = s.reconstruct(U, c, O.MU)
+        Vf = free.reconstruct(U, c, O.MU)
+        d, df = V[:, 0] - rho[c], Vf[:, 0] - rho[c]
+        assert np.abs(d).max() > 0                          # not first order
+        assert np.abs(d).max() < 0.9 * np.abs(df).max()     # limited: 0 < theta < 1
+        assert np.allclose(d[np.abs(df) > 0] / df[np.abs(df) > 0], (d / np.where(df == 0, 1, df))[np.abs(df) > 0][0])
