@@ -40,10 +40,18 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic of k_linear per cell, from one ncu capture of the kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum of a launch / its cells; the
 # kernel reads per-cell data only, so traffic scales with the cells).  A figure
-# holds only while the kernel sources are those the capture ran: their hash is
-# stored beside it, and a mismatch reports null.
-KERNEL_SOURCES = ("residual.cu", "kernels.cuh", "tma.cuh", "physics.cuh")
-TRAFFIC = {}
+# holds only while the kernel's sources (its header and what it includes) are
+# those the capture ran: their hash is stored beside it, and a mismatch
+# reports null.
+KERNEL_SOURCES = ("k_linear.cuh", "device_common.cuh", "kernels.cuh", "tma.cuh", "physics.cuh")
+TRAFFIC = {
+    # 98,363-cell quadrant mesh, order 3 hybrid FP32: 39,068,672 B read +
+    # 50,688 B written (the face values stay in L2 as dirty lines at exit)
+    ("quadrant", 3, "fp32", "hybrid"): {"bytes_per_cell": 397.704, "sources": "fb7ae58172ea4fc0"},
+    # 110,592-cell turbulence mesh, order 4 hybrid FP32: 447,695,360 B read +
+    # 44,607,488 B written
+    ("turbulence", 4, "fp32", "hybrid"): {"bytes_per_cell": 4451.523, "sources": "fb7ae58172ea4fc0"},
+}
 
 
 def kernel_source_hash() -> str:
@@ -337,7 +345,8 @@ def turbulence_variants(H, I, torch, dev, args):
                 ach = kb / (k_ms / k_n * 1e-3) / 1e9
                 peak, _ = _peaks()
                 entry["k_linear"] = {"achieved_GBs": ach, "frac": ach / peak, "avg_launch_us": 1e3 * k_ms / k_n,
-                                     "algorithmic_bytes_per_launch": kb}
+                                     "algorithmic_bytes_per_launch": kb,
+                                     "traffic": _traffic("turbulence", 4, "fp32", "hybrid", cells)}
                 entry["kernel_share"] = {k: round(v[0] / sum(x[0] for x in times.values()), 4)
                                          for k, v in times.items() if v[1]}
             out[f"{scheme}_{prec}"] = entry
@@ -433,16 +442,19 @@ def batched_variants(H, I, torch, dev, args):
 
 def adjoint_variants(H, I, torch, dev, args):
     """The adjoint workload: dJ/dU0 of J = sum |V| rho^2 after K checkpointed
-    SSP-RK3 steps (FP64, order 3 hybrid, HLLC, classes frozen along the
-    forward trajectory) on an open unit cube of 6 n^3 jittered tetrahedra
-    with a Gaussian density pulse ahead of a planar Mach 2 shock.  Reports the time
-    of the forward sweep and of the backward sweep (stage recomputation and
-    three residual VJPs per step) and the VJP rate."""
+    SSP-RK3 steps (FP64, order 3 hybrid, HLLC, Venkatakrishnan's limiter with
+    K = 5, classes frozen along the forward trajectory) on an open unit cube
+    of 6 n^3 jittered tetrahedra with a Gaussian density pulse ahead of a
+    planar Mach 2 shock.  Reports the time of the forward sweep and of the
+    backward sweep (stage recomputation and three residual VJPs per step), the
+    VJP rate, and the gradient against central differences of the whole
+    K-step trajectory (classes and step sizes frozen) along two directions:
+    a seeded random one and the density pulse."""
     from paper_2510_25906_gb300 import adjoint as A
     n = args.adjoint_n
     m, U0 = I.adjoint_problem(n)
     gm = H.Mesh(m)
-    g = H.Scheme(gm, order=3, flux="hllc", precision="fp64")
+    g = H.Scheme(gm, order=3, flux="hllc", precision="fp64", limiter="venkatakrishnan", venkat_k=5.0)
     U = torch.tensor(U0, device=dev)
     J = A.density_square_integral(gm.volumes())
     # one warm call of each kernel family
@@ -471,8 +483,31 @@ def adjoint_variants(H, I, torch, dev, args):
     torch.cuda.synchronize(dev)
     res_ms = e0.elapsed_time(e1) / reps
     hist = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+    # central differences of the same trajectory (h = 1e-6)
+    ccls, W = [], U.clone()
+    for h_ in dts:
+        _, _, W3, cc = A._stages(g, W, h_)
+        ccls.append(cc)
+        W = W3.contiguous()
+
+    def traj(Ux):
+        W = Ux.clone()
+        for cc, h_ in zip(ccls, dts):
+            W = A._stages(g, W, h_, classes=cc)[2].contiguous()
+        return J(W)[0]
+    rng = np.random.default_rng(1)
+    cen = torch.tensor(m.vertex_means(), device=dev)
+    dirs = {"random": torch.tensor(rng.standard_normal(U.shape), device=dev) * U.abs().mean(dim=1, keepdim=True),
+            "pulse": torch.zeros_like(U)}
+    dirs["pulse"][0] = torch.exp(-((cen - torch.tensor([0.75, 0.5, 0.5], device=dev)) ** 2).sum(1) / (2 * 0.08 ** 2))
+    fd_check = {}
+    for name, d in dirs.items():
+        fd = (traj(U + 1e-6 * d) - traj(U - 1e-6 * d)) / 2e-6
+        an = float((dJ * d).sum().item())
+        fd_check[name] = {"central_difference": fd, "adjoint": an, "rel": abs(fd - an) / abs(fd)}
     return {"workload": f"open unit cube, {n}^3 hexahedra cut into {m.n_cells} jittered tetrahedra, Gaussian density pulse ahead "
-                        f"of a planar Mach 2 shock, order 3 hybrid, HLLC, FP64, classes frozen",
+                        f"of a planar Mach 2 shock, order 3 hybrid, HLLC, Venkatakrishnan K = 5, FP64, classes frozen",
+            "fd_check": fd_check,
             "cells": int(m.n_cells), "steps": args.adjoint_steps, "objective": "sum |V| rho^2 after the steps",
             "J": Jv, "grad_norm": float(dJ.norm().item()), "classes_at_start": hist,
             "forward_plus_backward_s": total, "vjp_ms": vjp_ms, "residual_ms": res_ms,

@@ -79,6 +79,8 @@ extern "C" {
 #define HFV_SSPRK54 1
 #define HFV_BARTH_JESPERSEN 0
 #define HFV_VENKATAKRISHNAN 1
+#define HFV_CONSERVED 0
+#define HFV_CHARACTERISTIC 1
 
 /* cell classes written by the pipeline (Sec. 2.5; the paper's figures call
  * them Scheme 0 / 1 / 3 / -1) */
@@ -123,7 +125,10 @@ typedef struct {
     double stencil_factor;              /* M = stencil_factor * K(r, d); default 2 (Sec. 2.1) */
     int limiter;        /* MUSCL limiter: HFV_BARTH_JESPERSEN (default, Sec. 2.2) or
                            HFV_VENKATAKRISHNAN (the smooth limiter the paper runs with K = 5) */
-    int reserved;
+    int cweno_vars;     /* CWENOZ variables (Sec. 2.3 leaves the choice open): HFV_CONSERVED
+                           (default, component-wise) or HFV_CHARACTERISTIC (per face, projected
+                           with the eigenvectors of the flux Jacobian along its normal at the
+                           cell mean) */
     double venkat_k;    /* Venkatakrishnan threshold eps^2 = (K dx)^3, dx = |V|^(1/d); default 5 */
 } hfv_scheme_params;
 

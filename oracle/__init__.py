@@ -23,6 +23,7 @@ _lib = None
 FLUX = {"rusanov": 0, "hllc": 1, "hll": 2}
 SCHEME = {"hybrid": 0, "linear": 1, "cweno": 2, "muscl": 3}
 LIMITER = {"barth": 0, "venkatakrishnan": 1}
+CWENO_VARS = {"conserved": 0, "characteristic": 1}
 LIN, CW, MU, FIRST = 0, 1, 2, 3
 
 
@@ -42,7 +43,7 @@ class Params(C.Structure):
                 ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1p", C.c_double), ("cw_eps", C.c_double),
                 ("cw_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("pad", C.c_int), ("venkat_k", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double)]
 
 
 def default_params(**kw) -> dict:
@@ -51,7 +52,7 @@ def default_params(**kw) -> dict:
     Harten theta = 0.9, eps = 1e-14, deactivation (kappa dx)^n with kappa = 1, n = 1."""
     p = dict(order=3, flux="rusanov", scheme="hybrid", nad_vars=3, gamma=1.4, alpha_m=5e-3, beta_m=0.5,
              alpha_w=0.0, beta_w=0.0, kappa=1.0, n_exp=1.0, lambda1p=1e3, cw_eps=1e-3, cw_b=4.0,
-             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0, limiter="barth", pad=0, venkat_k=5.0)
+             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0, limiter="barth", cweno_vars="conserved", venkat_k=5.0)
     p.update(kw)
     return p
 
@@ -99,6 +100,7 @@ def _load():
         lib.or_rk54_step.argtypes = [C.c_void_p, P, D]
         lib.or_rk54_generic.argtypes = [I64, P, D, lib.RHS, C.c_void_p]
         lib.or_rk54_table.argtypes = [P, P]
+        lib.or_euler_eigen.argtypes = [C.c_int, D, P, P, P, P]
         lib.or_ops_built.restype = I64
         lib.or_ops_built.argtypes = [C.c_void_p]
         _lib = lib
@@ -111,6 +113,18 @@ def _p(a, ct=C.c_double):
 
 def _err(lib):
     return lib.or_last_error().decode()
+
+
+def euler_eigen(u, n, gamma: float = 1.4):
+    """Left (rows) and right (columns) eigenvectors of dF.n/dU at the
+    conserved state u along the unit normal n."""
+    lib = _load()
+    u = np.ascontiguousarray(u, np.float64)
+    d = u.size - 2
+    n = np.ascontiguousarray(n, np.float64)
+    L, R = np.zeros(d * 0 + (d + 2) ** 2), np.zeros((d + 2) ** 2)
+    lib.or_euler_eigen(d, gamma, _p(u), _p(n), _p(L), _p(R))
+    return L.reshape(d + 2, d + 2), R.reshape(d + 2, d + 2)
 
 
 def rk54_table():
@@ -228,6 +242,8 @@ class Scheme:
                 v = SCHEME[v] if isinstance(v, str) else v
             if k == "limiter":
                 v = LIMITER[v] if isinstance(v, str) else v
+            if k == "cweno_vars":
+                v = CWENO_VARS[v] if isinstance(v, str) else v
             setattr(cp, k, v)
         self._cp = cp
         self.h = self.lib.or_scheme_create(mesh.h, C.byref(cp))

@@ -495,7 +495,7 @@ typedef struct {
     double gamma, alpha_m, beta_m, alpha_w, beta_w, kappa, n_exp, lambda1p, cw_eps, cw_b, harten_theta, harten_eps;
     double stencil_factor;   /* M = stencil_factor * K(r,d) */
     int limiter;             /* MUSCL limiter: 0 Barth-Jespersen, 1 Venkatakrishnan */
-    int pad;
+    int cweno_vars;          /* CWENOZ in 0 conserved, 1 characteristic variables */
     double venkat_k;         /* Venkatakrishnan threshold eps^2 = (K dx)^3 */
 } or_params;
 
@@ -1045,13 +1045,25 @@ static void dir_coeffs(const or_scheme* s, const or_ops* o, const double* U, int
 }
 
 /* CWENOZ (Sec. 2.3) for variable v; also returns the weights and indicators */
+/* CWENOZ weights and polynomial (Sec. 2.3) of one variable from its p_opt
+ * coefficients aopt [N] and directional coefficients as [nf][d] */
+static void cweno_combine(or_scheme* s, or_ops* o, int64_t i, const double* aopt, double as[MAXNF][3],
+                          double* acw /*[N]*/, double* omega, double* SI);
+
 static void rec_cweno_var(or_scheme* s, or_ops* o, const double* U, int64_t i, int v, const double* aopt,
+                          double* acw /*[N]*/, double* omega, double* SI)
+{
+    int nf = n_faces_of(s, i);
+    double as[MAXNF][3];
+    for (int f = 0; f < nf; ++f) dir_coeffs(s, o, U, i, f, v, as[f]);
+    cweno_combine(s, o, i, aopt, as, acw, omega, SI);
+}
+
+static void cweno_combine(or_scheme* s, or_ops* o, int64_t i, const double* aopt, double as[MAXNF][3],
                           double* acw /*[N]*/, double* omega, double* SI)
 {
     int N = s->N, d = s->d, nf = n_faces_of(s, i), st = nf + 1;
     double lam1 = 1.0 - 1.0 / s->p.lambda1p, lams = (1.0 - lam1) / (st - 1);
-    double as[MAXNF][3];
-    for (int f = 0; f < nf; ++f) dir_coeffs(s, o, U, i, f, v, as[f]);
     /* p_1 = (p_opt - sum_s lambda_s p_s) / lambda_1 */
     double a1[128];
     for (int k = 0; k < N; ++k) {
@@ -1087,10 +1099,125 @@ static void rec_cweno_var(or_scheme* s, or_ops* o, const double* U, int64_t i, i
     }
 }
 
+/* Eigenvectors of the Euler flux Jacobian dF.n/dU at the state u (conserved
+ * variables, unit normal n): columns of R (right) and rows of L = R^-1
+ * (left), ordered acoustic (u.n - c), entropy, shear (one in 2D, two in 3D
+ * along t1, t2), acoustic (u.n + c).  Tangents: 2D t = (-n_y, n_x); 3D
+ * t1 = n x e_a / |n x e_a| with e_a the axis of the smallest |n_a|, t2 =
+ * n x t1. */
+void or_euler_eigen(int d, double gamma, const double* u, const double* n, double* L, double* R)
+{
+    const int nv = d + 2;
+    double vel[3] = {0, 0, 0}, q2 = 0.0, qn = 0.0;
+    for (int k = 0; k < d; ++k) { vel[k] = u[1 + k] / u[0]; q2 += vel[k] * vel[k]; qn += vel[k] * n[k]; }
+    const double p = (gamma - 1.0) * (u[d + 1] - 0.5 * u[0] * q2);
+    const double c = sqrt(gamma * p / u[0]), H = (u[d + 1] + p) / u[0];
+    double t[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int nt = d - 1;
+    if (d == 2) { t[0][0] = -n[1]; t[0][1] = n[0]; }
+    else {
+        int ax = 0;
+        for (int k = 1; k < 3; ++k) if (fabs(n[k]) < fabs(n[ax])) ax = k;
+        double e[3] = {0, 0, 0};
+        e[ax] = 1.0;
+        double a[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+        double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        for (int k = 0; k < 3; ++k) t[0][k] = a[k] / an;
+        t[1][0] = n[1] * t[0][2] - n[2] * t[0][1];
+        t[1][1] = n[2] * t[0][0] - n[0] * t[0][2];
+        t[1][2] = n[0] * t[0][1] - n[1] * t[0][0];
+    }
+    for (int k = 0; k < nv * nv; ++k) { L[k] = 0.0; R[k] = 0.0; }
+    /* right eigenvectors (column j of R at R[r * nv + j]) */
+    R[0 * nv + 0] = 1.0; R[0 * nv + 1] = 1.0; R[0 * nv + nv - 1] = 1.0;
+    for (int k = 0; k < d; ++k) {
+        R[(1 + k) * nv + 0] = vel[k] - c * n[k];
+        R[(1 + k) * nv + 1] = vel[k];
+        R[(1 + k) * nv + nv - 1] = vel[k] + c * n[k];
+    }
+    R[(d + 1) * nv + 0] = H - c * qn;
+    R[(d + 1) * nv + 1] = 0.5 * q2;
+    R[(d + 1) * nv + nv - 1] = H + c * qn;
+    for (int j = 0; j < nt; ++j) {
+        double ut = 0.0;
+        for (int k = 0; k < d; ++k) { R[(1 + k) * nv + 2 + j] = t[j][k]; ut += vel[k] * t[j][k]; }
+        R[(d + 1) * nv + 2 + j] = ut;
+    }
+    /* left eigenvectors (row i of L at L[i * nv + .]) */
+    const double b1 = (gamma - 1.0) / (c * c), b2 = 0.5 * b1 * q2;
+    L[0 * nv + 0] = 0.5 * (b2 + qn / c);
+    L[(nv - 1) * nv + 0] = 0.5 * (b2 - qn / c);
+    L[1 * nv + 0] = 1.0 - b2;
+    for (int k = 0; k < d; ++k) {
+        L[0 * nv + 1 + k] = 0.5 * (-b1 * vel[k] - n[k] / c);
+        L[(nv - 1) * nv + 1 + k] = 0.5 * (-b1 * vel[k] + n[k] / c);
+        L[1 * nv + 1 + k] = b1 * vel[k];
+    }
+    L[0 * nv + d + 1] = 0.5 * b1;
+    L[(nv - 1) * nv + d + 1] = 0.5 * b1;
+    L[1 * nv + d + 1] = -b1;
+    for (int j = 0; j < nt; ++j) {
+        double ut = 0.0;
+        for (int k = 0; k < d; ++k) { L[(2 + j) * nv + 1 + k] = t[j][k]; ut += vel[k] * t[j][k]; }
+        L[(2 + j) * nv + 0] = -ut;
+    }
+}
+
+/* CWENOZ in characteristic variables: for each face f of the cell, the
+ * p_opt and directional coefficients of every conserved variable are
+ * projected with the left eigenvectors of the Jacobian along the face's
+ * normal at the cell mean, each characteristic variable gets its own
+ * weights (Sec. 2.3), and the face's points are projected back with the
+ * right eigenvectors */
+static void rec_cweno_char(or_scheme* s, or_ops* o, const double* U, int64_t i, const double* a, double* V)
+{
+    int N = s->N, nv = s->nv, d = s->d, nf = n_faces_of(s, i);
+    double u0[5], as[5][MAXNF][3];
+    get_state(s, U, i, u0);
+    for (int v = 0; v < nv; ++v)
+        for (int f = 0; f < nf; ++f) dir_coeffs(s, o, U, i, f, v, as[v][f]);
+    for (int f = 0; f < nf; ++f) {
+        double pts[3 * 64], nrm[3], L[25], R[25];
+        cell_face_points(s, i, f, pts, nrm);
+        or_euler_eigen(d, s->p.gamma, u0, nrm, L, R);
+        double acw[5][128];
+        for (int w = 0; w < nv; ++w) {
+            double aw[128], asw[MAXNF][3], om[MAXNF + 1], SI[MAXNF + 1];
+            for (int k = 0; k < N; ++k) {
+                double sum = 0.0;
+                for (int v = 0; v < nv; ++v) sum += L[w * nv + v] * a[v * N + k];
+                aw[k] = sum;
+            }
+            for (int g = 0; g < nf; ++g)
+                for (int k = 0; k < d; ++k) {
+                    double sum = 0.0;
+                    for (int v = 0; v < nv; ++v) sum += L[w * nv + v] * as[v][g][k];
+                    asw[g][k] = sum;
+                }
+            cweno_combine(s, o, i, aw, asw, acw[w], om, SI);
+        }
+        for (int a0 = 0; a0 < s->nfp; ++a0) {
+            const int q = f * s->nfp + a0;
+            double cw[5];
+            for (int w = 0; w < nv; ++w) {
+                double sum = 0.0;
+                for (int k = 0; k < N; ++k) sum += o->Phi[q * N + k] * acw[w][k];
+                cw[w] = sum;
+            }
+            for (int v = 0; v < nv; ++v) {
+                double sum = u0[v];
+                for (int w = 0; w < nv; ++w) sum += R[v * nv + w] * cw[w];
+                V[q * nv + v] = sum;
+            }
+        }
+    }
+}
+
 static void rec_cweno(or_scheme* s, or_ops* o, const double* U, int64_t i, const double* a, double* V)
 {
     int N = s->N, nv = s->nv, Q = Q_of(s, i);
     double u0[5], acw[128], om[MAXNF + 1], SI[MAXNF + 1];
+    if (s->p.cweno_vars == 1) { rec_cweno_char(s, o, U, i, a, V); return; }
     get_state(s, U, i, u0);
     for (int v = 0; v < nv; ++v) {
         rec_cweno_var(s, o, U, i, v, &a[v * N], acw, om, SI);

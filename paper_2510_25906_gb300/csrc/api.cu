@@ -101,6 +101,7 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
         (p->precision != HFV_FP64 && p->precision != HFV_FP32) || (p->nad_vars & ~7) ||
         (p->time_scheme != HFV_SSPRK3 && p->time_scheme != HFV_SSPRK54) ||
         (p->limiter != HFV_BARTH_JESPERSEN && p->limiter != HFV_VENKATAKRISHNAN) || !(p->venkat_k >= 0.0) ||
+        (p->cweno_vars != HFV_CONSERVED && p->cweno_vars != HFV_CHARACTERISTIC) ||
         !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0)) {
         set_error("hfv_scheme_create: parameter out of range");
         return HFV_ERR_ARG;
@@ -205,6 +206,10 @@ extern "C" int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* c
 {
     if (!s || !U || !cls || !lam || !g) { set_error("hfv_residual_vjp: NULL argument"); return HFV_ERR_ARG; }
     if (s->p.precision != HFV_FP64) { set_error("hfv_residual_vjp: FP64 schemes only"); return HFV_ERR_ARG; }
+    if (s->p.cweno_vars != HFV_CONSERVED) {
+        set_error("hfv_residual_vjp: CWENOZ in conserved variables only");
+        return HFV_ERR_ARG;
+    }
     return launch_vjp(s, U, cls, lam, g, stream);
 }
 

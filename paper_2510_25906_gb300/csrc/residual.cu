@@ -18,577 +18,15 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <utility>
 
+#include "device_common.cuh"
 #include "hfv_internal.h"
+#include "k_linear.cuh"
 #include "kernels.cuh"
 #include "tma.cuh"
 
 namespace hfv {
-
-template <class T>
-__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
-template <class T>
-__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <class T>
-__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
-
-__device__ __forceinline__ float tpow(float x, float e) { return powf(x, e); }
-__device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
-
-// detector quantity of kind k: 0 density, 1 pressure, 2.. conserved variable k-1
-template <class T, int D>
-__device__ __forceinline__ T nad_value(const T* u, int k, T g)
-{
-    if (k == 0) return u[0];
-    if (k == 1) return pressure<T, D>(u, g);
-    return u[k - 1];
-}
-
-// ---------------------------------------------------------------------------
-// cell groups: G lanes (a power of two <= 32, inside one warp) own one cell;
-// lane q handles face point q.  Reductions stay inside the group.
-// ---------------------------------------------------------------------------
-template <int G>
-struct Grp {
-    unsigned mask;
-    int lane;
-    __device__ __forceinline__ Grp()
-    {
-        lane = threadIdx.x & (G - 1);
-        const int base = (threadIdx.x & 31) & ~(G - 1);
-        mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << base);
-    }
-    template <class T>
-    __device__ __forceinline__ T max(T v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w > v ? w : v; }
-        return v;
-    }
-    template <class T>
-    __device__ __forceinline__ T min(T v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) { T w = __shfl_xor_sync(mask, v, o); v = w < v ? w : v; }
-        return v;
-    }
-
-    template <class T>
-    __device__ __forceinline__ T sum(T v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
-        return v;
-    }
-    __device__ __forceinline__ bool any(bool b) const { return (__ballot_sync(mask, b) & mask) != 0u; }
-    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
-};
-
-// contiguous row of M values with the widest aligned vector loads (rows start
-// at (c * QMAX + q) * M elements: 16-byte aligned when M * sizeof(T) % 16 == 0)
-template <class T, int M>
-__device__ __forceinline__ void load_row(const T* __restrict__ p, T (&r)[M])
-{
-    if constexpr (sizeof(T) == 4 && M % 4 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 4) {
-            float4 v = __ldg(reinterpret_cast<const float4*>(p + m));
-            r[m] = v.x; r[m + 1] = v.y; r[m + 2] = v.z; r[m + 3] = v.w;
-        }
-    } else if constexpr (sizeof(T) == 4 && M % 2 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 2) {
-            float2 v = __ldg(reinterpret_cast<const float2*>(p + m));
-            r[m] = v.x; r[m + 1] = v.y;
-        }
-    } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 2) {
-            double2 v = __ldg(reinterpret_cast<const double2*>(p + m));
-            r[m] = v.x; r[m + 1] = v.y;
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) r[m] = __ldg(p + m);
-    }
-}
-
-template <class T, int M>
-__device__ __forceinline__ void load_row_smem(const T* p, T (&r)[M])
-{
-    if constexpr (sizeof(T) == 4 && M % 4 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 4) {
-            float4 v = *reinterpret_cast<const float4*>(p + m);
-            r[m] = v.x; r[m + 1] = v.y; r[m + 2] = v.z; r[m + 3] = v.w;
-        }
-    } else if constexpr (sizeof(T) == 4 && M % 2 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 2) {
-            float2 v = *reinterpret_cast<const float2*>(p + m);
-            r[m] = v.x; r[m + 1] = v.y;
-        }
-    } else if constexpr (sizeof(T) == 8 && M % 2 == 0) {
-#pragma unroll
-        for (int m = 0; m < M; m += 2) {
-            double2 v = *reinterpret_cast<const double2*>(p + m);
-            r[m] = v.x; r[m + 1] = v.y;
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < M; ++m) r[m] = p[m];
-    }
-}
-
-template <class T, int NV>
-__device__ __forceinline__ void store_state(T* __restrict__ p, const T (&w)[NV])
-{
-    if constexpr (sizeof(T) == 4 && NV == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(w[0], w[1], w[2], w[3]);
-    } else if constexpr (sizeof(T) == 8 && NV == 4) {
-        reinterpret_cast<double2*>(p)[0] = make_double2(w[0], w[1]);
-        reinterpret_cast<double2*>(p)[1] = make_double2(w[2], w[3]);
-    } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) p[v] = w[v];
-    }
-}
-
-template <class T, int NV>
-__device__ __forceinline__ void load_state(const T* __restrict__ p, T (&w)[NV])
-{
-    if constexpr (sizeof(T) == 4 && NV == 4) {
-        float4 v = *reinterpret_cast<const float4*>(p);
-        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
-    } else if constexpr (sizeof(T) == 8 && NV == 4) {
-        double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-        w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
-    } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) w[v] = p[v];
-    }
-}
-
-// cell-major state rows: P = 4 values (2D) or 8 (3D, 5 used), 16-byte aligned
-template <int NV>
-struct AoSP {
-    static constexpr int P = NV == 4 ? 4 : 8;
-};
-
-template <class T, int NV>
-__device__ __forceinline__ void load_cell(const T* __restrict__ UA, int64_t c, T (&u)[NV])
-{
-    const T* q = UA + c * AoSP<NV>::P;
-    if constexpr (sizeof(T) == 4) {
-        float4 a = __ldg(reinterpret_cast<const float4*>(q));
-        u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
-    } else {
-        double2 a = __ldg(reinterpret_cast<const double2*>(q)), b = __ldg(reinterpret_cast<const double2*>(q) + 1);
-        u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y;
-    }
-    if constexpr (NV == 5) u[4] = __ldg(q + 4);
-}
-
-// K1: persistent, warp-specialised.  Tiles of NG consecutive cells: a
-// producer warp streams each tile's contiguous L blocks and stencil ids into a
-// ring of shared-memory stages with bulk copies (TMA engine, mbarrier
-// completion); eight consumer warps hold NG groups of G lanes, one group per
-// cell.  A group gathers the M stencil states into rows of U_m - U_0, lane l
-// forms the candidate at face points l, l + G, ... (PPL of them) from their
-// rows of L, and the group runs the detector (bounds from the first stencil
-// layer = the face neighbours) and the Harten test.
-//
-// L block of a cell with Q face points: columns in chunks of W = 16 bytes /
-// sizeof(T); chunk j holds [Q][W] (the W values of every row for columns
-// jW .. jW+W-1), a last partial chunk of width M mod W holds [Q][M mod W].
-// One 16-byte load gives a lane W columns of its row, and the eight lanes of
-// a group read 128 contiguous bytes.
-template <class C, class T>
-struct K1Shape {
-    // 2D orders 2-4: four lanes per cell (one per face neighbour) with up to
-    // two face points each, so that the per-cell work of the detector and of
-    // the Harten test is shared by eight cells per warp instruction; one
-    // face point per lane elsewhere (more points per lane in 3D would need
-    // more cells per tile than a ring of stages of L holds: 3.8 KB of L per
-    // hexahedron at order 4)
-    static constexpr bool SMALL = C::D == 2 && C::QMAX <= 8;
-    static constexpr int PPL = SMALL ? C::QMAX / 4 : 1;
-    static constexpr int G = SMALL ? 4 : GroupSize<C::QMAX>::value;   // lanes per cell
-    static constexpr int SLOT = C::NFMAX <= 4 ? 4 : 8;       // lanes of one face-neighbour reduction
-    // lanes past the first SLOT take the bounds from the group's first lane
-    static constexpr bool NB_BCAST = G > SLOT;
-    static constexpr int CONSUMERS = 256;                    // 8 warps
-    static constexpr int NG = CONSUMERS / G;                 // cells per tile
-    static constexpr int PER16 = 16 / (int)sizeof(T);
-    static constexpr int LMAX = (C::QMAX * C::M + PER16 - 1) / PER16 * PER16;  // elements per cell block
-    static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
-    static constexpr int SBYTES = NG * C::M * 4;
-    static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
-    // rows of U_m - U_0 per cell: [M][4] and, with five variables, [M] of the
-    // fifth; cells 16 bytes apart modulo 128 so that the four cells of a warp
-    // read different banks
-    static constexpr int DU4 = C::M * 4 * (int)sizeof(T);
-    static constexpr int DU5 = C::NV == 5 ? (C::M * (int)sizeof(T) + 15) / 16 * 16 : 0;
-    static constexpr int CSTRIDE = (DU4 + DU5 + 127) / 128 * 128 + 16;
-    static constexpr int SU = NG * CSTRIDE;
-    // resident CTAs per SM aimed for (register and shared-memory budget)
-    static constexpr int MINB = sizeof(T) == 8 ? 1 : 2;
-    static constexpr int BUDGET = 227 * 1024 / MINB - (SU + 127) / 128 * 128 - 1024;
-    static constexpr int FIT = BUDGET / STAGE;
-    static constexpr int STAGES = FIT >= 4 ? 4 : FIT >= 3 ? 3 : 2;
-    static constexpr int SMEM = STAGES * STAGE + (SU + 127) / 128 * 128 + 2 * STAGES * 8;
-    static constexpr int THREADS = CONSUMERS + 32;
-    static_assert(SMEM <= 227 * 1024, "staging ring exceeds shared memory");
-};
-
-// min / max over the SLOT aligned lanes of a segment (xor offsets below SLOT
-// stay inside it).  The whole warp takes part (full mask): callers keep the
-// control flow warp-uniform.  Operands are finite or +-inf.
-__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
-__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
-
-template <int SLOT, class T>
-__device__ __forceinline__ T seg_min(T v)
-{
-#pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-template <int SLOT, class T>
-__device__ __forceinline__ T seg_max(T v)
-{
-#pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-template <class C, class T>
-__global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
-{
-    using S = K1Shape<C, T>;
-    constexpr int M = C::M, NV = C::NV, D = C::D, G = S::G, NG = S::NG, ST = S::STAGES, PPL = S::PPL;
-    constexpr int SLOT = S::SLOT, W = S::PER16, M4 = M / W * W, TW = M - M4;
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char* sU = smem + ST * S::STAGE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + ST * S::STAGE + (S::SU + 127) / 128 * 128);
-    uint64_t* empty = full + ST;
-    const int64_t nc = p.nc;
-    const int64_t ntiles = (nc + NG - 1) / NG;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < ST; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], S::CONSUMERS / 32);
-        }
-        mbar_init_fence();
-    }
-    __syncthreads();
-
-    if (threadIdx.x >= S::CONSUMERS) {
-        // ---------------- producer warp ----------------
-        if (threadIdx.x == S::CONSUMERS) {
-            int k = 0;
-            bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
-                const int s = k % ST;
-                if (k >= ST && !(ok = mbar_wait(&empty[s], ((k / ST) - 1) & 1))) break;
-                const int64_t c0 = tile * NG;
-                const int64_t lb = p.loff[c0], le = p.loff[c0 + NG];
-                const uint32_t lbytes = (uint32_t)((le - lb) * (int64_t)sizeof(T));
-                unsigned char* stage = smem + s * S::STAGE;
-                mbar_arrive_expect_tx(&full[s], lbytes + S::SBYTES);
-                if (lbytes) bulk_g2s(stage, p.L + lb, lbytes, &full[s]);
-                bulk_g2s(stage + S::LBYTES, p.sten + c0 * M, S::SBYTES, &full[s]);
-            }
-            if (!ok) atomicOr(p.status, 4);
-            // every issued copy has landed before the CTA may exit
-            const int issued = k;
-            for (int j = issued - ST > 0 ? issued - ST : 0; j < issued; ++j)
-                if (!mbar_wait(&full[j % ST], (j / ST) & 1)) { atomicOr(p.status, 4); break; }
-        }
-        return;
-    }
-
-    // ---------------- consumer warps ----------------
-    // Software pipeline: while tile k is computed from shared memory, the
-    // stencil states of tile k+1 are already in flight into registers.
-    constexpr int MI = (M + G - 1) / G;    // stencil cells per lane
-    const Grp<G> grp;
-    const int gi = threadIdx.x / G, lane = grp.lane;
-    T* dU4 = reinterpret_cast<T*>(sU + gi * S::CSTRIDE);          // [M][4]
-    T* dU5 = reinterpret_cast<T*>(sU + gi * S::CSTRIDE + S::DU4); // [M] (five variables)
-    T nu[MI][NV];                          // in-flight stencil states of the next tile
-    T nuc[NV];                             // the cell
-    int nnfv = 0;
-    int64_t nlrel = 0;
-    T nthr = T(0);
-    auto fetch = [&](int64_t tile_f, int stage_f) {
-        const int64_t cf = tile_f * NG + gi;
-        if (cf >= nc) {
-            // with several cells per warp, a group past the last cell runs on
-            // a quiet dummy cell with no faces (Q = n1 = 0) and stores
-            // nothing: the warp stays converged (a whole warp past the last
-            // cell skips the tile)
-            if constexpr (G < 32) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    nuc[v] = v == 0 ? T(1) : v == NV - 1 ? T(2.5) : T(0);
-#pragma unroll
-                    for (int i = 0; i < MI; ++i) nu[i][v] = nuc[v];
-                }
-                nnfv = 0;
-                nthr = T(0);
-                nlrel = 0;
-            }
-            return;
-        }
-        const int32_t* st = reinterpret_cast<const int32_t*>(smem + stage_f * S::STAGE + S::LBYTES) + gi * M;
-#pragma unroll
-        for (int i = 0; i < MI; ++i) {
-            const int m = lane + i * G;
-            if (m < M) load_cell<T, NV>(p.UA, st[m], nu[i]);
-        }
-        load_cell<T, NV>(p.UA, cf, nuc);
-        nnfv = p.nfc[cf];
-        nthr = p.dxthr[cf];
-        nlrel = p.loff[cf] - p.loff[tile_f * NG];
-    };
-    int k = 0;
-    int64_t tile = blockIdx.x;
-    bool alive = true;
-    if (tile < ntiles) {
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[0], 0))) {
-            if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
-            alive = false;
-        } else {
-            fetch(tile, 0);
-        }
-    }
-    while (alive && tile < ntiles) {
-        const int s = k % ST;
-        const int64_t c = tile * NG + gi;
-        T uc[NV], nb[NV];                  // the cell's state; face neighbour `lane` (lane < SLOT)
-        const int nfv = nnfv;
-        const int64_t lrel = nlrel;
-        const T thr = nthr;
-        const bool valid = c < nc;
-        const bool run = G < 32 || valid;   // warp-uniform
-        if (run) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                uc[v] = nuc[v];
-                nb[v] = lane < M ? nu[0][v] : uc[v];
-            }
-#pragma unroll
-            for (int i = 0; i < MI; ++i) {
-                const int m = lane + i * G;
-                if (m < M) {
-                    T row[NV];
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) row[v] = nu[i][v] - uc[v];
-                    if constexpr (sizeof(T) == 4) {
-                        *reinterpret_cast<float4*>(dU4 + m * 4) = make_float4(row[0], row[1], row[2], row[3]);
-                    } else {
-                        *reinterpret_cast<double2*>(dU4 + m * 4) = make_double2(row[0], row[1]);
-                        *reinterpret_cast<double2*>(dU4 + m * 4 + 2) = make_double2(row[2], row[3]);
-                    }
-                    if constexpr (NV == 5) dU5[m] = row[4];
-                }
-            }
-        }
-        const int64_t next = tile + gridDim.x;
-        if (next < ntiles) {
-            const int s1 = (k + 1) % ST;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s1], ((k + 1) / ST) & 1))) {
-                if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
-                alive = false;
-            } else {
-                fetch(next, s1);
-            }
-        }
-        const unsigned char* stage = smem + s * S::STAGE;
-        if (run) {
-            const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * C::NFP;
-            T w[PPL][NV];
-#pragma unroll
-            for (int j = 0; j < PPL; ++j)
-#pragma unroll
-                for (int v = 0; v < NV; ++v) w[j][v] = uc[v];
-            __syncwarp();
-            const T* lb = reinterpret_cast<const T*>(stage) + lrel;
-            // candidate: w = U_0 + sum_m L_qm (U_m - U_0), one chunk of W
-            // columns of L per 16-byte load
-            if constexpr (sizeof(T) == 4) {
-                float2 w01[PPL], w23[PPL];
-#pragma unroll
-                for (int j = 0; j < PPL; ++j) { w01[j] = make_float2(w[j][0], w[j][1]); w23[j] = make_float2(w[j][2], w[j][3]); }
-#pragma unroll
-                for (int m0 = 0; m0 < M4; m0 += 4) {
-                    float lv[PPL][4];
-#pragma unroll
-                    for (int j = 0; j < PPL; ++j) {
-                        const int q = lane + j * G;
-                        if (q < Q) {
-                            const float4 t = *reinterpret_cast<const float4*>(lb + m0 * Q + q * 4);
-                            lv[j][0] = t.x; lv[j][1] = t.y; lv[j][2] = t.z; lv[j][3] = t.w;
-                        } else {
-                            lv[j][0] = lv[j][1] = lv[j][2] = lv[j][3] = 0.0f;
-                        }
-                    }
-                    float4 e5 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    if constexpr (NV == 5) e5 = *reinterpret_cast<const float4*>(dU5 + m0);
-                    const float e5a[4] = {e5.x, e5.y, e5.z, e5.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 d = *reinterpret_cast<const float4*>(dU4 + (m0 + i) * 4);
-                        const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
-#pragma unroll
-                        for (int j = 0; j < PPL; ++j) {
-                            const float2 l2 = make_float2(lv[j][i], lv[j][i]);
-                            w01[j] = __ffma2_rn(l2, d01, w01[j]);
-                            w23[j] = __ffma2_rn(l2, d23, w23[j]);
-                            if constexpr (NV == 5) w[j][4] = fmaf(lv[j][i], e5a[i], w[j][4]);
-                        }
-                    }
-                }
-                if constexpr (TW == 2) {
-                    float lt[PPL][2];
-#pragma unroll
-                    for (int j = 0; j < PPL; ++j) {
-                        const int q = lane + j * G;
-                        if (q < Q) {
-                            const float2 t = *reinterpret_cast<const float2*>(lb + M4 * Q + q * 2);
-                            lt[j][0] = t.x; lt[j][1] = t.y;
-                        } else {
-                            lt[j][0] = lt[j][1] = 0.0f;
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const float4 d = *reinterpret_cast<const float4*>(dU4 + (M4 + i) * 4);
-                        const float2 d01 = make_float2(d.x, d.y), d23 = make_float2(d.z, d.w);
-#pragma unroll
-                        for (int j = 0; j < PPL; ++j) {
-                            const float2 l2 = make_float2(lt[j][i], lt[j][i]);
-                            w01[j] = __ffma2_rn(l2, d01, w01[j]);
-                            w23[j] = __ffma2_rn(l2, d23, w23[j]);
-                            if constexpr (NV == 5) w[j][4] = fmaf(lt[j][i], dU5[M4 + i], w[j][4]);
-                        }
-                    }
-                }
-                static_assert(TW == 0 || TW == 2, "FP32 stencil sizes are even");
-#pragma unroll
-                for (int j = 0; j < PPL; ++j) { w[j][0] = w01[j].x; w[j][1] = w01[j].y; w[j][2] = w23[j].x; w[j][3] = w23[j].y; }
-            } else {
-                static_assert(sizeof(T) == 4 || TW == 0, "FP64 stencil sizes are even");
-#pragma unroll 2
-                for (int m0 = 0; m0 < M; m0 += 2) {
-                    double lv[PPL][2];
-#pragma unroll
-                    for (int j = 0; j < PPL; ++j) {
-                        const int q = lane + j * G;
-                        if (q < Q) {
-                            const double2 t = *reinterpret_cast<const double2*>(lb + m0 * Q + q * 2);
-                            lv[j][0] = t.x; lv[j][1] = t.y;
-                        } else {
-                            lv[j][0] = lv[j][1] = 0.0;
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const double2 a = *reinterpret_cast<const double2*>(dU4 + (m0 + i) * 4);
-                        const double2 b = *reinterpret_cast<const double2*>(dU4 + (m0 + i) * 4 + 2);
-                        const double d[4] = {a.x, a.y, b.x, b.y};
-#pragma unroll
-                        for (int j = 0; j < PPL; ++j) {
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) w[j][v] = fma(lv[j][i], d[v], w[j][v]);
-                            if constexpr (NV == 5) w[j][4] = fma(lv[j][i], dU5[m0 + i], w[j][4]);
-                        }
-                    }
-                }
-            }
-            const int64_t q0 = c * C::QMAX;
-            const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
-            if (valid && lane == 0 && !(rb > T(0) && pb > T(0))) atomicOr(p.status, 1);
-            // Harten test of the candidate at the lane's points
-            const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
-            T pw[PPL];
-            bool fail = false;
-#pragma unroll
-            for (int j = 0; j < PPL; ++j) {
-                const int q = lane + j * G;
-                pw[j] = pressure<T, D>(w[j], p.gamma);
-                if (q < Q) {
-                    store_state<T, NV>(p.FS + (q0 + q) * NV, w[j]);
-                    fail = fail || !(tabs(w[j][0] - rb) <= rlim) || !(tabs(pw[j] - pb) <= plim);
-                }
-            }
-            int cl = CLS_LIN;
-            if (!p.forced && p.scheme == HFV_HYBRID) {
-                // detector: lane l < SLOT takes face neighbour l for the
-                // bounds, every lane its own face points for the classification
-                const bool has = lane < n1;
-                const int src = (threadIdx.x & 31) & ~(G - 1);   // the group's first lane
-                const bool det = n1 > 0;
-                const T pn = pressure<T, D>(nb, p.gamma);
-                const T sg = p.beta_w > T(0) ? T(1) : (p.beta_w < T(0) ? T(-1) : T(0));
-#pragma unroll
-                for (int kind = 0; kind < NV + 1; ++kind) {
-                    const bool use = kind == 0 ? (p.nad_vars & 1) : kind == 1 ? (p.nad_vars & 2) : (p.nad_vars & 4);
-                    if (!use) continue;
-                    const T qi = kind == 0 ? rb : kind == 1 ? pb : uc[kind - 1];
-                    const T qn = kind == 0 ? nb[0] : kind == 1 ? pn : nb[kind - 1];
-                    const T qj = has ? qn : qi;
-                    const T dd = tabs(qj - qi);
-                    T lo = seg_min<SLOT>(qj), hi = seg_max<SLOT>(qj);
-                    T dlo = seg_min<SLOT>(has ? dd : T(INFINITY));
-                    T dhi = seg_max<SLOT>(has ? dd : T(-INFINITY));
-                    if constexpr (S::NB_BCAST) {
-                        lo = __shfl_sync(0xffffffffu, lo, src);
-                        hi = __shfl_sync(0xffffffffu, hi, src);
-                        dlo = __shfl_sync(0xffffffffu, dlo, src);
-                        dhi = __shfl_sync(0xffffffffu, dhi, src);
-                    }
-                    // deactivated (smooth) unless the neighbour differences spread by thr
-                    if (det && !(dhi - dlo < thr)) {
-                        const T range = hi - lo;
-                        const T dm = tmax(p.alpha_m, p.beta_m * range);
-                        const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
-#pragma unroll
-                        for (int j = 0; j < PPL; ++j) {
-                            const int q = lane + j * G;
-                            if (q < Q) {
-                                const T x = kind == 0 ? w[j][0] : kind == 1 ? pw[j] : w[j][kind - 1];
-                                int kc;
-                                if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
-                                else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
-                                else kc = CLS_CW;
-                                cl = kc > cl ? kc : cl;
-                            }
-                        }
-                    }
-                }
-            }
-            const unsigned gbits = grp.mask;
-            const bool hfail = (__ballot_sync(0xffffffffu, fail) & gbits) != 0u;
-            const bool any_mu = (__ballot_sync(0xffffffffu, cl == CLS_MU) & gbits) != 0u;
-            const bool any_cw = (__ballot_sync(0xffffffffu, cl == CLS_CW) & gbits) != 0u;
-            if (valid && lane == 0) {
-                uint8_t out;
-                if (p.forced) out = p.forced_cls[c];
-                else if (p.scheme == HFV_HYBRID) out = any_mu ? CLS_MU : any_cw ? CLS_CW : CLS_LIN;
-                else out = p.scheme == HFV_PURE_LINEAR ? CLS_LIN : p.scheme == HFV_PURE_CWENOZ ? CLS_CW : CLS_MU;
-                p.raw[c] = out | (hfail ? HARTEN_FAIL : 0);
-            }
-        }
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
-        ++k;
-        tile = next;
-    }
-}
 
 // a first-order cell's face points all carry its cell mean
 template <class T>
@@ -609,6 +47,7 @@ __device__ __forceinline__ void write_mean(const KParams<T>& p, int64_t c)
 template <class T>
 __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
 {
+    pdl_wait();
     __shared__ int sc[2][8];
     const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
     int t = 255;
@@ -649,6 +88,7 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
 // shuffles); totals to counts[0..1]
 __global__ void __launch_bounds__(1024) k_scan(int32_t* bcount, int nblocks, int32_t* counts)
 {
+    pdl_wait();
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int q = 0; q < 2; ++q) {
@@ -692,6 +132,7 @@ __global__ void __launch_bounds__(1024) k_scan(int32_t* bcount, int nblocks, int
 __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls, int64_t nc, int32_t* bcount,
                                                  int nblocks, int32_t* queue, int32_t* counts, int fold)
 {
+    pdl_wait();
     __shared__ int s[2][8];
     __shared__ int base[2];
     __shared__ int red[2][8];
@@ -736,33 +177,175 @@ __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls
 // K3: CWENOZ on the CWENOZ queue, one group per queued cell (Sec. 2.3).
 // Lanes share the stencil gather; lane k forms coefficient k of p_opt;
 // lane (f, k) forms the directional degree-1 coefficients; lane v forms the
-// indicators and weights of variable v; lane q writes face point q.
-template <class C, class T>
+// indicators and weights of variable v; lane q writes face point q.  With
+// CHAR the variables are characteristic per face: lane f forms the face's
+// eigenvectors, lane (f, w) the weights of characteristic variable w there.
+template <class C, class T, bool CHAR>
 __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, unsigned nbl);
 template <class C, class T>
 __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, unsigned nbl);
 
 // K3 + K4 in one launch: the first `split` blocks work through the CWENOZ
 // queue, the others through the MUSCL queue (no divergence between them)
-template <class C, class T>
+template <class C, class T, bool CHAR>
 __global__ void __launch_bounds__(128) k_nonlinear(KParams<T> p, unsigned split)
 {
-    if (blockIdx.x < split) cweno_part<C, T>(p, blockIdx.x, split);
+    pdl_wait();
+    if (blockIdx.x < split) cweno_part<C, T, CHAR>(p, blockIdx.x, split);
     else muscl_part<C, T>(p, blockIdx.x - split, gridDim.x - split);
 }
 
+// the CWENOZ combination of one variable from its p_opt coefficients a[N]
+// and directional coefficients s[nf][D]: omega_1 / lambda_1 in c0 and the
+// degree-1 part sum_s (omega_s - omega_1 lambda_s / lambda_1) p_s in g[D]
+//   p_1 = (p_opt - sum_s lambda_s p_s) / lambda_1, SI = a^T OI a,
+//   tau = (sum_s |SI_s - SI_1| / nf)^b, w_s = lambda_s (1 + tau / (eps + SI_s))
 template <class C, class T>
+__device__ __forceinline__ void cweno_weights(const KParams<T>& p, const T* OI, int nf, const T (&a)[C::N],
+                                              const T (&s)[6][C::D], T& c0, T (&g)[C::D])
+{
+    constexpr int N = C::N, D = C::D;
+    const T lam1 = p.lam1, lams = (T(1) - lam1) / T(nf);
+    T sumlin[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s0 = T(0);
+        for (int f = 0; f < nf; ++f) s0 += s[f][k];
+        sumlin[k] = s0;
+    }
+    T a1[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) a1[k] = (a[k] - (k < D ? lams * sumlin[k < D ? k : 0] : T(0))) / lam1;
+    T si1 = T(0);
+    {
+        int o = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            T t = OI[o++] * a1[k];
+#pragma unroll
+            for (int l = k + 1; l < N; ++l) t += T(2) * OI[o++] * a1[l];
+            si1 += a1[k] * t;
+        }
+    }
+    T sis[6], tsum = T(0);
+    for (int f = 0; f < nf; ++f) {
+        T s0 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int o = k * N - k * (k - 1) / 2;
+            T t = OI[o] * s[f][k];
+#pragma unroll
+            for (int l = k + 1; l < D; ++l) t += T(2) * OI[o + (l - k)] * s[f][l];
+            s0 += s[f][k] * t;
+        }
+        sis[f] = s0;
+        tsum += tabs(s0 - si1);
+    }
+    const T tau = tpow(tsum / T(nf), p.b_cw);
+    const T w1 = lam1 * (T(1) + tau / (p.eps_cw + si1));
+    T wsum = w1, ws[6];
+    for (int f = 0; f < nf; ++f) {
+        ws[f] = lams * (T(1) + tau / (p.eps_cw + sis[f]));
+        wsum += ws[f];
+    }
+    const T om1 = w1 / wsum;
+    // p_cweno = (omega_1/lambda_1) p_opt + sum_s (omega_s - omega_1 lambda_s / lambda_1) p_s
+    c0 = om1 / lam1;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T gk = T(0);
+        for (int f = 0; f < nf; ++f) gk += (ws[f] / wsum - om1 * lams / lam1) * s[f][k];
+        g[k] = gk;
+    }
+}
+
+// eigenvectors of the Euler flux Jacobian dF.n/dU at the conserved state u
+// along the unit normal n: R columns, L = R^-1 rows, ordered u.n - c,
+// entropy, shear (t; in 3D t1, t2), u.n + c.  2D t = (-n_y, n_x); 3D t1 =
+// n x e_a / |n x e_a| for the axis a of the smallest |n_a|, t2 = n x t1.
+template <class T, int D>
+__device__ __forceinline__ void euler_eigenvectors(const T* u, const T* n, T g, T (*L)[D + 2], T (*R)[D + 2])
+{
+    constexpr int NV = D + 2;
+    T vel[3] = {T(0), T(0), T(0)}, q2 = T(0), qn = T(0);
+    const T ir = T(1) / u[0];
+#pragma unroll
+    for (int k = 0; k < D; ++k) { vel[k] = u[1 + k] * ir; q2 += vel[k] * vel[k]; qn += vel[k] * n[k]; }
+    const T pr = (g - T(1)) * (u[D + 1] - T(0.5) * u[0] * q2);
+    const T c = tsqrt<T>(g * pr * ir), H = (u[D + 1] + pr) * ir;
+    T t[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+    if (D == 2) {
+        t[0][0] = -n[1];
+        t[0][1] = n[0];
+    } else {
+        int ax = 0;
+        for (int k = 1; k < 3; ++k)
+            if (tabs(n[k]) < tabs(n[ax])) ax = k;
+        T e[3] = {T(0), T(0), T(0)};
+        e[ax] = T(1);
+        T a[3] = {n[1] * e[2] - n[2] * e[1], n[2] * e[0] - n[0] * e[2], n[0] * e[1] - n[1] * e[0]};
+        const T an = tsqrt<T>(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+        for (int k = 0; k < 3; ++k) t[0][k] = a[k] / an;
+        t[1][0] = n[1] * t[0][2] - n[2] * t[0][1];
+        t[1][1] = n[2] * t[0][0] - n[0] * t[0][2];
+        t[1][2] = n[0] * t[0][1] - n[1] * t[0][0];
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) { L[i][j] = T(0); R[i][j] = T(0); }
+    R[0][0] = T(1); R[0][1] = T(1); R[0][NV - 1] = T(1);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        R[1 + k][0] = vel[k] - c * n[k];
+        R[1 + k][1] = vel[k];
+        R[1 + k][NV - 1] = vel[k] + c * n[k];
+    }
+    R[D + 1][0] = H - c * qn;
+    R[D + 1][1] = T(0.5) * q2;
+    R[D + 1][NV - 1] = H + c * qn;
+    const T b1 = (g - T(1)) / (c * c), b2 = T(0.5) * b1 * q2;
+    L[0][0] = T(0.5) * (b2 + qn / c);
+    L[NV - 1][0] = T(0.5) * (b2 - qn / c);
+    L[1][0] = T(1) - b2;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        L[0][1 + k] = T(0.5) * (-b1 * vel[k] - n[k] / c);
+        L[NV - 1][1 + k] = T(0.5) * (-b1 * vel[k] + n[k] / c);
+        L[1][1 + k] = b1 * vel[k];
+    }
+    L[0][D + 1] = T(0.5) * b1;
+    L[NV - 1][D + 1] = T(0.5) * b1;
+    L[1][D + 1] = -b1;
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) {
+        T ut = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            R[1 + k][2 + j] = t[j][k];
+            L[2 + j][1 + k] = t[j][k];
+            ut += vel[k] * t[j][k];
+        }
+        R[D + 1][2 + j] = ut;
+        L[2 + j][0] = -ut;
+    }
+}
+
+template <class C, class T, bool CHAR>
 __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, unsigned nbl)
 {
     constexpr int M = C::M, NV = C::NV, D = C::D, NFP = C::NFP, N = C::N, MD = C::MD;
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
+    constexpr int NFC = CHAR ? C::NFMAX : 1;   // faces with their own weights
+    constexpr int NVC = CHAR ? NV : 1;
     __shared__ T sU[CPB][M][NV];
     __shared__ T sA[CPB][N][NV];          // p_opt coefficients
     __shared__ T sS[CPB][6][D][NV];       // directional coefficients
-    __shared__ T sC[CPB][NV][D + 1];      // per variable: omega_1 / lambda_1 and the linear combination
+    __shared__ T sC[CPB][NFC][NV][D + 1]; // per (face,) variable: omega_1 / lambda_1 and the degree-1 part
+    __shared__ T sL[CPB][NFC][NVC][NV];   // characteristic projection of each face (CHAR)
+    __shared__ T sR[CPB][NFC][NV][NVC];
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
-    const int64_t nc = p.nc;
     const int cnt = p.counts[0];
     for (int64_t i = (int64_t)bid * CPB + gi; i < cnt; i += (int64_t)nbl * CPB) {
         const int64_t c = p.queue[i];
@@ -775,8 +358,15 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
 #pragma unroll
             for (int v = 0; v < NV; ++v) sU[gi][m][v] = uj[v] - uc[v];
         }
-        grp.sync();
         const int nf = p.nfc[c] & 15;
+        if constexpr (CHAR) {
+            if (lane < nf) {
+                const T* n = p.nrm + (c * 6 + lane) * 3;
+                const T nn[3] = {n[0], n[1], n[2]};
+                euler_eigenvectors<T, D>(uc, nn, p.gamma, sL[gi][lane], sR[gi][lane]);
+            }
+        }
+        grp.sync();
         // p_opt: a_k = sum_m P_km (U_m - U_0)
         const T* P = p.P + c * (int64_t)N * M;
         for (int k = lane; k < N; k += G) {
@@ -811,63 +401,39 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
             for (int v = 0; v < NV; ++v) sS[gi][f][k][v] = acc[v];
         }
         grp.sync();
-        // indicators and weights, one lane per variable
-        if (lane < NV) {
-            const int v = lane;
-            const T lam1 = p.lam1, lams = (T(1) - lam1) / T(nf);
-            const T* OI = p.OI + c * (int64_t)C::NOI;
-            T sumlin[D];
+        // indicators and weights: one lane per variable, or per (face,
+        // characteristic variable)
+        const T* OI = p.OI + c * (int64_t)C::NOI;
+        for (int t = lane; t < (CHAR ? nf * NV : NV); t += G) {
+            const int f = CHAR ? t / NV : 0, w = CHAR ? t % NV : t;
+            T a[N], sd[6][D], c0, g[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                T s0 = T(0);
-                for (int f = 0; f < nf; ++f) s0 += sS[gi][f][k][v];
-                sumlin[k] = s0;
-            }
-            // p_1 = (p_opt - sum_s lambda_s p_s) / lambda_1
-            T a1[N];
+            for (int k = 0; k < N; ++k) {
+                if constexpr (CHAR) {
+                    T x = T(0);
 #pragma unroll
-            for (int k = 0; k < N; ++k) a1[k] = (sA[gi][k][v] - (k < D ? lams * sumlin[k < D ? k : 0] : T(0))) / lam1;
-            T si1 = T(0);
-            {
-                int o = 0;
-#pragma unroll
-                for (int k = 0; k < N; ++k) {
-                    T t = OI[o++] * a1[k];
-#pragma unroll
-                    for (int l = k + 1; l < N; ++l) t += T(2) * OI[o++] * a1[l];
-                    si1 += a1[k] * t;
+                    for (int u = 0; u < NV; ++u) x += sL[gi][f][w][u] * sA[gi][k][u];
+                    a[k] = x;
+                } else {
+                    a[k] = sA[gi][k][w];
                 }
             }
-            T sis[6], tsum = T(0);
-            for (int f = 0; f < nf; ++f) {
-                T s0 = T(0);
+            for (int h = 0; h < nf; ++h)
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const int o = k * N - k * (k - 1) / 2;
-                    T t = OI[o] * sS[gi][f][k][v];
+                    if constexpr (CHAR) {
+                        T x = T(0);
 #pragma unroll
-                    for (int l = k + 1; l < D; ++l) t += T(2) * OI[o + (l - k)] * sS[gi][f][l][v];
-                    s0 += sS[gi][f][k][v] * t;
+                        for (int u = 0; u < NV; ++u) x += sL[gi][f][w][u] * sS[gi][h][k][u];
+                        sd[h][k] = x;
+                    } else {
+                        sd[h][k] = sS[gi][h][k][w];
+                    }
                 }
-                sis[f] = s0;
-                tsum += tabs(s0 - si1);
-            }
-            const T tau = tpow(tsum / T(nf), p.b_cw);
-            const T w1 = lam1 * (T(1) + tau / (p.eps_cw + si1));
-            T wsum = w1, ws[6];
-            for (int f = 0; f < nf; ++f) {
-                ws[f] = lams * (T(1) + tau / (p.eps_cw + sis[f]));
-                wsum += ws[f];
-            }
-            const T om1 = w1 / wsum;
-            // p_cweno = (omega_1/lambda_1) p_opt + sum_s (omega_s - omega_1 lambda_s / lambda_1) p_s
-            sC[gi][v][0] = om1 / lam1;
+            cweno_weights<C, T>(p, OI, nf, a, sd, c0, g);
+            sC[gi][f][w][0] = c0;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                T gk = T(0);
-                for (int f = 0; f < nf; ++f) gk += (ws[f] / wsum - om1 * lams / lam1) * sS[gi][f][k][v];
-                sC[gi][v][1 + k] = gk;
-            }
+            for (int k = 0; k < D; ++k) sC[gi][f][w][1 + k] = g[k];
         }
         grp.sync();
         const int Q = nf * NFP;
@@ -880,12 +446,38 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
 #pragma unroll
             for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
             load_state<T, NV>(FS, w);
+            if constexpr (CHAR) {
+                // the linear candidate's increment in the face's
+                // characteristic variables, combined there, projected back
+                const int f = lane / NFP;
+                T dl[NV], cw[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                T s0 = uc[v] + sC[gi][v][0] * (w[v] - uc[v]);
+                for (int v = 0; v < NV; ++v) dl[v] = w[v] - uc[v];
 #pragma unroll
-                for (int k = 0; k < D; ++k) s0 += ph[k] * sC[gi][v][1 + k];
-                w[v] = s0;
+                for (int x = 0; x < NV; ++x) {
+                    T d0 = T(0);
+#pragma unroll
+                    for (int u = 0; u < NV; ++u) d0 += sL[gi][f][x][u] * dl[u];
+                    T s0 = sC[gi][f][x][0] * d0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) s0 += ph[k] * sC[gi][f][x][1 + k];
+                    cw[x] = s0;
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    T s0 = uc[v];
+#pragma unroll
+                    for (int x = 0; x < NV; ++x) s0 += sR[gi][f][v][x] * cw[x];
+                    w[v] = s0;
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    T s0 = uc[v] + sC[gi][0][v][0] * (w[v] - uc[v]);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) s0 += ph[k] * sC[gi][0][v][1 + k];
+                    w[v] = s0;
+                }
             }
             const T rb = uc[0], pb = pressure<T, D>(uc, p.gamma);
             const T rlim = p.h_theta * tmax(tabs(rb), p.h_eps), plim = p.h_theta * tmax(tabs(pb), p.h_eps);
@@ -999,82 +591,99 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
     }
 }
 
-// K6: Riemann fluxes at the face points and the residual, one group per cell,
-// lane q the flux at face point q; the group sums F w |S| in a fixed order.
-// Both sides' states come from FS (a first-order cell carries its mean
-// there); the neighbour's point is at a precomputed offset.  With a fused
-// Runge-Kutta stage, lane v < nv updates variable v of the cell.
-// resident blocks per SM aimed for: 12 (40 registers) for the FP32 3D
-// kernels, where the occupancy gain outweighs a few spilled registers
-template <class C, class T>
+// K6: Riemann fluxes at the face points and the residual, a group of FG
+// lanes per cell, lane f taking the NFP points of face f (they share the
+// face's normal and neighbour offset and lie next to each other in FS, on
+// both sides of the face).  Both sides' states come from FS (a first-order
+// cell carries its mean there).  The lanes' point sums are added in a fixed
+// butterfly; lanes v, v + FG, ... < nv finish variable v, with the
+// Runge-Kutta stage fused when one is given.  Every lane of the warp reaches
+// the shuffles (cells past the end carry no faces), so they take the full
+// mask.
+template <class C>
 struct FluxShape {
-    static constexpr int MINB = (C::D == 3 && sizeof(T) == 4) ? 12 : 1;
+    static constexpr int FG = C::NFMAX <= 4 ? 4 : 8;
+    static constexpr int CPB = 128 / FG;
 };
 
 template <class C, class T, int KIND>
-__global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> p, T* __restrict__ R)
+__global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
 {
-    constexpr int NV = C::NV, D = C::D, NFP = C::NFP;
-    constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
-    const Grp<G> grp;
-    const int gi = threadIdx.x / G, lane = grp.lane;
-    const int64_t c = (int64_t)blockIdx.x * CPB + gi;
-    if (c >= p.nc) return;
+    constexpr int NV = C::NV, D = C::D, NFP = C::NFP, G = FluxShape<C>::FG, CPB = FluxShape<C>::CPB;
+    const int lane = threadIdx.x & (G - 1);
     const int64_t nc = p.nc;
-    // geometry and connectivity first: none of it depends on the fluxes
-    const T ivol = lane < NV ? p.ivol[c] : T(0);
-    const int64_t q0 = c * C::QMAX;
-    const bool inq = lane < C::QMAX;
-    const int f = inq ? lane / NFP : 0, a = lane - f * NFP;
+    const int64_t c = (int64_t)blockIdx.x * CPB + threadIdx.x / G;
+    const bool valid = c < nc;
+    const int64_t cs = valid ? c : nc - 1;
+    const int f = lane;
     int32_t nb = -2;
-    T wq = T(0), nn[3] = {T(0), T(0), T(0)};
-    if (inq) {
-        nb = p.nfs[c * 6 + f];
-        wq = p.W[q0 + lane];
-        const T* n = p.nrm + (c * 6 + f) * 3;
+    T nn[3] = {T(0), T(0), T(0)};
+    if (valid && f < C::NFMAX) {
+        nb = p.nfs[cs * 6 + f];
+        const T* n = p.nrm + (cs * 6 + f) * 3;
         nn[0] = n[0]; nn[1] = n[1]; nn[2] = n[2];
     }
-    // the Runge-Kutta operands do not depend on the fluxes either
-    double u0 = 0.0, us = 0.0, cdt = 0.0;
-    const int64_t e = (int64_t)(lane < NV ? lane : 0) * nc + c;
-    const int sg = p.seg ? p.seg[c] : 0;
-    if (p.rk_b != 0.0 && lane < NV) {
-        us = p.Us[e];
-        cdt = p.dtc[sg];
-        if (p.rk_a != 0.0) u0 = p.U0[e];
+    // the Runge-Kutta operands (independent of the fluxes)
+    constexpr int NVL = (NV + G - 1) / G;   // variables finished per lane
+    double u0[NVL], us[NVL], cdt = 0.0;
+#pragma unroll
+    for (int k = 0; k < NVL; ++k) {
+        u0[k] = 0.0; us[k] = 0.0;
+        const int v = lane + k * G;
+        if (valid && p.rk_b != 0.0 && v < NV) {
+            us[k] = p.Us[(int64_t)v * nc + c];
+            if (p.rk_a != 0.0) u0[k] = p.U0[(int64_t)v * nc + c];
+        }
     }
+    if (valid && p.rk_b != 0.0) cdt = p.dtc[p.seg ? p.seg[c] : 0];
+    const T ivol = valid ? p.ivol[cs] : T(0);
+    // geometry and the stage operands above are constant or written two or
+    // more kernels back; the face states are the predecessor's output
+    pdl_wait();
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
     if (nb != -2) {
-        T wl[NV], wr[NV], F[NV];
-        load_state<T, NV>(p.FS + (q0 + lane) * NV, wl);
-        if (nb < 0) {
+        const int64_t q = cs * C::QMAX + f * NFP;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) wr[v] = wl[v];
-        } else {
-            load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
+        for (int a = 0; a < NFP; ++a) {
+            T wl[NV], wr[NV], F[NV];
+            load_state<T, NV>(p.FS + (q + a) * NV, wl);
+            if (nb < 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+            } else {
+                load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
+            }
+            const T wq = p.W[q + a];
+            riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] += F[v] * wq;
         }
-        riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = F[v] * wq;
     }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = grp.sum(acc[v]);
-    if (lane < NV) {
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    if (!valid) return;
+#pragma unroll
+    for (int k = 0; k < NVL; ++k) {
+        const int v = lane + k * G;
+        if (v >= NV) break;
         T val = acc[0];
 #pragma unroll
-        for (int v = 1; v < NV; ++v) val = lane == v ? acc[v] : val;
+        for (int x = 1; x < NV; ++x) val = v == x ? acc[x] : val;
         const T r = -val * ivol;
+        const int64_t e = (int64_t)v * nc + c;
         if (p.rk_b == 0.0) {
-            R[lane * nc + c] = r;
+            R[e] = r;
         } else {
-            // Runge-Kutta stage update of variable `lane` of cell c (FP64)
-            double x = p.rk_b * (us + cdt * (double)r);
-            if (p.rk_a != 0.0) x += p.rk_a * u0;
-            if (p.Rcopy) p.Rcopy[lane * nc + c] = r;
+            // Runge-Kutta stage update of variable v of cell c (FP64)
+            double x = p.rk_b * (us[k] + cdt * (double)r);
+            if (p.rk_a != 0.0) x += p.rk_a * u0[k];
+            if (p.Rcopy) p.Rcopy[e] = r;
             p.out[e] = x;
-            if (p.ua_next) p.ua_next[c * AoSP<NV>::P + lane] = (T)x;
+            if (p.ua_next) p.ua_next[c * AoSP<NV>::P + v] = (T)x;
         }
     }
 }
@@ -1091,6 +700,26 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
             return HFV_ERR_CUDA;                                                               \
         }                                                                                      \
     } while (0)
+
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// while its predecessor drains and waits for it in pdl_wait() (every kernel
+// launched this way calls it before touching the predecessor's output).
+constexpr int kPdl = 1;
+template <class... KA, class... A>
+static void pdl(void (*k)(KA...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = kPdl;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // scope guard: counts the launch and, when the scheme's timer is on, brackets
 // it with a pair of events on the launch stream
@@ -1148,6 +777,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
 template <class Tin, class T, int NV>
 __global__ void k_to_aos(int64_t nc, const Tin* __restrict__ U, T* __restrict__ UA)
 {
+    pdl_wait();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
     constexpr int P = AoSP<NV>::P;
@@ -1182,10 +812,10 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     KParams<T> p = make_params<T>(s, forced);
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
-    const unsigned gcell = (unsigned)((nc + CPB - 1) / CPB), g256 = (unsigned)((nc + 255) / 256);
+    const unsigned g256 = (unsigned)((nc + 255) / 256);
     if (!ua) {
         Launch l(s, KID_CVT, st);
-        k_to_aos<T, T, C::NV><<<g256, 256, 0, st>>>(nc, U, (T*)s->a.UA);
+        pdl(k_to_aos<T, T, C::NV>, g256, 256, 0, st, nc, U, (T*)s->a.UA);
         ua = (const T*)s->a.UA;
     }
     p.UA = ua;
@@ -1216,14 +846,14 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         const int64_t ntiles = (nc + S1::NG - 1) / S1::NG;
         const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per);
         Launch l(s, KID_LINEAR, st);
-        k_linear<C, T><<<g1, S1::THREADS, S1::SMEM, st>>>(p);
+        pdl(k_linear<C, T>, g1, S1::THREADS, S1::SMEM, st, p);
     }
-    { Launch l(s, KID_TAG, st); k_tag<T><<<s->nblocks, 256, 0, st>>>(p); }
+    { Launch l(s, KID_TAG, st); pdl(k_tag<T>, s->nblocks, 256, 0, st, p); }
     const int fold = s->nblocks <= 1024;
-    if (!fold) { Launch l(s, KID_SCAN, st); k_scan<<<1, 1024, 0, st>>>(s->a.bcount, s->nblocks, s->a.counts); }
+    if (!fold) { Launch l(s, KID_SCAN, st); pdl(k_scan, 1, 1024, 0, st, s->a.bcount, s->nblocks, s->a.counts); }
     {
         Launch l(s, KID_SCATTER, st);
-        k_scatter<<<s->nblocks, 256, 0, st>>>(s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue, s->a.counts, fold);
+        pdl(k_scatter, s->nblocks, 256, 0, st, s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue, s->a.counts, fold);
     }
     {
         // CWENOZ cells cost several times a MUSCL cell: by default 3/4 of the
@@ -1232,14 +862,16 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
             2, std::min<int64_t>((nc + CPB - 1) / CPB, (int64_t)s->sms * s->tune_nl_per_sm));
         const unsigned split = std::min<unsigned>(gq - 1, std::max<unsigned>(1, gq * s->tune_nl_cweno_pct / 100));
         Launch l(s, KID_CWENO, st);
-        k_nonlinear<C, T><<<gq, 128, 0, st>>>(p, split);
+        if (s->p.cweno_vars == HFV_CHARACTERISTIC) pdl(k_nonlinear<C, T, true>, gq, 128, 0, st, p, split);
+        else pdl(k_nonlinear<C, T, false>, gq, 128, 0, st, p, split);
     }
     {
         Launch l(s, KID_FLUX, st);
+        const unsigned gf = (unsigned)((nc + FluxShape<C>::CPB - 1) / FluxShape<C>::CPB);
         switch (s->p.flux) {
-        case HFV_RUSANOV: k_flux<C, T, kRusanov><<<gcell, 128, 0, st>>>(p, R); break;
-        case HFV_HLL: k_flux<C, T, kHLL><<<gcell, 128, 0, st>>>(p, R); break;
-        default: k_flux<C, T, kHLLC><<<gcell, 128, 0, st>>>(p, R); break;
+        case HFV_RUSANOV: pdl(k_flux<C, T, kRusanov>, gf, 128, 0, st, p, R); break;
+        case HFV_HLL: pdl(k_flux<C, T, kHLL>, gf, 128, 0, st, p, R); break;
+        default: pdl(k_flux<C, T, kHLLC>, gf, 128, 0, st, p, R); break;
         }
     }
     if (cls_out) HFV_CUDA_CHECK(cudaMemcpyAsync(cls_out, s->a.cls, nc, cudaMemcpyDeviceToDevice, st));
@@ -1252,12 +884,14 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
 // ---------------------------------------------------------------------------
 __global__ void k_set(double* x, double v, int n)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = v;
 }
 
 __global__ void k_dt_init(unsigned long long* x, int n)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = 0x7ff0000000000000ull;
 }
@@ -1269,6 +903,7 @@ struct RkWeights {
 };
 __global__ void k_rk_coef(const double* __restrict__ dt, int nseg, RkWeights w, double* __restrict__ dtc)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nseg) return;
     const double h = dt[i];
@@ -1283,6 +918,7 @@ __global__ void __launch_bounds__(256) k_rk_partial(int64_t n, int64_t nc, const
                                                    const double* __restrict__ c, const int32_t* __restrict__ seg,
                                                    double a52, double a53, double* __restrict__ P)
 {
+    pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cell = i % nc;
@@ -1303,6 +939,7 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
                                                   const int32_t* __restrict__ seg, double gamma, double cfl,
                                                   unsigned long long* dt_out)
 {
+    pdl_wait();
     constexpr int D = NV - 2, P = AoSP<NV>::P;
     __shared__ double red[8];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1412,15 +1049,15 @@ static int stage_in(hfv_scheme* s, const double* U, double cfl, double* dt_dev, 
     const unsigned g = (unsigned)((nc + 255) / 256);
     const hfv_dev_arrays& a = s->a;
     auto* out = (unsigned long long*)dt_dev;
-    if (dt_dev) { Launch l(s, KID_DT, st); k_dt_init<<<(s->nseg + 255) / 256, 256, 0, st>>>(out, s->nseg); }
+    if (dt_dev) { Launch l(s, KID_DT, st); pdl(k_dt_init, (s->nseg + 255) / 256, 256, 0, st, out, s->nseg); }
     Launch l(s, KID_CVT, st);
     const bool f32 = s->p.precision == HFV_FP32;
     if (s->nv == 4) {
-        if (f32) k_stage_in<float, 4><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
-        else k_stage_in<double, 4><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        if (f32) pdl(k_stage_in<float, 4>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        else pdl(k_stage_in<double, 4>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
     } else {
-        if (f32) k_stage_in<float, 5><<<g, 256, 0, st>>>(nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
-        else k_stage_in<double, 5><<<g, 256, 0, st>>>(nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        if (f32) pdl(k_stage_in<float, 5>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
+        else pdl(k_stage_in<double, 5>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out);
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
@@ -1436,7 +1073,7 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
     if (dt > 0.0) {
-        { Launch l(s, KID_DT, st); k_set<<<(s->nseg + 255) / 256, 256, 0, st>>>(s->a.dt, dt, s->nseg); }
+        { Launch l(s, KID_DT, st); pdl(k_set, (s->nseg + 255) / 256, 256, 0, st, s->a.dt, dt, s->nseg); }
         if ((rc = stage_in(s, U, cfl, nullptr, st)) != HFV_OK) return rc;
     } else if ((rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
         return rc;
@@ -1449,7 +1086,7 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
         rw.n = n;
         for (int k = 0; k < n; ++k) rw.w[k] = w[k];
         Launch l(s, KID_DT, st);
-        k_rk_coef<<<(s->nseg + 255) / 256, 256, 0, st>>>(s->a.dt, s->nseg, rw, s->a.dtc);
+        pdl(k_rk_coef, (s->nseg + 255) / 256, 256, 0, st, s->a.dt, s->nseg, rw, s->a.dtc);
         HFV_CUDA_CHECK(cudaGetLastError());
         return HFV_OK;
     };
@@ -1489,10 +1126,10 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
                 const unsigned g = (unsigned)((nvc + 255) / 256);
                 const double* c5 = s->a.dtc + 5 * (int64_t)s->nseg;
                 if (s->p.precision == HFV_FP32)
-                    k_rk_partial<float><<<g, 256, 0, st>>>(nvc, s->mesh->nc, s->a.U2, s->a.U3, (const float*)s->a.Rs, c5,
+                    pdl(k_rk_partial<float>, g, 256, 0, st, nvc, s->mesh->nc, s->a.U2, s->a.U3, (const float*)s->a.Rs, c5,
                                                           s->a.seg, a52, a53, s->a.U5);
                 else
-                    k_rk_partial<double><<<g, 256, 0, st>>>(nvc, s->mesh->nc, s->a.U2, s->a.U3, (const double*)s->a.Rs,
+                    pdl(k_rk_partial<double>, g, 256, 0, st, nvc, s->mesh->nc, s->a.U2, s->a.U3, (const double*)s->a.Rs,
                                                            c5, s->a.seg, a52, a53, s->a.U5);
             }
         }

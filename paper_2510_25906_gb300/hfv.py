@@ -28,6 +28,7 @@ SCHEME = {"hybrid": HFV_HYBRID, "linear": HFV_PURE_LINEAR, "cweno": HFV_PURE_CWE
 PRECISION = {"fp64": HFV_FP64, "fp32": HFV_FP32}
 TIME_SCHEME = {"ssprk3": 0, "ssprk54": 1}
 LIMITER = {"barth": 0, "venkatakrishnan": 1}
+CWENO_VARS = {"conserved": 0, "characteristic": 1}
 
 
 class HfvError(RuntimeError):
@@ -48,7 +49,7 @@ class hfv_scheme_params(C.Structure):
                 ("beta_m", C.c_double), ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1_prime", C.c_double), ("cweno_eps", C.c_double),
                 ("cweno_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("reserved", C.c_int), ("venkat_k", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double)]
 
 
 _lib = None
@@ -129,6 +130,8 @@ def default_params(**kw) -> hfv_scheme_params:
             v = TIME_SCHEME[v]
         elif k == "limiter" and isinstance(v, str):
             v = LIMITER[v]
+        elif k == "cweno_vars" and isinstance(v, str):
+            v = CWENO_VARS[v]
         setattr(p, k, v)
     return p
 

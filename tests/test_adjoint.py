@@ -185,3 +185,47 @@ def test_autograd_function_matches_vjp(H):
     g.residual(Ud.detach(), class_out=c)
     ref = g.residual_vjp(Ud.detach(), c, lam)
     assert torch.equal(gr, ref)
+
+
+def test_adjoint_workload_trajectory_gradient(H):
+    """The adjoint workload's shape at 6 * 12^3 tetrahedra: a Gaussian pulse
+    ahead of a planar Mach 2 shock, Venkatakrishnan's limiter (K = 5), ten
+    CFL steps.  Along the density pulse (no cell at a tie of the limiter's
+    bounds moves) the gradient matches central differences to 1e-6.  Along
+    a random direction the piecewise-constant states on both sides of the
+    shock put cells at ties of max / min (U_0 equal to a neighbour), where
+    the frozen-branch derivative is one of the one-sided ones and central
+    differences average them: the bar there is 1e-3."""
+    from paper_2510_25906_gb300 import adjoint as A
+    m, U0 = I.adjoint_problem(12)
+    gm = H.Mesh(m)
+    g = H.Scheme(gm, order=3, flux="hllc", precision="fp64", limiter="venkatakrishnan", venkat_k=5.0)
+    J = A.density_square_integral(gm.volumes())
+    U = torch.tensor(U0, device="cuda")
+    steps = 10
+    Jv, dJ, UN, dts = A.rk3_gradient(g, U, steps, J, cfl=0.5)
+    assert torch.isfinite(dJ).all()
+    cls, W = [], U.clone()
+    for h_ in dts:
+        _, _, W3, c = A._stages(g, W, h_)
+        cls.append(c)
+        W = W3.contiguous()
+    hist = np.bincount(torch.cat([c for stage in cls for c in stage]).cpu().numpy(), minlength=4)
+    assert (hist[1:] > 0).all(), hist
+
+    def traj(U0_):
+        W = U0_.clone()
+        for c, h_ in zip(cls, dts):
+            W = A._stages(g, W, h_, classes=c)[2].contiguous()
+        return J(W)[0]
+
+    cen = torch.tensor(m.vertex_means(), device="cuda")
+    pulse = torch.zeros_like(U)
+    pulse[0] = torch.exp(-((cen - torch.tensor([0.75, 0.5, 0.5], device="cuda")) ** 2).sum(1) / (2 * 0.08 ** 2))
+    rng = np.random.default_rng(1)
+    rand = torch.tensor(rng.standard_normal(U.shape), device="cuda") * U.abs().mean(dim=1, keepdim=True)
+    for d, bar in ((pulse, 1e-6), (rand, 1e-3)):
+        fd = (traj(U + 1e-6 * d) - traj(U - 1e-6 * d)) / 2e-6
+        an = float((dJ * d).sum().item())
+        print(f"adjoint workload: fd {fd:.10e} adjoint {an:.10e} rel {abs(fd - an) / abs(fd):.2e}")
+        assert abs(fd - an) <= bar * abs(fd)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from bounds import fp32_bound
 from paper_2510_25906_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -133,19 +134,6 @@ def test_stencils_bit_exact(H, name):
             assert (dr[c, f, nd[f]:] == -1).all()
 
 
-def _fp32_bound(m, om, osch, U, R):
-    """Arithmetic bound of an FP32 residual relative to max |R|: rounding the
-    state to FP32 moves every face flux by ~eps32 |F|, and the residual sums
-    them with weights |S| w / |V|:  c * eps32 * max_c sum_f |S_f| |F| / |V_c|."""
-    vol, _ = om.geometry()
-    fo, fn, nrm, area, sh = om.faces()
-    ssum = np.zeros(m.n_cells)
-    np.add.at(ssum, fo, area)
-    np.add.at(ssum, fn[fn >= 0], area[fn >= 0])
-    fscale = np.abs(U).max() * 4.0
-    return (4 * 6e-8 * fscale * (ssum / vol).max()) / np.abs(R).max(axis=1).min()
-
-
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("name", CASES)
 def test_forced_class_residual(H, name, precision, tol):
@@ -153,7 +141,7 @@ def test_forced_class_residual(H, name, precision, tol):
     discontinuous workloads; where max |R| is small against the face fluxes
     it is the difference of (the smooth density wave; the tetrahedral cases,
     whose cells have the largest surface-to-volume ratio), the larger of
-    1e-5 and the bound of the FP32 arithmetic itself (_fp32_bound)."""
+    1e-5 and the bound of the FP32 arithmetic itself (bounds.fp32_bound)."""
     m, om, osch, U, kw, R, raw, tag, fin = _prepared(name)
     assert len(np.unique(fin)) >= (1 if name == "wave_tri32" else 2)
     gm, g = _gpu(H, m, kw, precision)
@@ -169,7 +157,7 @@ def test_forced_class_residual(H, name, precision, tol):
         assert np.array_equal(cg, fin)
     ok = cg == fin
     if precision == "fp32" and (name == "wave_tri32" or name.startswith("tet")):
-        tol = max(tol, _fp32_bound(m, om, osch, U, R))
+        tol = max(tol, fp32_bound(m, om, U, R))
         assert tol < 1e-3
     err = _rel(Rg.double().cpu().numpy(), R, ok)
     print(f"{name} {precision}: max rel err {err:.2e} (bar {tol:.1e})")

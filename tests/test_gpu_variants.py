@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from bounds import fp32_bound
 from paper_2510_25906_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -137,3 +138,65 @@ def test_venkatakrishnan_adjoint_against_central_differences(H):
         scale = np.abs((Rp - Rm) * lam.cpu().numpy()).sum() / (2 * h)
         an = (grad * d).sum()
         assert abs(fd - an) <= 1e-6 * scale, (fd, an)
+
+
+@pytest.mark.parametrize("case", ["quadrant", "hex", "tet"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_characteristic_cweno_forced_class_residual(H, case, precision, tol):
+    """CWENOZ in characteristic variables (per face, projected with the
+    eigenvectors of the flux Jacobian along its normal) against the oracle,
+    every flagged cell forced to CWENOZ."""
+    if case == "quadrant":
+        m, U = _quadrant()
+        kw = dict(order=3, flux="hllc", cweno_vars="characteristic")
+    elif case == "hex":
+        m, U = _hex()
+        kw = dict(order=3, flux="hllc", cweno_vars="characteristic", kappa=0.1)
+    else:
+        m = I.structured_tet_mesh(4, 1.0, periodic=False, jitter=0.1, seed=6)
+        U = _smooth_3d(m)
+        kw = dict(order=3, flux="hllc", cweno_vars="characteristic")
+    osch = O.Scheme(O.Mesh(m), **kw)
+    fin = osch.residual(U)[3]
+    forced = np.where(fin == 2, 1, fin).astype(np.uint8)
+    Ro, _, _, fo = osch.residual(U, forced=forced)
+    assert (fo == 1).sum() > 10
+    g = H.Scheme(H.Mesh(m), precision=precision, **kw)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    cls = torch.empty(m.n_cells, dtype=torch.uint8, device="cuda")
+    R = g.residual(torch.tensor(U, dtype=dt, device="cuda"), forced=torch.tensor(fo, device="cuda"),
+                   class_out=cls).double().cpu().numpy()
+    ok = cls.cpu().numpy() == fo
+    if precision == "fp64":
+        assert ok.all()
+    if precision == "fp32" and case == "tet":
+        # the tetrahedra have the largest surface-to-volume ratio: the bar is
+        # the larger of 1e-5 and the bound of the FP32 arithmetic itself
+        tol = max(tol, fp32_bound(m, O.Mesh(m), U, Ro))
+        assert tol < 1e-3
+    scale = np.abs(Ro).max(axis=1)
+    err = (np.abs(R - Ro)[:, ok].max(axis=1) / scale).max()
+    print(f"characteristic CWENOZ {case} {precision}: {(fo == 1).sum()} CWENOZ cells, max rel err {err:.2e}")
+    assert err <= tol, err
+    # the characteristic form really differs from the conserved one here
+    Rc = O.Scheme(O.Mesh(m), **{**kw, "cweno_vars": "conserved"}).residual(U, forced=fo)[0]
+    assert np.abs(Rc - Ro).max() > 1e-8 * np.abs(Ro).max()
+
+
+def _smooth_3d(m):
+    c = m.vertex_means()
+    rho = 1.0 + 0.05 * np.sin(2 * math.pi * (c[:, 0] + c[:, 2])) + np.where(c[:, 1] < 0.5, 0.5, 0.0)
+    vel = np.stack([0.3 + 0.1 * np.cos(2 * math.pi * c[:, 2]), 0.1 * np.sin(2 * math.pi * c[:, 0]),
+                    -0.2 * np.ones(len(c))])
+    E = 1.0 / 0.4 + 0.5 * rho * (vel ** 2).sum(0)
+    return np.stack([rho, rho * vel[0], rho * vel[1], rho * vel[2], E])
+
+
+def test_adjoint_rejects_characteristic_cweno(H):
+    m, U = _quadrant(8)
+    g = H.Scheme(H.Mesh(m), precision="fp64", order=3, cweno_vars="characteristic")
+    Ud = torch.tensor(U, device="cuda")
+    cls = torch.zeros(m.n_cells, dtype=torch.uint8, device="cuda")
+    with pytest.raises(H.HfvError) as e:
+        g.residual_vjp(Ud, cls, torch.ones_like(Ud))
+    assert e.value.code == H.HFV_ERR_ARG

@@ -116,3 +116,110 @@ def test_venkatakrishnan_limits_at_a_jump():
         assert np.abs(d).max() > 0                          # not first order
         assert np.abs(d).max() < 0.9 * np.abs(df).max()     # limited: 0 < theta < 1
         assert np.allclose(d[np.abs(df) > 0] / df[np.abs(df) > 0], (d / np.where(df == 0, 1, df))[np.abs(df) > 0][0])
+
+
+# ---------------------------------------------------------------------------
+# CWENOZ in characteristic variables
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("u,n", [([1.2, 0.3, -0.4, 2.9], [0.6, 0.8]),
+                                 ([0.9, 0.2, -0.1, 0.35, 2.7], [0.36, 0.48, 0.8]),
+                                 ([1.1, 0.0, 0.0, 0.5, 3.1], [0.0, 0.0, 1.0])])
+def test_euler_eigenvectors_diagonalise_the_flux_jacobian(u, n):
+    """L R = I, and L (dF.n/dU) R = diag(u.n - c, u.n, ..., u.n + c) with
+    the Jacobian taken by central differences of the physical flux F(U, U)."""
+    u, n = np.array(u), np.array(n)
+    nv, d = u.size, u.size - 2
+    L, R = O.euler_eigen(u, n)
+    assert np.abs(L @ R - np.eye(nv)).max() < 1e-14
+    A = np.zeros((nv, nv))
+    h = 1e-6
+    n3 = np.zeros(3)
+    n3[:d] = n
+    for j in range(nv):
+        e = np.zeros(nv)
+        e[j] = h
+        A[:, j] = (O.flux("rusanov", u + e, u + e, n3) - O.flux("rusanov", u - e, u - e, n3)) / (2 * h)
+    D = L @ A @ R
+    vel = u[1:1 + d] / u[0]
+    p = 0.4 * (u[-1] - 0.5 * u[0] * vel @ vel)
+    c, qn = np.sqrt(1.4 * p / u[0]), vel @ n
+    ex = np.array([qn - c] + [qn] * (nv - 2) + [qn + c])
+    assert np.abs(D - np.diag(ex)).max() < 1e-8
+    assert np.abs(np.diag(D) - ex).max() < 1e-8
+
+
+@pytest.mark.parametrize("maker", [lambda: I.mixed_tri_quad_mesh(12, seed=5),
+                                   lambda: I.structured_hex_mesh(6, 1.0, periodic=False, jitter=0.1, seed=3)])
+def test_characteristic_cweno_equals_conserved_on_linear_data(maker):
+    """On linear data every indicator is equal, the weights are the linear
+    weights, and the characteristic projection (linear) commutes with the
+    reconstruction: both forms reproduce the plane."""
+    m = maker()
+    om = O.Mesh(m)
+    sc = O.Scheme(om, order=3)
+    sw = O.Scheme(om, order=3, cweno_vars="characteristic")
+    vm = m.vertex_means()
+    vol, cen = om.geometry()
+    g = np.array([0.3, -0.2, 0.1])[:m.dim]
+    rho = 1.5 + cen[:, :m.dim] @ g
+    mom = 0.2 + 0.1 * (cen[:, :m.dim] @ g)
+    if m.dim == 2:
+        U = np.stack([rho, mom, -mom, 3.0 + mom])
+    else:
+        U = np.stack([rho, mom, -mom, 0.5 * mom, 3.0 + mom])
+    for c in (7, 40, 101):
+        Vc = sc.reconstruct(U, c, O.CW)
+        Vw = sw.reconstruct(U, c, O.CW)
+        assert np.abs(Vc - Vw).max() < 1e-12
+        P = sc.face_points(c)
+        ex = 1.5 + P[:, :m.dim] @ g
+        assert np.abs(Vw[:, 0] - ex).max() < 1e-12
+
+
+def test_characteristic_cweno_conserves_and_preserves_free_stream():
+    m = I.mixed_tri_quad_mesh(10, seed=7, periodic=True)
+    om = O.Mesh(m)
+    vol, _ = om.geometry()
+    s = O.Scheme(om, order=3, flux="hllc", cweno_vars="characteristic", scheme="cweno")
+    n = m.n_cells
+    Uu = I.conserved_2d(np.full(n, 1.2), np.full(n, 0.4), np.full(n, -0.3), np.full(n, 0.8))
+    R, *_ = s.residual(Uu)
+    assert np.abs(R).max() < 1e-12
+    U = I.quadrant_state(m)
+    R, raw, tag, fin = s.residual(U)
+    assert (fin == 1).sum() > n // 3
+    tot = (R * vol).sum(axis=1)
+    assert np.abs(tot).max() < 1e-12 * (np.abs(R) * vol).sum()
+    # and it differs from conserved-variable CWENOZ at the discontinuities
+    Rc, *_ = O.Scheme(om, order=3, flux="hllc", scheme="cweno").residual(U)
+    assert np.abs(R - Rc).max() > 1e-6 * np.abs(Rc).max()
+
+
+def test_characteristic_cweno_on_a_contact_is_density_cweno():
+    """Across a contact (u, v and p constant, rho jumps) every difference of
+    conserved states is a multiple of the entropy eigenvector (1, u, v, q^2/2),
+    which does not depend on rho or on the face normal.  Its characteristic
+    projection is then rho's own data in the entropy field and zero in the
+    others, so the characteristic reconstruction gives rho exactly as the
+    component-wise one does, and rho u, rho v, E follow rho along that
+    eigenvector at every face point."""
+    m = I.mixed_tri_quad_mesh(16, seed=9)
+    om = O.Mesh(m)
+    vol, cen = om.geometry()
+    rho = 1.0 + 0.1 * np.sin(3 * cen[:, 1]) + np.where(cen[:, 0] < 0.47, 0.8, 0.0)
+    u, v, p = 0.3, -0.2, 1.0
+    U = I.conserved_2d(rho, np.full_like(rho, u), np.full_like(rho, v), np.full_like(rho, p))
+    sc = O.Scheme(om, order=3)
+    sw = O.Scheme(om, order=3, cweno_vars="characteristic")
+    near = np.argsort(np.abs(cen[:, 0] - 0.47))[:6]
+    moved = 0.0
+    for c in near:
+        Vc = sc.reconstruct(U, c, O.CW)
+        Vw = sw.reconstruct(U, c, O.CW)
+        assert np.abs(Vw[:, 0] - Vc[:, 0]).max() < 1e-12
+        assert np.abs(Vw[:, 1] - u * Vw[:, 0]).max() < 1e-12
+        assert np.abs(Vw[:, 2] - v * Vw[:, 0]).max() < 1e-12
+        assert np.abs(Vw[:, 3] - (p / 0.4 + 0.5 * (u * u + v * v) * Vw[:, 0])).max() < 1e-12
+        moved = max(moved, np.abs(Vw[:, 0] - sc.reconstruct(U, c, O.LIN)[:, 0]).max())
+    assert moved > 1e-3            # the nonlinear weights are really at work here
