@@ -20,6 +20,18 @@ namespace hfv {
 // writes nothing.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// asynchronous copy of one 4- or 8-byte element from global to shared
+// memory (completed by cp_async_wait_all in the issuing thread; other lanes
+// read it after a barrier)
+template <class T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element copies only");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"((int)sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <class T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 template <class T>

@@ -344,11 +344,42 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
     __shared__ T sC[CPB][NFC][NV][D + 1]; // per (face,) variable: omega_1 / lambda_1 and the degree-1 part
     __shared__ T sL[CPB][NFC][NVC][NV];   // characteristic projection of each face (CHAR)
     __shared__ T sR[CPB][NFC][NV][NVC];
+    // the cell's operators, copied asynchronously while the stencil states
+    // are gathered (P only where CPB copies of it fit in 16 KB)
+    constexpr int NOI = C::NOI, NDD = C::NFMAX * D * MD, NDIR = (C::NFMAX * MD + 3) / 4;
+    constexpr bool STAGE_P = (size_t)CPB * N * M * sizeof(T) <= 16384;
+    __shared__ __align__(16) T sP[STAGE_P ? CPB : 1][STAGE_P ? N * M : 1];
+    __shared__ T sOI[CPB][NOI];
+    __shared__ T sDd[CPB][NDD];
+    __shared__ uint32_t sDir[CPB][NDIR];  // directional stencil indices, four per word
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
     const int cnt = p.counts[0];
     for (int64_t i = (int64_t)bid * CPB + gi; i < cnt; i += (int64_t)nbl * CPB) {
         const int64_t c = p.queue[i];
+        const int nf = p.nfc[c] & 15;
+        if constexpr (STAGE_P) {
+            const T* P = p.P + c * (int64_t)N * M;
+            for (int e = lane; e < N * M; e += G) cp_async(&sP[gi][e], P + e);
+        }
+        {
+            const T* O = p.OI + c * (int64_t)NOI;
+            for (int e = lane; e < NOI; e += G) cp_async(&sOI[gi][e], O + e);
+            const T* Dm = p.Dd + c * (int64_t)(6 * D * MD);
+            for (int e = lane; e < nf * D * MD; e += G) cp_async(&sDd[gi][e], Dm + e);
+            // 6 MD bytes per cell, a multiple of four
+            const uint32_t* di = reinterpret_cast<const uint32_t*>(p.dir + c * 6 * MD);
+            for (int e = lane; e < (nf * MD + 3) / 4; e += G) cp_async(&sDir[gi][e], di + e);
+        }
+        // the face point's own inputs: quadrature map and linear candidate
+        const int Q = nf * NFP;
+        const int64_t q0 = c * C::QMAX;
+        T ph[D], wc[NV];
+        if (lane < Q) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
+            load_state<T, NV>(p.FS + (q0 + lane) * NV, wc);
+        }
         T uc[NV];
         load_cell<T, NV>(p.UA, c, uc);
         const int32_t* st = p.sten + c * M;
@@ -358,7 +389,6 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
 #pragma unroll
             for (int v = 0; v < NV; ++v) sU[gi][m][v] = uj[v] - uc[v];
         }
-        const int nf = p.nfc[c] & 15;
         if constexpr (CHAR) {
             if (lane < nf) {
                 const T* n = p.nrm + (c * 6 + lane) * 3;
@@ -366,12 +396,14 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
                 euler_eigenvectors<T, D>(uc, nn, p.gamma, sL[gi][lane], sR[gi][lane]);
             }
         }
+        cp_async_wait_all();
         grp.sync();
         // p_opt: a_k = sum_m P_km (U_m - U_0)
         const T* P = p.P + c * (int64_t)N * M;
         for (int k = lane; k < N; k += G) {
             T row[M];
-            load_row<T, M>(P + k * M, row);
+            if constexpr (STAGE_P) load_row_smem<T, M>(&sP[gi][k * M], row);
+            else load_row<T, M>(P + k * M, row);
             T acc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] = T(0);
@@ -385,8 +417,8 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
         // directional degree-1 polynomials
         for (int t = lane; t < nf * D; t += G) {
             const int f = t / D, k = t % D;
-            const uint8_t* idx = p.dir + (c * 6 + f) * MD;
-            const T* Dm = p.Dd + ((c * 6 + f) * D + k) * (int64_t)MD;
+            const uint8_t* idx = reinterpret_cast<const uint8_t*>(sDir[gi]) + f * MD;
+            const T* Dm = &sDd[gi][(f * D + k) * MD];
             T acc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] = T(0);
@@ -403,7 +435,7 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
         grp.sync();
         // indicators and weights: one lane per variable, or per (face,
         // characteristic variable)
-        const T* OI = p.OI + c * (int64_t)C::NOI;
+        const T* OI = sOI[gi];
         for (int t = lane; t < (CHAR ? nf * NV : NV); t += G) {
             const int f = CHAR ? t / NV : 0, w = CHAR ? t % NV : t;
             T a[N], sd[6][D], c0, g[D];
@@ -436,16 +468,11 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
             for (int k = 0; k < D; ++k) sC[gi][f][w][1 + k] = g[k];
         }
         grp.sync();
-        const int Q = nf * NFP;
-        const int64_t q0 = c * C::QMAX;
         bool fail = false;
         T w[NV];
         if (lane < Q) {
-            T* FS = p.FS + (q0 + lane) * NV;
-            T ph[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
-            load_state<T, NV>(FS, w);
+            for (int v = 0; v < NV; ++v) w[v] = wc[v];
             if constexpr (CHAR) {
                 // the linear candidate's increment in the face's
                 // characteristic variables, combined there, projected back
@@ -515,12 +542,25 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
     constexpr int G = GroupSize<C::QMAX>::value, CPB = 128 / G;
     __shared__ T sU[CPB][MD][NV];
     __shared__ T sG[CPB][NV][D];
+    __shared__ T sGm[CPB][D * MD];        // the gradient operator, copied during the gather
     const Grp<G> grp;
     const int gi = threadIdx.x / G, lane = grp.lane;
     const int64_t nc = p.nc;
     const int cnt = p.counts[1];
     for (int64_t i = (int64_t)bid * CPB + gi; i < cnt; i += (int64_t)nbl * CPB) {
         const int64_t c = p.queue[nc + i];
+        const int nfv = p.nfc[c];
+        const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
+        {
+            const T* Gsrc = p.G + c * (int64_t)D * MD;
+            for (int e = lane; e < D * MD; e += G) cp_async(&sGm[gi][e], Gsrc + e);
+        }
+        const int64_t q0 = c * C::QMAX;
+        T ph[D];
+        if (lane < Q)
+#pragma unroll
+            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
+        const T ivc = p.ivol[c];
         T uc[NV];
         load_cell<T, NV>(p.UA, c, uc);
         const int32_t* st = p.sten + c * M;
@@ -530,10 +570,9 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
 #pragma unroll
             for (int v = 0; v < NV; ++v) sU[gi][m][v] = uj[v];
         }
+        cp_async_wait_all();
         grp.sync();
-        const int nfv = p.nfc[c];
-        const int nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
-        const T* Gm = p.G + c * (int64_t)D * MD;
+        const T* Gm = sGm[gi];
         for (int t = lane; t < NV * D; t += G) {
             const int v = t / D, k = t % D;
             T acc = T(0);
@@ -542,15 +581,10 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
             sG[gi][v][k] = acc;
         }
         grp.sync();
-        const int64_t q0 = c * C::QMAX;
-        T ph[D];
-        if (lane < Q)
-#pragma unroll
-            for (int k = 0; k < D; ++k) ph[k] = p.Phil[(q0 + lane) * D + k];
         T w[NV];
         T eps2 = T(0);
         if (p.limiter == 1) {
-            const T vol = T(1) / p.ivol[c];
+            const T vol = T(1) / ivc;
             const T dx = D == 2 ? tsqrt<T>(vol) : tcbrt(vol);
             const T kd = p.venk_k * dx;
             eps2 = kd * kd * kd;
@@ -600,16 +634,19 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
 // Runge-Kutta stage fused when one is given.  Every lane of the warp reaches
 // the shuffles (cells past the end carry no faces), so they take the full
 // mask.
-template <class C>
+// resident blocks per SM aimed for: 2D FP32 ten (48 registers, measured
+// 5 % faster than 54), 3D FP32 nine (56), FP64 four (128)
+template <class C, class T>
 struct FluxShape {
     static constexpr int FG = C::NFMAX <= 4 ? 4 : 8;
     static constexpr int CPB = 128 / FG;
+    static constexpr int MINB = sizeof(T) == 8 ? 4 : C::D == 2 ? 10 : 9;
 };
 
 template <class C, class T, int KIND>
-__global__ void __launch_bounds__(128) k_flux(KParams<T> p, T* __restrict__ R)
+__global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> p, T* __restrict__ R)
 {
-    constexpr int NV = C::NV, D = C::D, NFP = C::NFP, G = FluxShape<C>::FG, CPB = FluxShape<C>::CPB;
+    constexpr int NV = C::NV, D = C::D, NFP = C::NFP, G = FluxShape<C, T>::FG, CPB = FluxShape<C, T>::CPB;
     const int lane = threadIdx.x & (G - 1);
     const int64_t nc = p.nc;
     const int64_t c = (int64_t)blockIdx.x * CPB + threadIdx.x / G;
@@ -867,7 +904,7 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     }
     {
         Launch l(s, KID_FLUX, st);
-        const unsigned gf = (unsigned)((nc + FluxShape<C>::CPB - 1) / FluxShape<C>::CPB);
+        const unsigned gf = (unsigned)((nc + FluxShape<C, T>::CPB - 1) / FluxShape<C, T>::CPB);
         switch (s->p.flux) {
         case HFV_RUSANOV: pdl(k_flux<C, T, kRusanov>, gf, 128, 0, st, p, R); break;
         case HFV_HLL: pdl(k_flux<C, T, kHLL>, gf, 128, 0, st, p, R); break;
