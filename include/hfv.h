@@ -53,11 +53,15 @@ extern "C" {
 #define HFV_ERR_STATE (-8)        /* call not valid for this handle (e.g. wrong precision) */
 
 /* cell types; local vertex order: TRI, QUAD counter-clockwise; HEX v0..v3
- * bottom face counter-clockwise seen from +z, v4..v7 above them */
+ * bottom face counter-clockwise seen from +z, v4..v7 above them.  3D meshes
+ * may mix TET, PRISM, PYRAMID and HEX; a mesh holding any cell but HEX is
+ * built for orders 2 and 3. */
 #define HFV_TRI 1
 #define HFV_QUAD 2
-#define HFV_TET 3 /* positive volume v0 v1 v2 v3; orders 2 and 3 */
+#define HFV_TET 3     /* positive volume v0 v1 v2 v3 */
 #define HFV_HEX 4
+#define HFV_PRISM 5   /* triangle v0 v1 v2 counter-clockwise seen from v3 v4 v5; v3, v4, v5 joined to v0, v1, v2 */
+#define HFV_PYRAMID 6 /* base v0 v1 v2 v3 counter-clockwise seen from the apex v4 */
 
 /* Riemann solvers at the face quadrature points (Sec. 2.4) */
 #define HFV_RUSANOV 0
@@ -98,7 +102,7 @@ typedef struct {
     int dim;                       /* 2 or 3 */
     int64_t n_nodes, n_cells;
     const double* node_xyz;        /* [n_nodes][dim] */
-    const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D); all HFV_HEX or all HFV_TET (3D) */
+    const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D); HFV_TET / PRISM / PYRAMID / HEX (3D) */
     const int64_t* cell_node_ptr;  /* [n_cells + 1] CSR offsets */
     const int32_t* cell_node_idx;  /* [cell_node_ptr[n_cells]] vertex ids in local order */
     const double* period;          /* [dim] periodic length per axis, 0 = open (transmissive) */

@@ -253,7 +253,7 @@ class Scheme:
         self.lib.or_scheme_sizes(self.h, sz)
         self.N, self.M, self.Md, self.nq, self.nfp, self.nv = list(sz)
         self.dim = mesh.dim
-        nf_of = {1: 3, 2: 4, 3: 4, 4: 6}
+        nf_of = {1: 3, 2: 4, 3: 4, 4: 6, 5: 5, 6: 5}
         self.nf = np.array([nf_of[int(t)] for t in mesh.src.cell_type], np.int32) if mesh.n_cells < 300000 else None
 
     def __del__(self):
@@ -262,7 +262,7 @@ class Scheme:
             self.h = None
 
     def _nf(self, c):
-        return {1: 3, 2: 4, 3: 4, 4: 6}[int(self.mesh.src.cell_type[c])]
+        return {1: 3, 2: 4, 3: 4, 4: 6, 5: 5, 6: 5}[int(self.mesh.src.cell_type[c])]
 
     def Q(self, c):
         return self._nf(c) * self.nfp

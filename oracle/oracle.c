@@ -44,6 +44,8 @@
 #define OR_QUAD 2
 #define OR_TET 3
 #define OR_HEX 4
+#define OR_PRISM 5
+#define OR_PYRAMID 6
 
 #define C_LIN 0
 #define C_CW 1
@@ -70,12 +72,53 @@ static const int HEX_F[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4},
  * (b-a) x (c-a) points outward: the face opposite vertex k is face k */
 static const int TET_F[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
 
-static int t_nverts(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_TET ? 4 : t == OR_HEX ? 8 : 0; }
-static int t_nfaces(int t) { return t == OR_TRI ? 3 : t == OR_QUAD ? 4 : t == OR_TET ? 4 : t == OR_HEX ? 6 : 0; }
-static int t_fnv(int t) { return t == OR_HEX ? 4 : t == OR_TET ? 3 : 2; }
+/* prism: triangles v0 v1 v2 and v3 v4 v5 (v3 over v0), then the three
+ * quadrilateral sides; pyramid: the four triangles to the apex v4, then the
+ * base v0 v1 v2 v3 (counter-clockwise seen from the apex).  Every face is
+ * listed with its area vector pointing out. */
+static const int PRISM_F[5][4] = {{0, 2, 1, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+static const int PYR_F[5][4] = {{0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}, {0, 3, 2, 1}};
+
+static int t_nverts(int t)
+{
+    switch (t) {
+    case OR_TRI: return 3;
+    case OR_QUAD: case OR_TET: return 4;
+    case OR_PYRAMID: return 5;
+    case OR_PRISM: return 6;
+    case OR_HEX: return 8;
+    }
+    return 0;
+}
+static int t_nfaces(int t)
+{
+    switch (t) {
+    case OR_TRI: return 3;
+    case OR_QUAD: case OR_TET: return 4;
+    case OR_PRISM: case OR_PYRAMID: return 5;
+    case OR_HEX: return 6;
+    }
+    return 0;
+}
+/* vertices of face f of a type-t cell */
+static int t_fnv(int t, int f)
+{
+    if (t == OR_TRI || t == OR_QUAD) return 2;
+    if (t == OR_TET) return 3;
+    if (t == OR_PRISM) return PRISM_F[f][3] < 0 ? 3 : 4;
+    if (t == OR_PYRAMID) return PYR_F[f][3] < 0 ? 3 : 4;
+    return 4;
+}
 static int t_fv(int t, int f, int k)
 {
-    return t == OR_TRI ? TRI_F[f][k] : t == OR_QUAD ? QUAD_F[f][k] : t == OR_TET ? TET_F[f][k] : HEX_F[f][k];
+    switch (t) {
+    case OR_TRI: return TRI_F[f][k];
+    case OR_QUAD: return QUAD_F[f][k];
+    case OR_TET: return TET_F[f][k];
+    case OR_PRISM: return PRISM_F[f][k];
+    case OR_PYRAMID: return PYR_F[f][k];
+    }
+    return HEX_F[f][k];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -156,6 +199,50 @@ static int cell_rule(int type, const double* v, int n, double* px, double* pw)
                     double s1 = gx[i], t = gx[j], u = gx[k];
                     for (int d = 0; d < 3; ++d) px[3 * np + d] = v[d] + s1 * a[d] + s1 * t * b[d] + s1 * t * u * cc[d];
                     pw[np++] = gw[i] * gw[j] * gw[k] * s1 * s1 * t * det;
+                }
+    } else if (type == OR_PRISM) {
+        /* x = (1-z) [T0 + a (T1-T0) + a b (T2-T1)] + z [same on the top
+         * triangle], the bottom triangle T0 T1 T2 = v0 v1 v2 and the top
+         * v3 v4 v5 in collapsed coordinates (a, b); |J| = a |det dx/d(p, q, z)|
+         * with (p, q) = (a (1-b), a b) the triangle's barycentric pair */
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    double a = gx[i], b = gx[j], z = gx[k];
+                    double p = a * (1.0 - b), q = a * b, Jm[3][3];
+                    for (int d = 0; d < 3; ++d) {
+                        double lo = v[d] + p * (v[3 + d] - v[d]) + q * (v[6 + d] - v[d]);
+                        double hi = v[9 + d] + p * (v[12 + d] - v[9 + d]) + q * (v[15 + d] - v[9 + d]);
+                        px[3 * np + d] = lo + z * (hi - lo);
+                        Jm[d][0] = (1.0 - z) * (v[3 + d] - v[d]) + z * (v[12 + d] - v[9 + d]);
+                        Jm[d][1] = (1.0 - z) * (v[6 + d] - v[d]) + z * (v[15 + d] - v[9 + d]);
+                        Jm[d][2] = hi - lo;
+                    }
+                    double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1])
+                               - Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0])
+                               + Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+                    pw[np++] = gw[i] * gw[j] * gw[k] * a * fabs(det);
+                }
+    } else if (type == OR_PYRAMID) {
+        /* the cone from the apex v4 over the bilinear base: x = B(s, t) +
+         * u (v4 - B(s, t)), B(0,0) = v0, B(1,0) = v1, B(1,1) = v2, B(0,1) = v3 */
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    double s = gx[i], t = gx[j], u = gx[k], Jm[3][3];
+                    for (int d = 0; d < 3; ++d) {
+                        double B = (1 - s) * (1 - t) * v[d] + s * (1 - t) * v[3 + d] + s * t * v[6 + d] + (1 - s) * t * v[9 + d];
+                        double Bs = (1 - t) * (v[3 + d] - v[d]) + t * (v[6 + d] - v[9 + d]);
+                        double Bt = (1 - s) * (v[9 + d] - v[d]) + s * (v[6 + d] - v[3 + d]);
+                        px[3 * np + d] = B + u * (v[12 + d] - B);
+                        Jm[d][0] = (1 - u) * Bs;
+                        Jm[d][1] = (1 - u) * Bt;
+                        Jm[d][2] = v[12 + d] - B;
+                    }
+                    double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1])
+                               - Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0])
+                               + Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
+                    pw[np++] = gw[i] * gw[j] * gw[k] * fabs(det);
                 }
     } else if (type == OR_HEX) {
         /* trilinear map over the unit cube; vertex k sits at corner (sx,sy,sz) */
@@ -247,7 +334,7 @@ static void sort4(int64_t* k, int n)
 
 static void face_centre(const or_mesh* m, int64_t c, int f, double* x)
 {
-    int t = m->type[c], fnv = t_fnv(t);
+    int t = m->type[c], fnv = t_fnv(t, f);
     x[0] = x[1] = x[2] = 0.0;
     for (int k = 0; k < fnv; ++k)
         for (int d = 0; d < 3; ++d) x[d] += m->xyz[3 * (int64_t)m->cidx[m->cptr[c] + t_fv(t, f, k)] + d];
@@ -257,14 +344,14 @@ static void face_centre(const or_mesh* m, int64_t c, int f, double* x)
 /* area vector of a local face (outward from cell c) */
 static void face_areavec(const or_mesh* m, int64_t c, int f, double* A)
 {
-    int t = m->type[c];
+    int t = m->type[c], fnv = t_fnv(t, f);
     double P[4][3];
-    for (int k = 0; k < t_fnv(t); ++k)
+    for (int k = 0; k < fnv; ++k)
         for (int d = 0; d < 3; ++d) P[k][d] = m->xyz[3 * (int64_t)m->cidx[m->cptr[c] + t_fv(t, f, k)] + d];
-    if (t_fnv(t) == 2) {
+    if (fnv == 2) {
         /* counter-clockwise cell: outward normal of edge a->b is (dy, -dx) */
         A[0] = P[1][1] - P[0][1]; A[1] = -(P[1][0] - P[0][0]); A[2] = 0.0;
-    } else if (t_fnv(t) == 3) {
+    } else if (fnv == 3) {
         double u[3], w[3];
         for (int d = 0; d < 3; ++d) { u[d] = P[1][d] - P[0][d]; w[d] = P[2][d] - P[0][d]; }
         A[0] = 0.5 * (u[1] * w[2] - u[2] * w[1]);
@@ -308,8 +395,8 @@ or_mesh* or_mesh_create(int dim, int64_t nn, int64_t nc, const double* xyz, cons
     for (int d = 0; d < 3; ++d) m->period[d] = d < dim ? period[d] : 0.0;
     for (int64_t c = 0; c < nc; ++c) {
         int t = type[c];
-        if ((dim == 2 && t != OR_TRI && t != OR_QUAD) || (dim == 3 && t != OR_HEX && t != OR_TET) ||
-            (dim == 3 && t != type[0]) ||
+        if ((dim == 2 && t != OR_TRI && t != OR_QUAD) ||
+            (dim == 3 && t != OR_HEX && t != OR_TET && t != OR_PRISM && t != OR_PYRAMID) ||
             cptr[c + 1] - cptr[c] != t_nverts(t)) { fail("unsupported cell type or vertex count"); or_mesh_free(m); return NULL; }
     }
 
@@ -321,7 +408,7 @@ or_mesh* or_mesh_create(int dim, int64_t nn, int64_t nc, const double* xyz, cons
     for (int64_t c = 0; c < nc; ++c) {
         int t = type[c];
         for (int f = 0; f < t_nfaces(t); ++f, ++h) {
-            int fnv = t_fnv(t);
+            int fnv = t_fnv(t, f);
             for (int k = 0; k < 4; ++k) H[h].key[k] = k < fnv ? cidx[cptr[c] + t_fv(t, f, k)] : -1;
             sort4(H[h].key, fnv);
             H[h].cell = c; H[h].face = f;
@@ -558,10 +645,13 @@ or_scheme* or_scheme_create(or_mesh* m, const or_params* p)
     s->Md = 2 * K_of(1, s->d);
     if (s->M < s->N || s->M < s->Md) { free(s); fail("stencil too small"); return NULL; }
     /* Gauss points per face direction, exact to degree >= r: ceil((r+1)/2) on
-     * edges and quadrilaterals; ceil((r+2)/2) per direction of the collapsed
-     * rule on triangles (a tetrahedron's faces), exact to degree 2 nq - 2 */
-    const int tet = s->d == 3 && m->type[0] == OR_TET;
-    s->nq = tet ? (r + 3) / 2 : (r + 2) / 2;
+     * edges and on the quadrilaterals of all-hexahedron meshes; ceil((r+2)/2)
+     * per direction of the collapsed rule on triangles, exact to degree
+     * 2 nq - 2, and on every face of a 3D mesh that has any cell other than
+     * a hexahedron (all faces then carry nq^2 points) */
+    int all_hex = s->d == 3;
+    for (int64_t c = 0; all_hex && c < m->nc; ++c) all_hex = m->type[c] == OR_HEX;
+    s->nq = s->d == 3 && !all_hex ? (r + 3) / 2 : (r + 2) / 2;
     s->nfp = s->d == 2 ? s->nq : s->nq * s->nq;
     /* monomial exponents by total degree, then descending powers of xi, eta */
     int k = 0;
@@ -582,14 +672,14 @@ or_scheme* or_scheme_create(or_mesh* m, const or_params* p)
         int64_t c = m->fo[g];
         int t = m->type[c], f = m->ffo[g];
         double P[4][3];
-        for (int kk = 0; kk < t_fnv(t); ++kk)
+        for (int kk = 0; kk < t_fnv(t, f); ++kk)
             for (int dd = 0; dd < 3; ++dd) P[kk][dd] = m->xyz[3 * (int64_t)m->cidx[m->cptr[c] + t_fv(t, f, kk)] + dd];
         if (s->d == 2) {
             for (int a = 0; a < s->nq; ++a) {
                 for (int dd = 0; dd < 3; ++dd) s->fqx[(g * s->nfp + a) * 3 + dd] = P[0][dd] + gx[a] * (P[1][dd] - P[0][dd]);
                 s->fqw[g * s->nfp + a] = gw[a] * m->farea[g];
             }
-        } else if (tet) {
+        } else if (t_fnv(t, f) == 3) {
             /* collapsed rule on the face triangle P0 P1 P2: x = P0 + u (P1-P0)
              * + u v (P2-P1), weight w_i w_j 2 u |S| (the map's Jacobian is
              * 2 |S| u) */
@@ -749,8 +839,8 @@ static int pinv_qr(const double* A, int M, int N, double* X)
 static double ipow(double x, int e) { double r = 1.0; for (int i = 0; i < e; ++i) r *= x; return r; }
 
 /* reference map of cell i: xi = Jinv (x - v0), from its corner simplex
- * (triangle v0 v1 v2; quadrilateral v0 v1 v3; tetrahedron v0 v1 v2 v3;
- * hexahedron v0 v1 v3 v4),
+ * (triangle v0 v1 v2; quadrilateral v0 v1 v3; tetrahedron and prism
+ * v0 v1 v2 v3; hexahedron and pyramid v0 v1 v3 v4),
  * the reading taken for the paper's transformation (Sec. 2.1) */
 static void ref_map(const or_scheme* s, int64_t i, double* x0, double Jinv[3][3], double* detJ)
 {
@@ -758,7 +848,8 @@ static void ref_map(const or_scheme* s, int64_t i, double* x0, double Jinv[3][3]
     double v[3 * MAXV];
     cell_verts(m, i, v);
     int t = m->type[i];
-    int c1 = 1, c2 = (t == OR_TRI || t == OR_TET) ? 2 : 3, c3 = t == OR_TET ? 3 : 4;
+    int simplex_first = t == OR_TRI || t == OR_TET || t == OR_PRISM;
+    int c1 = 1, c2 = simplex_first ? 2 : 3, c3 = (t == OR_TET || t == OR_PRISM) ? 3 : 4;
     double J[3][3] = {{0}};
     for (int d = 0; d < 3; ++d) {
         x0[d] = v[d];

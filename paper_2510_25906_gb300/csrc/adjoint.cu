@@ -470,7 +470,7 @@ int adjoint_prepare(hfv_scheme* s, cudaStream_t st)
 {
     if (s->adj.base) return HFV_OK;
     const int64_t nc = s->mesh->nc, M = s->M, nv = s->nv;
-    const int64_t qtot = nc * (s->d == 2 || s->tet ? 4 : 6) * s->nfp;
+    const int64_t qtot = nc * s->nfmax * s->nfp;
     std::vector<int64_t> ptr(nc + 1, 0);
     std::vector<int32_t> idx(nc * M);
     for (int64_t e = 0; e < nc * M; ++e) ++ptr[s->sten[e] + 1];
@@ -522,10 +522,15 @@ int launch_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double*
         case 3: return run_vjp<Cfg<2, 3>>(s, lam, g, st);
         case 4: return run_vjp<Cfg<2, 4>>(s, lam, g, st);
         }
-    } else if (s->tet) {
+    } else if (s->fam == 1) {
         switch (s->r) {
         case 1: return run_vjp<Cfg<3, 1, 1>>(s, lam, g, st);
         case 2: return run_vjp<Cfg<3, 2, 1>>(s, lam, g, st);
+        }
+    } else if (s->fam == 2) {
+        switch (s->r) {
+        case 1: return run_vjp<Cfg<3, 1, 2>>(s, lam, g, st);
+        case 2: return run_vjp<Cfg<3, 2, 2>>(s, lam, g, st);
         }
     } else {
         switch (s->r) {

@@ -19,7 +19,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-bool residual_supported(int d, int r, int tet);
+bool residual_supported(int d, int r, int fam);
 
 }  // namespace hfv
 
@@ -90,10 +90,10 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
     if (!mesh || !p || !out) { set_error("hfv_scheme_create: NULL argument"); return HFV_ERR_ARG; }
     *out = nullptr;
     const int r = p->order - 1;
-    const int tet = mesh->dim == 3 && mesh->type[0] == HFV_TET;
-    if (r < 1 || !residual_supported(mesh->dim, r, tet)) {
+    const int fam = element_family(mesh);
+    if (r < 1 || !residual_supported(mesh->dim, r, fam)) {
         set_error("hfv_scheme_create: order " + std::to_string(p->order) + " is not built for dim " +
-                  std::to_string(mesh->dim) + (tet ? " tetrahedra" : ""));
+                  std::to_string(mesh->dim) + (fam == 1 ? " tetrahedra" : fam == 2 ? " mixed elements" : ""));
         return HFV_ERR_ARG;
     }
     if (p->stencil_factor != 2.0) { set_error("hfv_scheme_create: only stencil_factor = 2 (M = 2K) is built"); return HFV_ERR_ARG; }

@@ -19,7 +19,10 @@ constexpr int kMaxOrder = 5;   // r <= 4
 // (v2 - v0) x (v3 - v1) is outward)
 int type_nverts(int t);
 int type_nfaces(int t);
-int type_face_nverts(int t);
+int face_nverts(int t, int f);
+// 0: 2D or all hexahedra, 1: all tetrahedra, 2: any other 3D mix of
+// tetrahedra, prisms, pyramids and hexahedra
+int element_family(const hfv_mesh* m);
 int type_face_vertex(int t, int f, int k);
 
 void set_error(const std::string& msg);
@@ -133,7 +136,8 @@ struct hfv_scheme {
     hfv_mesh* mesh = nullptr;
     hfv_scheme_params p{};
     int r = 0, d = 0, nv = 0, N = 0, M = 0, Md = 0, nq = 0, nfp = 0;
-    int tet = 0;                    // 3D mesh of tetrahedra (else hexahedra)
+    int fam = 0;                    // element family (element_family)
+    int nfmax = 4;                  // face slots per cell: 4 (2D, tetrahedra) or 6
     int64_t qtot = 0;
     int64_t nc_pad = 0;             // cells rounded up to a multiple of 64 (bulk-copy tiles)
     int64_t ltot = 0;               // elements of L

@@ -10,11 +10,13 @@ namespace hfv {
 
 constexpr int cK(int r, int d) { return d == 2 ? (r + 1) * (r + 2) / 2 : (r + 1) * (r + 2) * (r + 3) / 6; }
 
-// sizes fixed by (dimension, polynomial degree, tetrahedra or not): M =
+// sizes fixed by (dimension, polynomial degree, element family): M =
 // 2 K(r, d) central cells, N = K(r, d) - 1 coefficients, Md = 2 K(1, d),
-// nq Gauss points per face direction: ceil((r+1)/2) on edges and
-// quadrilaterals, ceil((r+2)/2) per direction of the collapsed rule on the
-// triangles of tetrahedra
+// nq Gauss points per face direction: ceil((r+1)/2) on edges and on the
+// quadrilaterals of hexahedral meshes, ceil((r+2)/2) per direction of the
+// collapsed rule on triangles, and on every face of a mesh with triangular
+// faces.  TET: 0 hexahedra, 1 tetrahedra (four faces), 2 any mix of
+// tetrahedra, prisms, pyramids and hexahedra (up to six faces)
 template <int D_, int R_, int TET_ = 0>
 struct Cfg {
     static constexpr int D = D_;
@@ -26,7 +28,7 @@ struct Cfg {
     static constexpr int MD = 2 * cK(1, D);
     static constexpr int NQ = TET ? (R + 3) / 2 : (R + 2) / 2;
     static constexpr int NFP = D == 2 ? NQ : NQ * NQ;
-    static constexpr int NFMAX = D == 2 ? 4 : TET ? 4 : 6;
+    static constexpr int NFMAX = D == 2 ? 4 : TET == 1 ? 4 : 6;
     static constexpr int QMAX = NFMAX * NFP;
     static constexpr int NOI = N * (N + 1) / 2;
 };

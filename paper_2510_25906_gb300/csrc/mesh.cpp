@@ -20,15 +20,45 @@ static const int kHexFaces[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4},
 // tetrahedron v0 v1 v2 v3 of positive volume: face k is opposite vertex k,
 // listed so that (p1 - p0) x (p2 - p0) points outward
 static const int kTetFaces[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+// prism: triangles v0 v1 v2 (counter-clockwise seen from the other end) and
+// v3 v4 v5 (v3 joined to v0); pyramid: base v0..v3 counter-clockwise seen
+// from the apex v4.  Triangular faces first, quadrilaterals after.
+static const int kPrismFaces[5][4] = {{0, 2, 1, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
+static const int kPyramidFaces[5][4] = {{0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}, {0, 3, 2, 1}};
 
-int type_nverts(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 8 : 0; }
-int type_nfaces(int t) { return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 6 : 0; }
-int type_face_nverts(int t) { return t == HFV_HEX ? 4 : t == HFV_TET ? 3 : 2; }
+int type_nverts(int t)
+{
+    return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 8 : t == HFV_PRISM ? 6 : t == HFV_PYRAMID ? 5 : 0;
+}
+int type_nfaces(int t)
+{
+    return t == HFV_TRI ? 3 : t == HFV_QUAD ? 4 : t == HFV_TET ? 4 : t == HFV_HEX ? 6 : t == HFV_PRISM || t == HFV_PYRAMID ? 5 : 0;
+}
+int face_nverts(int t, int f)
+{
+    if (t == HFV_TRI || t == HFV_QUAD) return 2;
+    if (t == HFV_TET) return 3;
+    if (t == HFV_PRISM) return f < 2 ? 3 : 4;
+    if (t == HFV_PYRAMID) return f < 4 ? 3 : 4;
+    return 4;
+}
+int element_family(const hfv_mesh* m)
+{
+    if (m->dim == 2) return 0;
+    bool hex = true, tet = true;
+    for (uint8_t t : m->type) {
+        hex = hex && t == HFV_HEX;
+        tet = tet && t == HFV_TET;
+    }
+    return hex ? 0 : tet ? 1 : 2;
+}
 int type_face_vertex(int t, int f, int k)
 {
     if (t == HFV_TRI) return kTriFaces[f][k];
     if (t == HFV_QUAD) return kQuadFaces[f][k];
     if (t == HFV_TET) return kTetFaces[f][k];
+    if (t == HFV_PRISM) return kPrismFaces[f][k];
+    if (t == HFV_PYRAMID) return kPyramidFaces[f][k];
     return kHexFaces[f][k];
 }
 
@@ -56,7 +86,8 @@ inline const double* node(const hfv_mesh* m, int64_t c, int k) { return &m->xyz[
 void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
 {
     int t = m->type[c];
-    if (type_face_nverts(t) == 2) {
+    const int fnv = face_nverts(t, f);
+    if (fnv == 2) {
         const double* a = node(m, c, type_face_vertex(t, f, 0));
         const double* b = node(m, c, type_face_vertex(t, f, 1));
         A[0] = b[1] - a[1];
@@ -67,7 +98,7 @@ void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
     const double* p0 = node(m, c, type_face_vertex(t, f, 0));
     const double* p1 = node(m, c, type_face_vertex(t, f, 1));
     const double* p2 = node(m, c, type_face_vertex(t, f, 2));
-    if (type_face_nverts(t) == 3) {
+    if (fnv == 3) {
         double e[3], g[3];
         for (int k = 0; k < 3; ++k) { e[k] = p1[k] - p0[k]; g[k] = p2[k] - p0[k]; }
         A[0] = 0.5 * (e[1] * g[2] - e[2] * g[1]);
@@ -83,12 +114,53 @@ void area_vector(const hfv_mesh* m, int64_t c, int f, double A[3])
     A[2] = 0.5 * (e[0] * g[1] - e[1] * g[0]);
 }
 
+// |V| = (1/3) sum_f int_f x . dA over the faces (triangles flat, quadrilaterals
+// bilinear), relative to vertex 0; the integrand of a bilinear face has
+// degree <= 2 per direction, so the 2x2 Gauss rule is exact
+double divergence_measure(const hfv_mesh* m, int64_t c)
+{
+    const int t = m->type[c];
+    const double* o = node(m, c, 0);
+    const double g = 0.5 / std::sqrt(3.0);
+    const double pts[2] = {0.5 - g, 0.5 + g};
+    double vol = 0.0;
+    for (int f = 0; f < type_nfaces(t); ++f) {
+        double p[4][3];
+        const int fnv = face_nverts(t, f);
+        for (int a = 0; a < fnv; ++a)
+            for (int k = 0; k < 3; ++k) p[a][k] = node(m, c, type_face_vertex(t, f, a))[k] - o[k];
+        if (fnv == 3) {
+            double e[3], h[3];
+            for (int k = 0; k < 3; ++k) { e[k] = p[1][k] - p[0][k]; h[k] = p[2][k] - p[0][k]; }
+            const double A[3] = {0.5 * (e[1] * h[2] - e[2] * h[1]), 0.5 * (e[2] * h[0] - e[0] * h[2]),
+                                 0.5 * (e[0] * h[1] - e[1] * h[0])};
+            for (int k = 0; k < 3; ++k) vol += (p[0][k] + p[1][k] + p[2][k]) / 3.0 * A[k] / 3.0;
+            continue;
+        }
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                const double s = pts[i], u = pts[j];
+                double x[3], xs[3], xu[3];
+                for (int k = 0; k < 3; ++k) {
+                    x[k] = (1 - s) * (1 - u) * p[0][k] + s * (1 - u) * p[1][k] + s * u * p[2][k] + (1 - s) * u * p[3][k];
+                    xs[k] = (1 - u) * (p[1][k] - p[0][k]) + u * (p[2][k] - p[3][k]);
+                    xu[k] = (1 - s) * (p[3][k] - p[0][k]) + s * (p[2][k] - p[1][k]);
+                }
+                const double n[3] = {xs[1] * xu[2] - xs[2] * xu[1], xs[2] * xu[0] - xs[0] * xu[2], xs[0] * xu[1] - xs[1] * xu[0]};
+                vol += 0.25 * (x[0] * n[0] + x[1] * n[1] + x[2] * n[2]) / 3.0;
+            }
+    }
+    return vol;
+}
+
 // cell measure: triangle cross product, quadrilateral shoelace, tetrahedron
 // triple product, hexahedron 2x2x2 Gauss rule on the trilinear map (exact:
-// det J has degree <= 2 per direction)
+// det J has degree <= 2 per direction), prism and pyramid by the divergence
+// theorem over their faces
 double cell_measure(const hfv_mesh* m, int64_t c)
 {
     int t = m->type[c];
+    if (t == HFV_PRISM || t == HFV_PYRAMID) return divergence_measure(m, c);
     if (t == HFV_TET) {
         const double* o = node(m, c, 0);
         double a[3], b[3], q[3];
@@ -174,9 +246,8 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
         for (int k = 0; k < 3; ++k) m->period[k] = k < d->dim ? d->period[k] : 0.0;
         for (int64_t c = 0; c < nc; ++c) {
             int t = m->type[c];
-            // 3D meshes are all hexahedra or all tetrahedra
             bool ok = (d->dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) ||
-                      (d->dim == 3 && (t == HFV_HEX || t == HFV_TET) && t == m->type[0]);
+                      (d->dim == 3 && (t == HFV_HEX || t == HFV_TET || t == HFV_PRISM || t == HFV_PYRAMID));
             ok = ok && m->cptr[c + 1] - m->cptr[c] == type_nverts(t);
             for (int64_t k = m->cptr[c]; ok && k < m->cptr[c + 1]; ++k) ok = m->cidx[k] >= 0 && m->cidx[k] < m->nn;
             if (!ok) {
@@ -205,7 +276,7 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
             int t = m->type[c];
             for (int f = 0; f < type_nfaces(t); ++f) {
                 Key4 k{{-1, -1, -1, -1}};
-                int fn = type_face_nverts(t);
+                int fn = face_nverts(t, f);
                 for (int q = 0; q < fn; ++q) k.v[q] = m->cidx[m->cptr[c] + type_face_vertex(t, f, q)];
                 std::sort(k.v, k.v + fn);
                 auto it = open.find(k);
@@ -233,11 +304,11 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
                 int f = (int)(kv.second % kMaxFaces);
                 int t = m->type[c];
                 double x[3] = {0, 0, 0};
-                for (int q = 0; q < type_face_nverts(t); ++q)
+                for (int q = 0; q < face_nverts(t, f); ++q)
                     for (int k = 0; k < 3; ++k) x[k] += node(m, c, type_face_vertex(t, f, q))[k];
                 Key4 key{{0, 0, 0, 0}};
                 for (int k = 0; k < 3; ++k) {
-                    double xc = x[k] / type_face_nverts(t);
+                    double xc = x[k] / face_nverts(t, f);
                     const int64_t S = int64_t(1) << 30;
                     if (m->period[k] > 0) {
                         int64_t q = std::llround(xc / m->period[k] * (double)S) % S;
@@ -260,13 +331,13 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
                     link(c2, f2, c, f);
                     double y[3] = {0, 0, 0};
                     int t2 = m->type[c2];
-                    for (int q = 0; q < type_face_nverts(t2); ++q)
+                    for (int q = 0; q < face_nverts(t2, f2); ++q)
                         for (int k = 0; k < 3; ++k) y[k] += node(m, c2, type_face_vertex(t2, f2, q))[k];
                     for (int k = 0; k < 3; ++k) {
                         // x_c2 + s * period lies next to c  (s integer)
                         int s = 0;
                         if (m->period[k] > 0)
-                            s = (int)std::lround((x[k] / type_face_nverts(t) - y[k] / type_face_nverts(t2)) / m->period[k]);
+                            s = (int)std::lround((x[k] / face_nverts(t, f) - y[k] / face_nverts(t2, f2)) / m->period[k]);
                         m->nshift[(c * kMaxFaces + f) * 3 + k] = (int8_t)s;
                         m->nshift[(c2 * kMaxFaces + f2) * 3 + k] = (int8_t)(-s);
                     }

@@ -797,7 +797,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.nfs = a.nfs;
     p.nv = s->nv;
     p.nfp = s->nfp;
-    p.qmax = (s->d == 2 || s->tet ? 4 : 6) * s->nfp;
+    p.qmax = s->nfmax * s->nfp;
     p.FS = (T*)a.FS; p.raw = a.raw; p.cls = a.cls; p.queue = a.queue; p.counts = a.counts;
     p.bcount = a.bcount; p.nblocks = s->nblocks; p.status = a.status;
     p.gamma = (T)s->p.gamma; p.alpha_m = (T)s->p.alpha_m; p.beta_m = (T)s->p.beta_m;
@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
 }
 
 template <class T>
-static auto pick(int d, int r, int tet)
+static auto pick(int d, int r, int fam)
     -> int (*)(hfv_scheme*, const T*, T*, const uint8_t*, uint8_t*, cudaStream_t, const T*, const StageRK*)
 {
     if (d == 2) {
@@ -1049,10 +1049,15 @@ static auto pick(int d, int r, int tet)
         case 3: return run_residual<Cfg<2, 3>, T>;
         case 4: return run_residual<Cfg<2, 4>, T>;
         }
-    } else if (tet) {
+    } else if (fam == 1) {
         switch (r) {
         case 1: return run_residual<Cfg<3, 1, 1>, T>;
         case 2: return run_residual<Cfg<3, 2, 1>, T>;
+        }
+    } else if (fam == 2) {
+        switch (r) {
+        case 1: return run_residual<Cfg<3, 1, 2>, T>;
+        case 2: return run_residual<Cfg<3, 2, 2>, T>;
         }
     } else {
         switch (r) {
@@ -1064,14 +1069,14 @@ static auto pick(int d, int r, int tet)
     return nullptr;
 }
 
-bool residual_supported(int d, int r, int tet) { return pick<double>(d, r, tet) != nullptr; }
+bool residual_supported(int d, int r, int fam) { return pick<double>(d, r, fam) != nullptr; }
 
 static int residual_any(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out,
                         cudaStream_t st, const void* ua, const StageRK* rk)
 {
     if (s->p.precision == HFV_FP32)
-        return pick<float>(s->d, s->r, s->tet)(s, (const float*)U, (float*)R, forced, cls_out, st, (const float*)ua, rk);
-    return pick<double>(s->d, s->r, s->tet)(s, (const double*)U, (double*)R, forced, cls_out, st, (const double*)ua, rk);
+        return pick<float>(s->d, s->r, s->fam)(s, (const float*)U, (float*)R, forced, cls_out, st, (const float*)ua, rk);
+    return pick<double>(s->d, s->r, s->fam)(s, (const double*)U, (double*)R, forced, cls_out, st, (const double*)ua, rk);
 }
 
 int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)

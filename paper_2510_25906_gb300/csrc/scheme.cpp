@@ -58,10 +58,13 @@ int build_stencils(hfv_scheme* s)
     s->M = (int)std::llround(s->p.stencil_factor * binom_K(s->r, d));
     s->Md = 2 * binom_K(1, d);
     // Gauss points per face direction, exact to degree >= r: ceil((r+1)/2) on
-    // edges and quadrilaterals, ceil((r+2)/2) per direction of the collapsed
-    // rule on triangles (tetrahedra), exact to degree 2 nq - 2
-    s->tet = d == 3 && m->type[0] == HFV_TET;
-    s->nq = s->tet ? (s->r + 3) / 2 : (s->r + 2) / 2;
+    // edges and on the quadrilaterals of hexahedral meshes, ceil((r+2)/2) per
+    // direction of the collapsed rule on triangles (exact to degree
+    // 2 nq - 2), used on every face of a mesh with triangular faces so that
+    // all faces carry nq^2 points
+    s->fam = element_family(m);
+    s->nfmax = d == 2 || s->fam == 1 ? 4 : 6;
+    s->nq = s->fam ? (s->r + 3) / 2 : (s->r + 2) / 2;
     s->nfp = d == 2 ? s->nq : s->nq * s->nq;
     if (s->M < s->N || s->M < s->Md || s->M > 255) {
         set_error("hfv_scheme_create: stencil size out of range");
@@ -72,7 +75,7 @@ int build_stencils(hfv_scheme* s)
     // face-point data live at a fixed stride per cell (the largest face count
     // of the dimension times the points per face): rows past a cell's own
     // face points are never read, so the padding costs memory, not traffic
-    const int64_t qs = (int64_t)(d == 2 || s->tet ? 4 : 6) * s->nfp;
+    const int64_t qs = (int64_t)s->nfmax * s->nfp;
     s->qoff.assign(nc + 1, 0);
     for (int64_t c = 0; c <= nc; ++c) s->qoff[c] = c * qs;
     s->qtot = s->qoff[nc];

@@ -144,7 +144,7 @@ int build_operators(hfv_scheme* s, void* stream)
     std::vector<int32_t> nbr(m->nbr.begin(), m->nbr.end());
     std::vector<int32_t> nfs(nc * 6, -1);
     {
-        const int64_t qs = (int64_t)(d == 2 || s->tet ? 4 : 6) * s->nfp;
+        const int64_t qs = (int64_t)s->nfmax * s->nfp;
         if (nc * qs >= (int64_t(1) << 31)) {
             set_error("hfv_scheme_create: mesh too large for 32-bit face-point offsets");
             return HFV_ERR_ARG;
@@ -173,7 +173,7 @@ int build_operators(hfv_scheme* s, void* stream)
                 for (int k = 0; k < 3; ++k) fk[cf * 3 + k] = m->nshift[cf * 3 + k];
             }
             int ot = m->type[oc];
-            for (int q = 0; q < type_face_nverts(ot); ++q) fvtx[cf * 4 + q] = m->cidx[m->cptr[oc] + type_face_vertex(ot, of, q)];
+            for (int q = 0; q < face_nverts(ot, of); ++q) fvtx[cf * 4 + q] = m->cidx[m->cptr[oc] + type_face_vertex(ot, of, q)];
         }
         ivol[c] = 1.0 / m->vol[c];
         double dx = d == 2 ? std::sqrt(m->vol[c]) : std::cbrt(m->vol[c]);

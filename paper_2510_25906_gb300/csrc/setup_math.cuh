@@ -90,8 +90,16 @@ struct SetupWork {
 
 namespace setup_detail {
 
-HD inline int nverts(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : 8; }
-HD inline int nfaces(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : 6; }
+// cell types as in hfv.h: 1 triangle, 2 quadrilateral, 3 tetrahedron,
+// 4 hexahedron, 5 prism, 6 pyramid
+HD inline int nverts(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : t == 5 ? 6 : t == 6 ? 5 : 8; }
+HD inline int nfaces(int t) { return t == 1 ? 3 : t == 2 ? 4 : t == 3 ? 4 : t == 5 || t == 6 ? 5 : 6; }
+// vertices of face f (prisms list their two triangles first, pyramids their
+// four triangles first)
+HD inline int face_nv(int t, int f)
+{
+    return t == 1 || t == 2 ? 2 : t == 3 ? 3 : t == 5 ? (f < 2 ? 3 : 4) : t == 6 ? (f < 4 ? 3 : 4) : 4;
+}
 
 HD inline double ipow(double x, int e)
 {
@@ -170,6 +178,56 @@ HD inline void cell_rule(const SetupParams& S, int t, const double v[8][3], F&& 
                     double x[3];
                     for (int q = 0; q < 3; ++q) x[q] = v[0][q] + s1 * a[q] + s1 * w * b[q] + s1 * w * z * cc[q];
                     f(x, S.gvw[i] * S.gvw[j] * S.gvw[k] * s1 * s1 * w * det);
+                }
+        return;
+    }
+    if (t == 5) {
+        // prism: the collapsed triangle (xi, eta) = (u (1 - w), u w) times
+        // zeta, x = (1 - zeta) T(v0, v1, v2) + zeta T(v3, v4, v5) with T the
+        // barycentric combination; weight u |det dx/d(xi, eta, zeta)|
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    const double u = S.gvx[i], w = S.gvx[j], z = S.gvx[k];
+                    const double xi = u * (1 - w), eta = u * w, l0 = 1 - xi - eta;
+                    double x[3], J[3][3];
+                    for (int q = 0; q < 3; ++q) {
+                        const double bot = l0 * v[0][q] + xi * v[1][q] + eta * v[2][q];
+                        const double top = l0 * v[3][q] + xi * v[4][q] + eta * v[5][q];
+                        x[q] = (1 - z) * bot + z * top;
+                        J[q][0] = (1 - z) * (v[1][q] - v[0][q]) + z * (v[4][q] - v[3][q]);
+                        J[q][1] = (1 - z) * (v[2][q] - v[0][q]) + z * (v[5][q] - v[3][q]);
+                        J[q][2] = top - bot;
+                    }
+                    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                    f(x, S.gvw[i] * S.gvw[j] * S.gvw[k] * u * fabs(det));
+                }
+        return;
+    }
+    if (t == 6) {
+        // pyramid: the unit cube collapsed onto the apex, x = (1 - s) B(a, b)
+        // + s v4 with B the bilinear base v0 v1 v2 v3; weight |det|, which
+        // carries (1 - s)^2
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                for (int k = 0; k < n; ++k) {
+                    const double a = S.gvx[i], b = S.gvx[j], sz = S.gvx[k];
+                    double x[3], J[3][3];
+                    for (int q = 0; q < 3; ++q) {
+                        const double B = (1 - a) * (1 - b) * v[0][q] + a * (1 - b) * v[1][q] + a * b * v[2][q] + (1 - a) * b * v[3][q];
+                        const double Ba = (1 - b) * (v[1][q] - v[0][q]) + b * (v[2][q] - v[3][q]);
+                        const double Bb = (1 - a) * (v[3][q] - v[0][q]) + a * (v[2][q] - v[1][q]);
+                        x[q] = (1 - sz) * B + sz * v[4][q];
+                        J[q][0] = (1 - sz) * Ba;
+                        J[q][1] = (1 - sz) * Bb;
+                        J[q][2] = v[4][q] - B;
+                    }
+                    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                    f(x, S.gvw[i] * S.gvw[j] * S.gvw[k] * fabs(det));
                 }
         return;
     }
@@ -262,8 +320,8 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     {
         const double* p0 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c]]];
         // corner simplex: triangle v0 v1 v2, quadrilateral v0 v1 v3,
-        // tetrahedron v0 v1 v2 v3, hexahedron v0 v1 v3 v4
-        int c1 = 1, c2 = (t == 1 || t == 3) ? 2 : 3, c3 = t == 3 ? 3 : 4;
+        // tetrahedron and prism v0 v1 v2 v3, hexahedron and pyramid v0 v1 v3 v4
+        int c1 = 1, c2 = (t == 1 || t == 3 || t == 5) ? 2 : 3, c3 = (t == 3 || t == 5) ? 3 : 4;
         const double* p1 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c] + c1]];
         const double* p2 = &S.xyz[3 * (int64_t)S.cidx[S.cptr[c] + c2]];
         for (int q = 0; q < 3; ++q) {
@@ -339,7 +397,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
         const int32_t* fv = &S.fvtx[(c * 6 + f) * 4];
         const int8_t* k = &S.fk[(c * 6 + f) * 3];
         double pv[4][3];
-        int nfv = d == 2 ? 2 : t == 3 ? 3 : 4;
+        const int nfv = face_nv(t, f);
         for (int a = 0; a < nfv; ++a)
             for (int q = 0; q < 3; ++q) pv[a][q] = S.xyz[3 * (int64_t)fv[a] + q] + k[q] * S.period[q];
         const double area = S.farea[c * 6 + f];
@@ -349,7 +407,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
                 double s = S.gfx[al];
                 for (int q = 0; q < 3; ++q) xp[q] = pv[0][q] + s * (pv[1][q] - pv[0][q]);
                 wgt = S.gfw[al] * area;
-            } else if (t == 3) {
+            } else if (nfv == 3) {
                 // triangle face: collapsed rule x = p0 + s (p1 - p0) + s u (p2 - p1),
                 // weight w_i w_j 2 s |S|
                 int i = al % S.nq, jj = al / S.nq;

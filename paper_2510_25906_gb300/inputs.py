@@ -41,7 +41,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-TRI, QUAD, TET, HEX = 1, 2, 3, 4
+TRI, QUAD, TET, HEX, PRISM, PYRAMID = 1, 2, 3, 4, 5, 6
 GAMMA = 1.4
 
 
@@ -227,6 +227,50 @@ def structured_tet_mesh(n: int, length: float = 1.0, periodic: bool = False, jit
     ncell = conn.shape[0]
     return Mesh(3, hx.nodes, np.full(ncell, TET, np.uint8), np.arange(ncell + 1, dtype=np.int64) * 4, conn.ravel(),
                 hx.period, f"tet{n}", {"n": n, "seed": seed})
+
+
+def mixed_element_mesh(n: int, nz: int | None = None, seed: int = 7, jitter: float = 0.15,
+                       p_pyramid: float = 0.3) -> Mesh:
+    """Open unit cube of all four 3D element types, conforming: the seeded
+    mixed triangle / quadrilateral mesh of [0,1]^2 (n x n, interior nodes
+    jittered) extruded through nz layers gives prisms and hexahedra
+    (interior layer heights jittered by up to `jitter` h); a seeded share
+    p_pyramid of the hexahedra is cut into six pyramids about its vertex
+    mean (each pyramid's base is a face of the hexahedron, so every
+    neighbour still sees that face whole), and in the bottom layer the
+    pyramid standing on the boundary z = 0 is cut into two tetrahedra."""
+    nz = n if nz is None else nz
+    rng = np.random.default_rng(seed)
+    base = mixed_tri_quad_mesh(n, seed=seed, jitter=jitter)
+    nb = base.n_nodes
+    zs = np.arange(nz + 1) / nz
+    z = np.repeat(zs[:, None], nb, axis=1)
+    z[1:nz] += jitter / nz * (rng.random((nz - 1, nb)) * 2.0 - 1.0)
+    nodes = np.concatenate([np.concatenate([base.nodes, z[k][:, None]], axis=1) for k in range(nz + 1)], axis=0)
+    nodes = [tuple(x) for x in nodes]
+    hex_faces = ((0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7))
+    conn, types = [], []
+    for k in range(nz):
+        for c in range(base.n_cells):
+            v = base.cell_idx[base.cell_ptr[c]:base.cell_ptr[c + 1]]
+            bot, top = [int(x) + k * nb for x in v], [int(x) + (k + 1) * nb for x in v]
+            if base.cell_type[c] == TRI:
+                conn.append(bot + top); types.append(PRISM)
+                continue
+            h = bot + top
+            if rng.random() >= p_pyramid:
+                conn.append(h); types.append(HEX)
+                continue
+            centre = len(nodes)
+            nodes.append(tuple(np.mean([nodes[i] for i in h], axis=0)))
+            for f, (a, b, cc, d) in enumerate(hex_faces):
+                pyr = [h[a], h[d], h[cc], h[b]]     # base counter-clockwise seen from the centre
+                if k == 0 and f == 0:
+                    conn.append([pyr[0], pyr[1], pyr[2], centre]); types.append(TET)
+                    conn.append([pyr[0], pyr[2], pyr[3], centre]); types.append(TET)
+                else:
+                    conn.append(pyr + [centre]); types.append(PYRAMID)
+    return _finish(3, np.asarray(nodes), types, conn, [0.0, 0.0, 0.0], f"mixed3d{n}", n=n, seed=seed)
 
 
 # ---------------------------------------------------------------------------
