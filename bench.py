@@ -244,7 +244,7 @@ def _k1_bytes(mesh, s, b):
     kernel: per cell U_i (nv b), stencil ids (4 M), L (Q M b), threshold (b),
     face-point states written (Q nv b), face counts + offsets + class (10).
     Stencil neighbours' states are L2 hits (U is read from DRAM once)."""
-    nf = np.where(mesh.cell_type == 4, 6, np.where(mesh.cell_type == 2, 4, 3)).astype(np.int64)
+    nf = np.array([0, 3, 4, 4, 6, 5, 5], np.int64)[mesh.cell_type]     # faces per cell type
     Q = nf * s.nfp
     per = s.nv * b + 4 * s.M + Q * s.M * b + b + Q * s.nv * b + 10
     return int(per.sum())

@@ -483,13 +483,11 @@ def mach2_shock_states(gamma: float = GAMMA, mach: float = 2.0):
     return (r, s * (1.0 - 1.0 / r), 0.0, 0.0, pr), (1.0, 0.0, 0.0, 0.0, 1.0)
 
 
-def adjoint_problem(n: int = 55, seed: int = 4, gamma: float = GAMMA):
-    """Open unit cube of n^3 hexahedra cut into 6 n^3 jittered tetrahedra
-    (55^3 * 6 = 998,250 cells by default): a Gaussian density pulse
+def shock_pulse_state(m: Mesh, gamma: float = GAMMA) -> np.ndarray:
+    """Conserved state on a 3D mesh of the unit cube: a Gaussian density pulse
     rho = 1 + 0.5 exp(-|x - (0.75, 0.5, 0.5)|^2 / (2 0.08^2)) in gas at rest
-    (p = 1) ahead of a planar Mach 2 shock at x = 0.4 moving along +x.
-    Cell values at the vertex means."""
-    m = structured_tet_mesh(n, 1.0, periodic=False, jitter=0.1, seed=seed)
+    (p = 1) ahead of a planar Mach 2 shock at x = 0.4 moving along +x,
+    evaluated at the cells' vertex means."""
     c = m.vertex_means()
     post, pre = mach2_shock_states(gamma)
     behind = c[:, 0] < 0.4
@@ -498,7 +496,14 @@ def adjoint_problem(n: int = 55, seed: int = 4, gamma: float = GAMMA):
     prim[:, 0] = np.where(behind, prim[:, 0], 1.0 + 0.5 * np.exp(-r2 / (2 * 0.08 ** 2)))
     rho, u, v, w, p = prim.T
     E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
-    return m, np.ascontiguousarray(np.stack([rho, rho * u, rho * v, rho * w, E]))
+    return np.ascontiguousarray(np.stack([rho, rho * u, rho * v, rho * w, E]))
+
+
+def adjoint_problem(n: int = 55, seed: int = 4, gamma: float = GAMMA):
+    """Open unit cube of n^3 hexahedra cut into 6 n^3 jittered tetrahedra
+    (55^3 * 6 = 998,250 cells by default) holding shock_pulse_state."""
+    m = structured_tet_mesh(n, 1.0, periodic=False, jitter=0.1, seed=seed)
+    return m, shock_pulse_state(m, gamma)
 
 
 def workload(name: str, scale: int | None = None):

@@ -52,6 +52,8 @@ def test_default_params(H):
     lambda: I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.2, seed=3),
     lambda: I.structured_tet_mesh(5, 1.0, periodic=False, jitter=0.1, seed=3),
     lambda: I.structured_tet_mesh(4, 1.0, periodic=True),
+    lambda: I.mixed_element_mesh(4, seed=7),
+    lambda: I.mixed_element_mesh(5, nz=3, seed=13),
 ])
 def test_connectivity_bit_exact_with_oracle(H, maker):
     m = maker()
@@ -82,3 +84,12 @@ def test_mesh_errors(H):
     with pytest.raises(H.HfvError) as e:
         H.Mesh(one)
     assert e.value.code == H.HFV_ERR_MESH
+
+
+def test_mixed_element_volumes_match_oracle(H):
+    """The library's measures (prisms and pyramids by the divergence theorem
+    over their faces) against the oracle's volume rules."""
+    m = I.mixed_element_mesh(5, seed=7)
+    vg = H.Mesh(m).volumes()
+    vo, _ = O.Mesh(m).geometry()
+    assert np.abs(vg - vo).max() <= 1e-14 * vo.max()

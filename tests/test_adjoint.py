@@ -73,6 +73,7 @@ CASES = {
                     dict(order=4, flux="hllc")),
     "tet_r2_hllc": (lambda: I.structured_tet_mesh(4, 1.0, periodic=False, jitter=0.1, seed=8), _hex_state,
                     dict(order=3, flux="hllc")),
+    "mixed3d_r2_hllc": (lambda: I.mixed_element_mesh(4, seed=7), _hex_state, dict(order=3, flux="hllc")),
 }
 
 
@@ -104,12 +105,14 @@ def test_vjp_against_central_differences(H, name):
         assert abs(fd - an) <= 1e-6 * scale, (fd, an, scale)
 
 
-@pytest.mark.parametrize("name", ["mixed_r2_hllc", "hex_r2_hllc", "tet_r2_hllc"])
+@pytest.mark.parametrize("name", ["mixed_r2_hllc", "hex_r2_hllc", "tet_r2_hllc", "mixed3d_r2_hllc"])
 def test_vjp_against_oracle_gradient(H, name):
     """The oracle's gradient: central differences of the oracle's FP64
     residual (classes forced), one input at a time."""
     mk, st, kw = CASES[name]
-    if name.startswith("mixed"):
+    if name.startswith("mixed3d"):
+        m = I.mixed_element_mesh(3, nz=2, seed=1, p_pyramid=0.6)   # every element type
+    elif name.startswith("mixed"):
         m = I.mixed_tri_quad_mesh(5, seed=4)
     elif name.startswith("hex"):
         m = I.structured_hex_mesh(3, 1.0, periodic=False, jitter=0.15, seed=5)

@@ -74,6 +74,12 @@ def _case(name):
     if name == "tet_r1_periodic":
         m = I.structured_tet_mesh(4, 1.0, periodic=True, jitter=0.0)
         return m, _tet_state(m), dict(order=2, flux="rusanov"), 1
+    if name == "mixed3d_r2":
+        m = I.mixed_element_mesh(6, seed=7)
+        return m, _tet_state(m), dict(order=3, flux="hllc"), 0
+    if name == "mixed3d_r1_hll":
+        m = I.mixed_element_mesh(5, nz=4, seed=13)
+        return m, _tet_state(m), dict(order=2, flux="hll"), 1
     raise KeyError(name)
 
 
@@ -90,7 +96,7 @@ def _tet_state(m):
 
 
 CASES = ["wave_tri32", "quadrant_r2", "quadrant_r4", "quadrant_r3_hll", "hex_r3", "hex_r2_open", "tet_r2_open",
-         "tet_r1_periodic"]
+         "tet_r1_periodic", "mixed3d_r2", "mixed3d_r1_hll"]
 _cache = {}
 
 
@@ -156,7 +162,7 @@ def test_forced_class_residual(H, name, precision, tol):
     if precision == "fp64":
         assert np.array_equal(cg, fin)
     ok = cg == fin
-    if precision == "fp32" and (name == "wave_tri32" or name.startswith("tet")):
+    if precision == "fp32" and (name == "wave_tri32" or name.startswith("tet") or name.startswith("mixed3d")):
         tol = max(tol, fp32_bound(m, om, U, R))
         assert tol < 1e-3
     err = _rel(Rg.double().cpu().numpy(), R, ok)
