@@ -356,6 +356,43 @@ def turbulence_variants(H, I, torch, dev, args):
     return out
 
 
+def mixed_variants(H, I, torch, dev, args):
+    """The 3D mixed-element workload: an open unit cube of tetrahedra, prisms,
+    pyramids and hexahedra (inputs.mixed_element_mesh), order 3, HLLC, a
+    Gaussian density pulse ahead of a Mach 2 shock; hybrid and pure CWENOZ
+    in FP32 and the hybrid in FP64, `steps` steps each, L2 flushed between
+    steps, with the candidate kernel's share of the measured HBM bandwidth
+    for the FP32 hybrid."""
+    t0 = time.perf_counter()
+    mesh = I.mixed_element_mesh(args.mixed_n)
+    U0 = I.shock_pulse_state(mesh)
+    gm = H.Mesh(mesh)
+    cells, steps = mesh.n_cells, args.mixed_steps
+    counts = np.bincount(mesh.cell_type, minlength=7)
+    out = {"workload": f"open unit cube, {cells} cells: {counts[3]} tetrahedra, {counts[5]} prisms, {counts[6]} pyramids, "
+                       f"{counts[4]} hexahedra; order 3, HLLC, SSP-RK3, Mach 2 shock and density pulse",
+           "cells": int(cells), "steps": steps, "mesh_s": round(time.perf_counter() - t0, 2)}
+    for scheme, prec in (("hybrid", "fp32"), ("cweno", "fp32"), ("hybrid", "fp64")):
+        g = H.Scheme(gm, order=3, flux="hllc", scheme=scheme, precision=prec)
+        ms, _, _, _ = time_steps(H, torch, g, U0, steps, 2, 0.5, dev)
+        entry = {"value": 3.0 * cells * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+        if (scheme, prec) == ("hybrid", "fp32"):
+            times = kernel_pass(H, torch, g, U0, steps, 0.5, dev)
+            k_ms, k_n = times["linear"]
+            kb = _k1_bytes(mesh, g, 4)
+            ach = kb / (k_ms / k_n * 1e-3) / 1e9
+            peak, _ = _peaks()
+            entry["k_linear"] = {"achieved_GBs": ach, "frac": ach / peak, "avg_launch_us": 1e3 * k_ms / k_n,
+                                 "algorithmic_bytes_per_launch": kb}
+            cls = torch.empty(cells, dtype=torch.uint8, device=dev)
+            g.residual(torch.tensor(U0, dtype=torch.float32, device=dev), class_out=cls)
+            out["classes_at_start"] = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+        out[f"{scheme}_{prec}"] = entry
+        del g
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_variants(H, I, torch, dev, args):
     """Independent open 2D problems of uneven size and order (the batched
     workload): one batched mesh and scheme per order, all advanced by one
@@ -535,6 +572,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--batched-autotune", type=int, default=1)
     ap.add_argument("--adjoint", type=int, default=1, help="also time the checkpointed adjoint (rank 0)")
+    ap.add_argument("--mixed", type=int, default=1, help="also time the 3D mixed-element workload (rank 0)")
+    ap.add_argument("--mixed-n", type=int, default=48)
+    ap.add_argument("--mixed-steps", type=int, default=10)
     ap.add_argument("--adjoint-n", type=int, default=55)
     ap.add_argument("--adjoint-steps", type=int, default=50)
     args = ap.parse_args()
@@ -624,6 +664,9 @@ def main():
     batched = None
     if args.batched and rank == 0:
         batched = batched_variants(H, I, torch, dev, args)
+    mixed = None
+    if args.mixed and rank == 0:
+        mixed = mixed_variants(H, I, torch, dev, args)
     adjoint = None
     if args.adjoint and rank == 0:
         adjoint = adjoint_variants(H, I, torch, dev, args)
@@ -648,7 +691,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if g.fp32 else "f64", "data": "synthetic",
                 "config": _config(args, mesh), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "classes_final": hist,
-                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence, "batched": batched, "adjoint": adjoint}
+                "wall_s_timed": wall, "variants": variants, "turbulence": turbulence, "mixed": mixed, "batched": batched,
+                "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
