@@ -210,7 +210,9 @@ __device__ __forceinline__ void cweno_weights(const KParams<T>& p, const T* OI, 
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         T s0 = T(0);
-        for (int f = 0; f < nf; ++f) s0 += s[f][k];
+#pragma unroll
+        for (int f = 0; f < C::NFMAX; ++f)
+            if (f < nf) s0 += s[f][k];
         sumlin[k] = s0;
     }
     T a1[N];
@@ -227,8 +229,10 @@ __device__ __forceinline__ void cweno_weights(const KParams<T>& p, const T* OI, 
             si1 += a1[k] * t;
         }
     }
-    T sis[6], tsum = T(0);
-    for (int f = 0; f < nf; ++f) {
+    T sis[C::NFMAX], tsum = T(0);
+#pragma unroll
+    for (int f = 0; f < C::NFMAX; ++f) {
+        if (f >= nf) break;
         T s0 = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -243,8 +247,10 @@ __device__ __forceinline__ void cweno_weights(const KParams<T>& p, const T* OI, 
     }
     const T tau = tpow(tsum / T(nf), p.b_cw);
     const T w1 = lam1 * (T(1) + tau / (p.eps_cw + si1));
-    T wsum = w1, ws[6];
-    for (int f = 0; f < nf; ++f) {
+    T wsum = w1, ws[C::NFMAX];
+#pragma unroll
+    for (int f = 0; f < C::NFMAX; ++f) {
+        if (f >= nf) break;
         ws[f] = lams * (T(1) + tau / (p.eps_cw + sis[f]));
         wsum += ws[f];
     }
@@ -254,7 +260,9 @@ __device__ __forceinline__ void cweno_weights(const KParams<T>& p, const T* OI, 
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         T gk = T(0);
-        for (int f = 0; f < nf; ++f) gk += (ws[f] / wsum - om1 * lams / lam1) * s[f][k];
+#pragma unroll
+        for (int f = 0; f < C::NFMAX; ++f)
+            if (f < nf) gk += (ws[f] / wsum - om1 * lams / lam1) * s[f][k];
         g[k] = gk;
     }
 }
@@ -450,9 +458,12 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
                     a[k] = sA[gi][k][w];
                 }
             }
-            for (int h = 0; h < nf; ++h)
+#pragma unroll
+            for (int h = 0; h < C::NFMAX; ++h)
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
+                    sd[h][k] = T(0);
+                    if (h >= nf) continue;
                     if constexpr (CHAR) {
                         T x = T(0);
 #pragma unroll
