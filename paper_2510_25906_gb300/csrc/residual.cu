@@ -523,7 +523,12 @@ __device__ __forceinline__ void cweno_part(const KParams<T>& p, unsigned bid, un
         }
         // a cell failing the Harten bound falls back to its mean at every point
         const bool anyf = grp.any(fail);
-        if (lane < Q) store_state<T, NV>(p.FS + (q0 + lane) * NV, anyf ? uc : w);
+        if (lane < Q) {
+            T o[NV];   // chosen element by element: the arrays stay in registers
+#pragma unroll
+            for (int v = 0; v < NV; ++v) o[v] = anyf ? uc[v] : w[v];
+            store_state<T, NV>(p.FS + (q0 + lane) * NV, o);
+        }
         if (anyf && lane == 0) p.cls[c] = CLS_FIRST;
         grp.sync();
     }
@@ -630,7 +635,12 @@ __device__ __forceinline__ void muscl_part(const KParams<T>& p, unsigned bid, un
         }
         // a cell failing the Harten bound falls back to its mean at every point
         const bool anyf = grp.any(fail);
-        if (lane < Q) store_state<T, NV>(p.FS + (q0 + lane) * NV, anyf ? uc : w);
+        if (lane < Q) {
+            T o[NV];   // chosen element by element: the arrays stay in registers
+#pragma unroll
+            for (int v = 0; v < NV; ++v) o[v] = anyf ? uc[v] : w[v];
+            store_state<T, NV>(p.FS + (q0 + lane) * NV, o);
+        }
         if (anyf && lane == 0) p.cls[c] = CLS_FIRST;
         grp.sync();
     }
