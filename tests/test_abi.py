@@ -93,3 +93,39 @@ def test_mixed_element_volumes_match_oracle(H):
     vg = H.Mesh(m).volumes()
     vo, _ = O.Mesh(m).geometry()
     assert np.abs(vg - vo).max() <= 1e-14 * vo.max()
+
+
+def test_mesh_edge_cases(H):
+    """Descriptors the library must refuse: no cells, a 3D type in a 2D
+    mesh, a vertex count that does not match the type, an inverted prism,
+    a face shared by three cells."""
+    tri = I.structured_tri_mesh(2, periodic=False, jitter=0.0)
+    empty = I.Mesh(2, tri.nodes, tri.cell_type[:0], tri.cell_ptr[:1], tri.cell_idx[:0], tri.period)
+    with pytest.raises(H.HfvError) as e:
+        H.Mesh(empty)
+    assert e.value.code == H.HFV_ERR_ARG
+    bad = I.Mesh(2, tri.nodes, tri.cell_type.copy(), tri.cell_ptr, tri.cell_idx, tri.period)
+    bad.cell_type[0] = I.PRISM
+    with pytest.raises(H.HfvError) as e:
+        H.Mesh(bad)
+    assert e.value.code == H.HFV_ERR_MESH
+    m = I.mixed_element_mesh(2, seed=1, p_pyramid=0.6)
+    pyr = int(np.nonzero(m.cell_type == I.PYRAMID)[0][0])
+    t = m.cell_type.copy()
+    t[pyr] = I.PRISM                                   # five vertices listed for a prism
+    with pytest.raises(H.HfvError) as e:
+        H.Mesh(I.Mesh(3, m.nodes, t, m.cell_ptr, m.cell_idx, m.period))
+    assert e.value.code == H.HFV_ERR_MESH
+    pr = int(np.nonzero(m.cell_type == I.PRISM)[0][0])
+    idx = m.cell_idx.copy()
+    a, b = m.cell_ptr[pr], m.cell_ptr[pr + 1]
+    idx[a:b] = np.concatenate([idx[a + 3:b], idx[a:a + 3]])   # top and bottom swapped: inverted
+    with pytest.raises(H.HfvError) as e:
+        H.Mesh(I.Mesh(3, m.nodes, m.cell_type, m.cell_ptr, idx, m.period))
+    assert e.value.code == H.HFV_ERR_MESH
+    nodes = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0], [0.5, -1.0], [0.2, 0.8]])
+    fan = I.Mesh(2, nodes, np.full(3, I.TRI, np.uint8), np.array([0, 3, 6, 9]),
+                 np.array([0, 1, 2, 1, 0, 3, 0, 1, 4], np.int32), np.zeros(2))
+    with pytest.raises(H.HfvError) as e:
+        H.Mesh(fan)
+    assert e.value.code == H.HFV_ERR_MESH

@@ -286,3 +286,8 @@ def test_argument_errors(H):
     g = H.Scheme(gm, order=3)
     with pytest.raises(ValueError):
         g.residual(torch.zeros((4, m.n_cells), dtype=torch.float32, device="cuda"))
+    # meshes with cells other than hexahedra are built for orders 2 and 3
+    mx = H.Mesh(I.mixed_element_mesh(3, seed=7))
+    with pytest.raises(H.HfvError) as e:
+        H.Scheme(mx, order=4)
+    assert e.value.code == H.HFV_ERR_ARG
