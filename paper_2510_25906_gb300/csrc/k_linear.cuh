@@ -32,8 +32,11 @@ struct K1Shape {
     // more cells per tile than a ring of stages of L holds: 3.8 KB of L per
     // hexahedron at order 4)
     static constexpr bool SMALL = C::D == 2 && C::QMAX <= 8;
-    static constexpr int PPL = SMALL ? C::QMAX / 4 : 1;
-    static constexpr int G = SMALL ? 4 : GroupSize<C::QMAX>::value;   // lanes per cell
+    // 3D with up to 32 face points and M <= 20 (order 3; hexahedra, prisms,
+    // pyramids): sixteen lanes per cell, two points each
+    static constexpr bool SMALL3 = C::D == 3 && C::QMAX > 16 && C::QMAX <= 32 && C::M <= 20;
+    static constexpr int PPL = SMALL ? C::QMAX / 4 : SMALL3 ? 2 : 1;
+    static constexpr int G = SMALL ? 4 : SMALL3 ? 16 : GroupSize<C::QMAX>::value;   // lanes per cell
     static constexpr int SLOT = C::NFMAX <= 4 ? 4 : 8;       // lanes of one face-neighbour reduction
     // lanes past the first SLOT take the bounds from the group's first lane
     static constexpr bool NB_BCAST = G > SLOT;
