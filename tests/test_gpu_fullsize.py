@@ -121,3 +121,17 @@ def test_turbulence_full_size(H, precision, tol):
     near = (np.abs(x - math.pi) < 3 * h) | (x < 3 * h) | (x > 2 * math.pi - 3 * h)
     _check(H, mesh, U, dict(order=4, flux="hllc"), precision, near, 40, 24, tol, seed=11, key=("turbulence", 4),
            smooth=True)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_mixed_elements_full_size(H, precision, tol):
+    """The 3D mixed-element workload (250,828 tetrahedra, prisms, pyramids and
+    hexahedra), order 3, the Mach 2 shock ahead of the density pulse; sampled
+    near the shock and at random.  FP32 bar: the larger of 1e-5 and the
+    bound of the FP32 arithmetic (tetrahedra and pyramids have the largest
+    surface-to-volume ratios)."""
+    mesh = I.mixed_element_mesh(48)
+    U = I.shock_pulse_state(mesh)
+    near = np.abs(mesh.vertex_means()[:, 0] - 0.4) < 3.0 / 48
+    _check(H, mesh, U, dict(order=3, flux="hllc"), precision, near, 300, 300, tol, seed=11, key=("mixed", 3),
+           smooth=True)
