@@ -272,7 +272,9 @@ HFV_API int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, i
  * and a stream capture records one graph with one branch per scheme): the
  * form a batch of problems of different orders takes, one batched mesh per
  * order.  U[k] is scheme k's state; cfl and dt as for hfv_step.  Schemes
- * must be distinct.  async; allocates nothing.  Errors: HFV_ERR_ARG. */
+ * must be distinct.  async; allocates nothing.  Errors: HFV_ERR_ARG (NULL
+ * entry, a scheme listed twice), HFV_ERR_CUDA and those of hfv_step; a
+ * failure still joins the branches forked before it into `stream`. */
 HFV_API int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n, double cfl, double dt, void* stream);
 
 /* End-to-end helper: copy U (host, FP64 [nv][n_cells]) to the device, take

@@ -283,23 +283,43 @@ extern "C" int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n
         set_error("hfv_step_many: bad argument");
         return HFV_ERR_ARG;
     }
-    for (int k = 0; k < n; ++k)
+    for (int k = 0; k < n; ++k) {
         if (!schemes[k] || !U[k]) { set_error("hfv_step_many: NULL scheme or state"); return HFV_ERR_ARG; }
+        // each scheme's fork / join events and scratch serve one step at a time
+        for (int j = 0; j < k; ++j)
+            if (schemes[j] == schemes[k]) { set_error("hfv_step_many: a scheme is listed twice"); return HFV_ERR_ARG; }
+    }
     // fork: every scheme's side stream waits for the caller's stream; each
     // step runs on its own side stream; join: the caller's stream waits for
     // all of them.  Under stream capture this records one graph with a
-    // branch per scheme.
+    // branch per scheme.  A failure still joins the branches already forked.
     cudaStream_t st = (cudaStream_t)stream;
-    for (int k = 0; k < n; ++k) {
+    int rc = HFV_OK, forked = 0;
+    for (int k = 0; k < n && rc == HFV_OK; ++k) {
         hfv_scheme* s = schemes[k];
-        API_CUDA(cudaEventRecord((cudaEvent_t)s->ev_fork, st));
-        API_CUDA(cudaStreamWaitEvent((cudaStream_t)s->side, (cudaEvent_t)s->ev_fork, 0));
-        const int rc = launch_step(s, U[k], cfl, dt, s->side);
-        if (rc != HFV_OK) return rc;
-        API_CUDA(cudaEventRecord((cudaEvent_t)s->ev_join, (cudaStream_t)s->side));
+        cudaError_t e = cudaEventRecord((cudaEvent_t)s->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)s->side, (cudaEvent_t)s->ev_fork, 0);
+        if (e != cudaSuccess) {
+            set_error(std::string("hfv_step_many: ") + cudaGetErrorString(e));
+            rc = HFV_ERR_CUDA;
+            break;
+        }
+        ++forked;
+        rc = launch_step(s, U[k], cfl, dt, s->side);
+        e = cudaEventRecord((cudaEvent_t)s->ev_join, (cudaStream_t)s->side);
+        if (rc == HFV_OK && e != cudaSuccess) {
+            set_error(std::string("hfv_step_many: ") + cudaGetErrorString(e));
+            rc = HFV_ERR_CUDA;
+        }
     }
-    for (int k = 0; k < n; ++k) API_CUDA(cudaStreamWaitEvent(st, (cudaEvent_t)schemes[k]->ev_join, 0));
-    return HFV_OK;
+    for (int k = 0; k < forked; ++k) {
+        const cudaError_t e = cudaStreamWaitEvent(st, (cudaEvent_t)schemes[k]->ev_join, 0);
+        if (e != cudaSuccess && rc == HFV_OK) {
+            set_error(std::string("hfv_step_many: ") + cudaGetErrorString(e));
+            rc = HFV_ERR_CUDA;
+        }
+    }
+    return rc;
 }
 
 extern "C" int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double cfl, double dt, void* stream)

@@ -168,6 +168,10 @@ def test_step_many_equals_sequential_and_captures(H):
     torch.cuda.synchronize()
     for w, r in zip(work, ref):
         assert np.array_equal(w.cpu().numpy(), r)
+    # a scheme listed twice would share its scratch between two branches
+    with pytest.raises(H.HfvError) as e:
+        H.step_many([schemes[0], schemes[0]], [states[0], states[0].clone()], cfl=0.5)
+    assert e.value.code == H.HFV_ERR_ARG
 
 
 @pytest.mark.gpu
