@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libhfv.so")
 
 HFV_OK, HFV_ERR_ARG, HFV_ERR_CUDA, HFV_ERR_OOM, HFV_ERR_MESH, HFV_ERR_STENCIL, HFV_ERR_NONPHYSICAL, \
     HFV_ERR_TIMEOUT, HFV_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
-HFV_TRI, HFV_QUAD, HFV_TET, HFV_HEX = 1, 2, 3, 4
+HFV_TRI, HFV_QUAD, HFV_TET, HFV_HEX, HFV_PRISM, HFV_PYRAMID = 1, 2, 3, 4, 5, 6
 HFV_RUSANOV, HFV_HLLC, HFV_HLL = 0, 1, 2
 HFV_HYBRID, HFV_PURE_LINEAR, HFV_PURE_CWENOZ, HFV_PURE_MUSCL = 0, 1, 2, 3
 HFV_FP64, HFV_FP32 = 0, 1
