@@ -100,7 +100,6 @@ struct hfv_dev_arrays {
     double* U4;
     double* U5;
     double* dt;        // [nseg] time step per problem
-    double* dtc;       // [6][nseg] stage step sizes of the step: factor times dt
     int32_t* seg;      // [nc] problem of each cell (batched meshes; null for one problem)
     double* Uio;       // [nv][nc] device state of hfv_advance_host
 };

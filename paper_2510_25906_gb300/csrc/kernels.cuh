@@ -83,13 +83,13 @@ struct KParams {
     int* status;
     // Runge-Kutta stage fused into the flux kernel (rk_b != 0): for every
     // variable, out = rk_a U0 + rk_b (Us + c R) in FP64 with the stage's step
-    // c = f dt (per problem, in dtc), and the next stage's cell-major copy
+    // c = rk_w dt (dt per problem), and the next stage's cell-major copy
     // into ua_next (may be null); R itself also into Rcopy when non-null
-    double rk_a, rk_b;
+    double rk_a, rk_b, rk_w;
     T* Rcopy;
     const double* U0;
     const double* Us;
-    const double* dtc;    // [problems]
+    const double* dt;     // [problems] the step
     const int32_t* seg;   // problem of each cell, or null (one problem)
     double* out;
     T* ua_next;

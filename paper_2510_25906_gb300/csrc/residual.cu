@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
             if (p.rk_a != 0.0) u0[k] = p.U0[(int64_t)v * nc + c];
         }
     }
-    if (valid && p.rk_b != 0.0) cdt = p.dtc[p.seg ? p.seg[c] : 0];
+    if (valid && p.rk_b != 0.0) cdt = p.rk_w * p.dt[p.seg ? p.seg[c] : 0];
     const T ivol = valid ? p.ivol[cs] : T(0);
     // geometry and the stage operands above are constant or written two or
     // more kernels back; the face states are the predecessor's output
@@ -855,7 +855,7 @@ __global__ void k_to_aos(int64_t nc, const Tin* __restrict__ U, T* __restrict__ 
 // fused Runge-Kutta stage applied in the flux kernel's epilogue (see KParams)
 struct StageRK {
     double a = 0.0, b = 0.0;
-    int coef = 0;             // row of the step's step-size table c = f dt (k_rk_coef)
+    double w = 1.0;           // the stage's step c = w dt
     const double* U0 = nullptr;
     const double* Us = nullptr;
     double* out = nullptr;
@@ -879,11 +879,12 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     p.UA = ua;
     if (rk) {
         p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.seg = s->a.seg;
-        p.dtc = s->a.dtc + (int64_t)rk->coef * s->nseg;
+        p.dt = s->a.dt;
+        p.rk_w = rk->w;
         p.out = rk->out; p.ua_next = (T*)rk->ua_next;
         p.Rcopy = rk->keep_R ? (T*)s->a.Rs : nullptr;
     } else {
-        p.rk_a = 0.0; p.rk_b = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dtc = nullptr;
+        p.rk_a = 0.0; p.rk_b = 0.0; p.rk_w = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr;
         p.seg = nullptr; p.out = nullptr; p.ua_next = nullptr; p.Rcopy = nullptr;
     }
     {
@@ -954,33 +955,20 @@ __global__ void k_dt_init(unsigned long long* x, int n)
     if (i < n) x[i] = 0x7ff0000000000000ull;
 }
 
-// the step's stage step sizes c_k = w_k dt per problem (row k of dtc)
-struct RkWeights {
-    double w[8];
-    int n;
-};
-__global__ void k_rk_coef(const double* __restrict__ dt, int nseg, RkWeights w, double* __restrict__ dtc)
-{
-    pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nseg) return;
-    const double h = dt[i];
-    for (int k = 0; k < w.n; ++k) dtc[k * nseg + i] = w.w[k] * h;
-}
-
 // SSP-RK(5,4): the part of the last stage known after stage 4,
-//   P = a52 u2 + a53 (u3 + c R(u3)),  c = (beta_53 / alpha_53) dt
+//   P = a52 u2 + a53 (u3 + c R(u3)),  c = w5 dt,  w5 = beta_53 / alpha_53
 template <class T>
 __global__ void __launch_bounds__(256) k_rk_partial(int64_t n, int64_t nc, const double* __restrict__ u2,
                                                    const double* __restrict__ u3, const T* __restrict__ R3,
-                                                   const double* __restrict__ c, const int32_t* __restrict__ seg,
-                                                   double a52, double a53, double* __restrict__ P)
+                                                   const double* __restrict__ dt, double w5,
+                                                   const int32_t* __restrict__ seg, double a52, double a53,
+                                                   double* __restrict__ P)
 {
     pdl_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t cell = i % nc;
-    P[i] = a52 * u2[i] + a53 * (u3[i] + c[seg ? seg[cell] : 0] * (double)R3[i]);
+    P[i] = a52 * u2[i] + a53 * (u3[i] + w5 * dt[seg ? seg[cell] : 0] * (double)R3[i]);
 }
 
 // FP64 state (structure of arrays) -> the first stage's cell-major copy, and,
@@ -1144,15 +1132,6 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     // stages alternate the cell-major copies UA, UB, UA, ...; each stage's
     // flux kernel writes the next one
     void* uab[2] = {s->a.UA, s->a.UB};
-    auto coefs = [&](const double* w, int n) -> int {
-        RkWeights rw;
-        rw.n = n;
-        for (int k = 0; k < n; ++k) rw.w[k] = w[k];
-        Launch l(s, KID_DT, st);
-        pdl(k_rk_coef, (s->nseg + 255) / 256, 256, 0, st, s->a.dt, s->nseg, rw, s->a.dtc);
-        HFV_CUDA_CHECK(cudaGetLastError());
-        return HFV_OK;
-    };
     if (s->p.time_scheme == HFV_SSPRK54) {
         // u_i = sum_j alpha_ij u_j + beta_ij dt L(u_j) (Spiteri and Ruuth's
         // SSP-RK(5,4), Shu-Osher form): stage i reads u_{i-1} and writes
@@ -1169,15 +1148,14 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
         double* u[5] = {U, s->a.U1, s->a.U2, s->a.U3, s->a.U4};
         const double A0[5] = {0.0, a20, a30, a40, 1.0};
         const double Bk[5] = {a10, a21, a32, a43, a54};
-        // c_k = (beta_k,k-1 / alpha_k,k-1) dt; row 5 (beta_53 / alpha_53) dt for P
+        // c_k = (beta_k,k-1 / alpha_k,k-1) dt; (beta_53 / alpha_53) dt for P
         const double W[6] = {b10 / a10, b21 / a21, b32 / a32, b43 / a43, b54 / a54, b53 / a53};
-        if ((rc = coefs(W, 6)) != HFV_OK) return rc;
         const int64_t nvc = (int64_t)s->nv * s->mesh->nc;
         for (int k = 0; k < 5; ++k) {
             StageRK rk;
             rk.a = A0[k];
             rk.b = Bk[k];
-            rk.coef = k;
+            rk.w = W[k];
             rk.U0 = k == 4 ? s->a.U5 : U;
             rk.Us = u[k];
             rk.out = k == 4 ? U : u[k + 1];
@@ -1187,13 +1165,12 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
             if (k == 3) {
                 Launch l(s, KID_RK, st);
                 const unsigned g = (unsigned)((nvc + 255) / 256);
-                const double* c5 = s->a.dtc + 5 * (int64_t)s->nseg;
                 if (s->p.precision == HFV_FP32)
-                    pdl(k_rk_partial<float>, g, 256, 0, st, nvc, s->mesh->nc, s->a.U2, s->a.U3, (const float*)s->a.Rs, c5,
-                                                          s->a.seg, a52, a53, s->a.U5);
+                    pdl(k_rk_partial<float>, g, 256, 0, st, nvc, s->mesh->nc, s->a.U2, s->a.U3, (const float*)s->a.Rs,
+                        (const double*)s->a.dt, W[5], s->a.seg, a52, a53, s->a.U5);
                 else
                     pdl(k_rk_partial<double>, g, 256, 0, st, nvc, s->mesh->nc, s->a.U2, s->a.U3, (const double*)s->a.Rs,
-                                                           c5, s->a.seg, a52, a53, s->a.U5);
+                        (const double*)s->a.dt, W[5], s->a.seg, a52, a53, s->a.U5);
             }
         }
         HFV_CUDA_CHECK(cudaGetLastError());
@@ -1202,13 +1179,11 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
     double* outs[3] = {s->a.U1, s->a.U2, U};
     const double* ins[3] = {U, s->a.U1, s->a.U2};
     const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
-    const double ones[3] = {1.0, 1.0, 1.0};
-    if ((rc = coefs(ones, 3)) != HFV_OK) return rc;
     for (int k = 0; k < 3; ++k) {
         StageRK rk;
         rk.a = A[k];
         rk.b = B[k];
-        rk.coef = k;
+        rk.w = 1.0;
         rk.U0 = U;
         rk.Us = ins[k];
         rk.out = outs[k];
