@@ -1,0 +1,40 @@
+"""Host-side pieces of bench.py (CPU): the reference arm's JSON line (the
+oracle timed on the host cores) carries the contract's keys, and the DRAM
+traffic figure is reported only while the candidate kernel's sources hash to
+the build it was captured on."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["warmup"] >= 3
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert "workload" in line["config"]
+
+
+def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    h = bench.kernel_source_hash()
+    monkeypatch.setitem(bench.TRAFFIC, ("quadrant", 3, "fp32", "hybrid"), {"bytes_per_cell": 400.0, "sources": h})
+    assert bench._traffic("quadrant", 3, "fp32", "hybrid", 1000) == 400000
+    assert bench._traffic("quadrant", 3, "fp64", "hybrid", 1000) is None
+    monkeypatch.setitem(bench.TRAFFIC, ("quadrant", 3, "fp32", "hybrid"), {"bytes_per_cell": 400.0, "sources": "0"})
+    assert bench._traffic("quadrant", 3, "fp32", "hybrid", 1000) is None
