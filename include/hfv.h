@@ -110,7 +110,8 @@ typedef struct {
 
 /* Scheme parameters.  hfv_default_params fills the defaults given here. */
 typedef struct {
-    int order;          /* r + 1, 2..5 (default 3); "order" as in Sec. 2.1 */
+    int order;          /* r + 1 (default 3), "order" as in Sec. 2.1: 2..5 in 2D, 2..4 on
+                           hexahedra, 2..3 on meshes with tetrahedra, prisms or pyramids */
     int flux;           /* HFV_RUSANOV / HFV_HLLC / HFV_HLL (default HLLC) */
     int scheme;         /* HFV_HYBRID (default) or a pure scheme */
     int nad_vars;       /* detector variables: bit0 density, bit1 pressure,
