@@ -43,7 +43,9 @@ class Params(C.Structure):
                 ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1p", C.c_double), ("cw_eps", C.c_double),
                 ("cw_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double),
+                ("mu0", C.c_double), ("t0", C.c_double), ("suth_s", C.c_double),
+                ("prandtl", C.c_double), ("visc_alpha", C.c_double)]
 
 
 def default_params(**kw) -> dict:
@@ -52,7 +54,8 @@ def default_params(**kw) -> dict:
     Harten theta = 0.9, eps = 1e-14, deactivation (kappa dx)^n with kappa = 1, n = 1."""
     p = dict(order=3, flux="rusanov", scheme="hybrid", nad_vars=3, gamma=1.4, alpha_m=5e-3, beta_m=0.5,
              alpha_w=0.0, beta_w=0.0, kappa=1.0, n_exp=1.0, lambda1p=1e3, cw_eps=1e-3, cw_b=4.0,
-             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0, limiter="barth", cweno_vars="conserved", venkat_k=5.0)
+             harten_theta=0.9, harten_eps=1e-14, stencil_factor=2.0, limiter="barth", cweno_vars="conserved", venkat_k=5.0,
+             mu0=0.0, t0=1.0, suth_s=110.4 / 288.15, prandtl=0.72, visc_alpha=4.0 / 3.0)
     p.update(kw)
     return p
 

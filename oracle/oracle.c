@@ -584,6 +584,11 @@ typedef struct {
     int limiter;             /* MUSCL limiter: 0 Barth-Jespersen, 1 Venkatakrishnan */
     int cweno_vars;          /* CWENOZ in 0 conserved, 1 characteristic variables */
     double venkat_k;         /* Venkatakrishnan threshold eps^2 = (K dx)^3 */
+    /* viscous terms (Sec. 2, eq. EulerEquationsDetails): mu0 = 0 gives the
+     * Euler equations; Sutherland's law (eq. sutherlandlaw) with reference
+     * temperature t0 and Sutherland temperature suth_s (same units), Prandtl
+     * number prandtl (eq. HeatConduct), penalty alpha of eq. viscous_jump */
+    double mu0, t0, suth_s, prandtl, visc_alpha;
 } or_params;
 
 typedef struct {
@@ -1123,6 +1128,113 @@ static void rec_linear(or_scheme* s, or_ops* o, const double* U, int64_t i, doub
         }
 }
 
+/* d/dxi_a of monomial k at xi */
+static double dmono(const or_scheme* s, int k, int a, const double* xi)
+{
+    int e = s->ex[k][a];
+    if (e == 0) return 0.0;
+    double r = e * ipow(xi[a], e - 1);
+    for (int b = 0; b < 3; ++b)
+        if (b != a) r *= ipow(xi[b], s->ex[k][b]);
+    return r;
+}
+
+/* Viscous gradients (Sec. 2, gradients for the viscous fluxes from the
+ * constrained least-squares reconstruction): at every face point of cell i,
+ * the gradient in physical coordinates of the unlimited degree-r polynomial
+ * of each conserved variable (grad p = sum_k a_k J^-T grad_xi phi_k), turned
+ * into the gradients of the velocity components and of T = p / rho by the
+ * chain rule at the same polynomial's value there.
+ * PG[q][k][j]: k < d velocity component k, k = d temperature; j = x, y, z. */
+static void rec_visc_grad(or_scheme* s, or_ops* o, const double* U, int64_t i, double* PG)
+{
+    int N = s->N, nv = s->nv, d = s->d, nfp = s->nfp, nf = n_faces_of(s, i);
+    double a[5 * 128], V[5 * 64], x0[3], Ji[3][3], det, pts[3 * 64], nrm[3];
+    double g = s->p.gamma;
+    rec_linear(s, o, U, i, a, V);
+    ref_map(s, i, x0, Ji, &det);
+    for (int f = 0; f < nf; ++f) {
+        cell_face_points(s, i, f, pts, nrm);
+        for (int al = 0; al < nfp; ++al) {
+            int q = f * nfp + al;
+            double xi[3], gc[5][3];
+            to_ref(x0, Ji, &pts[3 * al], xi);
+            if (d == 2) xi[2] = 0.0;
+            for (int v = 0; v < nv; ++v)
+                for (int j = 0; j < 3; ++j) {
+                    double sum = 0.0;
+                    if (j < d)
+                        for (int k = 0; k < N; ++k) {
+                            double dk = 0.0;
+                            for (int b = 0; b < d; ++b) dk += Ji[b][j] * dmono(s, k, b, xi);
+                            sum += a[v * N + k] * dk;
+                        }
+                    gc[v][j] = sum;
+                }
+            const double* w = &V[q * nv];
+            double rho = w[0], u[3] = {0, 0, 0}, u2 = 0.0;
+            for (int k = 0; k < d; ++k) { u[k] = w[1 + k] / rho; u2 += u[k] * u[k]; }
+            double p = (g - 1.0) * (w[d + 1] - 0.5 * rho * u2), T = p / rho;
+            double* out = &PG[(size_t)q * 4 * 3];
+            for (int j = 0; j < 3; ++j) {
+                /* grad u_k = (grad m_k - u_k grad rho) / rho */
+                for (int k = 0; k < d; ++k) out[k * 3 + j] = (gc[1 + k][j] - u[k] * gc[0][j]) / rho;
+                /* grad p = (g - 1)(grad E - sum_k u_k grad m_k + |u|^2 / 2 grad rho);
+                 * grad T = (grad p - T grad rho) / rho */
+                double gp = gc[d + 1][j] + 0.5 * u2 * gc[0][j];
+                for (int k = 0; k < d; ++k) gp -= u[k] * gc[1 + k][j];
+                gp *= (g - 1.0);
+                out[d * 3 + j] = (gp - T * gc[0][j]) / rho;
+            }
+        }
+    }
+}
+
+/* Viscous flux F_v . n at one face point (Sec. 2, eqs. Terms1, Stresses,
+ * HeatConduct, sutherlandlaw, viscous_jump): face state = mean of the two
+ * sides' primitive velocity and temperature; gradients = mean of the two
+ * sides' gradients plus the penalty (alpha / L_int)(W_R - W_L) n;
+ * tau_ij = mu (d_j u_i + d_i u_j - 2/3 div u delta_ij);
+ * Theta_j = sum_i u_i tau_ij + mu / Pr gamma / (gamma - 1) dT/dx_j. */
+static void visc_flux(const or_scheme* s, const double* WL, const double* WR, const double* GL, const double* GR,
+                      const double* n, double inv_lint, double* F)
+{
+    int d = s->d;
+    double g = s->p.gamma, pl[4], pr[4];   /* u_0..u_{d-1}, T */
+    for (int side = 0; side < 2; ++side) {
+        const double* w = side ? WR : WL;
+        double* q = side ? pr : pl;
+        double u2 = 0.0;
+        for (int k = 0; k < d; ++k) { q[k] = w[1 + k] / w[0]; u2 += q[k] * q[k]; }
+        q[d] = (g - 1.0) * (w[d + 1] - 0.5 * w[0] * u2) / w[0];
+    }
+    double um[3] = {0, 0, 0}, Tm = 0.5 * (pl[d] + pr[d]), G[4][3];
+    for (int k = 0; k < d; ++k) um[k] = 0.5 * (pl[k] + pr[k]);
+    for (int k = 0; k <= d; ++k)
+        for (int j = 0; j < d; ++j)
+            G[k][j] = 0.5 * (GL[k * 3 + j] + GR[k * 3 + j]) + s->p.visc_alpha * inv_lint * (pr[k] - pl[k]) * n[j];
+    double T0 = s->p.t0, S = s->p.suth_s;
+    double mu = s->p.mu0 * pow(Tm / T0, 1.5) * (T0 + S) / (Tm + S);
+    double div = 0.0;
+    for (int k = 0; k < d; ++k) div += G[k][k];
+    double tau[3][3];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) tau[i][j] = mu * (G[i][j] + G[j][i] - (i == j ? 2.0 / 3.0 * div : 0.0));
+    double kap = mu / s->p.prandtl * g / (g - 1.0);
+    F[0] = 0.0;
+    F[d + 1] = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < d; ++j) t += tau[i][j] * n[j];
+        F[1 + i] = t;
+    }
+    for (int j = 0; j < d; ++j) {
+        double th = kap * G[d][j];
+        for (int i = 0; i < d; ++i) th += um[i] * tau[i][j];
+        F[d + 1] += th * n[j];
+    }
+}
+
 /* directional degree-1 coefficients a_s for stencil f */
 static void dir_coeffs(const or_scheme* s, const or_ops* o, const double* U, int64_t i, int f, int v, double* as)
 {
@@ -1480,6 +1592,8 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
     uint8_t* fin = (uint8_t*)calloc(nc, 1);
     double* a = (double*)malloc(nv * N * sizeof(double));
     double* V = (double*)malloc(maxQ * nv * sizeof(double));
+    const int visc = s->p.mu0 > 0.0;
+    double* PG = visc ? (double*)malloc((size_t)(ns > 0 ? ns : 1) * maxQ * 12 * sizeof(double)) : NULL;
     int err = 0;
     /* a2 + a3: linear candidate and detector */
     if (!forced) {
@@ -1503,6 +1617,13 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
         }
     } else {
         for (int64_t c = 0; c < nc; ++c) if (need[c] & 2) { tag[c] = forced[c]; raw[c] = forced[c]; }
+    }
+    /* viscous gradients at the face points (Sec. 2) */
+    for (int64_t c = 0; c < nc && visc && !err; ++c) {
+        if (!(need[c] & 2)) continue;
+        or_ops* o = get_ops(s, c);
+        if (!o) { err = 1; break; }
+        rec_visc_grad(s, o, U, c, &PG[(size_t)slot[c] * maxQ * 12]);
     }
     /* a5 / a6 / a7: reconstruct by class, then the Harten bound */
     for (int64_t c = 0; c < nc && !err; ++c) {
@@ -1536,12 +1657,38 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
             if (!wo && !wn) continue;
             const double* WL = &FS[(size_t)slot[co] * maxQ * nv + (size_t)m->ffo[g] * s->nfp * nv];
             const double* WR = cn >= 0 ? &FS[(size_t)slot[cn] * maxQ * nv + (size_t)m->ffn[g] * s->nfp * nv] : WL;
+            double inv_lint = 0.0;
+            const double *GLp = NULL, *GRp = NULL;
+            if (visc) {
+                /* distance between the two cells' centres (vertex means), the
+                 * neighbour's moved into the owner's frame */
+                if (cn >= 0) {
+                    double l2 = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        double dx = m->vmean[3 * cn + k] + m->fshift[3 * g + k] - m->vmean[3 * co + k];
+                        l2 += dx * dx;
+                    }
+                    inv_lint = 1.0 / sqrt(l2);
+                }
+                GLp = &PG[(size_t)slot[co] * maxQ * 12 + (size_t)m->ffo[g] * s->nfp * 12];
+                GRp = cn >= 0 ? &PG[(size_t)slot[cn] * maxQ * 12 + (size_t)m->ffn[g] * s->nfp * 12] : GLp;
+            }
             for (int al = 0; al < s->nfp; ++al) {
                 or_flux(s->p.flux, s->d, s->p.gamma, &WL[al * nv], &WR[al * nv], &m->fnorm[3 * g], F);
                 double w = s->fqw[g * s->nfp + al];
                 for (int v = 0; v < nv; ++v) {
                     if (wo) R[(int64_t)v * nc + co] -= F[v] * w / m->vol[co];
                     if (wn) R[(int64_t)v * nc + cn] += F[v] * w / m->vol[cn];
+                }
+                if (visc) {
+                    /* + (1/|V|) sum F_v w |S| (eq. EulerEquationsDetails); an open
+                     * boundary's outside copies the inside state and gradient */
+                    visc_flux(s, &WL[al * nv], &WR[al * nv], &GLp[al * 12], &GRp[al * 12], &m->fnorm[3 * g],
+                              inv_lint, F);
+                    for (int v = 0; v < nv; ++v) {
+                        if (wo) R[(int64_t)v * nc + co] += F[v] * w / m->vol[co];
+                        if (wn) R[(int64_t)v * nc + cn] -= F[v] * w / m->vol[cn];
+                    }
                 }
             }
         }
@@ -1551,7 +1698,7 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
         if (tag_out && (need[c] & 2)) tag_out[c] = tag[c];
         if (fin_out && (need[c] & 2)) fin_out[c] = fin[c];
     }
-    free(need); free(slot); free(FS); free(raw); free(tag); free(fin); free(a); free(V);
+    free(need); free(slot); free(FS); free(raw); free(tag); free(fin); free(a); free(V); free(PG);
     return err ? -1 : 0;
 }
 
