@@ -2,8 +2,10 @@
 
 Bars (stated with each test):
   * stencils, connectivity, queues: bit-exact
-  * residual with the oracle's classes forced: <= 1e-12 (FP64), <= 1e-5 (FP32)
-    of max |R| per variable
+  * residual with the oracle's classes forced: <= 1e-12 (FP64) of max |R| per
+    variable; FP32 against the oracle on the same FP32-rounded state, <= 1e-5,
+    or 8 times the residual's own sensitivity to that rounding where the case
+    is ill-conditioned (bounds.fp32_bar)
   * free-running classes: >= 99.9 % agreement (FP64); mismatches are listed
 """
 import math
@@ -12,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from bounds import fp32_bound
+from bounds import fp32_bar, rounded
 from paper_2510_25906_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -140,14 +142,25 @@ def test_stencils_bit_exact(H, name):
             assert (dr[c, f, nd[f]:] == -1).all()
 
 
+_rounded_cache = {}
+
+
+def _oracle_of_rounded(name):
+    """the oracle's FP64 residual of the FP32-rounded state, classes forced"""
+    if name not in _rounded_cache:
+        m, om, osch, U, kw, R, raw, tag, fin = _prepared(name)
+        _rounded_cache[name] = osch.residual(rounded(U), forced=fin)[0]
+    return _rounded_cache[name]
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("name", CASES)
 def test_forced_class_residual(H, name, precision, tol):
-    """FP64: 1e-12 of max |R| per variable.  FP32: 1e-5 on the
-    discontinuous workloads; where max |R| is small against the face fluxes
-    it is the difference of (the smooth density wave; the tetrahedral cases,
-    whose cells have the largest surface-to-volume ratio), the larger of
-    1e-5 and the bound of the FP32 arithmetic itself (bounds.fp32_bound)."""
+    """FP64: 1e-12 of max |R| per variable.  FP32: against the oracle on the
+    same FP32-rounded state, max(1e-5, 8 E_in), E_in the change of the exact
+    residual under that rounding (bounds.fp32_bar): 1e-5 on every case but
+    the smooth density wave and the tetrahedral and mixed-element cases,
+    whose residuals are small next to the face fluxes."""
     m, om, osch, U, kw, R, raw, tag, fin = _prepared(name)
     assert len(np.unique(fin)) >= (1 if name == "wave_tri32" else 2)
     gm, g = _gpu(H, m, kw, precision)
@@ -162,11 +175,18 @@ def test_forced_class_residual(H, name, precision, tol):
     if precision == "fp64":
         assert np.array_equal(cg, fin)
     ok = cg == fin
-    if precision == "fp32" and (name == "wave_tri32" or name.startswith("tet") or name.startswith("mixed3d")):
-        tol = max(tol, fp32_bound(m, om, U, R))
-        assert tol < 1e-3
-    err = _rel(Rg.double().cpu().numpy(), R, ok)
-    print(f"{name} {precision}: max rel err {err:.2e} (bar {tol:.1e})")
+    # an FP32 Harten decision may differ from the FP64 one only for cells at
+    # the bound's edge: the comparison may drop at most 0.1 % of the cells
+    dropped = int((~ok).sum())
+    assert ok.any() and ok.mean() >= 0.999, (name, precision, dropped)
+    ref = R
+    e_in = 0.0
+    if precision == "fp32":
+        ref = _oracle_of_rounded(name)
+        tol, e_in = fp32_bar(R, ref, tol)
+    err = _rel(Rg.double().cpu().numpy(), ref, ok)
+    print(f"{name} {precision}: max rel err {err:.2e} (bar {tol:.1e}, input rounding {e_in:.1e}), "
+          f"{dropped} cells dropped")
     assert err <= tol, (name, precision, err)
 
 
