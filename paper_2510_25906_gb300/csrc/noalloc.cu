@@ -36,9 +36,14 @@ int scratch_for_current_device(int32_t** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (e != cudaSuccess) {
         set_error(std::string("hfv_class_queues_static: cudaGetDevice: ") + cudaGetErrorString(e));
         return HFV_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("hfv_class_queues_static: device index " + std::to_string(dev) + " is beyond the " +
+                  std::to_string(kMaxDevices) + " devices whose scratch address this library keeps");
+        return HFV_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_ptr[dev]) {

@@ -4,7 +4,10 @@ call cudaMalloc when they need the queues, e.g. inside a stream capture).
 It must produce the same counts and queues as the compaction inside
 hfv_residual: with classes forced, the residual compacts exactly the given
 CWENOZ and MUSCL cells, so both are compared bit for bit, on two calls in a
-row (the static scratch keeps the previous call's contents)."""
+row (the static scratch keeps the previous call's contents).  On a mesh of
+more than 1,024 blocks of 256 cells (where the residual runs its separate
+scan kernel and the scan here takes several block counts per thread) both
+are also compared with numpy's list of the class-1 and class-2 cells."""
 import ctypes
 
 import numpy as np
@@ -44,6 +47,34 @@ def test_static_scratch_compaction_matches_residual_queues(H):
             assert np.array_equal(cnt, ref_counts), (trial, call, cnt, ref_counts)
             assert np.array_equal(q[:cnt[0]], ref_c)
             assert np.array_equal(q[m.n_cells:m.n_cells + cnt[1]], ref_m)
+
+
+def test_static_scratch_compaction_beyond_1024_blocks_matches_numpy(H):
+    """300,000-odd cells (1,178 blocks and a ragged tail), seeded random
+    classes: counts and ascending queues equal np.nonzero, for this entry
+    point (two calls in a row) and for the residual's own compaction."""
+    m = I.structured_quad_mesh(548, 548, jitter=0.1, seed=3)   # 300,304 cells
+    nb = (m.n_cells + 255) // 256
+    assert nb > 1024 and m.n_cells % 256 != 0
+    U = I.quadrant_state(m)
+    g = H.Scheme(H.Mesh(m), order=2, flux="hllc", precision="fp32")
+    rng = np.random.default_rng(11)
+    for trial in range(2):
+        cls = rng.integers(0, 4, m.n_cells).astype(np.uint8)
+        want_c, want_m = np.nonzero(cls == 1)[0], np.nonzero(cls == 2)[0]
+        forced = torch.tensor(cls, device="cuda")
+        g.residual(torch.tensor(U, dtype=torch.float32, device="cuda"), forced=forced)
+        rc, (qc, qm) = g.queues()
+        assert rc.tolist() == [len(want_c), len(want_m)]
+        assert np.array_equal(qc, want_c) and np.array_equal(qm, want_m)
+        for call in range(2):
+            counts, queues = H.class_queues_static(forced)
+            torch.cuda.synchronize()
+            cnt = counts.cpu().numpy()
+            q = queues.cpu().numpy()
+            assert cnt.tolist() == [len(want_c), len(want_m)], (trial, call)
+            assert np.array_equal(q[:cnt[0]], want_c)
+            assert np.array_equal(q[m.n_cells:m.n_cells + cnt[1]], want_m)
 
 
 def test_static_scratch_rejects_oversized_input(H):
