@@ -95,6 +95,24 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def alu_peaks(H):
+    """FMA ceilings of the CUDA cores, measured here (hfv_fma_rate): FP64
+    DFMA, FP32 FFMA and packed FFMA2, FLOP/s."""
+    return {"fp64_flops": H.fma_rate("fp64", 100.0), "fp32_flops": H.fma_rate("fp32", 100.0),
+            "fp32x2_flops": H.fma_rate("fp32x2", 100.0)}
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def _env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -111,14 +129,24 @@ def _oracle_sample(mesh, band=0.05):
     return np.nonzero(np.abs(vm[:, 1] - 0.5) < band)[0].astype(np.int64)
 
 
-def _oracle_steps(mesh, U, order, flux, scheme, steps, warmup, band=0.05):
+def _oracle_block(mesh, k):
+    """a k x k x k block of cells about the domain's centre (3D sample)"""
+    vm = mesh.vertex_means()
+    lo, hi = vm.min(axis=0), vm.max(axis=0)
+    h = (hi - lo) / np.cbrt(mesh.n_cells)
+    inside = np.all(np.abs(vm - 0.5 * (lo + hi)) < 0.5 * k * h, axis=1)
+    return np.nonzero(inside)[0].astype(np.int64)
+
+
+def _oracle_steps(mesh, U, order, flux, scheme, steps, warmup, band=0.05, sample=None):
     """Time the FP64 oracle (single thread) on a band of cells across the
-    domain centre (every quadrant interface crosses it): one 'step' = three
-    residual evaluations of the band, the work of one SSP-RK3 step there."""
+    domain centre (every quadrant interface crosses it), or on the given
+    sample: one 'step' = three residual evaluations of the sample, the work of
+    one SSP-RK3 step there."""
     import oracle as O
     om = O.Mesh(mesh)
     s = O.Scheme(om, order=order, flux=flux, scheme=scheme)
-    smp = _oracle_sample(mesh, band)
+    smp = _oracle_sample(mesh, band) if sample is None else sample
     for _ in range(max(1, warmup)):
         s.residual(U, sample=smp)          # the first call also builds the operators
     t0 = time.perf_counter()
@@ -177,7 +205,7 @@ def reference_arm(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args, mesh, note="FP64 CPU oracle, single thread"),
+        "config": _config(args, mesh, note="FP64 CPU oracle, single thread", precision="fp64"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{ns} cells (|y - 0.5| < 0.05) of the {mesh.n_cells}-cell mesh, 3 residual "
                                    f"evaluations per step, operators built before timing"},
@@ -190,8 +218,10 @@ def _config(args, mesh, **extra):
     names = {"quadrant": "2D quadrant Riemann problem, seeded mixed tri/quad mesh of [0,1]^2",
              "turbulence": "3D decaying turbulence, periodic [0,2pi]^3, uniform hexahedra",
              "density_wave": "2D smooth density wave, periodic jittered triangles"}
+    # the workload names the problem only; the arithmetic is the "precision" key
+    # (the reference arm runs the same workload in the FP64 oracle)
     cfg = {"workload": f"{names[args.workload]}, {mesh.n_cells} cells, order {args.order} {args.scheme}, "
-                       f"SSP-RK3, {args.precision}",
+                       f"SSP-RK3",
            "cells": mesh.n_cells, "order": args.order, "scheme": args.scheme, "precision": args.precision,
            "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{args.gpus}"}
     cfg.update(extra)
@@ -254,6 +284,74 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+FACES = np.array([0, 3, 4, 4, 6, 5, 5], np.int64)     # faces per cell type (index = HFV_* type)
+# floating-point operations of one HLLC evaluation at a face point plus its
+# weighted accumulation (counted from physics.cuh: an FMA counts 2, a divide
+# or square root 1), 2D / 3D
+RIEMANN_FLOP = {2: 100, 3: 125}
+
+
+def path_model(mesh, s, b):
+    """Algorithmic bytes and flops per cell-residual of the whole path, the
+    per-class terms averaged over the mesh's cells:
+      B_lin   = nv b (U_i) + 4 M (stencil) + Q M b (L) + (nf/2)(d+1) b (face
+                normals and areas) + b (1/|V|) + 4 nf (face neighbours) + nv b (R)
+      B_cweno = (N M (P) + N(N+1)/2 (OI) + nf d Md (directional) + Q d (Phi_lin)) b
+                + nf Md (directional indices)
+      B_muscl = (d Md (gradient operator) + Q d (Phi_lin)) b
+    (gathers of neighbour states are L2 hits; face-state round trips are not
+    counted), and the flops
+      F_lin   = 2 Q M nv (candidate contraction) + Q F_riemann
+      F_cweno = 2 N M nv (p_opt) + 2 nf d Md nv (directional) + nv (N(N+1) + nf d(d+1)) (indicators)
+      F_muscl = 2 d Md nv."""
+    d, nv, M, N, Md = mesh.dim, s.nv, s.M, s.N, s.Md
+    nf = FACES[mesh.cell_type].astype(np.float64)
+    Q = nf * s.nfp
+    B_lin = nv * b + 4 * M + Q * M * b + (nf / 2) * (d + 1) * b + b + 4 * nf + nv * b
+    B_cw = (N * M + N * (N + 1) / 2 + nf * d * Md + Q * d) * b + nf * Md
+    B_mu = (d * Md + Q * d) * b
+    F_lin = 2 * Q * M * nv + Q * RIEMANN_FLOP[d]
+    F_cw = 2 * N * M * nv + 2 * nf * d * Md * nv + nv * (N * (N + 1) + nf * d * (d + 1))
+    F_mu = np.full_like(nf, 2.0 * d * Md * nv)
+    return {"B_lin": float(B_lin.mean()), "B_cweno": float(B_cw.mean()), "B_muscl": float(B_mu.mean()),
+            "F_lin": float(F_lin.mean()), "F_cweno": float(F_cw.mean()), "F_muscl": float(F_mu.mean())}
+
+
+def queue_fractions(torch, g, U, dev):
+    """CWENOZ and MUSCL queue lengths / cells of one residual at state U (FP64 device)."""
+    Ur = (U.float() if g.fp32 else U).contiguous()
+    g.residual(Ur)
+    torch.cuda.synchronize(dev)
+    counts, _ = g.queues()
+    return counts[0] / g.n_cells, counts[1] / g.n_cells
+
+
+def path_roofline(mesh, g, value, fq, peaks):
+    """The metric's "% of HBM roofline": B_alg x cell-residuals/s / peak, with
+    B_alg = B_lin + f_cweno B_cweno + f_muscl B_muscl at the measured queue
+    fractions.  FP64 paths are also held against the FP64 FMA ceiling: the
+    bound is the lower of HBM / B_alg and FP64 FLOP/s / F_alg."""
+    b = 4 if g.fp32 else 8
+    pm = path_model(mesh, g, b)
+    f_cw, f_mu = fq
+    B = pm["B_lin"] + f_cw * pm["B_cweno"] + f_mu * pm["B_muscl"]
+    F = pm["F_lin"] + f_cw * pm["F_cweno"] + f_mu * pm["F_muscl"]
+    hbm = peaks["hbm_gbs"] * 1e9
+    out = {"b_alg_per_cell_residual": B, "flop_per_cell_residual": F, "f_cweno": f_cw, "f_muscl": f_mu,
+           "achieved_GBs": B * value / 1e9, "peak_GBs": peaks["hbm_gbs"], "frac_hbm": B * value / hbm,
+           "hbm_ceiling": hbm / B}
+    if not g.fp32 and peaks.get("fp64_flops"):
+        alu = peaks["fp64_flops"] / F
+        out.update({"fp64_peak_tflops": peaks["fp64_flops"] / 1e12, "fp64_alu_ceiling": alu,
+                    "frac_fp64_alu": value / alu})
+        out["bound"] = "fp64_alu" if alu < out["hbm_ceiling"] else "hbm"
+        out["frac"] = value / min(alu, out["hbm_ceiling"])
+    else:
+        out["bound"] = "hbm"
+        out["frac"] = out["frac_hbm"]
+    return out
+
+
 def _k1_bytes(mesh, s, b):
     """Algorithmic bytes of one launch of the linear-candidate + detector
     kernel: per cell U_i (nv b), stencil ids (4 M), L (Q M b), threshold (b),
@@ -263,6 +361,29 @@ def _k1_bytes(mesh, s, b):
     Q = nf * s.nfp
     per = s.nv * b + 4 * s.M + Q * s.M * b + b + Q * s.nv * b + 10
     return int(per.sum())
+
+
+def kernel_roofline(mesh, g, times, peak, peak_kind, traffic):
+    """The candidate kernel's achieved bandwidth: the algorithmic bytes of one
+    launch -- B_lin of every cell (path_model; the candidate kernel reads
+    U_i, the stencil ids and L, the flux kernel the face geometry and writes
+    R) -- over the launch's average duration by events.  The kernel's own
+    byte count, which adds the face states it writes, is reported beside it."""
+    k_ms, k_n = times["linear"]
+    b = 4 if g.fp32 else 8
+    blin = path_model(mesh, g, b)["B_lin"] * mesh.n_cells
+    dur = k_ms / k_n * 1e-3 if k_n else None
+    achieved = blin / dur / 1e9 if dur else None
+    tot_ms = sum(v[0] for v in times.values())
+    return {"kernel": "k_linear (gather + linear candidate + detector + Harten test)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
+            "algorithmic_bytes_per_launch": int(round(blin)),
+            "kernel_bytes_per_launch": _k1_bytes(mesh, g, b),
+            "kernel_bytes_frac": (_k1_bytes(mesh, g, b) / dur / 1e9 / peak) if dur else None,
+            "avg_launch_us": 1e3 * k_ms / max(k_n, 1),
+            "kernel_share": {k: round(v[0] / tot_ms, 4) for k, v in times.items() if v[1]}}
 
 
 def time_steps(H, torch, g, U0, steps, warmup, cfl, dev, with_timer=False):
@@ -328,11 +449,14 @@ def e2e_pass(g, torch, U0, steps, cfl):
     return time.perf_counter() - t0, Uh.nbytes
 
 
-def turbulence_variants(H, I, torch, dev, args):
+def turbulence_variants(H, I, torch, dev, args, peaks):
     """The 3D workload: 128^3 periodic hexahedra, order 4, HLLC.  The seeded
     initial field is first advanced `pre` steps (hybrid, FP32; untimed input
     preparation) so that compressible structures have formed; every variant
-    then times `steps` steps from that same state, L2 flushed between steps."""
+    then times `steps` steps from that same state, L2 flushed between steps,
+    with its path roofline.  The FP32 hybrid also carries the candidate
+    kernel's roofline, the end-to-end rate through hfv_advance_host and the
+    oracle on a block of the mesh."""
     mesh, U0, d = I.workload("turbulence", args.turbulence_scale)
     gm = H.Mesh(mesh)
     cells, cfl, steps = mesh.n_cells, d["cfl"], args.turbulence_steps
@@ -347,23 +471,32 @@ def turbulence_variants(H, I, torch, dev, args):
     cls = torch.empty(cells, dtype=torch.uint8, device=dev)
     g.residual(U.float().contiguous(), class_out=cls)
     out["classes_at_start"] = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
+    peak, peak_kind = _peaks()
     for scheme in ("hybrid", "cweno"):
         for prec in ("fp32", "fp64"):
             gv = g if (scheme, prec) == ("hybrid", "fp32") else H.Scheme(gm, order=4, flux="hllc", scheme=scheme,
                                                                            precision=prec)
-            ms, _, _, _ = time_steps(H, torch, gv, Upre, steps, 2, cfl, dev)
-            entry = {"value": 3.0 * cells * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+            ms, _, _, Ufin = time_steps(H, torch, gv, Upre, steps, 3, cfl, dev)
+            value = 3.0 * cells * steps / (ms * 1e-3)
+            a0 = queue_fractions(torch, gv, torch.tensor(Upre, device=dev), dev)
+            a1 = queue_fractions(torch, gv, Ufin, dev)
+            del Ufin
+            entry = {"value": value, "ms_per_step": ms / steps,
+                     "path": path_roofline(mesh, gv, value, (0.5 * (a0[0] + a1[0]), 0.5 * (a0[1] + a1[1])), peaks)}
             if (scheme, prec) == ("hybrid", "fp32"):
                 times = kernel_pass(H, torch, gv, Upre, steps, cfl, dev)
-                k_ms, k_n = times["linear"]
-                kb = _k1_bytes(mesh, gv, 4)
-                ach = kb / (k_ms / k_n * 1e-3) / 1e9
-                peak, _ = _peaks()
-                entry["k_linear"] = {"achieved_GBs": ach, "frac": ach / peak, "avg_launch_us": 1e3 * k_ms / k_n,
-                                     "algorithmic_bytes_per_launch": kb,
-                                     "traffic": _traffic("turbulence", 4, "fp32", "hybrid", cells)}
-                entry["kernel_share"] = {k: round(v[0] / sum(x[0] for x in times.values()), 4)
-                                         for k, v in times.items() if v[1]}
+                entry["k_linear"] = kernel_roofline(mesh, gv, times, peak, peak_kind,
+                                                    _traffic("turbulence", 4, "fp32", "hybrid", cells))
+                e2e_s, nbytes = e2e_pass(gv, torch, Upre, steps, cfl)
+                entry["e2e"] = {"value": 3.0 * cells * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                                "d2h_bytes_per_step": nbytes, "api": "hfv_advance_host"}
+                if args.cpu_baseline:
+                    smp = _oracle_block(mesh, 8)
+                    v, ns, dt = _oracle_steps(mesh, Upre, 4, "hllc", "hybrid", 1, 1, sample=smp)
+                    entry["cpu_baseline"] = {
+                        "value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
+                        "sample": f"{ns} cells (an 8^3 block at the domain centre) of the {cells}-cell mesh, 1 step x "
+                                  f"3 residual evaluations, FP64, operators built before timing ({dt:.1f} s timed)"}
             out[f"{scheme}_{prec}"] = entry
             if gv is not g:
                 del gv
@@ -620,6 +753,9 @@ def main():
         return H.Scheme(gm, order=order, flux=dflt["flux"], scheme=scheme, precision=precision)
 
     g = make(args.order, args.scheme, args.precision)
+    peak, peak_kind = _peaks()
+    peaks = {"hbm_gbs": peak}
+    peaks.update(alu_peaks(H))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -637,21 +773,16 @@ def main():
     g.residual(Uf.contiguous(), class_out=cls)
     hist = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
 
+    # the metric's path roofline at the measured class queues (start and end of the timed steps)
+    fq0 = queue_fractions(torch, g, torch.tensor(U0, device=dev), dev)
+    fq1 = queue_fractions(torch, g, Ufin, dev)
+    fq = (0.5 * (fq0[0] + fq1[0]), 0.5 * (fq0[1] + fq1[1]))
     # dominant kernel: linear candidate + detector
     times = kernel_pass(H, torch, g, U0, args.steps, cfl, dev)
-    peak, peak_kind = _peaks()
-    k_ms, k_n = times["linear"]
-    b = 4 if g.fp32 else 8
-    kbytes = _k1_bytes(mesh, g, b)
-    achieved = kbytes / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
-    tot_ms = sum(v[0] for v in times.values())
-    roofline = {"kernel": "k_linear (gather + linear candidate + detector + Harten test)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": _traffic(args.workload, args.order, args.precision, args.scheme, cells),
-                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback",
-                "algorithmic_bytes_per_launch": kbytes, "avg_launch_us": 1e3 * k_ms / max(k_n, 1),
-                "kernel_share": {k: round(v[0] / tot_ms, 4) for k, v in times.items() if v[1]}}
+    roofline = kernel_roofline(mesh, g, times, peak, peak_kind,
+                               _traffic(args.workload, args.order, args.precision, args.scheme, cells))
+    roofline["path"] = path_roofline(mesh, g, value / world, fq, peaks)
+    roofline["alu_peaks_tflops"] = {k: v / 1e12 for k, v in peaks.items() if k.endswith("flops")}
 
     # end to end through the C ABI with host buffers
     e2e_s, nbytes = e2e_pass(g, torch, U0, args.steps, cfl)
@@ -666,15 +797,21 @@ def main():
                 for prec in ("fp32", "fp64"):
                     key = f"order{order}_{scheme}_{prec}"
                     if (order, scheme, prec) == (args.order, args.scheme, args.precision):
-                        variants[key] = {"value": value / world, "ms_per_step": ms_max / args.steps}
+                        variants[key] = {"value": value / world, "ms_per_step": ms_max / args.steps,
+                                         "path": roofline["path"]}
                         continue
                     gv = make(order, scheme, prec)
-                    msv, _, _, _ = time_steps(H, torch, gv, U0, args.steps, args.warmup, cfl, dev)
-                    variants[key] = {"value": 3.0 * cells * args.steps / (msv * 1e-3), "ms_per_step": msv / args.steps}
+                    msv, _, _, Uv = time_steps(H, torch, gv, U0, args.steps, args.warmup, cfl, dev)
+                    vv = 3.0 * cells * args.steps / (msv * 1e-3)
+                    a0 = queue_fractions(torch, gv, torch.tensor(U0, device=dev), dev)
+                    a1 = queue_fractions(torch, gv, Uv, dev)
+                    variants[key] = {"value": vv, "ms_per_step": msv / args.steps,
+                                     "path": path_roofline(mesh, gv, vv, (0.5 * (a0[0] + a1[0]), 0.5 * (a0[1] + a1[1])),
+                                                           peaks)}
                     del gv
     turbulence = None
     if args.turbulence and rank == 0:
-        turbulence = turbulence_variants(H, I, torch, dev, args)
+        turbulence = turbulence_variants(H, I, torch, dev, args, peaks)
     batched = None
     if args.batched and rank == 0:
         batched = batched_variants(H, I, torch, dev, args)
@@ -688,7 +825,7 @@ def main():
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
         v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 10, 1, band=0.2)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
                "sample": f"{ns} cells (|y - 0.5| < 0.2) of the {cells}-cell mesh, 10 steps x 3 residual "
                          f"evaluations, FP64, operators built before timing ({dt:.1f} s timed)"}
         procs = min(16, os.cpu_count() or 1)

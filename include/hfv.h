@@ -315,6 +315,16 @@ HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int r
 /* Number of kernels launched by this library in this process so far. */
 HFV_API int hfv_launch_count(int64_t* count);
 
+/* Fused multiply-add throughput of the current device's CUDA cores, the ALU
+ * ceiling of the residual paths (instrumentation; the paper has no
+ * counterpart).  kind 0 = FP64 (DFMA), 1 = FP32 (FFMA), 2 = packed FP32
+ * (FFMA2, two FMAs per instruction).  Every SM runs 2,048 threads of eight
+ * independent dependent-FMA chains; the loop count is calibrated so that a
+ * launch takes about target_ms (0 < target_ms <= 2000), and the best of three
+ * timed launches (CUDA events on `stream`) is written to *flops_per_s as
+ * 2 x FMAs / second.  sync.  Errors: HFV_ERR_ARG, HFV_ERR_CUDA. */
+HFV_API int hfv_fma_rate(int kind, double target_ms, double* flops_per_s, void* stream);
+
 /* Class-queue compaction that allocates nothing (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device
  * memory when they need the queues, e.g. code running inside a CUDA stream

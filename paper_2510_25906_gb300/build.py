@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhfv.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["mesh.cpp", "scheme.cpp", "setup.cu", "residual.cu", "adjoint.cu", "api.cu", "noalloc.cu"]
+UNITS = ["mesh.cpp", "scheme.cpp", "setup.cu", "residual.cu", "adjoint.cu", "api.cu", "noalloc.cu", "peak.cu"]
 
 
 def _nvcc() -> str:

@@ -89,6 +89,7 @@ def load():
         "hfv_kernel_times": [vp, vp, vp, C.c_int],
         "hfv_launch_count": [vp],
         "hfv_class_queues_static": [vp, C.c_int64, vp, vp, vp],
+        "hfv_fma_rate": [C.c_int, d, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -339,6 +340,15 @@ def launch_count() -> int:
     n = C.c_int64()
     _check(load().hfv_launch_count(C.byref(n)))
     return n.value
+
+
+def fma_rate(kind: str = "fp64", target_ms: float = 100.0, stream=None) -> float:
+    """hfv_fma_rate: the device's fused multiply-add rate in FLOP/s (2 per
+    FMA); kind "fp64" (DFMA), "fp32" (FFMA) or "fp32x2" (packed FFMA2)."""
+    k = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
+    out = C.c_double()
+    _check(load().hfv_fma_rate(k, float(target_ms), C.byref(out), _stream(stream)))
+    return out.value
 
 
 def class_queues_static(classes, counts=None, queues=None, stream=None):

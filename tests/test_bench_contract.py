@@ -27,6 +27,8 @@ def test_reference_arm_json_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+    # the arm times the FP64 oracle: its config must say so
+    assert line["dtype"] == "f64" and line["config"]["precision"] == "fp64"
 
 
 def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
