@@ -1144,9 +1144,10 @@ static double dmono(const or_scheme* s, int k, int a, const double* xi)
  * the gradient in physical coordinates of the unlimited degree-r polynomial
  * of each conserved variable (grad p = sum_k a_k J^-T grad_xi phi_k), turned
  * into the gradients of the velocity components and of T = p / rho by the
- * chain rule at the same polynomial's value there.
+ * chain rule at the cell's face-point state W (the state U_L that also enters
+ * the convective flux, eq. EulerEquationsDetails).
  * PG[q][k][j]: k < d velocity component k, k = d temperature; j = x, y, z. */
-static void rec_visc_grad(or_scheme* s, or_ops* o, const double* U, int64_t i, double* PG)
+static void rec_visc_grad(or_scheme* s, or_ops* o, const double* U, int64_t i, const double* Wf, double* PG)
 {
     int N = s->N, nv = s->nv, d = s->d, nfp = s->nfp, nf = n_faces_of(s, i);
     double a[5 * 128], V[5 * 64], x0[3], Ji[3][3], det, pts[3 * 64], nrm[3];
@@ -1171,7 +1172,7 @@ static void rec_visc_grad(or_scheme* s, or_ops* o, const double* U, int64_t i, d
                         }
                     gc[v][j] = sum;
                 }
-            const double* w = &V[q * nv];
+            const double* w = &Wf[q * nv];
             double rho = w[0], u[3] = {0, 0, 0}, u2 = 0.0;
             for (int k = 0; k < d; ++k) { u[k] = w[1 + k] / rho; u2 += u[k] * u[k]; }
             double p = (g - 1.0) * (w[d + 1] - 0.5 * rho * u2), T = p / rho;
@@ -1618,13 +1619,6 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
     } else {
         for (int64_t c = 0; c < nc; ++c) if (need[c] & 2) { tag[c] = forced[c]; raw[c] = forced[c]; }
     }
-    /* viscous gradients at the face points (Sec. 2) */
-    for (int64_t c = 0; c < nc && visc && !err; ++c) {
-        if (!(need[c] & 2)) continue;
-        or_ops* o = get_ops(s, c);
-        if (!o) { err = 1; break; }
-        rec_visc_grad(s, o, U, c, &PG[(size_t)slot[c] * maxQ * 12]);
-    }
     /* a5 / a6 / a7: reconstruct by class, then the Harten bound */
     for (int64_t c = 0; c < nc && !err; ++c) {
         if (!(need[c] & 2)) continue;
@@ -1645,6 +1639,13 @@ int or_residual(or_scheme* s, const double* U, double* R, const uint8_t* forced,
             }
         }
         fin[c] = (uint8_t)cls;
+    }
+    /* viscous gradients at the face points (Sec. 2), at the final face states */
+    for (int64_t c = 0; c < nc && visc && !err; ++c) {
+        if (!(need[c] & 2)) continue;
+        or_ops* o = get_ops(s, c);
+        if (!o) { err = 1; break; }
+        rec_visc_grad(s, o, U, c, &FS[(size_t)slot[c] * maxQ * nv], &PG[(size_t)slot[c] * maxQ * 12]);
     }
     /* a8: Riemann fluxes at the face points, summed into the residual */
     if (!err) {
@@ -1718,6 +1719,19 @@ double or_dt(or_scheme* s, const double* U, double cfl)
             double un = 0.0;
             for (int k = 0; k < s->d; ++k) un += u[1 + k] / u[0] * m->fnorm[3 * g + k];
             lam += (fabs(un) + cs) * m->farea[g];
+        }
+        if (s->p.mu0 > 0.0) {
+            /* viscous terms: the explicit diffusion limit, 4 nu sum_f |S_f|^2 / |V|
+             * with nu = max(4/3, gamma / Pr) mu / rho (momentum and heat) --
+             * a reading: the paper states a convective CFL number only */
+            double T = p / u[0], T0 = s->p.t0, S = s->p.suth_s, s2 = 0.0;
+            double mu = s->p.mu0 * pow(T / T0, 1.5) * (T0 + S) / (T + S);
+            double nu = fmax(4.0 / 3.0, s->p.gamma / s->p.prandtl) * mu / u[0];
+            for (int f = 0; f < n_faces_of(s, c); ++f) {
+                double a = m->farea[m->cface[c * MAXNF + f]];
+                s2 += a * a;
+            }
+            lam += 4.0 * nu * s2 / m->vol[c];
         }
         double t = cfl * m->vol[c] / lam;
         if (t < dt) dt = t;

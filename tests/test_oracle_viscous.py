@@ -77,21 +77,43 @@ def test_couette_flow_heats_interior_cells_at_mu():
 def test_penalty_term_closed_form(alpha):
     """Uniform squares (h = 1/16), u = x, rho = 1, cell means of E chosen so
     that every cell-mean pressure is 1; all cells forced first-order, so the
-    face states are the cell means while the gradients come from the exact
-    degree-2 polynomials.  Across an x-face the averaged gradient is e_x, the
-    penalty adds alpha (u_j - u_i) / h = alpha: du/dx = 1 + alpha, tau_xx =
-    4/3 mu (1 + alpha), and the work of the stress through the two x-faces,
+    face states are the cell means while the conserved gradients come from
+    the exact degree-2 polynomials (grad rho = 0, grad m_x = e_x).  Across an
+    x-face the averaged velocity gradient is e_x, the penalty adds
+    alpha (u_j - u_i) / h = alpha: du/dx = 1 + alpha, tau_xx = 4/3 mu (1 +
+    alpha), and the work of the stress through the two x-faces,
     (u_i + h/2) tau_xx h - (u_i - h/2) tau_xx h, over the area h^2 gives the
-    energy residual 4/3 (1 + alpha) mu0; the other components vanish."""
+    energy residual 4/3 (1 + alpha) mu0; the other components vanish.  The
+    Prandtl number is made huge: at a cell-mean state the temperature
+    gradient of the polynomial is not zero, and conduction is not what this
+    checks."""
     n = 16
     m = I.structured_quad_mesh(n, n, periodic=(False, True))
     xc = m.vertex_means()[:, 0]
     U = np.stack([np.ones(n * n), xc, 0 * xc, 2.5 + 0.5 * xc * xc])
     forced = np.full(n * n, O.FIRST, np.uint8)
-    _, dv = _visc(m, U, forced=forced, order=3, flux="hllc", visc_alpha=alpha)
+    _, dv = _visc(m, U, forced=forced, order=3, flux="hllc", visc_alpha=alpha, prandtl=1e30)
     inner = (xc > 4 / n) & (xc < 12 / n)
     want = np.array([0, 0, 0, 4.0 / 3.0 * (1 + alpha) * MU0])[:, None]
     assert np.abs(dv[:, inner] - want).max() < 1e-12, np.abs(dv[:, inner] - want).max()
+
+
+def test_viscous_time_step_keeps_the_quadrant_problem_physical():
+    """The CFL step with the diffusion limit (4 max(4/3, gamma/Pr) mu/rho
+    sum|S|^2/|V| added to the convective bound) is smaller than the inviscid
+    one, and viscous steps across the jumps of the 2D Riemann problem keep
+    density and pressure positive."""
+    m = I.mixed_tri_quad_mesh(20, seed=2)
+    U0 = I.quadrant_state(m)
+    om = O.Mesh(m)
+    sv = O.Scheme(om, order=3, flux="hllc", mu0=0.02)
+    s0 = O.Scheme(om, order=3, flux="hllc")
+    assert sv.dt(U0, 0.5) < s0.dt(U0, 0.5)
+    U = U0.copy()
+    for _ in range(3):
+        U = sv.rk3_step(U, sv.dt(U, 0.5))
+    p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+    assert np.isfinite(U).all() and (U[0] > 0).all() and (p > 0).all()
 
 
 def _manufactured():
