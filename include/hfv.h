@@ -110,8 +110,9 @@ typedef struct {
 
 /* Scheme parameters.  hfv_default_params fills the defaults given here. */
 typedef struct {
-    int order;          /* r + 1 (default 3), "order" as in Sec. 2.1: 2..5 in 2D, 2..4 on
-                           hexahedra, 2..3 on meshes with tetrahedra, prisms or pyramids */
+    int order;          /* r + 1 (default 3), "order" as in Sec. 2.1: 2..7 in 2D, 2..6 on
+                           hexahedra, 2..3 on meshes with tetrahedra, prisms or pyramids;
+                           hfv_residual_vjp: 2..5 in 2D, 2..4 on hexahedra */
     int flux;           /* HFV_RUSANOV / HFV_HLLC / HFV_HLL (default HLLC) */
     int scheme;         /* HFV_HYBRID (default) or a pure scheme */
     int nad_vars;       /* detector variables: bit0 density, bit1 pressure,
@@ -135,6 +136,15 @@ typedef struct {
                            with the eigenvectors of the flux Jacobian along its normal at the
                            cell mean) */
     double venkat_k;    /* Venkatakrishnan threshold eps^2 = (K dx)^3, dx = |V|^(1/d); default 5 */
+    /* viscous terms (Sec. 2, eq. EulerEquationsDetails; Navier-Stokes when mu0 > 0):
+     *   mu = mu0 (T / t0)^(3/2) (t0 + sutherland_s) / (T + sutherland_s)  (eq. sutherlandlaw),
+     *   T = p / rho, heat flux mu / prandtl gamma / (gamma - 1) grad T   (eq. HeatConduct),
+     *   face gradient = mean of the two sides' gradients + (visc_alpha / L_int)(W_R - W_L) n
+     *   (eq. viscous_jump; L_int between the cells' vertex means).  The gradients
+     *   are those of each side's unlimited least-squares polynomial (Sec. 2).
+     *   Defaults: mu0 = 0 (Euler), t0 = 1, sutherland_s = 110.4 / 288.15,
+     *   prandtl = 0.72, visc_alpha = 4/3 */
+    double mu0, t0, sutherland_s, prandtl, visc_alpha;
 } hfv_scheme_params;
 
 /* Fill *p with the defaults listed above.  Never fails for non-NULL p. */
@@ -248,7 +258,7 @@ HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt
  *        back to FIRST as in hfv_residual)
  *   lam  device FP64 [nv][n_cells], the adjoint of R
  *   g    device FP64 [nv][n_cells], output
- * FP64 schemes only.  The first call allocates the adjoint's scratch
+ * FP64 schemes of the Euler residual (mu0 = 0) only.  The first call allocates the adjoint's scratch
  * (face-point adjoints, per-stencil-entry contributions and the inverse
  * stencil map, about (Q_max + M + 1) nv 8 + 12 M bytes per cell), kept until
  * hfv_scheme_destroy.  The paper states no adjoint; this is the
@@ -308,7 +318,7 @@ HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
  * outputs, 16 entries each): ms[k] total milliseconds and launches[k] count
  * of kernel k: 0 linear candidate + detector, 1 tagging, 2 block counts,
  * 3 scan, 4 scatter, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage,
- * 9 time step, 10 FP32 conversion.  reset != 0 zeroes the totals after
+ * 9 time step, 10 FP32 conversion, 11 viscous gradients.  reset != 0 zeroes the totals after
  * reading.  sync. */
 HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset);
 

@@ -16,7 +16,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhfv.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = ["mesh.cpp", "scheme.cpp", "setup.cu", "residual.cu", "adjoint.cu", "api.cu", "noalloc.cu", "peak.cu"]
+UNITS = ["mesh.cpp", "scheme.cpp", "setup.cu", "residual.cu", "residual_2d.cu", "residual_2d_high.cu", "residual_3d.cu",
+         "residual_hex.cu", "residual_hex5.cu", "residual_hex6.cu", "adjoint.cu", "api.cu", "noalloc.cu", "peak.cu"]
 
 
 def _nvcc() -> str:

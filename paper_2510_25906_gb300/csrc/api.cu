@@ -61,6 +61,11 @@ extern "C" int hfv_default_params(hfv_scheme_params* p)
     p->harten_theta = 0.9;
     p->harten_eps = 1e-14;
     p->stencil_factor = 2.0;
+    p->mu0 = 0.0;
+    p->t0 = 1.0;
+    p->sutherland_s = 110.4 / 288.15;
+    p->prandtl = 0.72;
+    p->visc_alpha = 4.0 / 3.0;
     return HFV_OK;
 }
 
@@ -102,7 +107,9 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
         (p->time_scheme != HFV_SSPRK3 && p->time_scheme != HFV_SSPRK54) ||
         (p->limiter != HFV_BARTH_JESPERSEN && p->limiter != HFV_VENKATAKRISHNAN) || !(p->venkat_k >= 0.0) ||
         (p->cweno_vars != HFV_CONSERVED && p->cweno_vars != HFV_CHARACTERISTIC) ||
-        !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0)) {
+        !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0) ||
+        !(p->mu0 >= 0.0) || !(p->t0 > 0.0) || !(p->sutherland_s >= 0.0) || !(p->prandtl > 0.0) ||
+        !(p->visc_alpha >= 0.0)) {
         set_error("hfv_scheme_create: parameter out of range");
         return HFV_ERR_ARG;
     }
@@ -208,6 +215,10 @@ extern "C" int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* c
     if (s->p.precision != HFV_FP64) { set_error("hfv_residual_vjp: FP64 schemes only"); return HFV_ERR_ARG; }
     if (s->p.cweno_vars != HFV_CONSERVED) {
         set_error("hfv_residual_vjp: CWENOZ in conserved variables only");
+        return HFV_ERR_ARG;
+    }
+    if (s->p.mu0 > 0.0) {
+        set_error("hfv_residual_vjp: the Euler residual only (mu0 = 0)");
         return HFV_ERR_ARG;
     }
     return launch_vjp(s, U, cls, lam, g, stream);

@@ -102,12 +102,16 @@ struct hfv_dev_arrays {
     double* dt;        // [nseg] time step per problem
     int32_t* seg;      // [nc] problem of each cell (batched meshes; null for one problem)
     double* Uio;       // [nv][nc] device state of hfv_advance_host
+    // viscous terms (mu0 > 0 only, else null)
+    void* VX;          // [nc][d + d d] mean of xi over the cell, then J^-1 row by row
+    void* LINV;        // [nc][6] 1 / distance between the cell's and the face neighbour's vertex means (0: none)
+    void* GS;          // [qoff][d + 1][d] face-point gradients of the velocity components and of T
 };
 
 namespace hfv {
 // hot-path kernel ids for the optional per-kernel timer
 enum KernelId { KID_LINEAR, KID_TAG, KID_COUNT, KID_SCAN, KID_SCATTER, KID_CWENO, KID_MUSCL, KID_FLUX, KID_RK,
-                KID_DT, KID_CVT, KID_COUNT_ALL };
+                KID_DT, KID_CVT, KID_GRAD, KID_COUNT_ALL };
 struct KernelTimer {
     bool on = false;
     std::vector<void*> ev;          // cudaEvent_t pairs

@@ -35,24 +35,36 @@ struct K1Shape {
     // 3D with up to 32 face points and M <= 20 (order 3; hexahedra, prisms,
     // pyramids): sixteen lanes per cell, two points each
     static constexpr bool SMALL3 = C::D == 3 && C::QMAX > 16 && C::QMAX <= 32 && C::M <= 20;
-    static constexpr int PPL = SMALL ? C::QMAX / 4 : SMALL3 ? 2 : 1;
     static constexpr int G = SMALL ? 4 : SMALL3 ? 16 : GroupSize<C::QMAX>::value;   // lanes per cell
+    // face points per lane: two in the layouts above, and two where a
+    // hexahedron has more points than a warp has lanes (orders 5-6, 54 points)
+    static constexpr int PPL = SMALL ? C::QMAX / 4 : SMALL3 ? 2 : (C::QMAX + G - 1) / G;
     static constexpr int SLOT = C::NFMAX <= 4 ? 4 : 8;       // lanes of one face-neighbour reduction
     // lanes past the first SLOT take the bounds from the group's first lane
     static constexpr bool NB_BCAST = G > SLOT;
-    static constexpr int CONSUMERS = 256;                    // 8 warps
-    static constexpr int NG = CONSUMERS / G;                 // cells per tile
     static constexpr int PER16 = 16 / (int)sizeof(T);
     static constexpr int LMAX = (C::QMAX * C::M + PER16 - 1) / PER16 * PER16;  // elements per cell block
-    static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
-    static constexpr int SBYTES = NG * C::M * 4;
-    static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
     // rows of U_m - U_0 per cell: [M][4] and, with five variables, [M] of the
     // fifth; cells 16 bytes apart modulo 128 so that the four cells of a warp
     // read different banks
     static constexpr int DU4 = C::M * 4 * (int)sizeof(T);
     static constexpr int DU5 = C::NV == 5 ? (C::M * (int)sizeof(T) + 15) / 16 * 16 : 0;
     static constexpr int CSTRIDE = (DU4 + DU5 + 127) / 128 * 128 + 16;
+    // shared memory of two ring stages and the U_m - U_0 rows for a tile of
+    // `consumers` / G cells
+    static constexpr int two_stages(int consumers)
+    {
+        const int ng = consumers / G;
+        const int stage = (ng * LMAX * (int)sizeof(T) + ng * C::M * 4 + 127) / 128 * 128;
+        return 2 * stage + (ng * CSTRIDE + 127) / 128 * 128 + 4 * 8 + 1024;
+    }
+    // eight consumer warps, or four or two where a tile of the large blocks
+    // of L (orders 6-7 in 2D, FP64) would not leave room for two ring stages
+    static constexpr int CONSUMERS = two_stages(256) <= 227 * 1024 ? 256 : two_stages(128) <= 227 * 1024 ? 128 : 64;
+    static constexpr int NG = CONSUMERS / G;                 // cells per tile
+    static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
+    static constexpr int SBYTES = NG * C::M * 4;
+    static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
     static constexpr int SU = NG * CSTRIDE;
     // resident CTAs per SM aimed for (register and shared-memory budget)
     static constexpr int MINB = sizeof(T) == 8 ? 1 : 2;

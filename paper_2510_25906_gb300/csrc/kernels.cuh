@@ -97,6 +97,13 @@ struct KParams {
     T gamma, alpha_m, beta_m, alpha_w, beta_w, lam1, eps_cw, b_cw, h_theta, h_eps;
     int limiter;          // MUSCL: 0 Barth-Jespersen, 1 Venkatakrishnan
     T venk_k;
+    // viscous terms (mu0 > 0): per cell the mean of xi and the reference map
+    // J^-1 ([D + D D], xi = J^-1 (x - v0)), per cell-face 1 / L_int, and the
+    // face-point gradients of the velocity and temperature [qoff][D + 1][D]
+    const T* VX;
+    const T* LINV;
+    T* GS;
+    ViscParams vp;
 };
 
 }  // namespace hfv

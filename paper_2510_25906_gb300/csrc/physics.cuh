@@ -148,4 +148,69 @@ HDI void riemann(const T* UL, const T* UR, const T* n, T g, T* F)
     F[D + 1] = FK[D + 1] + SK * (Es - UK[D + 1]);
 }
 
+// Viscous flux F_v . n at one face point (Sec. 2: eqs. Terms1, Stresses,
+// HeatConduct, sutherlandlaw, viscous_jump).  wl, wr: the two sides'
+// conserved states; gl, gr: their gradients [D + 1][D] of the velocity
+// components and of T = p / rho; inv_lint = 1 / (distance between the cells'
+// centres), 0 on an open boundary.  Face state: the mean of the two sides'
+// velocity and temperature; face gradient: the mean of the two sides'
+// gradients plus (alpha / L_int)(W_R - W_L) n;
+//   tau_ij = mu (d_j u_i + d_i u_j - 2/3 div u delta_ij),
+//   Theta_j = sum_i u_i tau_ij + mu / Pr gamma / (gamma - 1) dT/dx_j,
+//   mu = mu0 (T / T0)^(3/2) (T0 + S) / (T + S).
+struct ViscParams {
+    double mu0, t0, suth, inv_pr, alpha;
+};
+
+template <class T, int D>
+HDI void viscous_flux(const T* wl, const T* wr, const T* gl, const T* gr, const T* n, T inv_lint, T g,
+                      const ViscParams& vp, T* F)
+{
+    T ql[D + 1], qr[D + 1];
+    {
+        const T il = T(1) / wl[0], ir = T(1) / wr[0];
+        T ul2 = T(0), ur2 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            ql[k] = wl[1 + k] * il;
+            qr[k] = wr[1 + k] * ir;
+            ul2 += ql[k] * ql[k];
+            ur2 += qr[k] * qr[k];
+        }
+        ql[D] = (g - T(1)) * (wl[D + 1] - T(0.5) * wl[0] * ul2) * il;
+        qr[D] = (g - T(1)) * (wr[D + 1] - T(0.5) * wr[0] * ur2) * ir;
+    }
+    T Gm[D + 1][D];
+#pragma unroll
+    for (int k = 0; k <= D; ++k) {
+        const T pen = T(vp.alpha) * inv_lint * (qr[k] - ql[k]);
+#pragma unroll
+        for (int j = 0; j < D; ++j) Gm[k][j] = T(0.5) * (gl[k * D + j] + gr[k * D + j]) + pen * n[j];
+    }
+    const T Tm = T(0.5) * (ql[D] + qr[D]), t0 = T(vp.t0), S = T(vp.suth);
+    const T tr = Tm / t0;
+    const T mu = T(vp.mu0) * tr * tsqrt<T>(tr) * (t0 + S) / (Tm + S);
+    T div = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) div += Gm[k][k];
+    const T kap = mu * T(vp.inv_pr) * g / (g - T(1));
+    F[0] = T(0);
+    T fe = T(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T fi = T(0);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const T tij = mu * (Gm[i][j] + Gm[j][i] - (i == j ? T(2) / T(3) * div : T(0)));
+            fi += tij * n[j];
+        }
+        F[1 + i] = fi;
+        // sum_j (sum_i u_i tau_ij) n_j = sum_i u_i (tau . n)_i (tau symmetric)
+        fe += T(0.5) * (ql[i] + qr[i]) * fi;
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) fe += kap * Gm[D][j] * n[j];
+    F[D + 1] = fe;
+}
+
 }  // namespace hfv

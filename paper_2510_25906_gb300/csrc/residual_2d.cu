@@ -1,0 +1,15 @@
+// residual_2d.cu -- the residual kernels instantiated for 2D meshes, orders 2-5.
+#include "residual_impl.cuh"
+
+namespace hfv {
+
+template int run_residual<Cfg<2, 1, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<2, 1, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+template int run_residual<Cfg<2, 2, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<2, 2, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+template int run_residual<Cfg<2, 3, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<2, 3, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+template int run_residual<Cfg<2, 4, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<2, 4, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+
+}  // namespace hfv

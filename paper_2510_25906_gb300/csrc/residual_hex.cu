@@ -1,0 +1,13 @@
+// residual_hex.cu -- the residual kernels instantiated for hexahedra, orders 2-4.
+#include "residual_impl.cuh"
+
+namespace hfv {
+
+template int run_residual<Cfg<3, 1, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<3, 1, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+template int run_residual<Cfg<3, 2, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<3, 2, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+template int run_residual<Cfg<3, 3, 0>, float>(hfv_scheme*, const float*, float*, const uint8_t*, uint8_t*, cudaStream_t, const float*, const StageRK*);
+template int run_residual<Cfg<3, 3, 0>, double>(hfv_scheme*, const double*, double*, const uint8_t*, uint8_t*, cudaStream_t, const double*, const StageRK*);
+
+}  // namespace hfv

@@ -117,6 +117,10 @@ int build_operators(hfv_scheme* s, void* stream)
            o_seg = take(s->nseg > 1 ? nc * 4 : 0);
     const bool rk54 = s->p.time_scheme == HFV_SSPRK54;
     size_t o_U3 = take(rk54 ? nv * nc * 8 : 0), o_U4 = take(rk54 ? nv * nc * 8 : 0), o_U5 = take(rk54 ? nv * nc * 8 : 0);
+    const bool visc = s->p.mu0 > 0.0;
+    const int nvx = d + d * d;
+    size_t o_VX = take(visc ? nc * nvx * b : 0), o_LINV = take(visc ? nc * 6 * b : 0),
+           o_GS = take(visc ? qt * (d + 1) * d * b : 0);
     s->arena_bytes = off;
     SETUP_CHECK(cudaMalloc(&s->arena, off));
     char* A = (char*)s->arena;
@@ -137,6 +141,9 @@ int build_operators(hfv_scheme* s, void* stream)
     a.U4 = rk54 ? (double*)(A + o_U4) : nullptr;
     a.U5 = rk54 ? (double*)(A + o_U5) : nullptr;
     a.Uio = (double*)(A + o_Uio);
+    a.VX = visc ? A + o_VX : nullptr;
+    a.LINV = visc ? A + o_LINV : nullptr;
+    a.GS = visc ? A + o_GS : nullptr;
     SETUP_CHECK(cudaMemsetAsync(s->arena, 0, off, st));
 
     // ---- host-side per-cell data ----
@@ -204,10 +211,19 @@ int build_operators(hfv_scheme* s, void* stream)
     size_t t_xyz = ttake(m->nn * 3 * 8), t_cptr = ttake((nc + 1) * 8), t_cidx = ttake(m->cidx.size() * 4),
            t_type = ttake(nc), t_sshift = ttake(nc * M * 3), t_nd = ttake(nc * 6), t_fvtx = ttake(nc * 24 * 4),
            t_fk = ttake(nc * 18), t_ws = ttake((size_t)chunk * M * N * 8), t_err = ttake(64);
-    size_t t_L = 0, t_P = 0, t_Phil = 0, t_OI = 0, t_D = 0, t_G = 0, t_W = 0;
+    // FP32 schemes build their operators in FP64 one chunk of cells at a time
+    // and convert each chunk into the arena, so the FP64 copies never exceed
+    // one chunk (hexahedra at order 6 carry 24 KB of L per cell in FP32)
+    const int64_t qs = (int64_t)s->nfmax * s->nfp;
+    int64_t lchunk = 0;
+    for (int64_t c0 = 0; c0 < nc; c0 += chunk)
+        lchunk = std::max<int64_t>(lchunk, s->loff[std::min(c0 + chunk, nc)] - s->loff[c0]);
+    size_t t_L = 0, t_P = 0, t_Phil = 0, t_OI = 0, t_D = 0, t_G = 0, t_W = 0, t_VX = 0;
     if (f32) {
-        t_L = ttake(lt * 8); t_P = ttake(nc * N * M * 8); t_Phil = ttake(qt * d * 8); t_OI = ttake(nc * NOI * 8);
-        t_D = ttake(nc * 6 * d * Md * 8); t_G = ttake(nc * d * Md * 8); t_W = ttake(qt * 8);
+        t_L = ttake(lchunk * 8); t_P = ttake(chunk * N * M * 8); t_Phil = ttake(chunk * qs * d * 8);
+        t_OI = ttake(chunk * NOI * 8); t_D = ttake(chunk * 6 * d * Md * 8); t_G = ttake(chunk * d * Md * 8);
+        t_W = ttake(chunk * qs * 8);
+        if (visc) t_VX = ttake(chunk * nvx * 8);
     }
     char* T = nullptr;
     SETUP_CHECK(cudaMalloc(&T, t_off));
@@ -253,22 +269,36 @@ int build_operators(hfv_scheme* s, void* stream)
     O.D = (double*)(f32 ? T + t_D : (char*)a.D);
     O.G = (double*)(f32 ? T + t_G : (char*)a.G);
     O.W = (double*)(f32 ? T + t_W : (char*)a.W);
+    O.VX = visc ? (double*)(f32 ? T + t_VX : (char*)a.VX) : nullptr;
     O.err = (int*)(T + t_err);
     double* ws = (double*)(T + t_ws);
-    // the per-cell build keeps its small matrices in local memory (~6.3 KB
+    // the per-cell build keeps its small matrices in local memory (~12 KB
     // of stack per thread): raise this context's stack limit for the build
+    constexpr size_t kStack = 16384;
     size_t old_stack = 0;
     SETUP_CHECK(cudaDeviceGetLimit(&old_stack, cudaLimitStackSize));
-    if (old_stack < 8192) SETUP_CHECK(cudaDeviceSetLimit(cudaLimitStackSize, 8192));
+    if (old_stack < kStack) SETUP_CHECK(cudaDeviceSetLimit(cudaLimitStackSize, kStack));
     for (int64_t c0 = 0; c0 < nc; c0 += chunk) {
         int64_t cn = std::min(chunk, nc - c0);
+        if (f32) { O.cbase = c0; O.qbase = s->qoff[c0]; O.lbase = s->loff[c0]; }
         k_setup<<<(unsigned)((cn + 63) / 64), 64, 0, st>>>(S, O, ws, chunk, c0, cn);
         SETUP_CHECK(cudaGetLastError());
+        if (f32) {
+            const int64_t l0 = s->loff[c0], q0 = s->qoff[c0];
+            convert<float>(O.L, (float*)a.L + l0, s->loff[c0 + cn] - l0, st);
+            convert<float>(O.P, (float*)a.P + c0 * N * M, cn * N * M, st);
+            convert<float>(O.Phil, (float*)a.Phil + q0 * d, (s->qoff[c0 + cn] - q0) * d, st);
+            convert<float>(O.OI, (float*)a.OI + c0 * NOI, cn * NOI, st);
+            convert<float>(O.D, (float*)a.D + c0 * 6 * d * Md, cn * 6 * d * Md, st);
+            convert<float>(O.G, (float*)a.G + c0 * d * Md, cn * d * Md, st);
+            convert<float>(O.W, (float*)a.W + q0, s->qoff[c0 + cn] - q0, st);
+            if (visc) convert<float>(O.VX, (float*)a.VX + c0 * nvx, cn * nvx, st);
+        }
     }
     int err_cell = big;
     SETUP_CHECK(cudaMemcpyAsync(&err_cell, O.err, 4, cudaMemcpyDeviceToHost, st));
     SETUP_CHECK(cudaStreamSynchronize(st));
-    if (old_stack < 8192) SETUP_CHECK(cudaDeviceSetLimit(cudaLimitStackSize, old_stack));
+    if (old_stack < kStack) SETUP_CHECK(cudaDeviceSetLimit(cudaLimitStackSize, old_stack));
     if (err_cell != big) {
         cudaFree(T);
         set_error("hfv_scheme_create: rank-deficient least-squares system at cell " + std::to_string(err_cell));
@@ -276,26 +306,42 @@ int build_operators(hfv_scheme* s, void* stream)
     }
     // per-precision copies of the small geometric arrays
     std::vector<double> nrm(m->fnorm.begin(), m->fnorm.end());
+    // viscous penalty (eq. viscous_jump): 1 / distance between the cell's and
+    // each face neighbour's centre (vertex means; the neighbour moved by its
+    // periodic shift), 0 on open boundaries
+    std::vector<double> linv(visc ? nc * 6 : 0, 0.0);
+    for (int64_t c = 0; visc && c < nc; ++c)
+        for (int f = 0; f < type_nfaces(m->type[c]); ++f) {
+            const int32_t j = m->nbr[c * kMaxFaces + f];
+            if (j < 0) continue;
+            double l2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double dx = m->vmean[3 * j + k] + m->nshift[(c * kMaxFaces + f) * 3 + k] * m->period[k] -
+                                  m->vmean[3 * c + k];
+                l2 += dx * dx;
+            }
+            linv[c * 6 + f] = 1.0 / std::sqrt(l2);
+        }
     double* h64 = nullptr;
-    SETUP_CHECK(cudaMalloc(&h64, al(nc * 8) * 2 + al(nc * 18 * 8)));
+    SETUP_CHECK(cudaMalloc(&h64, al(nc * 8) * 2 + al(nc * 18 * 8) + al(linv.size() * 8)));
     double* d_ivol = h64;
     double* d_thr = (double*)((char*)h64 + al(nc * 8));
     double* d_nrm = (double*)((char*)h64 + 2 * al(nc * 8));
+    double* d_linv = (double*)((char*)h64 + 2 * al(nc * 8) + al(nc * 18 * 8));
+    if (visc) SETUP_CHECK(cudaMemcpyAsync(d_linv, linv.data(), nc * 6 * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(d_ivol, ivol.data(), nc * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(d_thr, thr.data(), nc * 8, cudaMemcpyHostToDevice, st));
     SETUP_CHECK(cudaMemcpyAsync(d_nrm, nrm.data(), nc * 18 * 8, cudaMemcpyHostToDevice, st));
     if (f32) {
-        convert<float>(O.L, a.L, lt, st); convert<float>(O.P, a.P, nc * N * M, st);
-        convert<float>(O.Phil, a.Phil, qt * d, st); convert<float>(O.OI, a.OI, nc * NOI, st);
-        convert<float>(O.D, a.D, nc * 6 * d * Md, st); convert<float>(O.G, a.G, nc * d * Md, st);
-        convert<float>(O.W, a.W, qt, st);
         convert<float>(d_ivol, a.ivol, nc, st); convert<float>(d_thr, a.dxthr, nc, st); convert<float>(d_nrm, a.nrm, nc * 18, st);
         convert<float>(a.area, a.areaT, nc * 6, st);
+        if (visc) convert<float>(d_linv, a.LINV, nc * 6, st);
     } else {
         SETUP_CHECK(cudaMemcpyAsync(a.ivol, d_ivol, nc * 8, cudaMemcpyDeviceToDevice, st));
         SETUP_CHECK(cudaMemcpyAsync(a.dxthr, d_thr, nc * 8, cudaMemcpyDeviceToDevice, st));
         SETUP_CHECK(cudaMemcpyAsync(a.nrm, d_nrm, nc * 18 * 8, cudaMemcpyDeviceToDevice, st));
         SETUP_CHECK(cudaMemcpyAsync(a.areaT, a.area, nc * 6 * 8, cudaMemcpyDeviceToDevice, st));
+        if (visc) SETUP_CHECK(cudaMemcpyAsync(a.LINV, d_linv, nc * 6 * 8, cudaMemcpyDeviceToDevice, st));
     }
     SETUP_CHECK(cudaGetLastError());
     SETUP_CHECK(cudaStreamSynchronize(st));

@@ -33,10 +33,10 @@
 
 namespace hfv {
 
-constexpr int kNmax = 34;   // K(4, 3) - 1
-constexpr int kMmax = 70;   // 2 K(4, 3)
+constexpr int kNmax = 55;   // K(5, 3) - 1 (hexahedra at order 6)
+constexpr int kMmax = 112;  // 2 K(5, 3)
 constexpr int kGmax = 8;    // Gauss points per direction
-constexpr int kMomMax = 165; // moments of total degree <= 8 in 3D: K(8, 3)
+constexpr int kMomMax = 286; // moments of total degree <= 10 in 3D: K(10, 3)
 
 struct SetupParams {
     const double* xyz;       // [nn][3]
@@ -68,7 +68,11 @@ struct SetupOut {
     double* D;      // [nc][6][d][Md]
     double* G;      // [nc][d][Md]
     double* W;      // [qoff]
+    double* VX;     // [nc][d + d d] mean of xi, then J^-1 (viscous terms; null otherwise)
     int* err;       // first failing cell + 1 (0 = none)
+    // the arrays may hold a chunk of cells only: cell c is written at c - cbase,
+    // its face points at qoff[c] - qbase, its L block at loff[c] - lbase
+    int64_t cbase = 0, qbase = 0, lbase = 0;
 };
 
 // position of L_qm inside a cell's block of Q rows and M columns: column
@@ -364,6 +368,14 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     const double V0 = mom[0];
     double mean0[kNmax];
     for (int k = 0; k < N; ++k) mean0[k] = mom[moment_index(d, S.ex[k][0], S.ex[k][1], S.ex[k][2])] / V0;
+    if (O.VX) {
+        // the degree-1 monomials come first (xi, eta[, zeta]): their means,
+        // then the reference map, for gradients at the face points
+        double* vx = &O.VX[(c - O.cbase) * (int64_t)(d + d * d)];
+        for (int k = 0; k < d; ++k) vx[k] = mean0[k];
+        for (int b = 0; b < d; ++b)
+            for (int j = 0; j < d; ++j) vx[d + b * d + j] = Ji[b][j];
+    }
 
     // 3. A_mk over the stencil cells; reference volumes kept in Vr
     double Vr[kMmax], Alin[kMmax][3];
@@ -385,14 +397,14 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
     double diag[kNmax], beta[kNmax], x[kNmax], y[kMmax];
     auto atA = [&](int m, int k) -> double& { return Wk.A(m, k, N); };
     if (!householder(atA, M, N, diag, beta)) return false;
-    double* P = &O.P[c * (int64_t)N * M];
+    double* P = &O.P[(c - O.cbase) * (int64_t)N * M];
     for (int j = 0; j < M; ++j) {
         pinv_column(atA, M, N, diag, beta, j, x, y);
         for (int k = 0; k < N; ++k) P[k * M + j] = x[k] * Vr[j];
     }
 
     // 5. face points: basis values, L = Phi P, Phi_lin and weights
-    double* L = &O.L[S.loff[c]];
+    double* L = &O.L[S.loff[c] - O.lbase];
     for (int f = 0; f < nf; ++f) {
         const int32_t* fv = &S.fvtx[(c * 6 + f) * 4];
         const int8_t* k = &S.fk[(c * 6 + f) * 3];
@@ -434,14 +446,14 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
                 for (int kk = 0; kk < N; ++kk) s += phi[kk] * P[kk * M + m];
                 L[l_index(q, m, nf * S.nfp, M, S.lcw)] = s;   // block padded to 16 bytes
             }
-            for (int kk = 0; kk < d; ++kk) O.Phil[(q0 + q) * d + kk] = phi[kk];
-            O.W[q0 + q] = wgt;
+            for (int kk = 0; kk < d; ++kk) O.Phil[(q0 - O.qbase + q) * d + kk] = phi[kk];
+            O.W[q0 - O.qbase + q] = wgt;
         }
     }
 
     // 6. OI from the moments: D^beta psi_k = coef * monomial
     {
-        double* OI = &O.OI[c * (int64_t)(N * (N + 1) / 2)];
+        double* OI = &O.OI[(c - O.cbase) * (int64_t)(N * (N + 1) / 2)];
         for (int k = 0; k < N; ++k)
             for (int l = k; l < N; ++l) {
                 double s = 0.0;
@@ -477,7 +489,7 @@ HD inline bool setup_cell(const SetupParams& S, const SetupOut& O, const SetupWo
             for (int k = 0; k < d; ++k) Ad[b * 3 + k] = Alin[muscl ? b : idx[b]][k];
         auto atd = [&](int m, int k) -> double& { return Ad[m * 3 + k]; };
         if (!householder(atd, cnt, d, dg, bt)) return false;
-        double* out = muscl ? &O.G[c * (int64_t)d * Md] : &O.D[((c * 6 + f) * (int64_t)d) * Md];
+        double* out = muscl ? &O.G[(c - O.cbase) * (int64_t)d * Md] : &O.D[(((c - O.cbase) * 6 + f) * (int64_t)d) * Md];
         for (int b = 0; b < Md; ++b) {
             if (b < cnt) {
                 pinv_column(atd, cnt, d, dg, bt, b, xx, yy);

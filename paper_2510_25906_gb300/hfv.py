@@ -22,7 +22,7 @@ HFV_HYBRID, HFV_PURE_LINEAR, HFV_PURE_CWENOZ, HFV_PURE_MUSCL = 0, 1, 2, 3
 HFV_FP64, HFV_FP32 = 0, 1
 HFV_CLASS_LINEAR, HFV_CLASS_CWENOZ, HFV_CLASS_MUSCL, HFV_CLASS_FIRST = 0, 1, 2, 3
 
-KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux", "rk", "dt", "cvt"]
+KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux", "rk", "dt", "cvt", "grad"]
 FLUX = {"rusanov": HFV_RUSANOV, "hllc": HFV_HLLC, "hll": HFV_HLL}
 SCHEME = {"hybrid": HFV_HYBRID, "linear": HFV_PURE_LINEAR, "cweno": HFV_PURE_CWENOZ, "muscl": HFV_PURE_MUSCL}
 PRECISION = {"fp64": HFV_FP64, "fp32": HFV_FP32}
@@ -49,7 +49,9 @@ class hfv_scheme_params(C.Structure):
                 ("beta_m", C.c_double), ("alpha_w", C.c_double), ("beta_w", C.c_double), ("kappa", C.c_double),
                 ("n_exp", C.c_double), ("lambda1_prime", C.c_double), ("cweno_eps", C.c_double),
                 ("cweno_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
-                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double)]
+                ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double),
+                ("mu0", C.c_double), ("t0", C.c_double), ("sutherland_s", C.c_double), ("prandtl", C.c_double),
+                ("visc_alpha", C.c_double)]
 
 
 _lib = None

@@ -56,6 +56,12 @@ def _case(name):
     if name == "quadrant_r4":
         m = I.mixed_tri_quad_mesh(24, seed=2)
         return m, I.quadrant_state(m), dict(order=5, flux="hllc"), 2
+    if name == "quadrant_r5":
+        m = I.mixed_tri_quad_mesh(24, seed=2)
+        return m, I.quadrant_state(m), dict(order=6, flux="hllc"), 2
+    if name == "periodic_r6_hll":
+        m = I.mixed_tri_quad_mesh(22, seed=11, periodic=True)
+        return m, I.quadrant_state(m), dict(order=7, flux="hll"), 1
     if name == "quadrant_r3_hll":
         m = I.mixed_tri_quad_mesh(20, seed=11, periodic=True)
         return m, I.quadrant_state(m), dict(order=4, flux="hll"), 1
@@ -70,6 +76,16 @@ def _case(name):
         x = m.vertex_means()[:, 1]
         U[0] *= np.where(x < 0.5, 1.0, 0.7)
         return m, U, dict(order=3, flux="hllc"), 0
+    if name == "hex_r4_open":
+        m = I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.1, seed=5)
+        U = I.turbulence_state(I.structured_hex_mesh(7, 1.0, periodic=True), seed=5)
+        x = m.vertex_means()[:, 1]
+        U[0] *= np.where(x < 0.5, 1.0, 0.7)
+        return m, U, dict(order=5, flux="hllc"), 0
+    if name == "hex_r5":
+        # the paper's 128^3 hexahedra run at order 6 (Sec. 3.6)
+        m = I.structured_hex_mesh(9, 2 * math.pi, periodic=True)
+        return m, _hex_contact_state(m), dict(order=6, flux="hllc", kappa=0.1), 0
     if name == "tet_r2_open":
         m = I.structured_tet_mesh(5, 1.0, periodic=False, jitter=0.1, seed=6)
         return m, _tet_state(m), dict(order=3, flux="hllc"), 0
@@ -97,7 +113,7 @@ def _tet_state(m):
     return np.stack([rho, rho * vel[0], rho * vel[1], rho * vel[2], E])
 
 
-CASES = ["wave_tri32", "quadrant_r2", "quadrant_r4", "quadrant_r3_hll", "hex_r3", "hex_r2_open", "tet_r2_open",
+CASES = ["wave_tri32", "quadrant_r2", "quadrant_r4", "quadrant_r5", "periodic_r6_hll", "quadrant_r3_hll", "hex_r3", "hex_r2_open", "hex_r4_open", "hex_r5", "tet_r2_open",
          "tet_r1_periodic", "mixed3d_r2", "mixed3d_r1_hll"]
 _cache = {}
 
