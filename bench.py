@@ -462,7 +462,7 @@ def turbulence_variants(H, I, torch, dev, args, peaks):
     cells, cfl, steps = mesh.n_cells, d["cfl"], args.turbulence_steps
     out = {"workload": f"3D decaying turbulence, periodic [0,2pi]^3, {cells} hexahedra, order 4, HLLC, SSP-RK3",
            "pre_steps": args.turbulence_pre, "steps": steps}
-    g = H.Scheme(gm, order=4, flux="hllc", scheme="hybrid", precision="fp32")
+    g = H.Scheme(gm, order=4, flux="hllc", scheme="hybrid", precision="fp32", step_chain=1)
     U = torch.tensor(U0, device=dev)
     for _ in range(args.turbulence_pre):
         g.step(U, cfl=cfl)
@@ -475,7 +475,7 @@ def turbulence_variants(H, I, torch, dev, args, peaks):
     for scheme in ("hybrid", "cweno"):
         for prec in ("fp32", "fp64"):
             gv = g if (scheme, prec) == ("hybrid", "fp32") else H.Scheme(gm, order=4, flux="hllc", scheme=scheme,
-                                                                           precision=prec)
+                                                                           precision=prec, step_chain=1)
             ms, _, _, Ufin = time_steps(H, torch, gv, Upre, steps, 3, cfl, dev)
             value = 3.0 * cells * steps / (ms * 1e-3)
             a0 = queue_fractions(torch, gv, torch.tensor(Upre, device=dev), dev)
@@ -491,11 +491,11 @@ def turbulence_variants(H, I, torch, dev, args, peaks):
                 entry["e2e"] = {"value": 3.0 * cells * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                                 "d2h_bytes_per_step": nbytes, "api": "hfv_advance_host"}
                 if args.cpu_baseline:
-                    smp = _oracle_block(mesh, 8)
-                    v, ns, dt = _oracle_steps(mesh, Upre, 4, "hllc", "hybrid", 1, 1, sample=smp)
+                    smp = _oracle_block(mesh, 10)
+                    v, ns, dt = _oracle_steps(mesh, Upre, 4, "hllc", "hybrid", 50, 1, sample=smp)
                     entry["cpu_baseline"] = {
                         "value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
-                        "sample": f"{ns} cells (an 8^3 block at the domain centre) of the {cells}-cell mesh, 1 step x "
+                        "sample": f"{ns} cells (a 10^3 block at the domain centre) of the {cells}-cell mesh, 50 steps x "
                                   f"3 residual evaluations, FP64, operators built before timing ({dt:.1f} s timed)"}
             out[f"{scheme}_{prec}"] = entry
             if gv is not g:
@@ -505,7 +505,7 @@ def turbulence_variants(H, I, torch, dev, args, peaks):
     # Taylor-Green vortex at Re = 1600): mu0 = 1/1600 at the reference
     # temperature T0 = p/rho = 1/gamma of this field, hybrid, FP32
     gv = H.Scheme(gm, order=4, flux="hllc", scheme="hybrid", precision="fp32", mu0=1.0 / 1600.0, t0=1.0 / 1.4,
-                  prandtl=0.71)
+                  prandtl=0.71, step_chain=1)
     ms, _, _, Ufin = time_steps(H, torch, gv, Upre, steps, 3, cfl, dev)
     value = 3.0 * cells * steps / (ms * 1e-3)
     a0 = queue_fractions(torch, gv, torch.tensor(Upre, device=dev), dev)
@@ -530,23 +530,26 @@ def order6_variants(H, torch, dev, mesh, gm, Upre, cfl, args, peaks):
     54 face points per cell), FP32, HLLC, from the same pre-advanced field;
     `order6_steps` SSP-RK3 steps each, L2 flushed between steps."""
     out = {"workload": f"{mesh.n_cells} hexahedra, order 6, HLLC, SSP-RK3, FP32", "steps": args.order6_steps}
+    t0 = time.perf_counter()
+    g = H.Scheme(gm, order=6, flux="hllc", scheme="hybrid", precision="fp32", step_chain=1)
+    out["setup_s"] = time.perf_counter() - t0
+    out["setup_ms_stencils_operators"] = g.setup_ms()
+    out["device_bytes"] = g.device_bytes()
     for scheme in ("hybrid", "cweno"):
-        t0 = time.perf_counter()
-        g = H.Scheme(gm, order=6, flux="hllc", scheme=scheme, precision="fp32")
-        setup_s = time.perf_counter() - t0
+        g.set_kind(scheme)      # the same stencils and operators
         ms, _, _, Ufin = time_steps(H, torch, g, Upre, args.order6_steps, 3, cfl, dev)
         value = 3.0 * mesh.n_cells * args.order6_steps / (ms * 1e-3)
         a0 = queue_fractions(torch, g, torch.tensor(Upre, device=dev), dev)
         a1 = queue_fractions(torch, g, Ufin, dev)
-        out[scheme] = {"value": value, "ms_per_step": ms / args.order6_steps, "setup_s": setup_s,
-                       "device_bytes": g.device_bytes(),
+        out[scheme] = {"value": value, "ms_per_step": ms / args.order6_steps,
                        "path": path_roofline(mesh, g, value, (0.5 * (a0[0] + a1[0]), 0.5 * (a0[1] + a1[1])), peaks)}
         if scheme == "hybrid":
             cls = torch.empty(mesh.n_cells, dtype=torch.uint8, device=dev)
             g.residual(torch.tensor(Upre, device=dev).float().contiguous(), class_out=cls)
             out["classes_at_start"] = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
-        del g, Ufin
-        torch.cuda.empty_cache()
+        del Ufin
+    del g
+    torch.cuda.empty_cache()
     out["speedup_hybrid_vs_cweno"] = out["cweno"]["ms_per_step"] and out["cweno"]["ms_per_step"] / out["hybrid"]["ms_per_step"]
     return out
 
@@ -568,7 +571,7 @@ def mixed_variants(H, I, torch, dev, args):
                        f"{counts[4]} hexahedra; order 3, HLLC, SSP-RK3, Mach 2 shock and density pulse",
            "cells": int(cells), "steps": steps, "mesh_s": round(time.perf_counter() - t0, 2)}
     for scheme, prec in (("hybrid", "fp32"), ("cweno", "fp32"), ("hybrid", "fp64")):
-        g = H.Scheme(gm, order=3, flux="hllc", scheme=scheme, precision=prec)
+        g = H.Scheme(gm, order=3, flux="hllc", scheme=scheme, precision=prec, step_chain=1)
         ms, _, _, _ = time_steps(H, torch, g, U0, steps, 2, 0.5, dev)
         entry = {"value": 3.0 * cells * steps / (ms * 1e-3), "ms_per_step": ms / steps}
         if (scheme, prec) == ("hybrid", "fp32"):
@@ -628,7 +631,7 @@ def batched_variants(H, I, torch, dev, args):
     schemes, states = [], []
     for order, ks in sorted(groups.items()):
         gm = H.Mesh.batch([P[k]["mesh"] for k in ks])
-        schemes.append(H.Scheme(gm, order=order, flux="hllc", precision="fp32"))
+        schemes.append(H.Scheme(gm, order=order, flux="hllc", precision="fp32", step_chain=1))
         states.append(torch.tensor(np.concatenate([P[k]["U"] for k in ks], axis=1), device=dev))
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -649,7 +652,7 @@ def batched_variants(H, I, torch, dev, args):
     t0 = time.perf_counter()
     single = []
     for p in P:
-        g = H.Scheme(H.Mesh(p["mesh"]), order=p["order"], flux="hllc", precision="fp32")
+        g = H.Scheme(H.Mesh(p["mesh"]), order=p["order"], flux="hllc", precision="fp32", step_chain=1)
         single.append((g, torch.tensor(p["U"], device=dev)))
     t_setup1 = time.perf_counter() - t0
 
@@ -799,7 +802,7 @@ def main():
     gm = H.Mesh(mesh)
 
     def make(order, scheme, precision):
-        return H.Scheme(gm, order=order, flux=dflt["flux"], scheme=scheme, precision=precision)
+        return H.Scheme(gm, order=order, flux=dflt["flux"], scheme=scheme, precision=precision, step_chain=1)
 
     g = make(args.order, args.scheme, args.precision)
     peak, peak_kind = _peaks()
@@ -873,16 +876,16 @@ def main():
 
     cpu = None
     if args.cpu_baseline and rank == 0 and world == 1:
-        v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 10, 1, band=0.2)
+        v, ns, dt = _oracle_steps(mesh, U0, args.order, dflt["flux"], args.scheme, 50, 1, band=0.2)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": _cpu_model(),
-               "sample": f"{ns} cells (|y - 0.5| < 0.2) of the {cells}-cell mesh, 10 steps x 3 residual "
+               "sample": f"{ns} cells (|y - 0.5| < 0.2) of the {cells}-cell mesh, 50 steps x 3 residual "
                          f"evaluations, FP64, operators built before timing ({dt:.1f} s timed)"}
         procs = min(16, os.cpu_count() or 1)
         if procs > 1:
-            vp, nsp, dtp = _oracle_steps_parallel(mesh, U0, args.order, dflt["flux"], args.scheme, 10, 0.45, procs)
+            vp, nsp, dtp = _oracle_steps_parallel(mesh, U0, args.order, dflt["flux"], args.scheme, 200, 0.45, procs)
             cpu["all_cores"] = {"value": vp, "unit": UNIT, "cores": procs, "kind": "oracle",
                                 "sample": f"{nsp} cells (|y - 0.5| < 0.45) split into {procs} contiguous chunks, one "
-                                          f"spawned process each, 10 steps x 3 residual evaluations, FP64 "
+                                          f"spawned process each, 200 steps x 3 residual evaluations, FP64 "
                                           f"({dtp:.1f} s for the slowest process)"}
 
     if rank == 0:

@@ -145,6 +145,17 @@ typedef struct {
      *   Defaults: mu0 = 0 (Euler), t0 = 1, sutherland_s = 110.4 / 288.15,
      *   prandtl = 0.72, visc_alpha = 4/3 */
     double mu0, t0, sutherland_s, prandtl, visc_alpha;
+    /* chained steps (hfv_step with HFV_SSPRK3; default 0 = off).  1: the last
+     * stage of every step also writes the next step's FP32/FP64 stage copy of
+     * the state and, in CFL mode, reduces the next step's time step, so that a
+     * following hfv_step on the same U pointer, in the same mode (CFL or fixed
+     * dt) and with the same cfl, skips its stage-in copy and time-step
+     * reduction.  The caller promises that U is not written between such calls;
+     * calls that overwrite the scheme's stage copy (hfv_residual,
+     * hfv_compute_dt, hfv_autotune, hfv_residual_vjp, hfv_advance_host's
+     * upload) end the chain and the next step starts afresh.  Results are the
+     * same bits as with 0. */
+    int step_chain;
 } hfv_scheme_params;
 
 /* Fill *p with the defaults listed above.  Never fails for non-NULL p. */
@@ -267,6 +278,28 @@ HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt
 HFV_API int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g,
                              void* stream);
 
+/* One SSP-RK3 step that records (forced = 0) or imposes (forced != 0) the
+ * classes of its three stages: U (device FP64 [nv][n_cells], the step's
+ * start) -> U_out (device, another buffer), with U1 = U + dt R(U),
+ * U2 = 3/4 U + 1/4 (U1 + dt R(U1)), U_out = 1/3 U + 2/3 (U2 + dt R(U2));
+ * cls device uint8 [3][n_cells], stage k's final classes (as hfv_residual's
+ * class_out).  The forward sweep of a checkpointed adjoint: the state and
+ * cls of every step are its checkpoint.  Same schemes as hfv_residual_vjp;
+ * uses the adjoint's scratch.  async.  Errors: HFV_ERR_ARG, HFV_ERR_OOM. */
+HFV_API int hfv_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t* cls, int forced, double* U_out,
+                             void* stream);
+
+/* The adjoint of one SSP-RK3 step with its stages' classes frozen (the
+ * differentiation of hfv_step_classes; the paper states no adjoint): lam
+ * (device FP64 [nv][n_cells]) holds dJ/dU_{n+1} on entry and dJ/dU_n on
+ * return, for the step from U with step size dt and stage classes cls
+ * ([3][n_cells], as recorded by hfv_step_classes).  The stage states are
+ * recomputed from U; with J_k = dR/dU at stage k (its classes frozen):
+ *   l2 = 2/3 lam + dt J_2^T (2/3 lam),   l1 = 1/4 l2 + dt J_1^T (1/4 l2),
+ *   lam <- 1/3 lam + 3/4 l2 + l1 + dt J_0^T l1.
+ * async.  Errors: HFV_ERR_ARG, HFV_ERR_OOM, HFV_ERR_CUDA. */
+HFV_API int hfv_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream);
+
 /* Autotuner of the residual's launch shape for this scheme and state: the
  * persistent candidate kernel's resident CTAs per SM, and the CWENOZ / MUSCL
  * kernel's blocks per SM and the share of them given to the CWENOZ queue.
@@ -305,6 +338,28 @@ HFV_API int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues
  * else HFV_ERR_NONPHYSICAL when bit0 is set, else HFV_OK. */
 HFV_API int hfv_status(hfv_scheme* s, int* flags, int reset);
 
+/* Testing aid for the bounded waits of the candidate kernel (the paper has no
+ * counterpart).  consumer_wait_ns in 1..2e9 replaces the 2 s limit of its
+ * consumer warps' waits for the bulk copies (0: back to 2 s);
+ * withhold_copies != 0 makes its producer warp issue no copy at all, so that
+ * the consumers' first wait runs out: every later residual on the scheme then
+ * skips its candidates, records bit 2 for hfv_status (HFV_ERR_TIMEOUT) and
+ * returns -- its R is meaningless -- with no copy in flight and the context
+ * intact.  (0, 0) restores normal operation.  Errors: HFV_ERR_ARG. */
+HFV_API int hfv_debug_wait(hfv_scheme* s, int64_t consumer_wait_ns, int withhold_copies);
+
+/* Wall time of hfv_scheme_create's two phases (host output, 2 doubles, ms):
+ * ms[0] the stencils (host threads), ms[1] the operators (device, FP64). */
+HFV_API int hfv_scheme_setup_ms(const hfv_scheme* s, double* ms);
+
+/* Switch an existing scheme between the detector-driven hybrid and the pure
+ * schemes (HFV_HYBRID, HFV_PURE_LINEAR, HFV_PURE_CWENOZ, HFV_PURE_MUSCL): the
+ * stencils and operators do not depend on this choice (Sec. 2.5 selects among
+ * reconstructions built on the same stencils), so a comparison of hybrid and
+ * pure CWENOZ needs one setup.  Takes effect at the next residual; ends a
+ * step chain.  Errors: HFV_ERR_ARG. */
+HFV_API int hfv_scheme_set_kind(hfv_scheme* s, int scheme);
+
 /* Device bytes held by the scheme (operators + scratch). */
 HFV_API int hfv_scheme_device_bytes(const hfv_scheme* s, int64_t* bytes);
 
@@ -334,6 +389,19 @@ HFV_API int hfv_launch_count(int64_t* count);
  * timed launches (CUDA events on `stream`) is written to *flops_per_s as
  * 2 x FMAs / second.  sync.  Errors: HFV_ERR_ARG, HFV_ERR_CUDA. */
 HFV_API int hfv_fma_rate(int kind, double target_ms, double* flops_per_s, void* stream);
+
+/* The FP32 kernels' conversions between FP32 and FP64 (the Runge-Kutta
+ * update's increment and new state, the stage copy of the FP64 state, the
+ * time step's FP64 bits) applied to an array, for checking them against the
+ * hardware conversion (instrumentation; the paper has no counterpart).  They
+ * use integer instructions on the IEEE 754 bit layouts, because the
+ * conversion instruction occupies this GPU's FP64 pipe.  to_f32 = 1: in is
+ * device double [n], out device float [n], rounded to nearest, ties to even;
+ * to_f32 = 0: in device float [n], out device double [n], exact.  Every
+ * result equals the conversion instruction's, NaN payloads included.  async
+ * on `stream`.  Errors: HFV_ERR_ARG (bad to_f32, n < 0, null buffer with
+ * n > 0), HFV_ERR_CUDA. */
+HFV_API int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream);
 
 /* Class-queue compaction that allocates nothing (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device

@@ -77,29 +77,21 @@ def rk3_gradient(sch, U0, steps: int, dJdU, cfl: float = 0.5, dt: float | None =
     dJdU(U_N) -> (J, dJ/dU_N) gives the objective and its gradient.  dt:
     fixed step, or None for each step's CFL step from its starting state.
     Returns (J, dJ/dU0, U_N, dts)."""
-    torch = _torch()
     U = U0.detach().clone().contiguous()
     ckpt = []
     dts = []
     for _ in range(steps):
         h = float(dt) if dt is not None else float(sch.compute_dt(U, cfl)[0].item())
-        U1, U2, U3, cls = _stages(sch, U, h)
+        # hfv_step_classes: the step, with its stages' classes as the checkpoint
+        U3, cls = sch.step_classes(U, h)
         ckpt.append((U, cls, h))
         dts.append(h)
-        U = U3.contiguous()
+        U = U3
     J, lam = dJdU(U)
     lam = lam.contiguous()
     for U, cls, h in reversed(ckpt):
-        U1, U2, _, _ = _stages(sch, U, h, classes=cls)
-        # U3 = U/3 + 2/3 (U2 + h R(U2));  U2 = 3/4 U + 1/4 (U1 + h R(U1));  U1 = U + h R(U)
-        l2 = (2.0 / 3.0) * lam
-        lU = lam / 3.0
-        l2 = l2 + h * sch.residual_vjp(U2.contiguous(), cls[2], ((2.0 / 3.0) * lam).contiguous())
-        l1 = 0.25 * l2 + h * sch.residual_vjp(U1.contiguous(), cls[1], (0.25 * l2).contiguous())
-        lU = lU + 0.75 * l2
-        lU = lU + l1 + h * sch.residual_vjp(U.contiguous(), cls[0], l1.contiguous())
-        lam = lU.contiguous()
-    return J, lam, U3 if steps else U0, dts
+        sch.step_vjp(U, cls, h, lam)       # the transposed stages, in the library
+    return J, lam, U, dts
 
 
 def density_square_integral(vol):

@@ -481,9 +481,9 @@ int adjoint_prepare(hfv_scheme* s, cudaStream_t st)
     }
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t b_mu = al(qtot * nv * 8), b_a = al(nc * M * nv * 8), b_s0 = al(nc * nv * 8), b_ptr = al((nc + 1) * 8),
-                 b_idx = al(nc * M * 4);
+                 b_idx = al(nc * M * 4), b_x = al(nc * nv * 8);
     void* base = nullptr;
-    if (cudaMalloc(&base, b_mu + b_a + b_s0 + b_ptr + b_idx) != cudaSuccess) {
+    if (cudaMalloc(&base, b_mu + b_a + b_s0 + b_ptr + b_idx + 5 * b_x) != cudaSuccess) {
         set_error("hfv_residual_vjp: out of device memory for the adjoint scratch");
         return HFV_ERR_OOM;
     }
@@ -494,6 +494,12 @@ int adjoint_prepare(hfv_scheme* s, cudaStream_t st)
     s->adj.S0 = (double*)(b + b_mu + b_a);
     s->adj.inv_ptr = (int64_t*)(b + b_mu + b_a + b_s0);
     s->adj.inv_idx = (int32_t*)(b + b_mu + b_a + b_s0 + b_ptr);
+    char* x = b + b_mu + b_a + b_s0 + b_ptr + b_idx;
+    s->adj.X1 = (double*)x;
+    s->adj.X2 = (double*)(x + b_x);
+    s->adj.T = (double*)(x + 2 * b_x);
+    s->adj.G = (double*)(x + 3 * b_x);
+    s->adj.L2 = (double*)(x + 4 * b_x);
     if (cudaMemsetAsync(base, 0, b_mu + b_a + b_s0, st) != cudaSuccess ||
         cudaMemcpyAsync(s->adj.inv_ptr, ptr.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(s->adj.inv_idx, idx.data(), nc * M * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -541,6 +547,91 @@ int launch_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double*
     }
     set_error("hfv_residual_vjp: order not built");
     return HFV_ERR_ARG;
+}
+
+// out = a U0 + b (Us + dt R)  (a = 0: U0 unread)
+__global__ void __launch_bounds__(256) k_stage_combine(int64_t n, const double* __restrict__ U0,
+                                                      const double* __restrict__ Us, const double* __restrict__ R,
+                                                      double a, double b, double dt, double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = b * (Us[i] + dt * R[i]);
+    if (a != 0.0) x += a * U0[i];
+    out[i] = x;
+}
+
+// out = cx x + cy y + cz z + cg g  (null terms skipped)
+__global__ void __launch_bounds__(256) k_lincomb(int64_t n, double* __restrict__ out, double cx,
+                                                const double* __restrict__ x, double cy, const double* __restrict__ y,
+                                                double cz, const double* __restrict__ z, double cg,
+                                                const double* __restrict__ g)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = cx * x[i];
+    if (y) v += cy * y[i];
+    if (z) v += cz * z[i];
+    if (g) v += cg * g[i];
+    out[i] = v;
+}
+
+// One SSP-RK3 step, Shu-Osher form, from the residual with its classes
+// output (forced = 0) or given (forced != 0): cls [3][nc], one per stage.
+int launch_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t* cls, int forced, double* out, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = adjoint_prepare(s, st);
+    if (rc != HFV_OK) return rc;
+    const int64_t nc = s->mesh->nc, n = (int64_t)s->nv * nc;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    double* R = (double*)s->a.Rs;
+    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, B[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* Us = U;
+    double* outs[3] = {s->adj.X1, s->adj.X2, out};
+    for (int k = 0; k < 3; ++k) {
+        uint8_t* c = cls + k * nc;
+        rc = forced ? launch_residual(s, Us, R, c, nullptr, stream) : launch_residual(s, Us, R, nullptr, c, stream);
+        if (rc != HFV_OK) return rc;
+        note_launch();
+        k_stage_combine<<<g, 256, 0, st>>>(n, U, Us, R, A[k], B[k], dt, outs[k]);
+        Us = outs[k];
+    }
+    return cudaGetLastError() == cudaSuccess ? HFV_OK : HFV_ERR_CUDA;
+}
+
+// The adjoint of one SSP-RK3 step with the stages' classes frozen: lam holds
+// dJ/dU_{n+1} on entry and dJ/dU_n on return.  With U1 = U + h R(U),
+// U2 = 3/4 U + 1/4 (U1 + h R(U1)), U3 = 1/3 U + 2/3 (U2 + h R(U2)):
+//   l2 = 2/3 lam + h J2^T (2/3 lam)
+//   l1 = 1/4 l2 + h J1^T (1/4 l2)
+//   lam <- 1/3 lam + 3/4 l2 + l1 + h J0^T l1
+// (J_k = dR/dU at stage k with its classes).
+int launch_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nc = s->mesh->nc, n = (int64_t)s->nv * nc;
+    int rc = launch_step_classes(s, U, dt, const_cast<uint8_t*>(cls), 1, s->adj.L2, stream);   // U1, U2 (U3 unused)
+    if (rc != HFV_OK) return rc;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    hfv_adjoint_arrays& a = s->adj;
+    // stage 3
+    note_launch();
+    k_lincomb<<<g, 256, 0, st>>>(n, a.T, 2.0 / 3.0, lam, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr);
+    if ((rc = launch_vjp(s, a.X2, cls + 2 * nc, a.T, a.G, stream)) != HFV_OK) return rc;
+    note_launch();
+    k_lincomb<<<g, 256, 0, st>>>(n, a.L2, 1.0, a.T, dt, a.G, 0.0, nullptr, 0.0, nullptr);
+    // stage 2
+    note_launch();
+    k_lincomb<<<g, 256, 0, st>>>(n, a.T, 0.25, a.L2, 0.0, nullptr, 0.0, nullptr, 0.0, nullptr);
+    if ((rc = launch_vjp(s, a.X1, cls + nc, a.T, a.G, stream)) != HFV_OK) return rc;
+    note_launch();
+    k_lincomb<<<g, 256, 0, st>>>(n, a.T, 1.0, a.T, dt, a.G, 0.0, nullptr, 0.0, nullptr);   // T = l1
+    // stage 1
+    if ((rc = launch_vjp(s, U, cls, a.T, a.G, stream)) != HFV_OK) return rc;
+    note_launch();
+    k_lincomb<<<g, 256, 0, st>>>(n, lam, 1.0 / 3.0, lam, 0.75, a.L2, 1.0, a.T, dt, a.G);
+    return cudaGetLastError() == cudaSuccess ? HFV_OK : HFV_ERR_CUDA;
 }
 
 void adjoint_free(hfv_scheme* s)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <new>
 #include <string>
@@ -66,6 +67,7 @@ extern "C" int hfv_default_params(hfv_scheme_params* p)
     p->sutherland_s = 110.4 / 288.15;
     p->prandtl = 0.72;
     p->visc_alpha = 4.0 / 3.0;
+    p->step_chain = 0;
     return HFV_OK;
 }
 
@@ -109,7 +111,7 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
         (p->cweno_vars != HFV_CONSERVED && p->cweno_vars != HFV_CHARACTERISTIC) ||
         !(p->gamma > 1.0) || !(p->lambda1_prime > 1.0) || !(p->harten_theta > 0.0) || !(p->cweno_eps > 0.0) ||
         !(p->mu0 >= 0.0) || !(p->t0 > 0.0) || !(p->sutherland_s >= 0.0) || !(p->prandtl > 0.0) ||
-        !(p->visc_alpha >= 0.0)) {
+        !(p->visc_alpha >= 0.0) || (p->step_chain != 0 && p->step_chain != 1)) {
         set_error("hfv_scheme_create: parameter out of range");
         return HFV_ERR_ARG;
     }
@@ -123,13 +125,18 @@ extern "C" int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* p, voi
     s->mesh = mesh;
     s->p = *p;
     int rc;
+    const auto t0 = std::chrono::steady_clock::now();
     try {
         rc = build_stencils(s);
     } catch (const std::bad_alloc&) {
         rc = HFV_ERR_OOM;
         set_error("hfv_scheme_create: out of host memory");
     }
+    const auto t1 = std::chrono::steady_clock::now();
     if (rc == HFV_OK) rc = build_operators(s, stream);
+    const auto t2 = std::chrono::steady_clock::now();
+    s->setup_ms[0] = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    s->setup_ms[1] = std::chrono::duration<double, std::milli>(t2 - t1).count();
     if (rc == HFV_OK) {
         cudaStream_t side;
         cudaEvent_t e1, e2;
@@ -157,6 +164,22 @@ extern "C" int hfv_scheme_info(const hfv_scheme* s, int64_t* info)
     if (!s || !info) { set_error("hfv_scheme_info: NULL argument"); return HFV_ERR_ARG; }
     info[0] = s->N; info[1] = s->M; info[2] = s->Md; info[3] = s->nq; info[4] = s->nfp; info[5] = s->nv;
     info[6] = s->qtot; info[7] = s->p.precision;
+    return HFV_OK;
+}
+
+extern "C" int hfv_scheme_setup_ms(const hfv_scheme* s, double* ms)
+{
+    if (!s || !ms) { set_error("hfv_scheme_setup_ms: NULL argument"); return HFV_ERR_ARG; }
+    ms[0] = s->setup_ms[0];
+    ms[1] = s->setup_ms[1];
+    return HFV_OK;
+}
+
+extern "C" int hfv_scheme_set_kind(hfv_scheme* s, int scheme)
+{
+    if (!s || scheme < HFV_HYBRID || scheme > HFV_PURE_MUSCL) { set_error("hfv_scheme_set_kind: bad argument"); return HFV_ERR_ARG; }
+    s->p.scheme = scheme;
+    s->chain_ok = false;
     return HFV_OK;
 }
 
@@ -222,6 +245,30 @@ extern "C" int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* c
         return HFV_ERR_ARG;
     }
     return launch_vjp(s, U, cls, lam, g, stream);
+}
+
+static int vjp_scheme_ok(const hfv_scheme* s, const char* who)
+{
+    if (s->p.precision != HFV_FP64 || s->p.cweno_vars != HFV_CONSERVED || s->p.mu0 > 0.0) {
+        set_error(std::string(who) + ": FP64, conserved-variable, Euler (mu0 = 0) schemes only");
+        return HFV_ERR_ARG;
+    }
+    return HFV_OK;
+}
+
+extern "C" int hfv_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t* cls, int forced, double* U_out,
+                                void* stream)
+{
+    if (!s || !U || !cls || !U_out || !(dt > 0.0) || U == U_out) { set_error("hfv_step_classes: bad argument"); return HFV_ERR_ARG; }
+    int rc = vjp_scheme_ok(s, "hfv_step_classes");
+    return rc != HFV_OK ? rc : launch_step_classes(s, U, dt, cls, forced, U_out, stream);
+}
+
+extern "C" int hfv_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream)
+{
+    if (!s || !U || !cls || !lam || !(dt > 0.0) || U == lam) { set_error("hfv_step_vjp: bad argument"); return HFV_ERR_ARG; }
+    int rc = vjp_scheme_ok(s, "hfv_step_vjp");
+    return rc != HFV_OK ? rc : launch_step_vjp(s, U, cls, dt, lam, stream);
 }
 
 extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, int* shape)
@@ -339,6 +386,7 @@ extern "C" int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, doub
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)s->nv * s->mesh->nc * sizeof(double);
     double* work = s->a.Uio;   // device state owned by the scheme: no allocation here
+    s->chain_ok = false;       // new contents from the host: a chain starts afresh
     API_CUDA(cudaMemcpyAsync(work, U_host, bytes, cudaMemcpyHostToDevice, st));
     int rc = HFV_OK;
     for (int k = 0; k < n_steps && rc == HFV_OK; ++k) rc = launch_step(s, work, cfl, dt, stream);
@@ -355,6 +403,17 @@ extern "C" int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* que
     API_CUDA(cudaDeviceSynchronize());
     API_CUDA(cudaMemcpy(counts, s->a.counts, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (queues) API_CUDA(cudaMemcpy(queues, s->a.queue, 2 * s->mesh->nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return HFV_OK;
+}
+
+extern "C" int hfv_debug_wait(hfv_scheme* s, int64_t consumer_wait_ns, int withhold_copies)
+{
+    if (!s || consumer_wait_ns < 0 || consumer_wait_ns > 2000000000ll) {
+        set_error("hfv_debug_wait: NULL scheme or a limit outside 0..2e9 ns");
+        return HFV_ERR_ARG;
+    }
+    s->wait_ns = consumer_wait_ns > 0 ? (uint64_t)consumer_wait_ns : 2000000000ull;
+    s->withhold_copies = withhold_copies != 0;
     return HFV_OK;
 }
 

@@ -39,6 +39,52 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <class T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
+// FP32 <-> FP64 conversions in integer arithmetic on the IEEE 754 binary32 /
+// binary64 bit layouts, for the FP32 kernels: the conversion instructions
+// issue to the FP64 pipe, which on this GPU executes two lanes per clock per
+// SM (a warp's conversion holds it for 16 cycles), while these take a few
+// integer instructions.  Normal numbers and zeros take the integer path and
+// give exactly the conversion instruction's result (FP32 -> FP64 is exact;
+// FP64 -> FP32 rounds to nearest, ties to even); subnormal, out-of-range,
+// infinite and NaN operands fall back to the instruction.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        // sign | exponent rebiased 127 -> 1023 | the 23 fraction bits, the
+        // top 20 in the high word and the last 3 at the top of the low word
+        const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+        return __hiloint2double((int)hi, (int)(b << 29));
+    }
+    if ((b << 1) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)f;
+}
+__device__ __forceinline__ float f64_to_f32(double x)
+{
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e - 897u < 254u) {
+        // a normal FP32 exponent (1..254 after rebiasing): keep 23 of the 52
+        // fraction bits and round on the 29 dropped ones; a carry out of
+        // the fraction steps the exponent (to infinity past the largest float)
+        uint32_t r = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rest = lo & 0x1fffffffu;
+        r += (uint32_t)(rest > 0x10000000u) | ((uint32_t)(rest == 0x10000000u) & (r & 1u));
+        return __uint_as_float(r);
+    }
+    if (((hi << 1) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    return (float)x;
+}
+
+// an FP64 state value in the residual's precision T
+template <class T>
+__device__ __forceinline__ T to_t(double x)
+{
+    if constexpr (sizeof(T) == 4) return f64_to_f32(x);
+    else return x;
+}
+
 __device__ __forceinline__ float tpow(float x, float e) { return powf(x, e); }
 __device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
 

@@ -11,6 +11,8 @@
 namespace hfv {
 
 constexpr int kMaxFaces = 6;   // hexahedron
+constexpr int kDtSlots = 64;   // atomic slots per problem of the chained time-step minimum
+constexpr int kDtStride = 16;  // doubles between slots: each slot on its own 128-byte line
 constexpr int kMaxFaceVerts = 4;
 constexpr int kMaxOrder = 5;   // r <= 4
 
@@ -100,6 +102,7 @@ struct hfv_dev_arrays {
     double* U4;
     double* U5;
     double* dt;        // [nseg] time step per problem
+    double* dt_next;   // [nseg][kDtSlots] the next step's time step (chained steps; bits of positive doubles)
     int32_t* seg;      // [nc] problem of each cell (batched meshes; null for one problem)
     double* Uio;       // [nv][nc] device state of hfv_advance_host
     // viscous terms (mu0 > 0 only, else null)
@@ -132,6 +135,13 @@ struct hfv_adjoint_arrays {
     double* S0 = nullptr;       // [nc][nv] contributions to the cell itself
     int64_t* inv_ptr = nullptr; // [nc+1] inverse stencil map (CSR, ascending (c, m))
     int32_t* inv_idx = nullptr; // [nc*M] entries c * M + m
+    // [nv][nc] each: stage states, scaled adjoint, VJP result, stage adjoint
+    // (hfv_step_classes / hfv_step_vjp)
+    double* X1 = nullptr;
+    double* X2 = nullptr;
+    double* T = nullptr;
+    double* G = nullptr;
+    double* L2 = nullptr;
 };
 
 struct hfv_scheme {
@@ -154,6 +164,16 @@ struct hfv_scheme {
     int tune_nl_per_sm = 16;
     int tune_nl_cweno_pct = 75;
     int sms = 152, linear_per_sm_max = 1;   // filled at the first residual
+    // chained steps (step_chain): the stage copy UA and dt_next hold the step
+    // after the last hfv_step on chain_U (same mode and CFL number)
+    // candidate kernel's consumer wait limit and the copy-withholding switch
+    // of hfv_debug_wait
+    double setup_ms[2] = {0.0, 0.0};   // stencils (host), operators (device) of hfv_scheme_create
+    uint64_t wait_ns = 2000000000ull;
+    int withhold_copies = 0;
+    bool chain_ok = false, chain_fixed = false;
+    const double* chain_U = nullptr;
+    double chain_cfl = 0.0;
     // host copies kept for introspection
     std::vector<int32_t> sten;      // [nc][M]
     std::vector<int8_t> sshift;     // [nc][M][3]
@@ -178,5 +198,7 @@ int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced
 int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
 int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream);
 int launch_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g, void* stream);
+int launch_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t* cls, int forced, double* out, void* stream);
+int launch_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream);
 void adjoint_free(hfv_scheme* s);
 }  // namespace hfv

@@ -122,7 +122,9 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
 
     if (threadIdx.x >= S::CONSUMERS) {
         // ---------------- producer warp ----------------
-        if (threadIdx.x == S::CONSUMERS) {
+        // (with withhold_copies nothing is issued: the consumers' first wait
+        // runs out and the launch reports the timeout; no copy is in flight)
+        if (threadIdx.x == S::CONSUMERS && !p.withhold_copies) {
             int k = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     int64_t tile = blockIdx.x;
     bool alive = true;
     if (tile < ntiles) {
-        if (!__all_sync(0xffffffffu, mbar_wait(&full[0], 0))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&full[0], 0, p.wait_ns))) {
             if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
             alive = false;
         } else {
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) {
             const int s1 = (k + 1) % ST;
-            if (!__all_sync(0xffffffffu, mbar_wait(&full[s1], ((k + 1) / ST) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&full[s1], ((k + 1) / ST) & 1, p.wait_ns))) {
                 if ((threadIdx.x & 31) == 0) atomicOr(p.status, 4);
                 alive = false;
             } else {

@@ -81,11 +81,17 @@ struct KParams {
     int32_t* bcount;
     int nblocks;
     int* status;
-    // Runge-Kutta stage fused into the flux kernel (rk_b != 0): for every
-    // variable, out = rk_a U0 + rk_b (Us + c R) in FP64 with the stage's step
+    // Runge-Kutta stage fused into the flux kernel (rk_mode bit 0): for every
+    // variable, out = rk_a U0 + rk_b (Us + c R) with the stage's step
     // c = rk_w dt (dt per problem), and the next stage's cell-major copy
-    // into ua_next (may be null); R itself also into Rcopy when non-null
+    // into ua_next (may be null); R itself also into Rcopy when non-null.
+    // The state is FP64.  FP64 schemes evaluate the line in FP64; FP32
+    // schemes form the increment rk_bw dt R in FP32 (rk_bw = rk_b rk_w
+    // rounded to FP32; R is an FP32 value) and add it with one FP64 FMA per
+    // term: out = rk_a U0 + (rk_b Us + increment).  rk_mode bit 1: rk_a != 0.
     double rk_a, rk_b, rk_w;
+    float rk_bw;
+    int rk_mode;
     T* Rcopy;
     const double* U0;
     const double* Us;
@@ -103,7 +109,26 @@ struct KParams {
     const T* VX;
     const T* LINV;
     T* GS;
-    ViscParams vp;
+    ViscParams<T> vp;
+    // limit of the candidate kernel's consumer waits (ns) and, for testing the
+    // timeout path, a switch that makes its producer issue no bulk copy
+    uint64_t wait_ns;
+    int withhold_copies;
+    // chained steps: the last stage's flux kernel also reduces the next
+    // step's stable time step into dt_next (kDtSlots slots per problem, each
+    // on its own 128-byte line, as bits of positive doubles for atomicMin, a
+    // warp into slot (warp index) % kDtSlots so that no single line takes
+    // every warp's atomic; null in
+    // every other launch) from the new state, with the face areas areaT and
+    // cfl; the first stage's tagging kernel of the following step reduces
+    // dt_pending (the same array; null in every other launch) over the slots
+    // into dt_cur and resets it
+    unsigned long long* dt_next;
+    unsigned long long* dt_pending;
+    double* dt_cur;
+    const T* areaT;
+    T cfl;
+    int nseg;
 };
 
 }  // namespace hfv

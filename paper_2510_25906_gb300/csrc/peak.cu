@@ -1,7 +1,8 @@
 // peak.cu -- CUDA-core fused multiply-add throughput of the current device:
 // the ALU ceiling against which the FP64 (and FP32) residual paths are
 // reported next to the HBM ceiling.  Instrumentation; the paper has no
-// counterpart.
+// counterpart.  Also the FP32 kernels' integer FP32 <-> FP64 conversions
+// applied to an array, so that they can be checked against the hardware's.
 //
 // Each thread runs eight independent chains of dependent FMAs (x <- a x + b
 // with |a| < 1, so the values stay normal and bounded), enough independent
@@ -13,6 +14,7 @@
 #include <algorithm>
 #include <string>
 
+#include "device_common.cuh"
 #include "hfv_internal.h"
 
 namespace hfv {
@@ -75,10 +77,35 @@ int launch_peak(int kind, int iters, unsigned grid, cudaStream_t st)
     return HFV_OK;
 }
 
+__global__ void k_convert(int to_f32, int64_t n, const void* __restrict__ in, void* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (to_f32) static_cast<float*>(out)[i] = f64_to_f32(static_cast<const double*>(in)[i]);
+    else static_cast<double*>(out)[i] = f32_to_f64(static_cast<const float*>(in)[i]);
+}
+
 }  // namespace
 }  // namespace hfv
 
 using namespace hfv;
+
+extern "C" int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!in || !out)) || (to_f32 != 0 && to_f32 != 1)) {
+        set_error("hfv_convert: to_f32 must be 0 or 1, n >= 0, buffers non-null");
+        return HFV_ERR_ARG;
+    }
+    if (n == 0) return HFV_OK;
+    note_launch();
+    k_convert<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(to_f32, n, in, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("hfv_convert: ") + cudaGetErrorString(e));
+        return HFV_ERR_CUDA;
+    }
+    return HFV_OK;
+}
 
 extern "C" int hfv_fma_rate(int kind, double target_ms, double* flops_per_s, void* stream)
 {

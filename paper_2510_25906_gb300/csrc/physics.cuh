@@ -158,13 +158,15 @@ HDI void riemann(const T* UL, const T* UR, const T* n, T g, T* F)
 //   tau_ij = mu (d_j u_i + d_i u_j - 2/3 div u delta_ij),
 //   Theta_j = sum_i u_i tau_ij + mu / Pr gamma / (gamma - 1) dT/dx_j,
 //   mu = mu0 (T / T0)^(3/2) (T0 + S) / (T + S).
+// (in the residual's precision: FP32 kernels convert no FP64 operand)
+template <class T>
 struct ViscParams {
-    double mu0, t0, suth, inv_pr, alpha;
+    T mu0, t0, suth, inv_pr, alpha;
 };
 
 template <class T, int D>
 HDI void viscous_flux(const T* wl, const T* wr, const T* gl, const T* gr, const T* n, T inv_lint, T g,
-                      const ViscParams& vp, T* F)
+                      const ViscParams<T>& vp, T* F)
 {
     T ql[D + 1], qr[D + 1];
     {
@@ -183,17 +185,17 @@ HDI void viscous_flux(const T* wl, const T* wr, const T* gl, const T* gr, const 
     T Gm[D + 1][D];
 #pragma unroll
     for (int k = 0; k <= D; ++k) {
-        const T pen = T(vp.alpha) * inv_lint * (qr[k] - ql[k]);
+        const T pen = vp.alpha * inv_lint * (qr[k] - ql[k]);
 #pragma unroll
         for (int j = 0; j < D; ++j) Gm[k][j] = T(0.5) * (gl[k * D + j] + gr[k * D + j]) + pen * n[j];
     }
-    const T Tm = T(0.5) * (ql[D] + qr[D]), t0 = T(vp.t0), S = T(vp.suth);
+    const T Tm = T(0.5) * (ql[D] + qr[D]), t0 = vp.t0, S = vp.suth;
     const T tr = Tm / t0;
-    const T mu = T(vp.mu0) * tr * tsqrt<T>(tr) * (t0 + S) / (Tm + S);
+    const T mu = vp.mu0 * tr * tsqrt<T>(tr) * (t0 + S) / (Tm + S);
     T div = T(0);
 #pragma unroll
     for (int k = 0; k < D; ++k) div += Gm[k][k];
-    const T kap = mu * T(vp.inv_pr) * g / (g - T(1));
+    const T kap = mu * vp.inv_pr * g / (g - T(1));
     F[0] = T(0);
     T fe = T(0);
 #pragma unroll

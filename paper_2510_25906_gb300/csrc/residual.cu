@@ -84,17 +84,17 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
                                                   const T* __restrict__ ivol, const T* __restrict__ area,
                                                   const T* __restrict__ nrm, const uint8_t* __restrict__ nfc,
                                                   const int32_t* __restrict__ seg, double gamma, double cfl,
-                                                  unsigned long long* dt_out, ViscParams vp)
+                                                  unsigned long long* dt_out, ViscParams<T> vp)
 {
     pdl_wait();
-    constexpr int D = NV - 2, P = AoSP<NV>::P;
-    __shared__ double red[8];
+    constexpr int P = AoSP<NV>::P;
+    __shared__ T red[8];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double dtc = INFINITY;
+    T dtc = T(INFINITY);
     if (c < nc) {
         T u[P];
 #pragma unroll
-        for (int v = 0; v < P; ++v) u[v] = v < NV ? (T)U[v * nc + c] : T(0);
+        for (int v = 0; v < P; ++v) u[v] = v < NV ? to_t<T>(U[v * nc + c]) : T(0);
         T* q = UA + c * P;
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
@@ -103,37 +103,7 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
 #pragma unroll
             for (int v = 0; v < P; v += 2) *reinterpret_cast<double2*>(q + v) = make_double2(u[v], u[v + 1]);
         }
-        if (dt_out) {
-            const T g = (T)gamma, rho = u[0];
-            T m2 = T(0), vel[3] = {T(0), T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                vel[k] = u[1 + k] / rho;
-                m2 += u[1 + k] * u[1 + k];
-            }
-            const T pr = (g - T(1)) * (u[D + 1] - T(0.5) * m2 / rho);
-            const T a = tsqrt<T>(g * pr / rho);
-            T lam = T(0);
-            const int nf = nfc[c] & 15;
-            for (int f = 0; f < nf; ++f) {
-                const T* n = nrm + (c * 6 + f) * 3;
-                const T un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
-                lam += (tabs(un) + a) * area[c * 6 + f];
-            }
-            if (vp.mu0 > 0.0) {
-                // viscous terms: the explicit diffusion limit 4 nu sum_f |S_f|^2 / |V|,
-                // nu = max(4/3, gamma / Pr) mu / rho
-                const T tt = pr / rho, t0 = (T)vp.t0, S = (T)vp.suth, tr = tt / t0;
-                const T mu = (T)vp.mu0 * tr * tsqrt<T>(tr) * (t0 + S) / (tt + S);
-                const T nu = tmax(T(4) / T(3), g * (T)vp.inv_pr) * mu / rho;
-                T s2 = T(0);
-                for (int f = 0; f < nf; ++f) s2 += area[c * 6 + f] * area[c * 6 + f];
-                lam += T(4) * nu * s2 * ivol[c];
-            }
-            dtc = (double)((T)cfl * (T(1) / ivol[c]) / lam);
-            if (sizeof(T) == 8) dtc = (double)((T)cfl / (ivol[c] * lam));
-            if (!(dtc > 0.0)) dtc = 0.0;  // a non-physical state stops the step at dt = 0
-        }
+        if (dt_out) dtc = cell_dt<T, NV>(u, c, ivol, area, nrm, nfc[c] & 15, (T)gamma, (T)cfl, vp);
     }
     if (!dt_out) return;
     // problems are runs of consecutive cells: a block inside one problem
@@ -144,17 +114,19 @@ __global__ void __launch_bounds__(256) k_stage_in(int64_t nc, const double* __re
         const int64_t c1 = min(c0 + (int64_t)blockDim.x, nc) - 1;
         k0 = seg[c0];
         if (seg[c1] != k0) {
-            if (c < nc) atomicMin(dt_out + seg[c], (unsigned long long)__double_as_longlong(dtc));
+            if (c < nc) atomicMin(dt_out + seg[c], (unsigned long long)__double_as_longlong((double)dtc));
             return;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) dtc = fmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+    // the minimum in the residual's precision (see cell_dt_finish), one
+    // conversion to FP64 for the atomic
+    for (int o = 16; o > 0; o >>= 1) dtc = tmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dtc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = red[0];
-        for (int k = 1; k < 8; ++k) m = fmin(m, red[k]);
-        atomicMin(dt_out + k0, (unsigned long long)__double_as_longlong(m));
+        T m = red[0];
+        for (int k = 1; k < 8; ++k) m = tmin(m, red[k]);
+        atomicMin(dt_out + k0, (unsigned long long)__double_as_longlong((double)m));
     }
 }
 
@@ -205,6 +177,7 @@ static int residual_any(hfv_scheme* s, const void* U, void* R, const uint8_t* fo
 
 int launch_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)
 {
+    s->chain_ok = false;   // the stage copy is overwritten
     return residual_any(s, U, R, forced, cls_out, (cudaStream_t)stream, nullptr, nullptr);
 }
 
@@ -215,17 +188,17 @@ static int stage_in(hfv_scheme* s, const double* U, double cfl, double* dt_dev, 
     const unsigned g = (unsigned)((nc + 255) / 256);
     const hfv_dev_arrays& a = s->a;
     auto* out = (unsigned long long*)dt_dev;
-    ViscParams vp;
-    vp.mu0 = s->p.mu0; vp.t0 = s->p.t0; vp.suth = s->p.sutherland_s; vp.inv_pr = 1.0 / s->p.prandtl; vp.alpha = s->p.visc_alpha;
+    const ViscParams<float> vpf = visc_params<float>(s);
+    const ViscParams<double> vpd = visc_params<double>(s);
     if (dt_dev) { Launch l(s, KID_DT, st); pdl(k_dt_init, (s->nseg + 255) / 256, 256, 0, st, out, s->nseg); }
     Launch l(s, KID_CVT, st);
     const bool f32 = s->p.precision == HFV_FP32;
     if (s->nv == 4) {
-        if (f32) pdl(k_stage_in<float, 4>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vp);
-        else pdl(k_stage_in<double, 4>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vp);
+        if (f32) pdl(k_stage_in<float, 4>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vpf);
+        else pdl(k_stage_in<double, 4>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vpd);
     } else {
-        if (f32) pdl(k_stage_in<float, 5>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vp);
-        else pdl(k_stage_in<double, 5>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vp);
+        if (f32) pdl(k_stage_in<float, 5>, g, 256, 0, st, nc, U, (float*)a.UA, (const float*)a.ivol, (const float*)a.areaT, (const float*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vpf);
+        else pdl(k_stage_in<double, 5>, g, 256, 0, st, nc, U, (double*)a.UA, (const double*)a.ivol, (const double*)a.areaT, (const double*)a.nrm, a.nfc, a.seg, s->p.gamma, cfl, out, vpd);
     }
     HFV_CUDA_CHECK(cudaGetLastError());
     return HFV_OK;
@@ -233,6 +206,7 @@ static int stage_in(hfv_scheme* s, const double* U, double cfl, double* dt_dev, 
 
 int launch_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream)
 {
+    s->chain_ok = false;
     return stage_in(s, U, cfl, dt_dev, (cudaStream_t)stream);
 }
 
@@ -240,11 +214,25 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     int rc;
-    if (dt > 0.0) {
+    // chained steps (step_chain): the previous call's last stage already wrote
+    // this step's stage copy (and, in CFL mode, its time step into dt_next)
+    // when this call repeats its state, mode and CFL number
+    // (the viscous residual takes the stage-in pass: its flux kernel carries no chained epilogue)
+    const bool chain = s->p.step_chain && s->p.time_scheme == HFV_SSPRK3 && !(s->p.mu0 > 0.0);
+    const bool fixed = dt > 0.0;
+    const bool warm = chain && s->chain_ok && s->chain_U == U && s->chain_fixed == fixed && (fixed || s->chain_cfl == cfl);
+    s->chain_ok = false;
+    if (fixed) {
         { Launch l(s, KID_DT, st); pdl(k_set, (s->nseg + 255) / 256, 256, 0, st, s->a.dt, dt, s->nseg); }
-        if ((rc = stage_in(s, U, cfl, nullptr, st)) != HFV_OK) return rc;
-    } else if ((rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
+        if (!warm && (rc = stage_in(s, U, cfl, nullptr, st)) != HFV_OK) return rc;
+    } else if (!warm && (rc = stage_in(s, U, cfl, s->a.dt, st)) != HFV_OK) {
         return rc;
+    }
+    if (chain && !fixed && !warm) {
+        // the first step of a chain: dt_next starts at +inf for the last stage's minimum
+        Launch l(s, KID_DT, st);
+        pdl(k_dt_init, (s->nseg * kDtSlots * kDtStride + 255) / 256, 256, 0, st, (unsigned long long*)s->a.dt_next,
+            s->nseg * kDtSlots * kDtStride);
     }
     // stages alternate the cell-major copies UA, UB, UA, ...; each stage's
     // flux kernel writes the next one
@@ -304,10 +292,20 @@ int launch_step(hfv_scheme* s, double* U, double cfl, double dt, void* stream)
         rk.U0 = U;
         rk.Us = ins[k];
         rk.out = outs[k];
-        rk.ua_next = k < 2 ? uab[(k + 1) & 1] : nullptr;
+        rk.ua_next = k < 2 ? uab[(k + 1) & 1] : chain ? uab[0] : nullptr;
+        if (chain && !fixed) {
+            if (k == 0 && warm) rk.dt_pending = (unsigned long long*)s->a.dt_next;
+            if (k == 2) { rk.dt_next = (unsigned long long*)s->a.dt_next; rk.cfl = cfl; }
+        }
         if ((rc = residual_any(s, nullptr, s->a.Rs, nullptr, nullptr, st, uab[k & 1], &rk)) != HFV_OK) return rc;
     }
     HFV_CUDA_CHECK(cudaGetLastError());
+    if (chain) {
+        s->chain_ok = true;
+        s->chain_U = U;
+        s->chain_fixed = fixed;
+        s->chain_cfl = cfl;
+    }
     return HFV_OK;
 }
 

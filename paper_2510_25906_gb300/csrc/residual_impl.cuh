@@ -34,6 +34,89 @@
 
 namespace hfv {
 
+// The stable time step of one cell from its state u (the precision of the
+// residual; FP64 for FP64 schemes):
+//   dt = cfl |V| / (sum_f (|u . n_f| + a) |S_f| [+ 4 nu sum_f |S_f|^2 / |V|])
+// with the diffusion limit when mu0 > 0 (nu = max(4/3, gamma / Pr) mu / rho);
+// 0 for a non-physical state (it stops the step).  One function for the
+// stage-in kernel and the chained flux epilogue, so that both give the same bits.
+// in three parts, so that the flux kernel can spread the face terms over
+// its face lanes and still sum them in the same order with the same FMAs
+template <class T, int NV, int P>
+__device__ __forceinline__ void cell_dt_state(const T (&u)[P], T g, T (&vel)[3], T& a, T& pr)
+{
+    constexpr int D = NV - 2;
+    const T rho = u[0];
+    T m2 = T(0);
+    vel[0] = vel[1] = vel[2] = T(0);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: a stability estimate; one fast reciprocal (as the Riemann solver)
+        const T ir = trcp<T>(rho);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            vel[k] = u[1 + k] * ir;
+            m2 += u[1 + k] * u[1 + k];
+        }
+        pr = (g - T(1)) * (u[D + 1] - T(0.5) * m2 * ir);
+        a = fsqrt<T>(g * pr * ir);
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            vel[k] = u[1 + k] / rho;
+            m2 += u[1 + k] * u[1 + k];
+        }
+        pr = (g - T(1)) * (u[D + 1] - T(0.5) * m2 / rho);
+        a = tsqrt<T>(g * pr / rho);
+    }
+}
+template <class T>
+__device__ __forceinline__ T cell_dt_face(const T (&vel)[3], T a, const T* n)
+{
+    const T un = vel[0] * n[0] + vel[1] * n[1] + vel[2] * n[2];
+    return tabs(un) + a;
+}
+// lam = sum_f face_f area_f (accumulated by the caller in face order), s2 =
+// sum_f area_f^2; the step in the residual's precision (kept there for the
+// minimum: FP64 instructions are scarce on this GPU, and the minimum of FP32
+// values converted to FP64 is the conversion of their minimum)
+template <class T, bool VISC>
+__device__ __forceinline__ T cell_dt_finish(T lam, T s2, T rho, T pr, T ivol, T g, T cfl, const ViscParams<T>& vp)
+{
+    if constexpr (VISC) {
+        const T tt = pr / rho, t0 = vp.t0, S = vp.suth, tr = tt / t0;
+        const T mu = vp.mu0 * tr * tsqrt<T>(tr) * (t0 + S) / (tt + S);
+        const T nu = tmax(T(4) / T(3), g * vp.inv_pr) * mu / rho;
+        lam += T(4) * nu * s2 * ivol;
+    }
+    T dtc = cfl * (T(1) / ivol) / lam;
+    if (sizeof(T) == 8) dtc = cfl / (ivol * lam);
+    return dtc > T(0) ? dtc : T(0);   // a non-physical state stops the step at dt = 0
+}
+// a time step as the bits of the FP64 value, for the atomic minimum over cells
+template <class T>
+__device__ __forceinline__ unsigned long long dt_bits(T dtc)
+{
+    if constexpr (sizeof(T) == 4) return (unsigned long long)__double_as_longlong(f32_to_f64(dtc));
+    else return (unsigned long long)__double_as_longlong(dtc);
+}
+template <class T, int NV, int P>
+__device__ __forceinline__ T cell_dt(const T (&u)[P], int64_t c, const T* __restrict__ ivol,
+                                          const T* __restrict__ area, const T* __restrict__ nrm, int nf, T g,
+                                          T cfl, const ViscParams<T>& vp)
+{
+    T vel[3], a, pr;
+    cell_dt_state<T, NV>(u, g, vel, a, pr);
+    T lam = T(0), s2 = T(0);
+    for (int f = 0; f < nf; ++f) {
+        const T ar = area[c * 6 + f];
+        const T t = cell_dt_face<T>(vel, a, nrm + (c * 6 + f) * 3);
+        lam += t * ar;
+        s2 += ar * ar;
+    }
+    return vp.mu0 > T(0) ? cell_dt_finish<T, true>(lam, s2, u[0], pr, ivol[c], g, cfl, vp)
+                        : cell_dt_finish<T, false>(lam, s2, u[0], pr, ivol[c], g, cfl, vp);
+}
+
 // a first-order cell's face points all carry its cell mean
 template <class T>
 __device__ __forceinline__ void write_mean(const KParams<T>& p, int64_t c)
@@ -55,6 +138,17 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
 {
     pdl_wait();
     __shared__ int sc[2][8];
+    if (p.dt_pending && blockIdx.x == 0)
+        for (int k = threadIdx.x; k < p.nseg; k += 256) {
+            unsigned long long m = 0x7ff0000000000000ull;
+            for (int j = 0; j < kDtSlots; ++j) {
+                const int64_t e = ((int64_t)k * kDtSlots + j) * kDtStride;
+                const unsigned long long x = p.dt_pending[e];
+                m = x < m ? x : m;
+                p.dt_pending[e] = 0x7ff0000000000000ull;
+            }
+            p.dt_cur[k] = __longlong_as_double((long long)m);
+        }
     const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
     int t = 255;
     if (c < p.nc) {
@@ -857,7 +951,7 @@ struct FluxShape {
     static constexpr int MINB = sizeof(T) == 8 ? 4 : C::D == 2 ? 10 : 9;
 };
 
-template <class C, class T, int KIND, bool VISC = false>
+template <class C, class T, int KIND, bool VISC = false, bool CHAIN = false>
 __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> p, T* __restrict__ R)
 {
     constexpr int NV = C::NV, D = C::D, NFP = C::NFP, G = FluxShape<C, T>::FG, CPB = FluxShape<C, T>::CPB;
@@ -876,20 +970,42 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
     }
     // the Runge-Kutta operands (independent of the fluxes)
     constexpr int NVL = (NV + G - 1) / G;   // variables finished per lane
+    constexpr bool F32 = sizeof(T) == 4;
+    const bool rk = p.rk_mode & 1, rk_a = p.rk_mode & 2;
     double u0[NVL], us[NVL], cdt = 0.0;
+    float cdtf = 0.0f;
 #pragma unroll
     for (int k = 0; k < NVL; ++k) {
         u0[k] = 0.0; us[k] = 0.0;
         const int v = lane + k * G;
-        if (valid && p.rk_b != 0.0 && v < NV) {
+        if (valid && rk && v < NV) {
             us[k] = p.Us[(int64_t)v * nc + c];
-            if (p.rk_a != 0.0) u0[k] = p.U0[(int64_t)v * nc + c];
+            if (rk_a) u0[k] = p.U0[(int64_t)v * nc + c];
         }
     }
-    if (valid && p.rk_b != 0.0) cdt = p.rk_w * p.dt[p.seg ? p.seg[c] : 0];
+    if (valid && rk) {
+        const double dtk = p.dt[p.seg ? p.seg[c] : 0];
+        if constexpr (F32) cdtf = p.rk_bw * f64_to_f32(dtk);
+        else cdt = p.rk_w * dtk;
+    }
     const T ivol = valid ? p.ivol[cs] : T(0);
     T linv = T(0);
     if (VISC && valid && f < C::NFMAX) linv = p.LINV[cs * 6 + f];
+    // the chained time step's geometry, loaded here: after the state stores
+    // below the compiler could not move these loads ahead of them, and each
+    // block would wait on two more memory round trips at its end
+    T af = T(0);
+    int dseg = 0;   // the problem the atomic goes to, or -1 - the cell's problem when the warp spans two
+    if constexpr (CHAIN) {
+        if (nb != -2) af = p.areaT[cs * 6 + f];
+        if (p.seg) {
+            constexpr int CPW = 32 / G;
+            const int64_t w0 = min((int64_t)blockIdx.x * CPB + (threadIdx.x >> 5) * CPW, nc - 1);
+            const int64_t w1 = min(w0 + (int64_t)CPW, nc) - 1;
+            dseg = p.seg[w0];
+            if (p.seg[w1] != dseg) dseg = -1 - p.seg[cs];
+        }
+    }
     // geometry and the stage operands above are constant or written two or
     // more kernels back; the face states are the predecessor's output
     pdl_wait();
@@ -931,25 +1047,77 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
     for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-    if (!valid) return;
+    T xs[NVL];   // the new state in the residual's precision (the next stage's copy)
 #pragma unroll
     for (int k = 0; k < NVL; ++k) {
+        xs[k] = T(0);
         const int v = lane + k * G;
-        if (v >= NV) break;
+        if (!valid || v >= NV) continue;
         T val = acc[0];
 #pragma unroll
         for (int x = 1; x < NV; ++x) val = v == x ? acc[x] : val;
         const T r = -val * ivol;
         const int64_t e = (int64_t)v * nc + c;
-        if (p.rk_b == 0.0) {
+        if (!rk) {
             R[e] = r;
         } else {
-            // Runge-Kutta stage update of variable v of cell c (FP64)
-            double x = p.rk_b * (us[k] + cdt * (double)r);
-            if (p.rk_a != 0.0) x += p.rk_a * u0[k];
+            // Runge-Kutta stage update of variable v of cell c into the FP64 state
+            double x;
+            if constexpr (F32) {
+                x = fma(p.rk_b, us[k], f32_to_f64(cdtf * r));
+                if (rk_a) x = fma(p.rk_a, u0[k], x);
+                xs[k] = f64_to_f32(x);
+            } else {
+                x = p.rk_b * (us[k] + cdt * (double)r);
+                if (rk_a) x += p.rk_a * u0[k];
+                xs[k] = x;
+            }
             if (p.Rcopy) p.Rcopy[e] = r;
             p.out[e] = x;
-            if (p.ua_next) p.ua_next[c * AoSP<NV>::P + v] = (T)x;
+            if (p.ua_next) p.ua_next[c * AoSP<NV>::P + v] = xs[k];
+        }
+    }
+    if constexpr (CHAIN) {
+        // chained steps (the last stage's launch): the next step's time step
+        // from the new state; a warp inside one problem reduces first, a warp
+        // across a boundary takes one atomic per cell
+        constexpr int P = AoSP<NV>::P;
+        const int base = (threadIdx.x & 31) & ~(G - 1);
+        T u[P];
+#pragma unroll
+        for (int v = 0; v < P; ++v) u[v] = T(0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = __shfl_sync(0xffffffffu, xs[v / G], base + v % G);
+        // every lane holds the new state; lane f takes face f's term with the
+        // normal it already has, the first lane sums them in face order
+        T vel[3], a, pr;
+        cell_dt_state<T, NV>(u, p.gamma, vel, a, pr);
+        T tf = T(0);
+        if (nb != -2) tf = cell_dt_face<T>(vel, a, nn);
+        // a lane past the cell's faces holds tf = af = 0: its term adds an
+        // exact zero, so the sums equal those over the cell's own faces
+        T lam = T(0), s2 = T(0);
+#pragma unroll
+        for (int h = 0; h < C::NFMAX; ++h) {
+            const T th = __shfl_sync(0xffffffffu, tf, base + h), ah = __shfl_sync(0xffffffffu, af, base + h);
+            lam += th * ah;
+            s2 += ah * ah;
+        }
+        T dtc = T(INFINITY);
+        if (valid && lane == 0) dtc = cell_dt_finish<T, false>(lam, s2, u[0], pr, ivol, p.gamma, p.cfl, p.vp);
+        constexpr int CPW = 32 / G;   // cells per warp
+        const int64_t w0 = (int64_t)blockIdx.x * CPB + (threadIdx.x >> 5) * CPW;
+        const int slot = (blockIdx.x * 4 + (threadIdx.x >> 5)) & (kDtSlots - 1);
+        if (w0 < nc) {
+            if (dseg < 0) {
+                if (valid && lane == 0)
+                    atomicMin(p.dt_next + ((int64_t)(-1 - dseg) * kDtSlots + slot) * kDtStride, dt_bits(dtc));
+            } else {
+#pragma unroll
+                for (int o = 16; o >= G; o >>= 1) dtc = tmin(dtc, __shfl_xor_sync(0xffffffffu, dtc, o));
+                if ((threadIdx.x & 31) == 0)
+                    atomicMin(p.dt_next + ((int64_t)dseg * kDtSlots + slot) * kDtStride, dt_bits(dtc));
+            }
         }
     }
 }
@@ -1008,6 +1176,19 @@ struct Launch {
     }
 };
 
+// the viscous constants in the residual's precision
+template <class T>
+ViscParams<T> visc_params(const hfv_scheme* s)
+{
+    ViscParams<T> vp;
+    vp.mu0 = (T)s->p.mu0;
+    vp.t0 = (T)s->p.t0;
+    vp.suth = (T)s->p.sutherland_s;
+    vp.inv_pr = (T)(1.0 / s->p.prandtl);
+    vp.alpha = (T)s->p.visc_alpha;
+    return vp;
+}
+
 template <class T>
 KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
 {
@@ -1039,11 +1220,17 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.VX = (const T*)a.VX;
     p.LINV = (const T*)a.LINV;
     p.GS = (T*)a.GS;
-    p.vp.mu0 = s->p.mu0;
-    p.vp.t0 = s->p.t0;
-    p.vp.suth = s->p.sutherland_s;
-    p.vp.inv_pr = 1.0 / s->p.prandtl;
-    p.vp.alpha = s->p.visc_alpha;
+    p.vp = visc_params<T>(s);
+    p.wait_ns = s->wait_ns;
+    p.withhold_copies = s->withhold_copies;
+    p.dt_next = nullptr;
+    p.dt_pending = nullptr;
+    p.dt_cur = a.dt;
+    p.areaT = (const T*)a.areaT;
+    p.cfl = T(0);
+    p.rk_mode = 0;
+    p.rk_bw = 0.0f;
+    p.nseg = s->nseg;
     return p;
 }
 
@@ -1077,6 +1264,11 @@ struct StageRK {
     double* out = nullptr;
     void* ua_next = nullptr;
     bool keep_R = false;      // also store R (into Rs)
+    // chained steps: reduce the next step's time step into dt_next (last stage,
+    // with cfl), or move dt_pending into the current step's (first stage)
+    unsigned long long* dt_next = nullptr;
+    unsigned long long* dt_pending = nullptr;
+    double cfl = 0.0;
 };
 
 template <class C, class T>
@@ -1097,10 +1289,16 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         p.rk_a = rk->a; p.rk_b = rk->b; p.U0 = rk->U0; p.Us = rk->Us; p.seg = s->a.seg;
         p.dt = s->a.dt;
         p.rk_w = rk->w;
+        p.rk_bw = (float)(rk->b * rk->w);
+        p.rk_mode = (rk->b != 0.0 ? 1 : 0) | (rk->a != 0.0 ? 2 : 0);
         p.out = rk->out; p.ua_next = (T*)rk->ua_next;
         p.Rcopy = rk->keep_R ? (T*)s->a.Rs : nullptr;
+        p.dt_next = rk->dt_next;
+        p.dt_pending = rk->dt_pending;
+        p.cfl = (T)rk->cfl;
     } else {
-        p.rk_a = 0.0; p.rk_b = 0.0; p.rk_w = 0.0; p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr;
+        p.rk_a = 0.0; p.rk_b = 0.0; p.rk_w = 0.0; p.rk_bw = 0.0f; p.rk_mode = 0;
+        p.U0 = nullptr; p.Us = nullptr; p.dt = nullptr;
         p.seg = nullptr; p.out = nullptr; p.ua_next = nullptr; p.Rcopy = nullptr;
     }
     {
@@ -1149,13 +1347,16 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     {
         Launch l(s, KID_FLUX, st);
         const unsigned gf = (unsigned)((nc + FluxShape<C, T>::CPB - 1) / FluxShape<C, T>::CPB);
-        switch (s->p.flux + (visc ? 3 : 0)) {
+        switch (s->p.flux + (visc ? 3 : p.dt_next ? 6 : 0)) {
         case HFV_RUSANOV: pdl(k_flux<C, T, kRusanov>, gf, 128, 0, st, p, R); break;
         case HFV_HLL: pdl(k_flux<C, T, kHLL>, gf, 128, 0, st, p, R); break;
         case HFV_HLLC: pdl(k_flux<C, T, kHLLC>, gf, 128, 0, st, p, R); break;
         case 3 + HFV_RUSANOV: pdl(k_flux<C, T, kRusanov, true>, gf, 128, 0, st, p, R); break;
         case 3 + HFV_HLL: pdl(k_flux<C, T, kHLL, true>, gf, 128, 0, st, p, R); break;
-        default: pdl(k_flux<C, T, kHLLC, true>, gf, 128, 0, st, p, R); break;
+        case 3 + HFV_HLLC: pdl(k_flux<C, T, kHLLC, true>, gf, 128, 0, st, p, R); break;
+        case 6 + HFV_RUSANOV: pdl(k_flux<C, T, kRusanov, false, true>, gf, 128, 0, st, p, R); break;
+        case 6 + HFV_HLL: pdl(k_flux<C, T, kHLL, false, true>, gf, 128, 0, st, p, R); break;
+        default: pdl(k_flux<C, T, kHLLC, false, true>, gf, 128, 0, st, p, R); break;
         }
     }
     if (cls_out) HFV_CUDA_CHECK(cudaMemcpyAsync(cls_out, s->a.cls, nc, cudaMemcpyDeviceToDevice, st));

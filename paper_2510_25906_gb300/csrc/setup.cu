@@ -113,7 +113,8 @@ int build_operators(hfv_scheme* s, void* stream)
            o_bcount = take(2 * (size_t)s->nblocks * 4), o_status = take(64);
     size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b), o_UB = take(nc * (nv == 4 ? 4 : 8) * b),
            o_areaT = take(nc * 6 * b),
-           o_dt = take(std::max<int64_t>(64, 8 * (int64_t)s->nseg)), o_Uio = take(nv * nc * 8),
+           o_dt = take(std::max<int64_t>(64, 8 * (int64_t)s->nseg)), o_dtn = take(8 * kDtSlots * kDtStride * (int64_t)s->nseg),
+           o_Uio = take(nv * nc * 8),
            o_seg = take(s->nseg > 1 ? nc * 4 : 0);
     const bool rk54 = s->p.time_scheme == HFV_SSPRK54;
     size_t o_U3 = take(rk54 ? nv * nc * 8 : 0), o_U4 = take(rk54 ? nv * nc * 8 : 0), o_U5 = take(rk54 ? nv * nc * 8 : 0);
@@ -136,6 +137,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.counts = (int32_t*)(A + o_counts); a.bcount = (int32_t*)(A + o_bcount); a.status = (int*)(A + o_status);
     a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA; a.UB = A + o_UB; a.areaT = A + o_areaT;
     a.dt = (double*)(A + o_dt);
+    a.dt_next = (double*)(A + o_dtn);
     a.seg = s->nseg > 1 ? (int32_t*)(A + o_seg) : nullptr;
     a.U3 = rk54 ? (double*)(A + o_U3) : nullptr;
     a.U4 = rk54 ? (double*)(A + o_U4) : nullptr;

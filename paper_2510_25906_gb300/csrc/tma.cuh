@@ -47,10 +47,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
-// wait for the phase with the given parity to complete; false on timeout.
-// A waiting thread is suspended inside try_wait (woken when the phase
-// completes), so a stalled warp takes no issue slots.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// wait for the phase with the given parity to complete; false once limit_ns
+// of unsuccessful polls have passed.  A waiting thread is suspended inside
+// try_wait (woken when the phase completes), so a stalled warp takes no
+// issue slots.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitNs)
 {
     const uint32_t a = smem_u32(bar);
     uint64_t t0 = 0;
@@ -66,7 +67,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
         if (done) return true;
         const uint64_t t = global_ns();
         if (t0 == 0) t0 = t;
-        else if (t - t0 > kWaitNs) return false;
+        else if (t - t0 > limit_ns) return false;
     }
 }
 

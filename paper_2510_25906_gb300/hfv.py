@@ -51,7 +51,7 @@ class hfv_scheme_params(C.Structure):
                 ("cweno_b", C.c_double), ("harten_theta", C.c_double), ("harten_eps", C.c_double),
                 ("stencil_factor", C.c_double), ("limiter", C.c_int), ("cweno_vars", C.c_int), ("venkat_k", C.c_double),
                 ("mu0", C.c_double), ("t0", C.c_double), ("sutherland_s", C.c_double), ("prandtl", C.c_double),
-                ("visc_alpha", C.c_double)]
+                ("visc_alpha", C.c_double), ("step_chain", C.c_int)]
 
 
 _lib = None
@@ -92,6 +92,12 @@ def load():
         "hfv_launch_count": [vp],
         "hfv_class_queues_static": [vp, C.c_int64, vp, vp, vp],
         "hfv_fma_rate": [C.c_int, d, vp, vp],
+        "hfv_convert": [C.c_int, C.c_int64, vp, vp, vp],
+        "hfv_debug_wait": [vp, C.c_int64, C.c_int],
+        "hfv_step_classes": [vp, vp, d, vp, C.c_int, vp, vp],
+        "hfv_step_vjp": [vp, vp, vp, d, vp, vp],
+        "hfv_scheme_setup_ms": [vp, vp],
+        "hfv_scheme_set_kind": [vp, C.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -304,6 +310,44 @@ class Scheme:
         _check(load().hfv_advance_host(self.h, U.ctypes.data, n_steps, cfl, dt, _stream(stream)))
         return U
 
+    def step_classes(self, U, dt: float, cls=None, forced: bool = False, U_out=None, stream=None):
+        """hfv_step_classes: one SSP-RK3 step of U into U_out (returned) with
+        the stages' classes recorded into (or, forced, taken from) cls [3, n]."""
+        import torch
+        u = self._state(U, torch.float64)
+        if U_out is None:
+            U_out = torch.empty_like(U)
+        if cls is None:
+            cls = torch.empty((3, self.n_cells), dtype=torch.uint8, device=U.device)
+        if not (cls.is_cuda and cls.dtype == torch.uint8 and cls.is_contiguous() and cls.numel() == 3 * self.n_cells):
+            raise ValueError("cls must be a contiguous CUDA uint8 tensor of 3 x n_cells")
+        _check(load().hfv_step_classes(self.h, u, float(dt), C.c_void_p(cls.data_ptr()), 1 if forced else 0,
+                                       self._state(U_out, torch.float64), _stream(stream)))
+        return U_out, cls
+
+    def step_vjp(self, U, cls, dt: float, lam, stream=None):
+        """hfv_step_vjp: lam (dJ/dU after the step) becomes dJ/dU before it, in place."""
+        import torch
+        if not (cls.is_cuda and cls.dtype == torch.uint8 and cls.is_contiguous() and cls.numel() == 3 * self.n_cells):
+            raise ValueError("cls must be a contiguous CUDA uint8 tensor of 3 x n_cells")
+        _check(load().hfv_step_vjp(self.h, self._state(U, torch.float64), C.c_void_p(cls.data_ptr()), float(dt),
+                                   self._state(lam, torch.float64), _stream(stream)))
+        return lam
+
+    def setup_ms(self):
+        """hfv_scheme_setup_ms: (stencils, operators) wall time of the setup, ms."""
+        ms = np.zeros(2)
+        _check(load().hfv_scheme_setup_ms(self.h, ms.ctypes.data))
+        return float(ms[0]), float(ms[1])
+
+    def set_kind(self, scheme: str):
+        """hfv_scheme_set_kind: hybrid or a pure scheme on the same operators."""
+        _check(load().hfv_scheme_set_kind(self.h, SCHEME[scheme]))
+
+    def debug_wait(self, consumer_wait_ns: int = 0, withhold_copies: bool = False):
+        """hfv_debug_wait: testing aid of the bounded waits."""
+        _check(load().hfv_debug_wait(self.h, int(consumer_wait_ns), 1 if withhold_copies else 0))
+
     def queues(self):
         counts = np.zeros(2, np.int32)
         q = np.zeros((2, self.n_cells), np.int32)
@@ -351,6 +395,20 @@ def fma_rate(kind: str = "fp64", target_ms: float = 100.0, stream=None) -> float
     out = C.c_double()
     _check(load().hfv_fma_rate(k, float(target_ms), C.byref(out), _stream(stream)))
     return out.value
+
+
+def convert(x, stream=None):
+    """hfv_convert: the FP32 kernels' integer conversions applied to a
+    contiguous CUDA tensor; float64 -> float32 (round to nearest even) or
+    float32 -> float64 (exact)."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous() or x.dtype not in (torch.float32, torch.float64):
+        raise ValueError("convert: a contiguous CUDA float32 or float64 tensor")
+    to_f32 = x.dtype == torch.float64
+    out = torch.empty(x.shape, dtype=torch.float32 if to_f32 else torch.float64, device=x.device)
+    _check(load().hfv_convert(1 if to_f32 else 0, x.numel(), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                              _stream(stream)))
+    return out
 
 
 def class_queues_static(classes, counts=None, queues=None, stream=None):
