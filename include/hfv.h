@@ -371,9 +371,9 @@ HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
 
 /* Fold the pending event pairs into per-kernel totals and read them (host
  * outputs, 16 entries each): ms[k] total milliseconds and launches[k] count
- * of kernel k: 0 linear candidate + detector, 1 tagging, 2 block counts,
- * 3 scan, 4 scatter, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage,
- * 9 time step, 10 FP32 conversion, 11 viscous gradients.  reset != 0 zeroes the totals after
+ * of kernel k: 0 linear candidate + detector, 1 tagging and queue
+ * compaction, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage, 9 time
+ * step, 10 FP32 conversion, 11 viscous gradients (2, 3, 4: no kernel).  reset != 0 zeroes the totals after
  * reading.  sync. */
 HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset);
 

@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <chrono>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -402,7 +403,13 @@ extern "C" int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* que
     if (!s || !counts) { set_error("hfv_get_queues: NULL argument"); return HFV_ERR_ARG; }
     API_CUDA(cudaDeviceSynchronize());
     API_CUDA(cudaMemcpy(counts, s->a.counts, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (queues) API_CUDA(cudaMemcpy(queues, s->a.queue, 2 * s->mesh->nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (queues) {
+        // the device queues hold each block's cells in ascending order, the
+        // blocks in the order of their range reservations: sort the copies
+        const int64_t nc = s->mesh->nc;
+        API_CUDA(cudaMemcpy(queues, s->a.queue, 2 * nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < 2; ++q) std::sort(queues + q * nc, queues + q * nc + counts[q]);
+    }
     return HFV_OK;
 }
 

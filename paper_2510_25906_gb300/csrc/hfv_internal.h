@@ -89,7 +89,6 @@ struct hfv_dev_arrays {
     uint8_t* cls;      // [nc] final class
     int32_t* queue;    // [2][nc] CWENOZ / MUSCL queues
     int32_t* counts;   // [2] + block counts
-    int32_t* bcount;   // [2][nblocks]
     int* status;       // [1]
     // time stepping scratch
     double* U1;        // [nv][nc]
@@ -112,7 +111,8 @@ struct hfv_dev_arrays {
 };
 
 namespace hfv {
-// hot-path kernel ids for the optional per-kernel timer
+// hot-path kernel ids for the optional per-kernel timer (KID_COUNT, KID_SCAN and
+// KID_SCATTER are kept for the numbering only: tagging does the queue compaction)
 enum KernelId { KID_LINEAR, KID_TAG, KID_COUNT, KID_SCAN, KID_SCATTER, KID_CWENO, KID_MUSCL, KID_FLUX, KID_RK,
                 KID_DT, KID_CVT, KID_GRAD, KID_COUNT_ALL };
 struct KernelTimer {

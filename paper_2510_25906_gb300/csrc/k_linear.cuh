@@ -194,6 +194,10 @@ __global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> 
     // the producer streams constant data only; the states are the
     // predecessor's output
     pdl_wait();
+    // the queue counts of this residual start at zero for the tagging
+    // kernel's range reservations (their readers of the previous residual
+    // have completed: they ran before the predecessor)
+    if (blockIdx.x == 0 && threadIdx.x == 0) { p.counts[0] = 0; p.counts[1] = 0; }
     int k = 0;
     int64_t tile = blockIdx.x;
     bool alive = true;

@@ -78,8 +78,6 @@ struct KParams {
     uint8_t* cls;
     int32_t* queue;
     int32_t* counts;
-    int32_t* bcount;
-    int nblocks;
     int* status;
     // Runge-Kutta stage fused into the flux kernel (rk_mode bit 0): for every
     // variable, out = rk_a U0 + rk_b (Us + c R) with the stage's step

@@ -11,9 +11,9 @@
 //                 NADDeactivatedCriteria), Harten test of the candidate
 //   K2 k_tag      class of a cell = max over itself and its face neighbours
 //                 (tagging of the flagged cells' neighbourhood); linear cells
-//                 that fail the Harten bound become first-order
-//      (k_tag also counts) k_scan / k_scatter: warp-ballot compaction of the CWENOZ and
-//                 MUSCL cells into two queues in ascending cell order
+//                 that fail the Harten bound become first-order; the CWENOZ
+//                 and MUSCL cells go into two queues (warp ballots, one
+//                 atomic range reservation per block and queue)
 //   K3 k_cweno    CWENOZ on the CWENOZ queue (Sec. 2.3)
 //   K4 k_muscl    MUSCL + Barth-Jespersen on the MUSCL queue (Sec. 2.2)
 //      (both apply the Harten bound, eq. harten_jump_fix)
@@ -129,15 +129,21 @@ __device__ __forceinline__ void write_mean(const KParams<T>& p, int64_t c)
         for (int v = 0; v < nv; ++v) fs[q * nv + v] = u[v];
 }
 
-// K2a: tagging of the flagged cells' face neighbourhood (class = max over the
+// K2: tagging of the flagged cells' face neighbourhood (class = max over the
 // cell and its face neighbours), first-order for linear cells that broke the
-// Harten bound, and the per-block counts of the CWENOZ / MUSCL queues
-// (blocks of 256 cells, warp ballots)
+// Harten bound, and the CWENOZ / MUSCL queues.  A block of 256 cells counts
+// its queued cells with warp ballots, reserves its ranges of the two queues
+// with one atomic add each on counts[0..1] (zeroed by the candidate kernel
+// of the same residual) and writes its cells there in ascending order.  The
+// blocks' ranges follow the order of their atomics, so the queues hold each
+// class's cells in a run-dependent block order; a queued cell's
+// reconstruction depends only on the cell, so the residual does not.
 template <class T>
 __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
 {
     pdl_wait();
     __shared__ int sc[2][8];
+    __shared__ int base[2];
     if (p.dt_pending && blockIdx.x == 0)
         for (int k = threadIdx.x; k < p.nseg; k += 256) {
             unsigned long long m = 0x7ff0000000000000ull;
@@ -180,97 +186,14 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
     if (threadIdx.x < 2) {
         int sum = 0;
         for (int k = 0; k < 8; ++k) sum += sc[threadIdx.x][k];
-        p.bcount[threadIdx.x * p.nblocks + blockIdx.x] = sum;
-    }
-}
-
-// exclusive scan of the block counts (one block of 1024 threads, warp
-// shuffles); totals to counts[0..1]
-static __global__ void __launch_bounds__(1024) k_scan(int32_t* bcount, int nblocks, int32_t* counts)
-{
-    pdl_wait();
-    __shared__ int wsum[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = 0; q < 2; ++q) {
-        int32_t* b = bcount + q * nblocks;
-        const int per = (nblocks + 1023) / 1024;
-        const int lo = threadIdx.x * per, hi = min(lo + per, nblocks);
-        int v = 0;
-        for (int i = lo; i < hi; ++i) v += b[i];
-        int x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            int z = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, z, o);
-                if (lane >= o) z += y;
-            }
-            wsum[lane] = z;
-        }
-        __syncthreads();
-        int run = x - v + (w > 0 ? wsum[w - 1] : 0);
-        for (int i = lo; i < hi; ++i) {
-            const int e = b[i];
-            b[i] = run;
-            run += e;
-        }
-        if (threadIdx.x == 0) counts[q] = wsum[31];
-        __syncthreads();
-    }
-}
-
-// K2c: scatter into the queues.  With fold != 0 (few blocks) every block
-// first sums the counts of the blocks before it, replacing the separate
-// scan, and the last block writes the totals.
-static __global__ void __launch_bounds__(256) k_scatter(const uint8_t* __restrict__ cls, int64_t nc, int32_t* bcount,
-                                                 int nblocks, int32_t* queue, int32_t* counts, int fold)
-{
-    pdl_wait();
-    __shared__ int s[2][8];
-    __shared__ int base[2];
-    __shared__ int red[2][8];
-    const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    const int t = c < nc ? cls[c] : 255;
-    const unsigned b1 = __ballot_sync(0xffffffffu, t == CLS_CW);
-    const unsigned b2 = __ballot_sync(0xffffffffu, t == CLS_MU);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { s[0][w] = __popc(b1); s[1][w] = __popc(b2); }
-    if (fold) {
-        // exclusive prefix of this block: sum of the earlier blocks' counts
-        int p0 = 0, p1 = 0;
-        for (int i = threadIdx.x; i < (int)blockIdx.x; i += 256) { p0 += bcount[i]; p1 += bcount[nblocks + i]; }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            p0 += __shfl_xor_sync(0xffffffffu, p0, o);
-            p1 += __shfl_xor_sync(0xffffffffu, p1, o);
-        }
-        if (lane == 0) { red[0][w] = p0; red[1][w] = p1; }
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            int sum = 0;
-            for (int k = 0; k < 8; ++k) sum += red[threadIdx.x][k];
-            base[threadIdx.x] = sum;
-            if (blockIdx.x == (unsigned)nblocks - 1) counts[threadIdx.x] = sum + bcount[threadIdx.x * nblocks + blockIdx.x];
-        }
-    } else if (threadIdx.x < 2) {
-        base[threadIdx.x] = bcount[threadIdx.x * nblocks + blockIdx.x];
+        base[threadIdx.x] = sum ? atomicAdd(p.counts + threadIdx.x, sum) : 0;
     }
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
     if (t == CLS_CW || t == CLS_MU) {
         const int q = t == CLS_CW ? 0 : 1;
-        const unsigned b = q == 0 ? b1 : b2;
-        int off = base[q];
-        for (int k = 0; k < w; ++k) off += s[q][k];
-        off += __popc(b & lt);
-        queue[q * nc + off] = (int32_t)c;
+        int off = base[q] + __popc((q == 0 ? b1 : b2) & ((1u << lane) - 1u));
+        for (int k = 0; k < w; ++k) off += sc[q][k];
+        p.queue[q * p.nc + off] = (int32_t)c;
     }
 }
 
@@ -948,7 +871,12 @@ template <class C, class T>
 struct FluxShape {
     static constexpr int FG = C::NFMAX <= 4 ? 4 : 8;
     static constexpr int CPB = 128 / FG;
-    static constexpr int MINB = sizeof(T) == 8 ? 4 : C::D == 2 ? 10 : 9;
+    // 2D FP32 with at most two points per face: every face point's states
+    // are loaded before the first Riemann solve (PRE), at eight blocks per
+    // SM (64 registers); 2 % faster per step on the quadrant than ten
+    // blocks with point-by-point loads
+    static constexpr bool PRE = sizeof(T) == 4 && C::D == 2 && C::NFP <= 2;
+    static constexpr int MINB = sizeof(T) == 8 ? 4 : C::D == 2 ? (PRE ? 8 : 10) : 9;
 };
 
 template <class C, class T, int KIND, bool VISC = false, bool CHAIN = false>
@@ -991,6 +919,14 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
     const T ivol = valid ? p.ivol[cs] : T(0);
     T linv = T(0);
     if (VISC && valid && f < C::NFMAX) linv = p.LINV[cs * 6 + f];
+    // quadrature weights x face area (constant): ahead of the wait where
+    // every face point is preloaded
+    constexpr bool PRE = FluxShape<C, T>::PRE && !VISC;
+    T wqa[PRE ? NFP : 1];
+    if constexpr (PRE) {
+#pragma unroll
+        for (int a = 0; a < NFP; ++a) wqa[a] = nb != -2 ? p.W[cs * C::QMAX + f * NFP + a] : T(0);
+    }
     // the chained time step's geometry, loaded here: after the state stores
     // below the compiler could not move these loads ahead of them, and each
     // block would wait on two more memory round trips at its end
@@ -1014,17 +950,38 @@ __global__ void __launch_bounds__(128, FluxShape<C, T>::MINB) k_flux(KParams<T> 
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
     if (nb != -2) {
         const int64_t q = cs * C::QMAX + f * NFP;
+        constexpr int NP = PRE ? NFP : 1;
+        T WL[NP][NV], WR[NP][NV];
+        if constexpr (PRE) {
+#pragma unroll
+            for (int a = 0; a < NFP; ++a) {
+                load_state<T, NV>(p.FS + (q + a) * NV, WL[a]);
+                if (nb < 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) WR[a][v] = WL[a][v];
+                } else {
+                    load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, WR[a]);
+                }
+            }
+        }
 #pragma unroll
         for (int a = 0; a < NFP; ++a) {
             T wl[NV], wr[NV], F[NV];
-            load_state<T, NV>(p.FS + (q + a) * NV, wl);
-            if (nb < 0) {
+            if constexpr (PRE) {
 #pragma unroll
-                for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+                for (int v = 0; v < NV; ++v) { wl[v] = WL[a][v]; wr[v] = WR[a][v]; }
             } else {
-                load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
+                load_state<T, NV>(p.FS + (q + a) * NV, wl);
+                if (nb < 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) wr[v] = wl[v];
+                } else {
+                    load_state<T, NV>(p.FS + ((int64_t)nb + a) * NV, wr);
+                }
             }
-            const T wq = p.W[q + a];
+            T wq;
+            if constexpr (PRE) wq = wqa[a];
+            else wq = p.W[q + a];
             riemann<T, D, KIND>(wl, wr, nn, p.gamma, F);
             if constexpr (VISC) {
                 // minus the viscous flux (eq. EulerEquationsDetails); an open
@@ -1209,7 +1166,7 @@ KParams<T> make_params(hfv_scheme* s, const uint8_t* forced)
     p.nfp = s->nfp;
     p.qmax = s->nfmax * s->nfp;
     p.FS = (T*)a.FS; p.raw = a.raw; p.cls = a.cls; p.queue = a.queue; p.counts = a.counts;
-    p.bcount = a.bcount; p.nblocks = s->nblocks; p.status = a.status;
+    p.status = a.status;
     p.gamma = (T)s->p.gamma; p.alpha_m = (T)s->p.alpha_m; p.beta_m = (T)s->p.beta_m;
     p.alpha_w = (T)s->p.alpha_w; p.beta_w = (T)s->p.beta_w;
     p.lam1 = (T)(1.0 - 1.0 / s->p.lambda1_prime);
@@ -1323,12 +1280,6 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
     }
     const bool visc = s->p.mu0 > 0.0;
     { Launch l(s, KID_TAG, st); pdl(k_tag<T>, s->nblocks, 256, 0, st, p); }
-    const int fold = s->nblocks <= 1024;
-    if (!fold) { Launch l(s, KID_SCAN, st); pdl(k_scan, 1, 1024, 0, st, s->a.bcount, s->nblocks, s->a.counts); }
-    {
-        Launch l(s, KID_SCATTER, st);
-        pdl(k_scatter, s->nblocks, 256, 0, st, s->a.cls, nc, s->a.bcount, s->nblocks, s->a.queue, s->a.counts, fold);
-    }
     {
         // CWENOZ cells cost several times a MUSCL cell: by default 3/4 of the
         // blocks take the CWENOZ queue

@@ -110,7 +110,7 @@ int build_operators(hfv_scheme* s, void* stream)
            o_ivol = take(nc * b), o_thr = take(nc * b);
     size_t o_vol = take(nc * 8), o_area = take(nc * 6 * 8), o_nrm64 = take(nc * 18 * 8);
     size_t o_FS = take(qt * nv * b), o_raw = take(nc), o_cls = take(nc), o_queue = take(2 * nc * 4), o_counts = take(64),
-           o_bcount = take(2 * (size_t)s->nblocks * 4), o_status = take(64);
+           o_status = take(64);
     size_t o_U1 = take(nv * nc * 8), o_U2 = take(nv * nc * 8), o_Rs = take(nv * nc * b), o_UA = take(nc * (nv == 4 ? 4 : 8) * b), o_UB = take(nc * (nv == 4 ? 4 : 8) * b),
            o_areaT = take(nc * 6 * b),
            o_dt = take(std::max<int64_t>(64, 8 * (int64_t)s->nseg)), o_dtn = take(8 * kDtSlots * kDtStride * (int64_t)s->nseg),
@@ -134,7 +134,7 @@ int build_operators(hfv_scheme* s, void* stream)
     a.nrm = A + o_nrm; a.ivol = A + o_ivol; a.dxthr = A + o_thr;
     a.vol = (double*)(A + o_vol); a.area = (double*)(A + o_area); a.nrm64 = (double*)(A + o_nrm64);
     a.FS = A + o_FS; a.raw = (uint8_t*)(A + o_raw); a.cls = (uint8_t*)(A + o_cls); a.queue = (int32_t*)(A + o_queue);
-    a.counts = (int32_t*)(A + o_counts); a.bcount = (int32_t*)(A + o_bcount); a.status = (int*)(A + o_status);
+    a.counts = (int32_t*)(A + o_counts); a.status = (int*)(A + o_status);
     a.U1 = (double*)(A + o_U1); a.U2 = (double*)(A + o_U2); a.Rs = A + o_Rs; a.UA = A + o_UA; a.UB = A + o_UB; a.areaT = A + o_areaT;
     a.dt = (double*)(A + o_dt);
     a.dt_next = (double*)(A + o_dtn);
