@@ -8,11 +8,16 @@
 //      face point.  W_cq enters the cell's own flux evaluation as the left
 //      state and the neighbour's evaluation of the same face as the right
 //      state (each face is evaluated by both cells), so
-//        mu_cq = -w_q [ J_L(W_cq, W_nq, n)^T lam_c / |V_c|
-//                     + J_R(W_nq, W_cq, -n)^T lam_n / |V_n| ],
+//        mu_cq = -w_q J_L(W_cq, W_nq, n)^T lam_c / |V_c|
+//                - w'_q J_R(W_nq, W_cq, -n)^T lam_n / |V_n|,
 //      with J_L + J_R at an open boundary (outside state = inside state).
-//      The Riemann Jacobians come from the solver itself evaluated on dual
-//      numbers (the wave pattern taken as in the plain evaluation).
+//      The Rusanov, HLL and HLLC fluxes are conservative under the exchange
+//      of the sides, F(b, a, -n) = -F(a, b, n) (the wave speeds map to
+//      minus each other), so J_R(W_nq, W_cq, -n) = -J_L(W_cq, W_nq, n) and
+//        mu_cq = J_L(W_cq, W_nq, n)^T (w'_q lam_n / |V_n| - w_q lam_c / |V_c|):
+//      one Jacobian per face point.  It comes from the solver itself
+//      evaluated on dual numbers (the wave pattern taken as in the plain
+//      evaluation).
 //   2. The face states per class (the detector, tagging and Harten decisions
 //      frozen):
 //        LINEAR (Sec. 2.1)  W_q = U_0 + sum_m L_qm (U_m - U_0):
@@ -138,24 +143,14 @@ __global__ void __launch_bounds__(128) k_flux_vjp(AdjParams p)
     } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) wr[v] = p.FS[((int64_t)nb + a) * NV + v];
-        flux_jt<D, KIND>(wl, wr, n, p.gamma, lc, 0, mu);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) mu[v] *= -wq * p.ivol[c];
-        // the neighbour's evaluation of this face: its state left, ours right
+        // the cell's and the neighbour's weights of this face point, through
+        // the one Jacobian of the cell's own evaluation
         const int64_t j = p.nbr[c * 6 + f];
-        const int fj = p.nbrf[c * 6 + f];
-        double lj[NV], nj[3], mj[NV];
+        const double sc = -wq * p.ivol[c], sj = p.W[(int64_t)nb + a] * p.ivol[j];
+        double y[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            lj[v] = p.lam[(int64_t)v * p.nc + j];
-            mj[v] = 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) nj[k] = p.nrm[(j * 6 + fj) * 3 + k];
-        flux_jt<D, KIND>(wr, wl, nj, p.gamma, lj, 1, mj);
-        const double s = -p.W[(int64_t)nb + a] * p.ivol[j];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) mu[v] += s * mj[v];
+        for (int v = 0; v < NV; ++v) y[v] = sc * lc[v] + sj * p.lam[(int64_t)v * p.nc + j];
+        flux_jt<D, KIND>(wl, wr, n, p.gamma, y, 0, mu);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) p.MU[q * NV + v] = mu[v];
@@ -362,17 +357,14 @@ __device__ void muscl_var(const AdjParams& p, int64_t c, int nf, int n1, const S
 
 constexpr int kTan = 8;   // tangents per dual evaluation
 
-// one thread per (queued cell, variable, chunk of kTan inputs): inputs are
+// one item per (queued cell, variable, chunk of kTan inputs): inputs are
 // U_0 (index 0) and the stencil values U_m (index m + 1)
 template <class C>
-__global__ void __launch_bounds__(64) k_recon_nl_vjp(AdjParams p, int which)
+__device__ void nl_vjp_item(const AdjParams& p, int which, int64_t t)
 {
     constexpr int NV = C::NV, M = C::M, NFP = C::NFP, P4 = AoS<NV>::P;
     constexpr int NCH = (M + 1 + kTan - 1) / kTan;
     using S = Dual<kTan>;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cnt = p.counts[which];
-    if (t >= (int64_t)cnt * NV * NCH) return;
     const int ch = (int)(t % NCH);
     const int v = (int)((t / NCH) % NV);
     const int64_t c = p.queue[which * p.nc + t / (NCH * NV)];
@@ -401,6 +393,17 @@ __global__ void __launch_bounds__(64) k_recon_nl_vjp(AdjParams p, int which)
         if (e == 0) p.S0[c * NV + v] = s;
         else p.A[(c * M + (e - 1)) * NV + v] = s;
     }
+}
+
+// the items of one queue, the grid striding over them (the queue length is
+// on the device: a grid sized for the worst case would be mostly empty)
+template <class C>
+__global__ void __launch_bounds__(64) k_recon_nl_vjp(AdjParams p, int which)
+{
+    constexpr int NCH = (C::M + 1 + kTan - 1) / kTan;
+    const int64_t n = (int64_t)p.counts[which] * C::NV * NCH;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        nl_vjp_item<C>(p, which, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -448,9 +451,16 @@ int run_vjp(hfv_scheme* s, const double* lam, double* g, cudaStream_t st)
     }
     note_launch();
     k_recon_lin_vjp<C><<<(unsigned)((nc + 3) / 4), 128, 0, st>>>(p);
-    // queued cells: at most nc per queue (the count itself lives on the device)
+    // queued cells: at most nc per queue (the count itself lives on the
+    // device); at most 64 blocks of 64 threads per SM, striding
     constexpr int NCH = (C::M + 1 + kTan - 1) / kTan;
-    const unsigned gn = (unsigned)((nc * C::NV * NCH + 63) / 64);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 1;
+    }
+    const unsigned gn = (unsigned)std::min<int64_t>((nc * C::NV * NCH + 63) / 64, (int64_t)sms * 32);
     for (int which = 0; which < 2; ++which) {
         note_launch();
         k_recon_nl_vjp<C><<<gn, 64, 0, st>>>(p, which);
