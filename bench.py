@@ -717,6 +717,27 @@ def adjoint_variants(H, I, torch, dev, args):
     e1.record()
     torch.cuda.synchronize(dev)
     res_ms = e0.elapsed_time(e1) / reps
+    # one VJP with the per-kernel timer (events around every launch): the
+    # forward residual it re-evaluates and the three VJP kernel families
+    g.kernel_timer(True)
+    g.kernel_times(reset=True)
+    g.residual_vjp(U, cls, lam)
+    torch.cuda.synchronize(dev)
+    kt = {k: v[0] for k, v in g.kernel_times(reset=True).items() if v[1]}
+    g.kernel_timer(False)
+    vjp_kernels = {k: round(v, 4) for k, v in kt.items() if k.startswith("vjp_")}
+    vjp_kernels["forward_residual"] = round(sum(v for k, v in kt.items() if not k.startswith("vjp_")), 4)
+    # the stencil gather of the VJP reads, per cell, its own contribution
+    # S0 (nv doubles), its inverse-map range (8 bytes) and M (index, nv
+    # doubles) contributions, and writes nv doubles of the gradient
+    nv, M = U.shape[0], g.M
+    b_gather = (2 * nv * 8 + 8 + M * (4 + nv * 8)) * m.n_cells
+    peak, _ = _peaks()
+    gather = None
+    if "vjp_gather" in kt:
+        gbs = b_gather / (kt["vjp_gather"] * 1e-3) / 1e9
+        gather = {"bound": "hbm", "algorithmic_bytes": int(b_gather), "achieved": gbs, "peak": peak, "unit": "GB/s",
+                  "frac": gbs / peak}
     hist = np.bincount(cls.cpu().numpy(), minlength=4).tolist()
     # central differences of the same trajectory (h = 1e-6)
     ccls, W = [], U.clone()
@@ -745,7 +766,9 @@ def adjoint_variants(H, I, torch, dev, args):
             "fd_check": fd_check,
             "cells": int(m.n_cells), "steps": args.adjoint_steps, "objective": "sum |V| rho^2 after the steps",
             "J": Jv, "grad_norm": float(dJ.norm().item()), "classes_at_start": hist,
-            "forward_plus_backward_s": total, "vjp_ms": vjp_ms, "residual_ms": res_ms,
+            "forward_plus_backward_s": total, "vjp_ms": vjp_ms, "residual_ms": res_ms, "vjp_over_residual": vjp_ms / res_ms,
+            "vjp_kernels_ms": vjp_kernels, "vjp_gather_roofline": gather,
+            "flux_vjp_ns_per_face_point": (kt["vjp_flux"] * 1e6 / (m.n_cells * 4 * g.nfp)) if "vjp_flux" in kt else None,
             "vjp_cells_per_s": m.n_cells / (vjp_ms * 1e-3), "checkpoint_bytes": int(args.adjoint_steps * U.numel() * 8)}
 
 

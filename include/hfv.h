@@ -373,7 +373,9 @@ HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
  * outputs, 16 entries each): ms[k] total milliseconds and launches[k] count
  * of kernel k: 0 linear candidate + detector, 1 tagging and queue
  * compaction, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage, 9 time
- * step, 10 FP32 conversion, 11 viscous gradients (2, 3, 4: no kernel).  reset != 0 zeroes the totals after
+ * step, 10 FP32 conversion, 11 viscous gradients, 12 flux VJP, 13
+ * reconstruction VJPs (linear and first-order cells, CWENOZ and MUSCL
+ * queues), 14 stencil gather of the VJP (2, 3, 4: no kernel).  reset != 0 zeroes the totals after
  * reading.  sync. */
 HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset);
 

@@ -15,18 +15,18 @@
 //      of the sides, F(b, a, -n) = -F(a, b, n) (the wave speeds map to
 //      minus each other), so J_R(W_nq, W_cq, -n) = -J_L(W_cq, W_nq, n) and
 //        mu_cq = J_L(W_cq, W_nq, n)^T (w'_q lam_n / |V_n| - w_q lam_c / |V_c|):
-//      one Jacobian per face point.  It comes from the solver itself
-//      evaluated on dual numbers (the wave pattern taken as in the plain
+//      one vector-Jacobian product per face point, by the reverse mode of
+//      the solver (riemann_vjp; the wave pattern taken as in the plain
 //      evaluation).
 //   2. The face states per class (the detector, tagging and Harten decisions
 //      frozen):
 //        LINEAR (Sec. 2.1)  W_q = U_0 + sum_m L_qm (U_m - U_0):
 //          a_cm = sum_q L_qm mu_cq,  a_c0 = sum_q mu_cq - sum_m a_cm
 //        FIRST              W_q = U_0:  a_c0 = sum_q mu_cq
-//        CWENOZ (Sec. 2.3), MUSCL + Barth-Jespersen (Sec. 2.2): the
-//          per-variable reconstruction re-evaluated on dual numbers seeded
-//          on U_0 and the stencil values, limiter bounds and minima taken as
-//          in the plain evaluation.
+//        CWENOZ (Sec. 2.3), MUSCL + Barth-Jespersen or Venkatakrishnan
+//          (Sec. 2.2): the reverse mode of the per-variable reconstruction,
+//          one thread per (cell, variable), limiter bounds and minima taken
+//          as in the plain evaluation.
 //      a_cm is the contribution to the m-th stencil cell of c.
 //   3. k_gather_vjp: g_j = a_j0 + sum over the (c, m) with sten[c][m] = j of
 //      a_cm, in ascending (c, m): deterministic, no atomics.
@@ -36,9 +36,9 @@
 #include <string>
 #include <vector>
 
-#include "dual.cuh"
 #include "hfv_internal.h"
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace hfv {
 namespace {
@@ -86,30 +86,208 @@ struct AoS {
 // ---------------------------------------------------------------------------
 // 1. Riemann flux
 // ---------------------------------------------------------------------------
+// Reverse mode of riemann<double, D, KIND> (physics.cuh): gL += (dF/dUL)^T y
+// and gR += (dF/dUR)^T y at (UL, UR, n), every branch taken as in the plain
+// evaluation.  The plain statements are recomputed first; then each one's
+// adjoint, last to first (x_b denotes dJ/dx for J = y . F).
 template <int D, int KIND>
-__device__ void flux_jt(const double* WL, const double* WR, const double* n, double g, const double* lam, int which,
-                        double* out)
+__device__ __forceinline__ void riemann_vjp(const double* UL, const double* UR, const double* n, double g,
+                                            const double* y, double* gL, double* gR)
 {
-    // out += J^T lam, J = dF/dW_L (which = 0), dF/dW_R (1), or both (2)
     constexpr int NV = D + 2;
-    using DT = Dual<NV>;
-    DT L[NV], R[NV], nn[3], F[NV];
+    // ---- plain evaluation ----
+    const double il = 1.0 / UL[0], ir = 1.0 / UR[0];
+    double ml2 = 0.0, mr2 = 0.0, mnl = 0.0, mnr = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        ml2 += UL[1 + k] * UL[1 + k];
+        mr2 += UR[1 + k] * UR[1 + k];
+        mnl += UL[1 + k] * n[k];
+        mnr += UR[1 + k] * n[k];
+    }
+    const double unl = mnl * il, unr = mnr * ir;
+    const double pl = (g - 1.0) * (UL[D + 1] - 0.5 * ml2 * il);
+    const double pr = (g - 1.0) * (UR[D + 1] - 0.5 * mr2 * ir);
+    double FL[NV], FR[NV];
+    FL[0] = mnl;
+    FR[0] = mnr;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        FL[1 + k] = UL[1 + k] * unl + pl * n[k];
+        FR[1 + k] = UR[1 + k] * unr + pr * n[k];
+    }
+    FL[D + 1] = (UL[D + 1] + pl) * unl;
+    FR[D + 1] = (UR[D + 1] + pr) * unr;
+    const double cl = ::sqrt(g * pl * il), cr = ::sqrt(g * pr * ir);
+    // ---- adjoints ----
+    double FL_b[NV], FR_b[NV], UL_b[NV], UR_b[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { FL_b[v] = 0.0; FR_b[v] = 0.0; UL_b[v] = 0.0; UR_b[v] = 0.0; }
+    double unl_b = 0.0, unr_b = 0.0, pl_b = 0.0, pr_b = 0.0, cl_b = 0.0, cr_b = 0.0, il_b = 0.0, ir_b = 0.0;
+    if (KIND == kRusanov) {
+        // F = (FL + FR) / 2 - s (UR - UL) / 2,  s = max(|unl| + cl, |unr| + cr)
+        const double al = (unl < 0.0 ? -unl : unl) + cl, ar = (unr < 0.0 ? -unr : unr) + cr;
+        const double sp = al > ar ? al : ar;
+        double s_b = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            FL_b[v] += 0.5 * y[v];
+            FR_b[v] += 0.5 * y[v];
+            UR_b[v] -= 0.5 * sp * y[v];
+            UL_b[v] += 0.5 * sp * y[v];
+            s_b -= 0.5 * y[v] * (UR[v] - UL[v]);
+        }
+        if (al > ar) {
+            unl_b += unl < 0.0 ? -s_b : s_b;
+            cl_b += s_b;
+        } else {
+            unr_b += unr < 0.0 ? -s_b : s_b;
+            cr_b += s_b;
+        }
+    } else {
+        const bool lmin = unl - cl < unr - cr, rmax = unl + cl > unr + cr;
+        const double SL = lmin ? unl - cl : unr - cr, SR = rmax ? unl + cl : unr + cr;
+        double SL_b = 0.0, SR_b = 0.0;
+        if (SL >= 0.0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FL_b[v] += y[v];
+        } else if (SR <= 0.0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) FR_b[v] += y[v];
+        } else if (KIND == kHLL) {
+            // F = N inv,  N = SR FL - SL FR + SL SR (UR - UL),  inv = 1 / (SR - SL)
+            const double inv = 1.0 / (SR - SL);
+            double inv_b = 0.0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double dU = UR[v] - UL[v];
+                const double N = SR * FL[v] - SL * FR[v] + SL * SR * dU;
+                const double N_b = y[v] * inv;
+                inv_b += y[v] * N;
+                FL_b[v] += SR * N_b;
+                FR_b[v] -= SL * N_b;
+                UR_b[v] += SL * SR * N_b;
+                UL_b[v] -= SL * SR * N_b;
+                SR_b += N_b * (FL[v] + SL * dU);
+                SL_b += N_b * (SR * dU - FR[v]);
+            }
+            SR_b -= inv * inv * inv_b;
+            SL_b += inv * inv * inv_b;
+        } else {
+            // HLLC: the contact speed and the star state on its upwind side K
+            const double ml = UL[0] * (SL - unl), mr = UR[0] * (SR - unr);
+            const double num = pr - pl + ml * unl - mr * unr, rden = 1.0 / (ml - mr);
+            const double Ss = num * rden;
+            const bool left = Ss >= 0.0;
+            const double* UK = left ? UL : UR;
+            const double* FK = left ? FL : FR;
+            const double SK = left ? SL : SR, unk = left ? unl : unr, pk = left ? pl : pr, mk = left ? ml : mr;
+            const double ik = left ? il : ir;
+            const double rS = 1.0 / (SK - Ss), fac = mk * rS, dS = Ss - unk, rm = 1.0 / mk;
+            const double E1 = UK[D + 1] * ik + dS * (Ss + pk * rm), Es = fac * E1;
+            double FK_b[NV], UK_b[NV];
+            double SK_b = 0.0, fac_b = 0.0, ik_b = 0.0, dS_b = 0.0;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { FK_b[v] = y[v]; UK_b[v] = 0.0; }
+            // F[1+k] = FK[1+k] + SK (fac (UK[1+k] ik + dS n_k) - UK[1+k])
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double yk = y[1 + k], inner = UK[1 + k] * ik + dS * n[k];
+                SK_b += yk * (fac * inner - UK[1 + k]);
+                fac_b += yk * SK * inner;
+                UK_b[1 + k] += yk * SK * (fac * ik - 1.0);
+                ik_b += yk * SK * fac * UK[1 + k];
+                dS_b += yk * SK * fac * n[k];
+            }
+            // F[0] = FK[0] + SK (fac - UK[0])
+            SK_b += y[0] * (fac - UK[0]);
+            fac_b += y[0] * SK;
+            UK_b[0] -= y[0] * SK;
+            // F[D+1] = FK[D+1] + SK (Es - UK[D+1]),  Es = fac E1
+            SK_b += y[D + 1] * (Es - UK[D + 1]);
+            UK_b[D + 1] -= y[D + 1] * SK;
+            const double Es_b = y[D + 1] * SK;
+            fac_b += Es_b * E1;
+            const double E1_b = Es_b * fac;
+            // E1 = UK[D+1] ik + dS (Ss + pk rm)
+            UK_b[D + 1] += E1_b * ik;
+            ik_b += E1_b * UK[D + 1];
+            dS_b += E1_b * (Ss + pk * rm);
+            double Ss_b = E1_b * dS;
+            const double pk_b = E1_b * dS * rm;
+            double mk_b = -rm * rm * (E1_b * dS * pk);
+            // dS = Ss - unk;  fac = mk rS;  rS = 1 / (SK - Ss)
+            Ss_b += dS_b;
+            const double unk_b = -dS_b;
+            mk_b += fac_b * rS;
+            const double rS_b = fac_b * mk;
+            SK_b -= rS * rS * rS_b;
+            Ss_b += rS * rS * rS_b;
+            // Ss = num rden;  rden = 1 / (ml - mr);  num = pr - pl + ml unl - mr unr
+            const double num_b = Ss_b * rden, den_b = -rden * rden * (Ss_b * num);
+            double ml_b = den_b + num_b * unl, mr_b = -den_b - num_b * unr;
+            pr_b += num_b;
+            pl_b -= num_b;
+            unl_b += num_b * ml;
+            unr_b -= num_b * mr;
+            // the upwind side's quantities back to their own side
+            if (left) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { FL_b[v] += FK_b[v]; UL_b[v] += UK_b[v]; }
+                SL_b += SK_b; unl_b += unk_b; pl_b += pk_b; ml_b += mk_b; il_b += ik_b;
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { FR_b[v] += FK_b[v]; UR_b[v] += UK_b[v]; }
+                SR_b += SK_b; unr_b += unk_b; pr_b += pk_b; mr_b += mk_b; ir_b += ik_b;
+            }
+            // ml = UL0 (SL - unl),  mr = UR0 (SR - unr)
+            UL_b[0] += ml_b * (SL - unl);
+            SL_b += ml_b * UL[0];
+            unl_b -= ml_b * UL[0];
+            UR_b[0] += mr_b * (SR - unr);
+            SR_b += mr_b * UR[0];
+            unr_b -= mr_b * UR[0];
+        }
+        // SL = min(unl - cl, unr - cr),  SR = max(unl + cl, unr + cr)
+        if (lmin) { unl_b += SL_b; cl_b -= SL_b; } else { unr_b += SL_b; cr_b -= SL_b; }
+        if (rmax) { unl_b += SR_b; cl_b += SR_b; } else { unr_b += SR_b; cr_b += SR_b; }
+    }
+    // the sides' fluxes, sound speeds, pressures and normal velocities
+    auto side = [&](const double* U, double i, double un, double p, double c, double m2, double mn, const double* F_b,
+                    double un_b, double p_b, double c_b, double i_b, double* U_b) {
+        // F[0] = mn;  F[1+k] = U[1+k] un + p n_k;  F[D+1] = (U[D+1] + p) un
+        double mn_b = F_b[0];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            U_b[1 + k] += F_b[1 + k] * un;
+            un_b += F_b[1 + k] * U[1 + k];
+            p_b += F_b[1 + k] * n[k];
+        }
+        U_b[D + 1] += F_b[D + 1] * un;
+        p_b += F_b[D + 1] * un;
+        un_b += F_b[D + 1] * (U[D + 1] + p);
+        // c = sqrt(g p i)
+        const double z_b = c_b * 0.5 / c;
+        p_b += z_b * g * i;
+        i_b += z_b * g * p;
+        // p = (g - 1) (U[D+1] - m2 i / 2)
+        U_b[D + 1] += (g - 1.0) * p_b;
+        const double m2_b = -0.5 * (g - 1.0) * i * p_b;
+        i_b -= 0.5 * (g - 1.0) * m2 * p_b;
+        // un = mn i
+        mn_b += un_b * i;
+        i_b += un_b * mn;
+        // mn = sum_k U[1+k] n_k;  m2 = sum_k U[1+k]^2;  i = 1 / U[0]
+#pragma unroll
+        for (int k = 0; k < D; ++k) U_b[1 + k] += mn_b * n[k] + 2.0 * U[1 + k] * m2_b;
+        U_b[0] -= i * i * i_b;
+    };
+    side(UL, il, unl, pl, cl, ml2, mnl, FL_b, unl_b, pl_b, cl_b, il_b, UL_b);
+    side(UR, ir, unr, pr, cr, mr2, mnr, FR_b, unr_b, pr_b, cr_b, ir_b, UR_b);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        L[v] = DT(WL[v]);
-        R[v] = DT(WR[v]);
-        if (which == 0 || which == 2) L[v].d[v] = 1.0;
-        if (which == 1 || which == 2) R[v].d[v] = 1.0;
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) nn[k] = DT(n[k]);
-    riemann<DT, D, KIND>(L, R, nn, DT(g), F);
-#pragma unroll
-    for (int j = 0; j < NV; ++j) {
-        double s = 0.0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s += lam[v] * F[v].d[j];
-        out[j] += s;
+        gL[v] += UL_b[v];
+        gR[v] += UR_b[v];
     }
 }
 
@@ -137,9 +315,13 @@ __global__ void __launch_bounds__(128) k_flux_vjp(AdjParams p)
     for (int k = 0; k < 3; ++k) n[k] = p.nrm[(c * 6 + f) * 3 + k];
     const double wq = p.W[q];
     if (nb < 0) {
-        flux_jt<D, KIND>(wl, wl, n, p.gamma, lc, 2, mu);
+        // open boundary: the outside state is the inside one, J_L + J_R
+        double gr[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) mu[v] *= -wq * p.ivol[c];
+        for (int v = 0; v < NV; ++v) gr[v] = 0.0;
+        riemann_vjp<D, KIND>(wl, wl, n, p.gamma, lc, mu, gr);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) mu[v] = (mu[v] + gr[v]) * (-wq * p.ivol[c]);
     } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) wr[v] = p.FS[((int64_t)nb + a) * NV + v];
@@ -150,180 +332,230 @@ __global__ void __launch_bounds__(128) k_flux_vjp(AdjParams p)
         double y[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) y[v] = sc * lc[v] + sj * p.lam[(int64_t)v * p.nc + j];
-        flux_jt<D, KIND>(wl, wr, n, p.gamma, y, 0, mu);
+        double gr[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) gr[v] = 0.0;
+        riemann_vjp<D, KIND>(wl, wr, n, p.gamma, y, mu, gr);   // gr unused: dropped by the compiler
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) p.MU[q * NV + v] = mu[v];
 }
 
 // ---------------------------------------------------------------------------
-// 2. face states: linear and first-order cells, one warp per cell
+// 2. face states: linear and first-order cells
 // ---------------------------------------------------------------------------
 // L_qm in a cell's block (FP64: column chunks of two, [M/2][Q][2])
 __device__ __forceinline__ double l_at(const double* Lc, int q, int m, int Q) { return Lc[(m >> 1) * Q * 2 + q * 2 + (m & 1)]; }
 
+// one thread per (cell, variable): a_cm = sum_q L_qm mu_cq for every m, and
+// a_c0 = sum_q mu_cq - sum_m a_cm (FP64 instructions are this GPU's scarce
+// resource: no lane idles on a short stencil and no sum goes through shuffles)
 template <class C>
 __global__ void __launch_bounds__(128) k_recon_lin_vjp(AdjParams p)
 {
     constexpr int NV = C::NV, M = C::M, NFP = C::NFP;
-    const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (c >= p.nc) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.nc * NV) return;
+    const int64_t c = t / NV;
+    const int v = (int)(t - c * NV);
     const int cl = p.cls[c];
     const int Q = (p.nfc[c] & 15) * NFP;
-    const double* mu = p.MU + c * C::QMAX * NV;
-    double* A = p.A + c * M * NV;
-    double sq[NV], sa[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { sq[v] = 0.0; sa[v] = 0.0; }
-    for (int q = lane; q < Q; q += 32)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sq[v] += mu[q * NV + v];
-    const double* Lc = p.L + p.loff[c];
-    for (int m = lane; m < M; m += 32) {
-        double am[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) am[v] = 0.0;
-        if (cl == CLS_LIN) {
-            for (int q = 0; q < Q; ++q) {
-                const double l = l_at(Lc, q, m, Q);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) am[v] += l * mu[q * NV + v];
-            }
+    const double* mu = p.MU + c * C::QMAX * NV + v;
+    double* A = p.A + c * M * NV + v;
+    double sq = 0.0;
+    for (int q = 0; q < Q; ++q) sq += mu[q * NV];
+    double sa = 0.0;
+    if (cl == CLS_LIN) {
+        const double* Lc = p.L + p.loff[c];
+        for (int m = 0; m < M; ++m) {
+            double am = 0.0;
+            for (int q = 0; q < Q; ++q) am += l_at(Lc, q, m, Q) * mu[q * NV];
+            A[m * NV] = am;
+            sa += am;
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            A[m * NV + v] = am[v];
-            sa[v] += am[v];
-        }
+    } else {
+        for (int m = 0; m < M; ++m) A[m * NV] = 0.0;
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            sq[v] += __shfl_xor_sync(0xffffffffu, sq[v], o);
-            sa[v] += __shfl_xor_sync(0xffffffffu, sa[v], o);
-        }
-    if (lane < NV) {
-        double x = 0.0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-            if (v == lane) x = (cl == CLS_LIN || cl == CLS_FIRST) ? sq[v] - sa[v] : 0.0;
-        p.S0[c * NV + lane] = x;
-    }
+    p.S0[c * NV + v] = (cl == CLS_LIN || cl == CLS_FIRST) ? sq - sa : 0.0;
 }
 
 // ---------------------------------------------------------------------------
-// 2. face states: CWENOZ and MUSCL cells, dual numbers
+// 2. face states: CWENOZ and MUSCL cells, reverse mode
 // ---------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ T dabs(const T& x) { return x < 0.0 ? -x : x; }
-template <class T>
-__device__ __forceinline__ T dmin(const T& a, const T& b) { return a < b ? a : b; }
-template <class T>
-__device__ __forceinline__ T dmax(const T& a, const T& b) { return a > b ? a : b; }
-__device__ __forceinline__ double tpow(double x, double e) { return pow(x, e); }
-
-// CWENOZ face values of one variable (Sec. 2.3), as the forward kernel forms
-// them: p_opt from P, the directional degree-1 polynomials from D, p_1,
-// the indicators through OI, tau and the weights, and
-// W_q = U_0 + (omega_1 / lambda_1) (p_opt(x_q) - U_0) + sum_k Phi_qk G_k
-template <class C, class S>
-__device__ void cweno_var(const AdjParams& p, int64_t c, int nf, const S& u0, const S* um, S* w)
+// Reverse mode of the CWENOZ face values of one variable (Sec. 2.3), formed
+// as the forward kernel forms them: p_opt from P, the directional degree-1
+// polynomials from D, p_1, the indicators through OI, tau and the weights,
+// and
+//   W_q = U_0 + (omega_1 / lambda_1) lin_q + sum_k Phi_qk g_k,
+//   lin_q = sum_m L_qm (U_m - U_0),  g_k = sum_s coef_s sd_sk.
+// Given wb[q] = dJ/dW_q, returns dJ/dU_0 and dJ/dU_m.  The plain values are
+// evaluated first, then the adjoints last to first (x_b = dJ/dx); |x| takes
+// slope +1 at 0 and tau = x^b slope b x^(b-1) (1 at x = 0 for b = 1).
+template <class C>
+__device__ void cweno_var_vjp(const AdjParams& p, int64_t c, int nf, double u0, const double* um, const double* wb,
+                              double& u0_b, double* um_b)
 {
     constexpr int M = C::M, N = C::N, D = C::D, MD = C::MD, NFP = C::NFP;
-    S du[M];
+    // ---- plain values ----
+    double du[M];
     for (int m = 0; m < M; ++m) du[m] = um[m] - u0;
-    S a[N];
     const double* P = p.P + c * (int64_t)N * M;
+    double a[N];
     for (int k = 0; k < N; ++k) {
-        S acc(0.0);
+        double acc = 0.0;
         for (int m = 0; m < M; ++m) acc += P[k * M + m] * du[m];
         a[k] = acc;
     }
-    S sd[6][D];
+    double sd[6][D];
     for (int f = 0; f < nf; ++f)
         for (int k = 0; k < D; ++k) {
             const uint8_t* idx = p.dir + (c * 6 + f) * MD;
             const double* Dm = p.Dd + ((c * 6 + f) * D + k) * (int64_t)MD;
-            S acc(0.0);
+            double acc = 0.0;
             for (int b = 0; b < MD; ++b) acc += Dm[b] * du[idx[b]];
             sd[f][k] = acc;
         }
-    const double lam1 = p.lam1, lams = (1.0 - lam1) / nf;
+    const double lam1 = p.lam1, lams = (1.0 - lam1) / nf, eps = p.eps_cw;
     const double* OI = p.OI + c * (int64_t)C::NOI;
-    S a1[N];
+    // OI packed by rows of its upper triangle: entry (k, l >= k) at k N - k (k - 1) / 2 + l - k
+    auto oi = [&](int k, int l) { return k <= l ? OI[k * N - k * (k - 1) / 2 + (l - k)] : OI[l * N - l * (l - 1) / 2 + (k - l)]; };
+    double a1[N];
     for (int k = 0; k < N; ++k) {
-        S sl(0.0);
+        double sl = 0.0;
         if (k < D)
             for (int f = 0; f < nf; ++f) sl += sd[f][k];
         a1[k] = (a[k] - lams * sl) / lam1;
     }
-    S si1(0.0);
-    {
-        int o = 0;
-        for (int k = 0; k < N; ++k) {
-            S t = OI[o++] * a1[k];
-            for (int l = k + 1; l < N; ++l) t += 2.0 * OI[o++] * a1[l];
-            si1 += a1[k] * t;
-        }
+    double OIa1[N], si1 = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double t = 0.0;
+        for (int l = 0; l < N; ++l) t += oi(k, l) * a1[l];
+        OIa1[k] = t;
+        si1 += a1[k] * t;
     }
-    S sis[6], tsum(0.0);
+    double sis[6], e[6], OIsd[6][D], tsum = 0.0;
     for (int f = 0; f < nf; ++f) {
-        S s0(0.0);
+        double s0 = 0.0;
         for (int k = 0; k < D; ++k) {
-            const int o = k * N - k * (k - 1) / 2;
-            S t = OI[o] * sd[f][k];
-            for (int l = k + 1; l < D; ++l) t += 2.0 * OI[o + (l - k)] * sd[f][l];
+            double t = 0.0;
+            for (int l = 0; l < D; ++l) t += oi(k, l) * sd[f][l];
+            OIsd[f][k] = t;
             s0 += sd[f][k] * t;
         }
         sis[f] = s0;
-        tsum += dabs(s0 - si1);
+        e[f] = s0 - si1;
+        tsum += e[f] < 0.0 ? -e[f] : e[f];
     }
-    const S tau = tpow(tsum / (double)nf, p.b_cw);
-    const S w1 = lam1 * (1.0 + tau / (p.eps_cw + si1));
-    S wsum = w1, ws[6];
+    const double x = tsum / (double)nf, tau = ::pow(x, p.b_cw);
+    const double w1 = lam1 * (1.0 + tau / (eps + si1));
+    double ws[6], wsum = w1;
     for (int f = 0; f < nf; ++f) {
-        ws[f] = lams * (1.0 + tau / (p.eps_cw + sis[f]));
+        ws[f] = lams * (1.0 + tau / (eps + sis[f]));
         wsum += ws[f];
     }
-    const S om1 = w1 / wsum;
-    const S c0 = om1 / lam1;
-    S gk[D];
-    for (int k = 0; k < D; ++k) {
-        S acc(0.0);
-        for (int f = 0; f < nf; ++f) acc += (ws[f] / wsum - om1 * lams / lam1) * sd[f][k];
-        gk[k] = acc;
-    }
+    const double om1 = w1 / wsum, c0 = om1 / lam1;
+    // ---- adjoints ----
+    // W_q = U_0 + c0 lin_q + sum_k Phi_qk g_k
     const int Q = nf * NFP;
     const double* Lc = p.L + p.loff[c];
+    double du_b[M], gk_b[D], c0_b = 0.0;
+    for (int m = 0; m < M; ++m) du_b[m] = 0.0;
+    for (int k = 0; k < D; ++k) gk_b[k] = 0.0;
+    u0_b = 0.0;
     for (int q = 0; q < Q; ++q) {
-        S lin(0.0);
-        for (int m = 0; m < M; ++m) lin += l_at(Lc, q, m, Q) * du[m];
-        S s0 = u0 + c0 * lin;
-        for (int k = 0; k < D; ++k) s0 += p.Phil[(c * C::QMAX + q) * D + k] * gk[k];
-        w[q] = s0;
+        const double wq = wb[q], cw = c0 * wq;
+        u0_b += wq;
+        double lin = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double l = l_at(Lc, q, m, Q);
+            lin += l * du[m];
+            du_b[m] += cw * l;
+        }
+        c0_b += wq * lin;
+        for (int k = 0; k < D; ++k) gk_b[k] += wq * p.Phil[(c * C::QMAX + q) * D + k];
+    }
+    // g_k = sum_s coef_s sd_sk,  coef_s = ws_s / wsum - om1 lams / lam1
+    double sd_b[6][D], ws_b[6], wsum_b = 0.0, om1_b = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        const double coef = ws[f] / wsum - om1 * lams / lam1;
+        double coef_b = 0.0;
+        for (int k = 0; k < D; ++k) {
+            sd_b[f][k] = coef * gk_b[k];
+            coef_b += gk_b[k] * sd[f][k];
+        }
+        ws_b[f] = coef_b / wsum;
+        wsum_b -= coef_b * ws[f] / (wsum * wsum);
+        om1_b -= coef_b * lams / lam1;
+    }
+    // c0 = om1 / lam1;  om1 = w1 / wsum;  wsum = w1 + sum_s ws_s
+    om1_b += c0_b / lam1;
+    double w1_b = om1_b / wsum;
+    wsum_b -= om1_b * w1 / (wsum * wsum);
+    w1_b += wsum_b;
+    // ws_s = lams (1 + tau / (eps + SI_s)),  w1 = lam1 (1 + tau / (eps + SI_1))
+    double tau_b = w1_b * lam1 / (eps + si1), si1_b = -w1_b * lam1 * tau / ((eps + si1) * (eps + si1)), sis_b[6];
+    for (int f = 0; f < nf; ++f) {
+        ws_b[f] += wsum_b;
+        tau_b += ws_b[f] * lams / (eps + sis[f]);
+        sis_b[f] = -ws_b[f] * lams * tau / ((eps + sis[f]) * (eps + sis[f]));
+    }
+    // tau = x^b, x = tsum / nf;  tsum = sum_s |SI_s - SI_1|
+    const double slope = x != 0.0 ? p.b_cw * ::pow(x, p.b_cw - 1.0) : (p.b_cw == 1.0 ? 1.0 : 0.0);
+    const double tsum_b = tau_b * slope / (double)nf;
+    for (int f = 0; f < nf; ++f) {
+        const double sg = e[f] < 0.0 ? -tsum_b : tsum_b;
+        sis_b[f] += sg;
+        si1_b -= sg;
+    }
+    // SI_s = sd_s^T OI sd_s (its D x D block);  SI_1 = a1^T OI a1
+    for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < D; ++k) sd_b[f][k] += 2.0 * sis_b[f] * OIsd[f][k];
+    // a1_k = (a_k - lams sum_s sd_sk [k < D]) / lam1
+    double a_b[N];
+    for (int k = 0; k < N; ++k) {
+        const double a1_b = 2.0 * si1_b * OIa1[k];
+        a_b[k] = a1_b / lam1;
+        if (k < D)
+            for (int f = 0; f < nf; ++f) sd_b[f][k] -= lams * a1_b / lam1;
+    }
+    // sd_sk = sum_b Dm_skb du[idx_s[b]];  a_k = sum_m P_km du_m
+    for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < D; ++k) {
+            const uint8_t* idx = p.dir + (c * 6 + f) * MD;
+            const double* Dm = p.Dd + ((c * 6 + f) * D + k) * (int64_t)MD;
+            for (int b = 0; b < MD; ++b) du_b[idx[b]] += Dm[b] * sd_b[f][k];
+        }
+    for (int m = 0; m < M; ++m) {
+        double acc = du_b[m];
+        for (int k = 0; k < N; ++k) acc += P[k * M + m] * a_b[k];
+        um_b[m] = acc;            // du_m = U_m - U_0
+        u0_b -= acc;
     }
 }
 
-// MUSCL face values of one variable (Sec. 2.2): degree-1 gradient from the
-// first Md stencil cells, Barth-Jespersen limiter with bounds over the cell
-// and its face neighbours, one limiter value for all points
-template <class C, class S>
-__device__ void muscl_var(const AdjParams& p, int64_t c, int nf, int n1, const S& u0, const S* um, S* w)
+// Reverse mode of the MUSCL face values of one variable (Sec. 2.2): the
+// degree-1 gradient from the first Md stencil cells, Barth-Jespersen or
+// Venkatakrishnan limiter with bounds over the cell and its face neighbours,
+// one limiter value for all points, W_q = U_0 + theta dl_q.  The minima and
+// maxima take the later operand on ties, as the forward kernel does; the
+// adjoint follows the operand that was taken.
+template <class C>
+__device__ void muscl_var_vjp(const AdjParams& p, int64_t c, int nf, int n1, double u0, const double* um,
+                              const double* wb, double& u0_b, double* um_b)
 {
-    constexpr int D = C::D, MD = C::MD, NFP = C::NFP;
-    S gr[D];
+    constexpr int M = C::M, D = C::D, MD = C::MD, NFP = C::NFP;
     const double* Gm = p.G + c * (int64_t)D * MD;
+    double gr[D];
     for (int k = 0; k < D; ++k) {
-        S acc(0.0);
+        double acc = 0.0;
         for (int b = 0; b < MD; ++b) acc += Gm[k * MD + b] * (um[b] - u0);
         gr[k] = acc;
     }
-    S lo = u0, hi = u0;
+    double lo = u0, hi = u0;
+    int lo_i = -1, hi_i = -1;   // -1: the cell itself
     for (int m = 0; m < n1; ++m) {
-        lo = dmin(lo, um[m]);
-        hi = dmax(hi, um[m]);
+        if (!(lo < um[m])) { lo = um[m]; lo_i = m; }
+        if (!(hi > um[m])) { hi = um[m]; hi_i = m; }
     }
     double eps2 = 0.0;
     if (p.limiter == 1) {
@@ -332,67 +564,96 @@ __device__ void muscl_var(const AdjParams& p, int64_t c, int nf, int n1, const S
         eps2 = kd * kd * kd;
     }
     const int Q = nf * NFP;
-    S th(1.0);
-    S dl[C::QMAX];
+    double dl[C::QMAX];
+    double th = 1.0;
+    int th_q = -1;   // the point whose limiter ratio theta is; -1: theta is the constant 1
     for (int q = 0; q < Q; ++q) {
-        S d0(0.0);
+        double d0 = 0.0;
         for (int k = 0; k < D; ++k) d0 += p.Phil[(c * C::QMAX + q) * D + k] * gr[k];
         dl[q] = d0;
-        S t(1.0);
+        double t = 1.0;
+        bool ratio = false;
         if (p.limiter == 1) {
             if (d0 > 0.0 || d0 < 0.0) {
-                const S d1 = (d0 > 0.0 ? hi : lo) - u0;
-                const S num = (d1 * d1 + eps2) * d0 + 2.0 * d0 * d0 * d1;
-                const S den = d0 * (d1 * d1 + 2.0 * d0 * d0 + d1 * d0 + eps2);
-                t = dmin(S(1.0), num / den);
+                const double d1 = (d0 > 0.0 ? hi : lo) - u0;
+                const double r = ((d1 * d1 + eps2) * d0 + 2.0 * d0 * d0 * d1) / (d0 * (d1 * d1 + 2.0 * d0 * d0 + d1 * d0 + eps2));
+                ratio = !(1.0 < r);
+                t = ratio ? r : 1.0;
             }
-        } else {
-            if (d0 > 0.0) t = dmin(S(1.0), (hi - u0) / d0);
-            else if (d0 < 0.0) t = dmin(S(1.0), (lo - u0) / d0);
+        } else if (d0 > 0.0 || d0 < 0.0) {
+            const double r = ((d0 > 0.0 ? hi : lo) - u0) / d0;
+            ratio = !(1.0 < r);
+            t = ratio ? r : 1.0;
         }
-        th = dmin(th, t);
+        if (!(th < t)) { th = t; th_q = ratio ? q : -1; }
     }
-    for (int q = 0; q < Q; ++q) w[q] = u0 + th * dl[q];
+    // ---- adjoints ----
+    double dl_b[C::QMAX], th_b = 0.0;
+    u0_b = 0.0;
+    for (int m = 0; m < M; ++m) um_b[m] = 0.0;
+    for (int q = 0; q < Q; ++q) {
+        u0_b += wb[q];
+        th_b += wb[q] * dl[q];
+        dl_b[q] = th * wb[q];
+    }
+    if (th_q >= 0) {
+        const double d0 = dl[th_q];
+        const bool up = d0 > 0.0;
+        double ext_b, d0_b;
+        if (p.limiter == 1) {
+            const double d1 = (up ? hi : lo) - u0;
+            const double num = (d1 * d1 + eps2) * d0 + 2.0 * d0 * d0 * d1;
+            const double den = d0 * (d1 * d1 + 2.0 * d0 * d0 + d1 * d0 + eps2);
+            const double num_b = th_b / den, den_b = -th_b * num / (den * den);
+            d0_b = num_b * (d1 * d1 + eps2 + 4.0 * d0 * d1) + den_b * (d1 * d1 + 6.0 * d0 * d0 + 2.0 * d1 * d0 + eps2);
+            ext_b = num_b * (2.0 * d1 * d0 + 2.0 * d0 * d0) + den_b * (2.0 * d0 * d1 + d0 * d0);
+        } else {
+            const double r = ((up ? hi : lo) - u0) / d0;
+            ext_b = th_b / d0;
+            d0_b = -th_b * r / d0;
+        }
+        u0_b -= ext_b;   // d1 (or the bound's gap) = bound - U_0
+        const int ei = up ? hi_i : lo_i;
+        if (ei < 0) u0_b += ext_b;
+        else um_b[ei] += ext_b;
+        dl_b[th_q] += d0_b;
+    }
+    // dl_q = sum_k Phi_qk gr_k;  gr_k = sum_b G_kb (U_b - U_0)
+    double gr_b[D];
+    for (int k = 0; k < D; ++k) {
+        double acc = 0.0;
+        for (int q = 0; q < Q; ++q) acc += p.Phil[(c * C::QMAX + q) * D + k] * dl_b[q];
+        gr_b[k] = acc;
+    }
+    for (int b = 0; b < MD; ++b) {
+        double acc = 0.0;
+        for (int k = 0; k < D; ++k) acc += Gm[k * MD + b] * gr_b[k];
+        um_b[b] += acc;
+        u0_b -= acc;
+    }
 }
 
-constexpr int kTan = 8;   // tangents per dual evaluation
-
-// one item per (queued cell, variable, chunk of kTan inputs): inputs are
-// U_0 (index 0) and the stencil values U_m (index m + 1)
+// one item per (queued cell, variable): the face values' adjoints of that
+// variable back to U_0 (S0) and to the stencil values (A)
 template <class C>
 __device__ void nl_vjp_item(const AdjParams& p, int which, int64_t t)
 {
     constexpr int NV = C::NV, M = C::M, NFP = C::NFP, P4 = AoS<NV>::P;
-    constexpr int NCH = (M + 1 + kTan - 1) / kTan;
-    using S = Dual<kTan>;
-    const int ch = (int)(t % NCH);
-    const int v = (int)((t / NCH) % NV);
-    const int64_t c = p.queue[which * p.nc + t / (NCH * NV)];
+    const int v = (int)(t % NV);
+    const int64_t c = p.queue[which * p.nc + t / NV];
     const int cl = p.cls[c];
     if (cl != (which == 0 ? CLS_CW : CLS_MU)) return;   // fell back to first order: handled as such
     const int nfv = p.nfc[c], nf = nfv & 15, n1 = nfv >> 4, Q = nf * NFP;
-    S u0(p.UA[c * P4 + v]);
-    S um[M];
+    const double u0 = p.UA[c * P4 + v];
+    double um[M], wb[C::QMAX], um_b[M], u0_b;
     const int32_t* st = p.sten + c * M;
-    for (int m = 0; m < M; ++m) um[m] = S(p.UA[(int64_t)st[m] * P4 + v]);
-    const int e0 = ch * kTan;
-    for (int k = 0; k < kTan; ++k) {
-        const int e = e0 + k;
-        if (e == 0) u0.d[k] = 1.0;
-        else if (e <= M) um[e - 1].d[k] = 1.0;
-    }
-    S w[C::QMAX];
-    if (which == 0) cweno_var<C, S>(p, c, nf, u0, um, w);
-    else muscl_var<C, S>(p, c, nf, n1, u0, um, w);
+    for (int m = 0; m < M; ++m) um[m] = p.UA[(int64_t)st[m] * P4 + v];
     const double* mu = p.MU + c * C::QMAX * NV;
-    for (int k = 0; k < kTan; ++k) {
-        const int e = e0 + k;
-        if (e > M) break;
-        double s = 0.0;
-        for (int q = 0; q < Q; ++q) s += mu[q * NV + v] * w[q].d[k];
-        if (e == 0) p.S0[c * NV + v] = s;
-        else p.A[(c * M + (e - 1)) * NV + v] = s;
-    }
+    for (int q = 0; q < Q; ++q) wb[q] = mu[q * NV + v];
+    if (which == 0) cweno_var_vjp<C>(p, c, nf, u0, um, wb, u0_b, um_b);
+    else muscl_var_vjp<C>(p, c, nf, n1, u0, um, wb, u0_b, um_b);
+    p.S0[c * NV + v] = u0_b;
+    for (int m = 0; m < M; ++m) p.A[(c * M + m) * NV + v] = um_b[m];
 }
 
 // the items of one queue, the grid striding over them (the queue length is
@@ -400,8 +661,7 @@ __device__ void nl_vjp_item(const AdjParams& p, int which, int64_t t)
 template <class C>
 __global__ void __launch_bounds__(64) k_recon_nl_vjp(AdjParams p, int which)
 {
-    constexpr int NCH = (C::M + 1 + kTan - 1) / kTan;
-    const int64_t n = (int64_t)p.counts[which] * C::NV * NCH;
+    const int64_t n = (int64_t)p.counts[which] * C::NV;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         nl_vjp_item<C>(p, which, t);
 }
@@ -443,30 +703,35 @@ int run_vjp(hfv_scheme* s, const double* lam, double* g, cudaStream_t st)
     const int64_t nc = p.nc;
     constexpr int CPB = 128 / GroupSize<C::QMAX>::value;
     const unsigned gf = (unsigned)((nc + CPB - 1) / CPB);
-    note_launch();
-    switch (s->p.flux) {
-    case HFV_RUSANOV: k_flux_vjp<C, kRusanov><<<gf, 128, 0, st>>>(p); break;
-    case HFV_HLL: k_flux_vjp<C, kHLL><<<gf, 128, 0, st>>>(p); break;
-    default: k_flux_vjp<C, kHLLC><<<gf, 128, 0, st>>>(p); break;
+    {
+        Launch l(s, KID_VJP_FLUX, st);
+        switch (s->p.flux) {
+        case HFV_RUSANOV: k_flux_vjp<C, kRusanov><<<gf, 128, 0, st>>>(p); break;
+        case HFV_HLL: k_flux_vjp<C, kHLL><<<gf, 128, 0, st>>>(p); break;
+        default: k_flux_vjp<C, kHLLC><<<gf, 128, 0, st>>>(p); break;
+        }
     }
-    note_launch();
-    k_recon_lin_vjp<C><<<(unsigned)((nc + 3) / 4), 128, 0, st>>>(p);
+    {
+        Launch l(s, KID_VJP_RECON, st);
+        k_recon_lin_vjp<C><<<(unsigned)((nc * C::NV + 127) / 128), 128, 0, st>>>(p);
+    }
     // queued cells: at most nc per queue (the count itself lives on the
     // device); at most 64 blocks of 64 threads per SM, striding
-    constexpr int NCH = (C::M + 1 + kTan - 1) / kTan;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             sms = 1;
     }
-    const unsigned gn = (unsigned)std::min<int64_t>((nc * C::NV * NCH + 63) / 64, (int64_t)sms * 32);
+    const unsigned gn = (unsigned)std::min<int64_t>((nc * C::NV + 63) / 64, (int64_t)sms * 32);
     for (int which = 0; which < 2; ++which) {
-        note_launch();
+        Launch l(s, KID_VJP_RECON, st);
         k_recon_nl_vjp<C><<<gn, 64, 0, st>>>(p, which);
     }
-    note_launch();
-    k_gather_vjp<C::NV, C::M><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(p);
+    {
+        Launch l(s, KID_VJP_GATHER, st);
+        k_gather_vjp<C::NV, C::M><<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(p);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("hfv_residual_vjp: ") + cudaGetErrorString(e));

@@ -114,7 +114,7 @@ namespace hfv {
 // hot-path kernel ids for the optional per-kernel timer (KID_COUNT, KID_SCAN and
 // KID_SCATTER are kept for the numbering only: tagging does the queue compaction)
 enum KernelId { KID_LINEAR, KID_TAG, KID_COUNT, KID_SCAN, KID_SCATTER, KID_CWENO, KID_MUSCL, KID_FLUX, KID_RK,
-                KID_DT, KID_CVT, KID_GRAD, KID_COUNT_ALL };
+                KID_DT, KID_CVT, KID_GRAD, KID_VJP_FLUX, KID_VJP_RECON, KID_VJP_GATHER, KID_COUNT_ALL };
 struct KernelTimer {
     bool on = false;
     std::vector<void*> ev;          // cudaEvent_t pairs

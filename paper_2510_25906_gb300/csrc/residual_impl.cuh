@@ -28,6 +28,7 @@
 
 #include "device_common.cuh"
 #include "hfv_internal.h"
+#include "launch.cuh"
 #include "k_linear.cuh"
 #include "kernels.cuh"
 #include "tma.cuh"
@@ -1108,27 +1109,6 @@ static void pdl(void (*k)(KA...), unsigned grid, unsigned block, size_t smem, cu
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
-
-// scope guard: counts the launch and, when the scheme's timer is on, brackets
-// it with a pair of events on the launch stream
-struct Launch {
-    KernelTimer* t;
-    cudaStream_t st;
-    int pair = -1;
-    Launch(hfv_scheme* s, int kid, cudaStream_t stream) : t(&s->timer), st(stream)
-    {
-        note_launch();
-        if (t->on && 2 * (t->used + 1) <= (int)t->ev.size()) {
-            pair = t->used++;
-            t->kid[pair] = kid;
-            cudaEventRecord((cudaEvent_t)t->ev[2 * pair], st);
-        }
-    }
-    ~Launch()
-    {
-        if (pair >= 0) cudaEventRecord((cudaEvent_t)t->ev[2 * pair + 1], st);
-    }
-};
 
 // the viscous constants in the residual's precision
 template <class T>

@@ -22,7 +22,8 @@ HFV_HYBRID, HFV_PURE_LINEAR, HFV_PURE_CWENOZ, HFV_PURE_MUSCL = 0, 1, 2, 3
 HFV_FP64, HFV_FP32 = 0, 1
 HFV_CLASS_LINEAR, HFV_CLASS_CWENOZ, HFV_CLASS_MUSCL, HFV_CLASS_FIRST = 0, 1, 2, 3
 
-KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux", "rk", "dt", "cvt", "grad"]
+KERNELS = ["linear", "tag", "count", "scan", "scatter", "cweno", "muscl", "flux", "rk", "dt", "cvt", "grad",
+           "vjp_flux", "vjp_recon", "vjp_gather"]
 FLUX = {"rusanov": HFV_RUSANOV, "hllc": HFV_HLLC, "hll": HFV_HLL}
 SCHEME = {"hybrid": HFV_HYBRID, "linear": HFV_PURE_LINEAR, "cweno": HFV_PURE_CWENOZ, "muscl": HFV_PURE_MUSCL}
 PRECISION = {"fp64": HFV_FP64, "fp32": HFV_FP32}
