@@ -153,8 +153,12 @@ typedef struct {
      * reduction.  The caller promises that U is not written between such calls;
      * calls that overwrite the scheme's stage copy (hfv_residual,
      * hfv_compute_dt, hfv_autotune, hfv_residual_vjp, hfv_advance_host's
-     * upload) end the chain and the next step starts afresh.  Results are the
-     * same bits as with 0. */
+     * upload) end the chain and the next step starts afresh.  The chain knows
+     * the state by its address only: new contents at the same address (U
+     * written by the caller, or a buffer freed and allocated again at that
+     * address) must be preceded by one of those calls, e.g. hfv_compute_dt,
+     * or they are stepped from the stale copy.  Results are the same bits as
+     * with 0. */
     int step_chain;
 } hfv_scheme_params;
 
