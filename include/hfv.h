@@ -409,6 +409,14 @@ HFV_API int hfv_fma_rate(int kind, double target_ms, double* flops_per_s, void* 
  * n > 0), HFV_ERR_CUDA. */
 HFV_API int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream);
 
+/* The FP64 kernels' reciprocal (the Riemann solvers, the pressure) applied
+ * to an array: out[i] ~ 1 / in[i] from the hardware's approximate reciprocal
+ * refined by two Newton-Raphson steps, within about an ulp for normal inputs
+ * with normal reciprocals (instrumentation; the paper has no counterpart).
+ * in, out: device double [n].  async on `stream`.  Errors: HFV_ERR_ARG
+ * (n < 0, null buffer with n > 0), HFV_ERR_CUDA. */
+HFV_API int hfv_rcp64(int64_t n, const double* in, double* out, void* stream);
+
 /* Class-queue compaction that allocates nothing (the paper has no
  * counterpart: this is an interface for callers that cannot allocate device
  * memory when they need the queues, e.g. code running inside a CUDA stream

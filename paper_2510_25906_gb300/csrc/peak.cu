@@ -1,8 +1,9 @@
 // peak.cu -- CUDA-core fused multiply-add throughput of the current device:
 // the ALU ceiling against which the FP64 (and FP32) residual paths are
 // reported next to the HBM ceiling.  Instrumentation; the paper has no
-// counterpart.  Also the FP32 kernels' integer FP32 <-> FP64 conversions
-// applied to an array, so that they can be checked against the hardware's.
+// counterpart.  Also the FP32 kernels' integer FP32 <-> FP64 conversions and
+// the FP64 kernels' reciprocal applied to an array, so that they can be
+// checked against the hardware's conversions and against 1/x.
 //
 // Each thread runs eight independent chains of dependent FMAs (x <- a x + b
 // with |a| < 1, so the values stay normal and bounded), enough independent
@@ -15,6 +16,7 @@
 #include <string>
 
 #include "device_common.cuh"
+#include "physics.cuh"
 #include "hfv_internal.h"
 
 namespace hfv {
@@ -77,6 +79,12 @@ int launch_peak(int kind, int iters, unsigned grid, cudaStream_t st)
     return HFV_OK;
 }
 
+__global__ void k_rcp64(int64_t n, const double* __restrict__ in, double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = trcp<double>(in[i]);
+}
+
 __global__ void k_convert(int to_f32, int64_t n, const void* __restrict__ in, void* __restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -89,6 +97,23 @@ __global__ void k_convert(int to_f32, int64_t n, const void* __restrict__ in, vo
 }  // namespace hfv
 
 using namespace hfv;
+
+extern "C" int hfv_rcp64(int64_t n, const double* in, double* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!in || !out))) {
+        set_error("hfv_rcp64: n >= 0 and non-null buffers");
+        return HFV_ERR_ARG;
+    }
+    if (n == 0) return HFV_OK;
+    note_launch();
+    k_rcp64<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, in, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string("hfv_rcp64: ") + cudaGetErrorString(e));
+        return HFV_ERR_CUDA;
+    }
+    return HFV_OK;
+}
 
 extern "C" int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream)
 {

@@ -16,7 +16,7 @@ namespace hfv {
 
 enum { kRusanov = 0, kHLLC = 1, kHLL = 2 };
 
-// generic forms (used by the dual numbers of the adjoint); FP32 and FP64 below
+// generic forms; FP32 and FP64 below
 template <class T>
 HDI T tsqrt(T x) { return sqrt(x); }
 template <>
@@ -24,12 +24,31 @@ HDI float tsqrt<float>(float x) { return ::sqrtf(x); }
 template <>
 HDI double tsqrt<double>(double x) { return ::sqrt(x); }
 
-// reciprocal and square root: IEEE in FP64; in FP32 the hardware
-// approximations (about 2 ulp), far inside the FP32 path's 1e-5 bar
+// reciprocal and square root.  FP32: the hardware approximations (about
+// 2 ulp), far inside the FP32 path's 1e-5 bar.  FP64 square root: IEEE.
+// FP64 reciprocal on the device: the hardware's approximate reciprocal as
+// the seed y0, then two Newton-Raphson steps for f(y) = 1/y - x,
+//   e = 1 - x y,  y <- y + y e  (each step squares the relative error),
+// with fused multiply-adds: within about an ulp of 1/x for x and 1/x
+// normal, one seed and four FMAs where the correctly rounded division
+// takes several more FP64 instructions (this GPU's FP64 pipe executes two
+// lanes per clock per SM, and the FP64 flux kernels keep it ~88 % busy).
 template <class T>
 HDI T trcp(T x) { return T(1) / x; }
 template <>
-HDI double trcp<double>(double x) { return 1.0 / x; }
+HDI double trcp<double>(double x)
+{
+#ifdef __CUDA_ARCH__
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+#else
+    return 1.0 / x;
+#endif
+}
 template <>
 HDI float trcp<float>(float x)
 {

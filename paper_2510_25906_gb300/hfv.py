@@ -94,6 +94,7 @@ def load():
         "hfv_class_queues_static": [vp, C.c_int64, vp, vp, vp],
         "hfv_fma_rate": [C.c_int, d, vp, vp],
         "hfv_convert": [C.c_int, C.c_int64, vp, vp, vp],
+        "hfv_rcp64": [C.c_int64, vp, vp, vp],
         "hfv_debug_wait": [vp, C.c_int64, C.c_int],
         "hfv_step_classes": [vp, vp, d, vp, C.c_int, vp, vp],
         "hfv_step_vjp": [vp, vp, vp, d, vp, vp],
@@ -409,6 +410,16 @@ def convert(x, stream=None):
     out = torch.empty(x.shape, dtype=torch.float32 if to_f32 else torch.float64, device=x.device)
     _check(load().hfv_convert(1 if to_f32 else 0, x.numel(), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
                               _stream(stream)))
+    return out
+
+
+def rcp64(x, stream=None):
+    """hfv_rcp64: the FP64 kernels' reciprocal of a contiguous CUDA float64 tensor."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous() or x.dtype != torch.float64:
+        raise ValueError("rcp64: a contiguous CUDA float64 tensor")
+    out = torch.empty_like(x)
+    _check(load().hfv_rcp64(x.numel(), C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

@@ -93,3 +93,26 @@ def test_convert_rejects_bad_arguments(H):
     assert lib.hfv_convert(1, -1, None, None, None) == H.HFV_ERR_ARG
     assert lib.hfv_convert(1, 4, None, None, None) == H.HFV_ERR_ARG
     assert lib.hfv_convert(1, 0, None, None, None) == H.HFV_OK
+
+
+def test_fp64_reciprocal_within_one_ulp(H):
+    """The FP64 kernels' reciprocal (hardware seed and two Newton-Raphson
+    steps) against numpy's correctly rounded 1/x: at most one ulp apart over
+    normal inputs of either sign whose reciprocals are normal, and exact on
+    powers of two."""
+    rng = np.random.default_rng(20251031)
+    n = 1 << 20
+    mant = rng.uniform(1.0, 2.0, n)
+    expo = rng.integers(-1000, 1000, n)
+    sign = np.where(rng.integers(0, 2, n) == 1, -1.0, 1.0)
+    x = sign * np.ldexp(mant, expo)
+    x = np.concatenate([x, np.ldexp(1.0, np.arange(-1000, 1001)), -np.ldexp(1.0, np.arange(-1000, 1001)),
+                        [1.0, 3.0, 7.0, 0.1, 1.0 / 3.0, 1.4, 0.4]])
+    got = H.rcp64(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = 1.0 / x
+    ulps = np.abs(got - ref) / np.spacing(np.abs(ref))
+    worst = int(np.argmax(ulps))
+    assert ulps.max() <= 1.0, (x[worst], got[worst], ref[worst], ulps.max())
+    p2 = np.abs(np.log2(np.abs(x)) - np.round(np.log2(np.abs(x)))) == 0
+    assert np.array_equal(got[p2], ref[p2])
+    print(f"reciprocal: max {ulps.max():.2f} ulp, {np.mean(ulps > 0) * 100:.2f} % not correctly rounded")
