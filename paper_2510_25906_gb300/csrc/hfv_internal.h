@@ -152,7 +152,7 @@ struct hfv_scheme {
     int fam = 0;                    // element family (element_family)
     int nfmax = 4;                  // face slots per cell: 4 (2D, tetrahedra) or 6
     int64_t qtot = 0;
-    int64_t nc_pad = 0;             // cells rounded up to a multiple of 64 (bulk-copy tiles)
+    int64_t nc_pad = 0;             // cells rounded up to a multiple of 192 (bulk-copy tiles of 8-64 or 48 cells)
     int64_t ltot = 0;               // elements of L
     std::vector<int64_t> loff;      // [nc_pad+1]
     int nblocks = 0;

@@ -59,15 +59,26 @@ struct K1Shape {
         return 2 * stage + (ng * CSTRIDE + 127) / 128 * 128 + 4 * 8 + 1024;
     }
     // eight consumer warps, or four or two where a tile of the large blocks
-    // of L (orders 6-7 in 2D, FP64) would not leave room for two ring stages
-    static constexpr int CONSUMERS = two_stages(256) <= 227 * 1024 ? 256 : two_stages(128) <= 227 * 1024 ? 128 : 64;
+    // of L (orders 6-7 in 2D, FP64) would not leave room for two ring stages.
+    // 2D orders 2-3 in FP32: six consumer warps (48-cell tiles) and three
+    // CTAs per SM, each with a three-stage ring: 3 % faster per quadrant step
+    // than two CTAs of eight warps (29.1 against 31.0 us per launch), where
+    // two CTAs of six warps with four stages measured 4 % slower and three
+    // CTAs of eight warps with two stages 13 % slower
+    static constexpr bool TRIPLE = SMALL && C::M <= 12 && sizeof(T) == 4;
+    static constexpr int CONSUMERS = TRIPLE ? 192
+                                     : two_stages(256) <= 227 * 1024 ? 256
+                                     : two_stages(128) <= 227 * 1024 ? 128 : 64;
     static constexpr int NG = CONSUMERS / G;                 // cells per tile
+    // the per-cell arrays are padded to a multiple of 192 cells (nc_pad): the
+    // last tile's bulk copies stay inside them
+    static_assert(192 % NG == 0, "tile size must divide the cell padding");
     static constexpr int LBYTES = NG * LMAX * (int)sizeof(T);
     static constexpr int SBYTES = NG * C::M * 4;
     static constexpr int STAGE = (LBYTES + SBYTES + 127) / 128 * 128;
     static constexpr int SU = NG * CSTRIDE;
     // resident CTAs per SM aimed for (register and shared-memory budget)
-    static constexpr int MINB = sizeof(T) == 8 ? 1 : 2;
+    static constexpr int MINB = sizeof(T) == 8 ? 1 : TRIPLE ? 3 : 2;
     static constexpr int BUDGET = 227 * 1024 / MINB - (SU + 127) / 128 * 128 - 1024;
     static constexpr int FIT = BUDGET / STAGE;
     static constexpr int STAGES = FIT >= 4 ? 4 : FIT >= 3 ? 3 : 2;
@@ -100,7 +111,7 @@ __device__ __forceinline__ T seg_max(T v)
 }
 
 template <class C, class T>
-__global__ void __launch_bounds__(288, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
+__global__ void __launch_bounds__(K1Shape<C, T>::THREADS, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
 {
     using S = K1Shape<C, T>;
     constexpr int M = C::M, NV = C::NV, D = C::D, G = S::G, NG = S::NG, ST = S::STAGES, PPL = S::PPL;

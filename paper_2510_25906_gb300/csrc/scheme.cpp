@@ -82,7 +82,7 @@ int build_stencils(hfv_scheme* s)
     // L: compact per-cell blocks of Q_c x M values, each padded to 16 bytes so
     // that a run of consecutive cells is one aligned bulk copy
     const int per16 = s->p.precision == HFV_FP32 ? 4 : 2;
-    s->nc_pad = (nc + 63) / 64 * 64;
+    s->nc_pad = (nc + 191) / 192 * 192;   // a whole number of tiles of every tile size (8-64 cells, 48)
     s->loff.assign(s->nc_pad + 1, 0);
     for (int64_t c = 0; c < s->nc_pad; ++c) {
         int64_t blk = c < nc ? (int64_t)type_nfaces(m->type[c]) * s->nfp * M : 0;
