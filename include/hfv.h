@@ -305,15 +305,25 @@ HFV_API int hfv_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t*
 HFV_API int hfv_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream);
 
 /* Autotuner of the residual's launch shape for this scheme and state: the
- * persistent candidate kernel's resident CTAs per SM, and the CWENOZ / MUSCL
+ * persistent candidate kernel's tile shape (2D FP32 orders 2-3: 0 = tiles of
+ * 48 cells, three CTAs per SM; 1 = tiles of 64 cells, two CTAs per SM; one
+ * shape elsewhere) and resident CTAs per SM, and the CWENOZ / MUSCL
  * kernel's blocks per SM and the share of them given to the CWENOZ queue.
  * Coordinate descent over candidate values, each timed with CUDA events over
  * `reps` residuals of U (device, the scheme's precision, [nv][n_cells]) on
  * `stream`; the fastest shape is kept for every later call on the scheme.
- * shape (host, 3 ints, may be NULL) receives it.  The results of the
- * residual do not depend on the shape.  sync.  Errors: HFV_ERR_ARG,
- * HFV_ERR_CUDA. */
+ * shape (host, 4 ints, may be NULL) receives it: {candidate CTAs per SM
+ * (0: as many as fit), nonlinear blocks per SM, CWENOZ share in %, tile
+ * shape}.  The results of the residual do not depend on the shape.  sync.
+ * Errors: HFV_ERR_ARG, HFV_ERR_CUDA. */
 HFV_API int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, int* shape);
+
+/* Set the launch shape hfv_autotune reports (host, 4 ints, same order and
+ * meaning), e.g. one tuned earlier for the same mesh and order; a tile shape
+ * that the configuration lacks falls back to its only one.  The paper has no
+ * counterpart.  Errors: HFV_ERR_ARG (NULL, a value out of range: CTAs per SM
+ * 0..64, blocks per SM 1..64, share 1..99 %, tile 0 or 1). */
+HFV_API int hfv_scheme_set_shape(hfv_scheme* s, const int* shape);
 
 /* hfv_step on several schemes at once, each on its own stream forked from
  * `stream` and joined back into it (so their kernels may run concurrently,

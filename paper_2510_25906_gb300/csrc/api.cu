@@ -315,6 +315,16 @@ extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream
     };
     if (rc == HFV_OK) rc = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);   // fills sms and the occupancy bound
     if (rc == HFV_OK) API_CUDA(cudaStreamSynchronize(st));
+    if (rc == HFV_OK && s->linear_tiles > 1) {
+        // the candidate kernel's tile shape first, each at its full occupancy
+        static const int tiles[] = {0, 1};
+        const int keep = s->tune_linear_per_sm;
+        s->tune_linear_per_sm = 0;
+        rc = tune(&s->tune_linear_tile, tiles, 2);
+        if (rc == HFV_OK) rc = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);   // the chosen shape's bound
+        if (rc == HFV_OK) API_CUDA(cudaStreamSynchronize(st));
+        if (rc != HFV_OK) s->tune_linear_per_sm = keep;
+    }
     if (rc == HFV_OK) {
         int per[8], n = 0;
         for (int k = 1; k <= s->linear_per_sm_max && n < 8; ++k) per[n++] = k;
@@ -332,7 +342,22 @@ extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream
         shape[0] = s->tune_linear_per_sm;
         shape[1] = s->tune_nl_per_sm;
         shape[2] = s->tune_nl_cweno_pct;
+        shape[3] = s->tune_linear_tile;
     }
+    return HFV_OK;
+}
+
+extern "C" int hfv_scheme_set_shape(hfv_scheme* s, const int* shape)
+{
+    if (!s || !shape || shape[0] < 0 || shape[0] > 64 || shape[1] < 1 || shape[1] > 64 || shape[2] < 1 ||
+        shape[2] > 99 || (shape[3] != 0 && shape[3] != 1)) {
+        set_error("hfv_scheme_set_shape: NULL argument or a value out of range");
+        return HFV_ERR_ARG;
+    }
+    s->tune_linear_per_sm = shape[0];
+    s->tune_nl_per_sm = shape[1];
+    s->tune_nl_cweno_pct = shape[2];
+    s->tune_linear_tile = shape[3];
     return HFV_OK;
 }
 

@@ -161,6 +161,8 @@ struct hfv_scheme {
     // SM of the candidate kernel (0 = as many as fit), blocks per SM of the
     // CWENOZ / MUSCL kernel and the percentage of them on the CWENOZ queue
     int tune_linear_per_sm = 0;
+    int tune_linear_tile = 0;          // 0: the default tile shape, 1: the alternative (linear_tiles = 2)
+    int linear_tiles = 1;              // tile shapes built for this scheme's configuration
     int tune_nl_per_sm = 16;
     int tune_nl_cweno_pct = 75;
     int sms = 152, linear_per_sm_max = 1;   // filled at the first residual

@@ -23,7 +23,7 @@ namespace hfv {
 // jW .. jW+W-1), a last partial chunk of width M mod W holds [Q][M mod W].
 // One 16-byte load gives a lane W columns of its row, and the eight lanes of
 // a group read 128 contiguous bytes.
-template <class C, class T>
+template <class C, class T, bool WIDE = false>
 struct K1Shape {
     // 2D orders 2-4: four lanes per cell (one per face neighbour) with up to
     // two face points each, so that the per-cell work of the detector and of
@@ -65,7 +65,9 @@ struct K1Shape {
     // than two CTAs of eight warps (29.1 against 31.0 us per launch), where
     // two CTAs of six warps with four stages measured 4 % slower and three
     // CTAs of eight warps with two stages 13 % slower
-    static constexpr bool TRIPLE = SMALL && C::M <= 12 && sizeof(T) == 4;
+    // (WIDE: the two-CTA shape, the autotuner's alternative for these)
+    static constexpr bool TRIPLE = !WIDE && SMALL && C::M <= 12 && sizeof(T) == 4;
+    static constexpr bool HAS_WIDE = WIDE || TRIPLE;
     static constexpr int CONSUMERS = TRIPLE ? 192
                                      : two_stages(256) <= 227 * 1024 ? 256
                                      : two_stages(128) <= 227 * 1024 ? 128 : 64;
@@ -110,10 +112,10 @@ __device__ __forceinline__ T seg_max(T v)
     return v;
 }
 
-template <class C, class T>
-__global__ void __launch_bounds__(K1Shape<C, T>::THREADS, K1Shape<C, T>::MINB) k_linear(KParams<T> p)
+template <class C, class T, bool WIDE = false>
+__global__ void __launch_bounds__(K1Shape<C, T, WIDE>::THREADS, K1Shape<C, T, WIDE>::MINB) k_linear(KParams<T> p)
 {
-    using S = K1Shape<C, T>;
+    using S = K1Shape<C, T, WIDE>;
     constexpr int M = C::M, NV = C::NV, D = C::D, G = S::G, NG = S::NG, ST = S::STAGES, PPL = S::PPL;
     constexpr int SLOT = S::SLOT, W = S::PER16, M4 = M / W * W, TW = M - M4;
     extern __shared__ __align__(128) unsigned char smem[];

@@ -1205,6 +1205,32 @@ struct StageRK {
     double cfl = 0.0;
 };
 
+// the persistent candidate kernel in tile shape WIDE: one CTA per (SM x
+// resident CTAs), fewer if the tuned count says so
+template <class C, class T, bool WIDE>
+static int launch_linear(hfv_scheme* s, const KParams<T>& p, cudaStream_t st)
+{
+    using S1 = K1Shape<C, T, WIDE>;
+    static int sms = 0, per_max = 0;   // per instantiation: SMs and resident CTAs per SM
+    if (!sms) {
+        HFV_CUDA_CHECK(cudaFuncSetAttribute(k_linear<C, T, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1::SMEM));
+        int dev = 0, n = 0, per = 0;
+        HFV_CUDA_CHECK(cudaGetDevice(&dev));
+        HFV_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        HFV_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_linear<C, T, WIDE>, S1::THREADS, S1::SMEM));
+        per_max = per > 0 ? per : 1;
+        sms = n;
+    }
+    s->sms = sms;
+    s->linear_per_sm_max = per_max;
+    const int per = s->tune_linear_per_sm > 0 ? std::min(s->tune_linear_per_sm, per_max) : per_max;
+    const int64_t ntiles = (p.nc + S1::NG - 1) / S1::NG;
+    const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per);
+    Launch l(s, KID_LINEAR, st);
+    pdl(k_linear<C, T, WIDE>, g1, S1::THREADS, S1::SMEM, st, p);
+    return HFV_OK;
+}
+
 template <class C, class T>
 int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t* cls_out, cudaStream_t st,
                  const T* ua, const StageRK* rk)
@@ -1236,24 +1262,14 @@ int run_residual(hfv_scheme* s, const T* U, T* R, const uint8_t* forced, uint8_t
         p.seg = nullptr; p.out = nullptr; p.ua_next = nullptr; p.Rcopy = nullptr;
     }
     {
-        using S1 = K1Shape<C, T>;
-        static int sms = 0, per_max = 0;   // per instantiation: SMs and resident CTAs per SM
-        if (!sms) {
-            HFV_CUDA_CHECK(cudaFuncSetAttribute(k_linear<C, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, S1::SMEM));
-            int dev = 0, n = 0, per = 0;
-            HFV_CUDA_CHECK(cudaGetDevice(&dev));
-            HFV_CUDA_CHECK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-            HFV_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_linear<C, T>, S1::THREADS, S1::SMEM));
-            per_max = per > 0 ? per : 1;
-            sms = n;
-        }
-        s->sms = sms;
-        s->linear_per_sm_max = per_max;
-        const int per = s->tune_linear_per_sm > 0 ? std::min(s->tune_linear_per_sm, per_max) : per_max;
-        const int64_t ntiles = (nc + S1::NG - 1) / S1::NG;
-        const unsigned g1 = (unsigned)std::min<int64_t>(ntiles, (int64_t)sms * per);
-        Launch l(s, KID_LINEAR, st);
-        pdl(k_linear<C, T>, g1, S1::THREADS, S1::SMEM, st, p);
+        // the candidate kernel in the scheme's tile shape (2D FP32 orders 2-3
+        // have two, hfv_autotune picks one)
+        constexpr bool ALT = K1Shape<C, T>::HAS_WIDE;
+        s->linear_tiles = ALT ? 2 : 1;
+        int rc1;
+        if (ALT && s->tune_linear_tile == 1) rc1 = launch_linear<C, T, ALT>(s, p, st);
+        else rc1 = launch_linear<C, T, false>(s, p, st);
+        if (rc1 != HFV_OK) return rc1;
     }
     const bool visc = s->p.mu0 > 0.0;
     { Launch l(s, KID_TAG, st); pdl(k_tag<T>, s->nblocks, 256, 0, st, p); }

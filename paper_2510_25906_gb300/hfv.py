@@ -100,6 +100,7 @@ def load():
         "hfv_step_vjp": [vp, vp, vp, d, vp, vp],
         "hfv_scheme_setup_ms": [vp, vp],
         "hfv_scheme_set_kind": [vp, C.c_int],
+        "hfv_scheme_set_shape": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -288,11 +289,17 @@ class Scheme:
 
     def autotune(self, U, reps: int = 5, stream=None):
         """hfv_autotune on a state in the scheme's precision; returns the shape
-        (candidate-kernel CTAs per SM, nonlinear blocks per SM, CWENOZ share %)."""
+        (candidate-kernel CTAs per SM, nonlinear blocks per SM, CWENOZ share %,
+        candidate-kernel tile shape)."""
         u = self._state(U, self.dtype)
-        shape = (C.c_int * 3)()
+        shape = (C.c_int * 4)()
         _check(load().hfv_autotune(self.h, u, reps, _stream(stream), shape))
         return tuple(shape)
+
+    def set_shape(self, shape):
+        """hfv_scheme_set_shape: a launch shape as autotune returns it."""
+        arr = (C.c_int * 4)(*[int(x) for x in shape])
+        _check(load().hfv_scheme_set_shape(self.h, arr))
 
     def step(self, U, cfl: float = 0.5, dt: float = -1.0, want_dt: bool = False, stream=None):
         """hfv_step on an FP64 state in place; returns dt when want_dt (a

@@ -205,5 +205,28 @@ def test_autotune_keeps_results(H):
     R0 = g.residual(U).cpu().numpy()
     shape = g.autotune(U, reps=2)
     assert 1 <= shape[0] <= 8 and shape[1] in (2, 4, 8, 16, 32) and shape[2] in (50, 67, 75, 85, 95), shape
+    assert shape[3] in (0, 1), shape
     R1 = g.residual(U).cpu().numpy()
     assert np.array_equal(R0, R1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_candidate_tile_shapes_give_the_same_bits(H, order):
+    """The candidate kernel's two tile shapes (48-cell tiles at three CTAs
+    per SM, 64-cell tiles at two; 2D FP32 orders 2-3) and any CTA count give
+    the same residual bits; at order 4, which has one shape, the second
+    falls back to it."""
+    P = I.batched_problems(6, seed=53, min_cells=2000, max_cells=30000, orders=(order,))
+    gm = H.Mesh.batch([p["mesh"] for p in P])
+    g = H.Scheme(gm, order=order, flux="hllc", precision="fp32")
+    U = torch.tensor(np.concatenate([p["U"] for p in P], axis=1), dtype=torch.float32, device="cuda")
+    out = []
+    for shape in ((0, 16, 75, 0), (0, 16, 75, 1), (1, 4, 50, 0), (1, 4, 50, 1)):
+        g.set_shape(shape)
+        cls = torch.empty(U.shape[1], dtype=torch.uint8, device="cuda")
+        out.append((g.residual(U, class_out=cls).cpu().numpy(), cls.cpu().numpy()))
+    for R, c in out[1:]:
+        assert np.array_equal(R, out[0][0]) and np.array_equal(c, out[0][1])
+    with pytest.raises(H.HfvError):
+        g.set_shape((0, 16, 75, 2))
