@@ -88,7 +88,7 @@ struct hfv_dev_arrays {
     uint8_t* raw;      // [nc] raw class | 0x80 when the linear candidate breaks the Harten bound
     uint8_t* cls;      // [nc] final class
     int32_t* queue;    // [2][nc] CWENOZ / MUSCL queues
-    int32_t* counts;   // [2] + block counts
+    int32_t* counts;   // [2] queue lengths (CWENOZ, MUSCL)
     int* status;       // [1]
     // time stepping scratch
     double* U1;        // [nv][nc]

@@ -4,10 +4,10 @@ call cudaMalloc when they need the queues, e.g. inside a stream capture).
 It must produce the same counts and queues as the compaction inside
 hfv_residual: with classes forced, the residual compacts exactly the given
 CWENOZ and MUSCL cells, so both are compared bit for bit, on two calls in a
-row (the static scratch keeps the previous call's contents).  On a mesh of
-more than 1,024 blocks of 256 cells (where the residual runs its separate
-scan kernel and the scan here takes several block counts per thread) both
-are also compared with numpy's list of the class-1 and class-2 cells."""
+row (the static scratch keeps the previous call's contents; the residual's
+queues are read back sorted).  On a mesh of more than 1,024 blocks of 256
+cells (where the scan here takes several block counts per thread) both are
+also compared with numpy's list of the class-1 and class-2 cells."""
 import ctypes
 
 import numpy as np
