@@ -46,12 +46,12 @@ L2_FLUSH_BYTES = 256 << 20
 # reports null.
 KERNEL_SOURCES = ("k_linear.cuh", "device_common.cuh", "kernels.cuh", "tma.cuh", "physics.cuh")
 TRAFFIC = {
-    # the 249,601-cell quadrant mesh itself, order 3 hybrid FP32: 99,136,000 B
-    # read + 8,089,344 B written per launch
-    ("quadrant", 3, "fp32", "hybrid"): {"bytes_per_cell": 429.587, "sources": "82c527aaeef099dc"},
-    # 110,592-cell turbulence mesh, order 4 hybrid FP32: 447,681,792 B read +
-    # 44,238,848 B written
-    ("turbulence", 4, "fp32", "hybrid"): {"bytes_per_cell": 4448.067, "sources": "82c527aaeef099dc"},
+    # the 249,601-cell quadrant mesh itself, order 3 hybrid FP32: 99,144,960 B
+    # read + 8,281,856 B written per launch
+    ("quadrant", 3, "fp32", "hybrid"): {"bytes_per_cell": 430.394, "sources": "a1f3e660e08e75d8"},
+    # 110,592-cell turbulence mesh, order 4 hybrid FP32: 447,680,256 B read +
+    # 43,790,336 B written
+    ("turbulence", 4, "fp32", "hybrid"): {"bytes_per_cell": 4443.998, "sources": "a1f3e660e08e75d8"},
 }
 
 
@@ -421,12 +421,15 @@ def kernel_pass(H, torch, g, U0, steps, cfl, dev):
     """Eager steps with the library's per-kernel event timer (events recorded
     on the launch stream around every kernel), L2 flushed between steps; the
     kernels of a step are queued behind a ~2 ms sleep kernel, so they run
-    back to back as in the graph-timed region."""
+    back to back as in the graph-timed region.  Each kernel's time is the
+    median over the steps of its per-step total, times the number of steps:
+    a step whose launches waited on a slow host does not move it."""
     st = torch.cuda.Stream(device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     U = torch.tensor(U0, dtype=torch.float64, device=dev)
     g.kernel_timer(True)
     g.kernel_times(reset=True)
+    per_step = []
     with torch.cuda.stream(st):
         for _ in range(steps):
             flush.zero_()
@@ -434,8 +437,15 @@ def kernel_pass(H, torch, g, U0, steps, cfl, dev):
             # the step, so no event pair spans a host launch gap
             torch.cuda._sleep(4_000_000)
             g.step(U, cfl=cfl, stream=st)
-            times = g.kernel_times()
+            per_step.append(g.kernel_times(reset=True))
     g.kernel_timer(False)
+    times = {}
+    for k in per_step[0]:
+        n = sum(t[k][1] for t in per_step)
+        if n:
+            times[k] = (float(np.median([t[k][0] for t in per_step])) * len(per_step), n)
+        else:
+            times[k] = (0.0, 0)
     return times
 
 

@@ -56,6 +56,28 @@ def test_chained_steps_are_bit_identical(H, precision):
     assert np.array_equal(Ua, Ub)
 
 
+@pytest.mark.parametrize("case", ["hex_o4_fp32", "mixed3d_o3_fp32", "hex_o3_fp64"])
+def test_chained_steps_are_bit_identical_in_3d(H, case):
+    """the chained epilogue on eight-lane groups (hexahedra, mixed elements:
+    up to six faces per cell), with a shock in the mixed case"""
+    if case.startswith("hex"):
+        m = I.structured_hex_mesh(12, jitter=0.1, seed=3)
+        U0 = I.turbulence_state(m, seed=3)
+        order = 4 if "o4" in case else 3
+    else:
+        m = I.mixed_element_mesh(6, seed=7)
+        U0 = I.shock_pulse_state(m)
+        order = 3
+    kw = dict(order=order, flux="hllc", precision=case.rsplit("_", 1)[1])
+    gm = H.Mesh(m)
+    g0 = H.Scheme(gm, **kw)
+    g1 = H.Scheme(gm, step_chain=1, **kw)
+    Ua, da = _run(g0, U0, 4, cfl=0.4)
+    Ub, db = _run(g1, U0, 4, cfl=0.4)
+    assert np.array_equal(da, db), (da, db)
+    assert np.array_equal(Ua, Ub)
+
+
 def test_chain_broken_by_residual_and_by_another_state(H):
     m = I.mixed_tri_quad_mesh(32, seed=4)
     U0 = I.quadrant_state(m)
