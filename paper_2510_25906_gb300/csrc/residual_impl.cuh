@@ -145,17 +145,25 @@ __global__ void __launch_bounds__(256) k_tag(KParams<T> p)
     pdl_wait();
     __shared__ int sc[2][8];
     __shared__ int base[2];
-    if (p.dt_pending && blockIdx.x == 0)
-        for (int k = threadIdx.x; k < p.nseg; k += 256) {
-            unsigned long long m = 0x7ff0000000000000ull;
-            for (int j = 0; j < kDtSlots; ++j) {
-                const int64_t e = ((int64_t)k * kDtSlots + j) * kDtStride;
-                const unsigned long long x = p.dt_pending[e];
-                m = x < m ? x : m;
-                p.dt_pending[e] = 0x7ff0000000000000ull;
+    if (p.dt_pending && blockIdx.x == 0) {
+        // one warp per problem folds its slots (two per lane, loaded together)
+        // and resets them; the minimum of the bits does not depend on the order
+        static_assert(kDtSlots == 64, "two slots per lane");
+        const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
+        for (int k = wq; k < p.nseg; k += 8) {
+            const int64_t e0 = ((int64_t)k * kDtSlots + lq) * kDtStride, e1 = e0 + 32 * kDtStride;
+            const unsigned long long x0 = p.dt_pending[e0], x1 = p.dt_pending[e1];
+            unsigned long long m = x0 < x1 ? x0 : x1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, m, o);
+                m = y < m ? y : m;
             }
-            p.dt_cur[k] = __longlong_as_double((long long)m);
+            p.dt_pending[e0] = 0x7ff0000000000000ull;
+            p.dt_pending[e1] = 0x7ff0000000000000ull;
+            if (lq == 0) p.dt_cur[k] = __longlong_as_double((long long)m);
         }
+    }
     const int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x;
     int t = 255;
     if (c < p.nc) {
