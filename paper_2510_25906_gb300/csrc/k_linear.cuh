@@ -97,19 +97,63 @@ __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); 
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
 
+// FP64 decisions in integer instructions.  An FP64 compare, minimum or
+// maximum occupies this GPU's FP64 pipe (two lanes per clock per SM) as long
+// as an FMA does; on the key below, a signed 64-bit integer that orders as
+// the double does (the sign-magnitude bits with the magnitude bits of a
+// negative number flipped; -0 taken as +0), they take a few integer
+// instructions and give the same decisions for every non-NaN operand.  The
+// key maps back to the value (a zero comes back as +0, which changes no sum
+// or product the detector forms from it).  FP32 keeps the plain operations.
+__device__ __forceinline__ long long okey(double x)
+{
+    long long b = __double_as_longlong(x);
+    b = (b << 1) == 0 ? 0 : b;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double okey_inv(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL)); }
+__device__ __forceinline__ bool dle(float a, float b) { return a <= b; }
+__device__ __forceinline__ bool dle(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ bool dlt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool dlt(double a, double b) { return okey(a) < okey(b); }
+__device__ __forceinline__ float dmaxv(float a, float b) { return a > b ? a : b; }
+__device__ __forceinline__ double dmaxv(double a, double b) { return okey(a) > okey(b) ? a : b; }
+__device__ __forceinline__ float dabsv(float x) { return x < 0.0f ? -x : x; }
+__device__ __forceinline__ double dabsv(double x) { return fabs(x); }   // a sign-bit operation
+
 template <int SLOT, class T>
 __device__ __forceinline__ T seg_min(T v)
 {
+    if constexpr (sizeof(T) == 8) {
+        long long k = okey(v);
 #pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+        for (int o = SLOT / 2; o > 0; o >>= 1) {
+            const long long y = __shfl_xor_sync(0xffffffffu, k, o);
+            k = y < k ? y : k;
+        }
+        return okey_inv(k);
+    } else {
+#pragma unroll
+        for (int o = SLOT / 2; o > 0; o >>= 1) v = vmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
 }
 template <int SLOT, class T>
 __device__ __forceinline__ T seg_max(T v)
 {
+    if constexpr (sizeof(T) == 8) {
+        long long k = okey(v);
 #pragma unroll
-    for (int o = SLOT / 2; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+        for (int o = SLOT / 2; o > 0; o >>= 1) {
+            const long long y = __shfl_xor_sync(0xffffffffu, k, o);
+            k = y > k ? y : k;
+        }
+        return okey_inv(k);
+    } else {
+#pragma unroll
+        for (int o = SLOT / 2; o > 0; o >>= 1) v = vmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
 }
 
 template <class C, class T, bool WIDE = false>
@@ -379,7 +423,7 @@ __global__ void __launch_bounds__(K1Shape<C, T, WIDE>::THREADS, K1Shape<C, T, WI
                 pw[j] = pressure<T, D>(w[j], p.gamma);
                 if (q < Q) {
                     store_state<T, NV>(p.FS + (q0 + q) * NV, w[j]);
-                    fail = fail || !(tabs(w[j][0] - rb) <= rlim) || !(tabs(pw[j] - pb) <= plim);
+                    fail = fail || !dle(dabsv(w[j][0] - rb), rlim) || !dle(dabsv(pw[j] - pb), plim);
                 }
             }
             int cl = CLS_LIN;
@@ -398,7 +442,7 @@ __global__ void __launch_bounds__(K1Shape<C, T, WIDE>::THREADS, K1Shape<C, T, WI
                     const T qi = kind == 0 ? rb : kind == 1 ? pb : uc[kind - 1];
                     const T qn = kind == 0 ? nb[0] : kind == 1 ? pn : nb[kind - 1];
                     const T qj = has ? qn : qi;
-                    const T dd = tabs(qj - qi);
+                    const T dd = dabsv(qj - qi);
                     T lo = seg_min<SLOT>(qj), hi = seg_max<SLOT>(qj);
                     T dlo = seg_min<SLOT>(has ? dd : T(INFINITY));
                     T dhi = seg_max<SLOT>(has ? dd : T(-INFINITY));
@@ -409,18 +453,18 @@ __global__ void __launch_bounds__(K1Shape<C, T, WIDE>::THREADS, K1Shape<C, T, WI
                         dhi = __shfl_sync(0xffffffffu, dhi, src);
                     }
                     // deactivated (smooth) unless the neighbour differences spread by thr
-                    if (det && !(dhi - dlo < thr)) {
+                    if (det && !dlt(dhi - dlo, thr)) {
                         const T range = hi - lo;
-                        const T dm = tmax(p.alpha_m, p.beta_m * range);
-                        const T dw = sg * tmax(p.alpha_w, tabs(p.beta_w * range));
+                        const T dm = dmaxv(p.alpha_m, p.beta_m * range);
+                        const T dw = sg * dmaxv(p.alpha_w, dabsv(p.beta_w * range));
 #pragma unroll
                         for (int j = 0; j < PPL; ++j) {
                             const int q = lane + j * G;
                             if (q < Q) {
                                 const T x = kind == 0 ? w[j][0] : kind == 1 ? pw[j] : w[j][kind - 1];
                                 int kc;
-                                if (x <= lo - dm || x >= hi + dm) kc = CLS_MU;
-                                else if (lo - dw < x && x < hi + dw) kc = CLS_LIN;
+                                if (dle(x, lo - dm) || dle(hi + dm, x)) kc = CLS_MU;
+                                else if (dlt(lo - dw, x) && dlt(x, hi + dw)) kc = CLS_LIN;
                                 else kc = CLS_CW;
                                 cl = kc > cl ? kc : cl;
                             }
