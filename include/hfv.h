@@ -309,9 +309,11 @@ HFV_API int hfv_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, dou
  * 48 cells, three CTAs per SM; 1 = tiles of 64 cells, two CTAs per SM; one
  * shape elsewhere) and resident CTAs per SM, and the CWENOZ / MUSCL
  * kernel's blocks per SM and the share of them given to the CWENOZ queue.
- * Coordinate descent over candidate values, each timed with CUDA events over
- * `reps` residuals of U (device, the scheme's precision, [nv][n_cells]) on
- * `stream`; the fastest shape is kept for every later call on the scheme.
+ * Coordinate descent over candidate values, each timed twice with CUDA
+ * events over `reps` residuals of U (device, the scheme's precision,
+ * [nv][n_cells]) on `stream` (the better time counts); a candidate replaces
+ * the current value only when 2 % faster, and the shape found is kept for
+ * every later call on the scheme.
  * shape (host, 4 ints, may be NULL) receives it: {candidate CTAs per SM
  * (0: as many as fit), nonlinear blocks per SM, CWENOZ share in %, tile
  * shape}.  The results of the residual do not depend on the shape.  sync.
