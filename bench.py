@@ -439,6 +439,13 @@ def kernel_pass(H, torch, g, U0, steps, cfl, dev):
             g.step(U, cfl=cfl, stream=st)
             per_step.append(g.kernel_times(reset=True))
     g.kernel_timer(False)
+    return median_kernel_times(per_step)
+
+
+def median_kernel_times(per_step):
+    """{kernel: (ms, launches)} per step -> {kernel: (median per-step ms x
+    steps, all launches)}: a kernel's steady-state total, robust to a few
+    steps that waited on the host."""
     times = {}
     for k in per_step[0]:
         n = sum(t[k][1] for t in per_step)

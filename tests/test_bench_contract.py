@@ -40,3 +40,18 @@ def test_traffic_figure_follows_the_kernel_sources(monkeypatch):
     assert bench._traffic("quadrant", 3, "fp64", "hybrid", 1000) is None
     monkeypatch.setitem(bench.TRAFFIC, ("quadrant", 3, "fp32", "hybrid"), {"bytes_per_cell": 400.0, "sources": "0"})
     assert bench._traffic("quadrant", 3, "fp32", "hybrid", 1000) is None
+
+
+def test_kernel_times_are_the_median_over_steps():
+    """One step whose first launch waited on the host does not move a
+    kernel's reported time; kernels that ran in one step only report zero
+    time (their steady-state share) but keep their launch count."""
+    sys.path.insert(0, ROOT)
+    import bench
+    steps = [{"linear": (0.030 * 3, 3), "tag": (0.005 * 3, 3), "cvt": (0.0, 0)} for _ in range(9)]
+    steps[4] = {"linear": (0.030 * 3 + 0.110, 3), "tag": (0.005 * 3, 3), "cvt": (0.0, 0)}
+    steps[0]["cvt"] = (0.011, 1)
+    t = bench.median_kernel_times(steps)
+    assert t["linear"][1] == 27 and abs(t["linear"][0] / t["linear"][1] - 0.030) < 1e-12
+    assert abs(t["tag"][0] - 0.005 * 27) < 1e-12
+    assert t["cvt"] == (0.0, 1)
