@@ -173,6 +173,57 @@ def test_stencil_rule_brute_force(maker, order):
         assert st.tolist() == _brute_stencil(m, om, c, s.M)
 
 
+@pytest.mark.parametrize("maker,order", [
+    (lambda: I.structured_tri_mesh(10, periodic=True, jitter=0.2, seed=3), 3),
+    (lambda: I.mixed_tri_quad_mesh(10, seed=2), 5),
+    (lambda: I.structured_quad_mesh(9, 8), 3),
+    (lambda: I.structured_hex_mesh(6, 1.0, periodic=True, jitter=0.1, seed=5), 3),
+])
+def test_directional_stencils_brute_force(maker, order):
+    """The directional stencils (reading R7) rebuilt from the reading's own
+    words: for each face, the central-stencil cells (in stencil order) whose
+    vertex mean, periodic shift included, lies beyond the cell's vertex mean
+    along the face's outward unit normal by at least h / 2^21 (the signed
+    distance rounded to h / 2^20 is positive; h = |V|^(1/d)), at most Md of
+    them; with fewer than d + 1 the first Md central cells.  Compared per cell
+    as a multiset over the faces, so independent of the local face order."""
+    m = maker()
+    om = O.Mesh(m)
+    s = O.Scheme(om, order=order)
+    d = m.dim
+    vm = np.zeros((m.n_cells, 3))
+    vm[:, :d] = m.vertex_means()[:, :d]
+    vol, _ = om.geometry()
+    fo, fn, nrm, _, _ = om.faces()
+    normals = [[] for _ in range(m.n_cells)]
+    for g in range(len(fo)):
+        normals[fo[g]].append(nrm[g])
+        if fn[g] >= 0:
+            normals[fn[g]].append(-nrm[g])
+    checked = 0
+    for c in range(0, m.n_cells, max(1, m.n_cells // 40)):
+        st, dirs = s.stencil(c)
+        nd = s.operator(c, "nd").astype(int)
+        shift = s.operator(c, "shift")
+        h = vol[c] ** (1.0 / d)
+        pos = vm[st] + shift
+        got = sorted(tuple(sorted(dirs[f][:nd[f]].tolist())) for f in range(len(nd)))
+        assert len(normals[c]) == len(nd)
+        want, ambiguous = [], False
+        for n in normals[c]:
+            x = (pos - vm[c]) @ n / h * 2.0 ** 20
+            ambiguous |= bool(np.any(np.abs(x - 0.5) < 1e-3))
+            cand = [a for a in range(s.M) if x[a] >= 0.5][:s.Md]
+            if len(cand) < d + 1:
+                cand = list(range(s.Md))
+            want.append(tuple(sorted(cand)))
+        if ambiguous:
+            continue
+        assert got == sorted(want), (c, got, sorted(want))
+        checked += 1
+    assert checked >= 20
+
+
 def test_stencil_size_rule():
     # M = 2 K(r, d), K(r, d) = prod_{l=1..d}(r+l)/d!  (Sec. 2.1)
     expect2d = {2: 6, 3: 12, 4: 20, 5: 30, 6: 42}
