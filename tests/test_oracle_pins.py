@@ -158,6 +158,8 @@ def _brute_stencil(m, om, c, M):
     (lambda: I.structured_tri_mesh(10, periodic=True, jitter=0.2, seed=3), 3),
     (lambda: I.mixed_tri_quad_mesh(10, seed=2), 5),
     (lambda: I.structured_hex_mesh(6, 1.0, periodic=True), 4),
+    (lambda: I.structured_tet_mesh(4, periodic=True, jitter=0.1, seed=6), 3),
+    (lambda: I.mixed_element_mesh(4, seed=7), 3),
 ])
 def test_stencil_rule_brute_force(maker, order):
     m = maker()
@@ -178,6 +180,8 @@ def test_stencil_rule_brute_force(maker, order):
     (lambda: I.mixed_tri_quad_mesh(10, seed=2), 5),
     (lambda: I.structured_quad_mesh(9, 8), 3),
     (lambda: I.structured_hex_mesh(6, 1.0, periodic=True, jitter=0.1, seed=5), 3),
+    (lambda: I.structured_tet_mesh(4, periodic=True, jitter=0.1, seed=6), 3),
+    (lambda: I.mixed_element_mesh(4, seed=7), 3),
 ])
 def test_directional_stencils_brute_force(maker, order):
     """The directional stencils (reading R7) rebuilt from the reading's own
