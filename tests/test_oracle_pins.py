@@ -228,6 +228,37 @@ def test_directional_stencils_brute_force(maker, order):
     assert checked >= 20
 
 
+def _hand_mesh(spec):
+    if spec["mesh"] == "quad":
+        n = spec["n"]
+        return I.structured_quad_mesh(n, n, periodic=(spec["periodic"],) * 2)
+    return I.structured_hex_mesh(spec["n"], 1.0, periodic=spec["periodic"])
+
+
+@pytest.mark.parametrize("case", _golden("stencils_hand.json")["cases"],
+                         ids=lambda c: f'{c["mesh"]}{c["n"]}_o{c["order"]}_c{c["cell"]}')
+def test_stencils_against_hand_enumeration(case):
+    """Central and directional stencils of a few cells of uniform 5x5, 4x4
+    periodic and 3x3x3 meshes, enumerated by hand (Sec. 2.1, 2.3; readings R3
+    and R7); the fixture gives each derivation."""
+    m = _hand_mesh(case)
+    s = O.Scheme(O.Mesh(m), order=case["order"])
+    st, dirs = s.stencil(case["cell"])
+    assert st.tolist() == case["stencil"]
+    if "directional" in case:
+        nd = s.operator(case["cell"], "nd").astype(int)
+        got = sorted(sorted(dirs[f][:nd[f]].tolist()) for f in range(len(nd)))
+        assert got == sorted(case["directional"])
+
+
+def test_stencil_construction_fails_on_a_mesh_too_small():
+    spec = _golden("stencils_hand.json")["too_small"]
+    m = _hand_mesh(spec)
+    with pytest.raises(RuntimeError, match="fewer than M cells"):
+        s = O.Scheme(O.Mesh(m), order=spec["order"])
+        s.stencil(0)
+
+
 def test_stencil_size_rule():
     # M = 2 K(r, d), K(r, d) = prod_{l=1..d}(r+l)/d!  (Sec. 2.1)
     expect2d = {2: 6, 3: 12, 4: 20, 5: 30, 6: 42}
