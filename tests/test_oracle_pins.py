@@ -634,6 +634,33 @@ def test_transmissive_boundary_conserves_up_to_boundary_flux():
     assert np.abs(R).max() < 1e-11
 
 
+@pytest.mark.parametrize("dim,periodic", [(2, False), (2, True), (3, False)])
+def test_time_step_closed_form(dim, periodic):
+    """R16 on uniform meshes, where the face sum is written by hand: the
+    faces of an hx x hy rectangle are two of length hy with normals +-x and
+    two of length hx with normals +-y, so sum_f (|u.n_f| + a)|S_f| =
+    2(|u| + a) hy + 2(|v| + a) hx (in 3D, 2 h^2 per axis); dt = CFL min |V| / that."""
+    g = 1.4
+    rng = np.random.default_rng(3 + dim)
+    if dim == 2:
+        nx, ny = 6, 4
+        m = I.structured_quad_mesh(nx, ny, periodic=(periodic, periodic))
+        hs = np.array([1.0 / nx, 1.0 / ny])
+    else:
+        m = I.structured_hex_mesh(4, 1.0, periodic=periodic)
+        hs = np.full(3, 0.25)
+    n = m.n_cells
+    rho, p = 0.5 + rng.random(n), 0.5 + rng.random(n)
+    vel = rng.uniform(-1.0, 1.0, (dim, n))
+    U = np.concatenate([rho[None], rho * vel, (p / (g - 1) + 0.5 * rho * (vel ** 2).sum(0))[None]])
+    a = np.sqrt(g * p / rho)
+    vol = np.prod(hs)
+    lam = sum(2.0 * (np.abs(vel[k]) + a) * vol / hs[k] for k in range(dim))
+    want = 0.5 * np.min(vol / lam)
+    got = O.Scheme(O.Mesh(m), order=2).dt(U, 0.5)
+    assert abs(got - want) <= 1e-14 * want
+
+
 def test_ssp_rk3_amplification_factor():
     lam = np.array([-1.0, -0.3, 0.5, -2.0])
     dt = 0.4
