@@ -226,6 +226,17 @@ HFV_API int hfv_scheme_info(const hfv_scheme* s, int64_t* info);
  * -1 past its size; dir may be NULL.  sync. */
 HFV_API int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* dir);
 
+/* The same stencils without a scheme or a GPU: the host builder that
+ * hfv_scheme_create runs (central stencil of Sec. 2.1, directional stencils
+ * of Sec. 2.3), for a mesh at an order, so the lists equal hfv_get_stencils'
+ * of a scheme of that order.  sizes[0..1] (required) receive M and Md; central
+ * (NULL: sizes only) and dir (may be NULL) have the layouts of
+ * hfv_get_stencils: [n_cells][M] and [n_cells][6][Md].  Host outputs,
+ * caller-owned.  Errors: HFV_ERR_ARG (NULL mesh or sizes, order outside
+ * 2..7), HFV_ERR_STENCIL (a cell reaches fewer than M cells within 16 face
+ * layers), HFV_ERR_OOM.  sync; touches no GPU. */
+HFV_API int hfv_stencils_host(const hfv_mesh* mesh, int order, int32_t* sizes, int32_t* central, int32_t* dir);
+
 /* One residual evaluation R(U) = dU/dt (eq. EulerEquationsDetails, inviscid)
  * with the hybrid pipeline of Sec. 2.5: linear candidate, detector
  * (eqs. DMP, NADMUSCL, NADCWENOZ, marginm, marginw, NADDeactivatedCriteria),

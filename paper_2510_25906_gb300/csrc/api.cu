@@ -6,6 +6,7 @@
 #include <chrono>
 #include <algorithm>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -205,6 +206,30 @@ extern "C" int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* 
             }
     }
     return HFV_OK;
+}
+
+extern "C" int hfv_stencils_host(const hfv_mesh* mesh, int order, int32_t* sizes, int32_t* central, int32_t* dir)
+{
+    if (!mesh || !sizes) { set_error("hfv_stencils_host: NULL argument"); return HFV_ERR_ARG; }
+    if (order < 2 || order > 7) { set_error("hfv_stencils_host: order must be 2..7"); return HFV_ERR_ARG; }
+    // the builder of hfv_scheme_create on a scheme that never reaches the
+    // device: only its host fields are filled, and its destructor frees
+    // host memory only
+    std::unique_ptr<hfv_scheme> s;
+    try {
+        s.reset(new hfv_scheme());
+        s->mesh = const_cast<hfv_mesh*>(mesh);
+        hfv_default_params(&s->p);
+        s->p.order = order;
+        const int rc = build_stencils(s.get());
+        if (rc != HFV_OK) return rc;
+    } catch (const std::bad_alloc&) {
+        set_error("hfv_stencils_host: out of host memory");
+        return HFV_ERR_OOM;
+    }
+    sizes[0] = s->M;
+    sizes[1] = s->Md;
+    return central ? hfv_get_stencils(s.get(), central, dir) : HFV_OK;
 }
 
 extern "C" int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* forced, uint8_t* cls_out, void* stream)

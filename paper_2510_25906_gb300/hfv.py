@@ -77,6 +77,7 @@ def load():
         "hfv_scheme_create": [vp, vp, vp, vp],
         "hfv_scheme_info": [vp, vp],
         "hfv_get_stencils": [vp, vp, vp],
+        "hfv_stencils_host": [vp, C.c_int, vp, vp, vp],
         "hfv_residual": [vp, vp, vp, vp, vp, vp],
         "hfv_compute_dt": [vp, vp, d, vp, vp],
         "hfv_step": [vp, vp, d, d, vp, vp],
@@ -205,6 +206,17 @@ class Mesh:
         nbrf = np.zeros((self.n_cells, 6), np.int8)
         _check(load().hfv_mesh_connectivity(self.h, nbr.ctypes.data, nbrf.ctypes.data))
         return nbr, nbrf
+
+    def stencils(self, order: int):
+        """hfv_stencils_host: (central [n_cells, M], dir [n_cells, 6, Md]) of
+        this mesh at `order`, built on the host (no GPU)."""
+        lib = load()
+        sz = np.zeros(2, np.int32)
+        _check(lib.hfv_stencils_host(self.h, order, sz.ctypes.data, None, None))
+        cen = np.zeros((self.n_cells, int(sz[0])), np.int32)
+        dr = np.zeros((self.n_cells, 6, int(sz[1])), np.int32)
+        _check(lib.hfv_stencils_host(self.h, order, sz.ctypes.data, cen.ctypes.data, dr.ctypes.data))
+        return cen, dr
 
 
 class Scheme:

@@ -1,6 +1,8 @@
 """Host-side checks of libhfv without a GPU: it builds, loads, exports every
-symbol the header declares, and its host mesh ingestion (pure CPU code)
-agrees bit for bit with the oracle's connectivity."""
+symbol the header declares, and its host mesh ingestion and stencil builder
+(pure CPU code) agree bit for bit with the oracle's connectivity and
+stencils, and with stencils enumerated by hand."""
+import json
 import math
 import os
 import re
@@ -129,3 +131,85 @@ def test_mesh_edge_cases(H):
     with pytest.raises(H.HfvError) as e:
         H.Mesh(fan)
     assert e.value.code == H.HFV_ERR_MESH
+
+
+# ---------------------------------------------------------------------------
+# the library's host stencil builder (hfv_stencils_host) without a GPU
+# ---------------------------------------------------------------------------
+
+def _compare_stencils(H, m, order, step=1):
+    """Central and directional stencils of every step-th cell, bit for bit
+    against the oracle's; entries past a directional stencil's size and the
+    rows of faces a cell does not have are -1."""
+    cen, dr = H.Mesh(m).stencils(order)
+    osch = O.Scheme(O.Mesh(m), order=order)
+    assert cen.shape[1] == osch.M and dr.shape[2] == osch.Md
+    for c in range(0, m.n_cells, step):
+        st, od = osch.stencil(c)
+        assert np.array_equal(cen[c], st), c
+        nd = osch.operator(c, "nd").astype(int)
+        nf = od.shape[0]
+        for f in range(nf):
+            assert np.array_equal(dr[c, f, :nd[f]], od[f, :nd[f]]), (c, f)
+            assert (dr[c, f, nd[f]:] == -1).all(), (c, f)
+        assert (dr[c, nf:] == -1).all(), c
+
+
+@pytest.mark.parametrize("maker,orders", [
+    (lambda: I.structured_tri_mesh(24, periodic=True, jitter=0.2, seed=1), (2, 3, 5, 7)),
+    (lambda: I.mixed_tri_quad_mesh(30, seed=2), (3, 4, 6)),
+    (lambda: I.mixed_tri_quad_mesh(20, seed=9, periodic=True), (3, 5)),
+    (lambda: I.structured_hex_mesh(12, 2 * math.pi, periodic=True), (2, 4, (6, 17))),
+    (lambda: I.structured_hex_mesh(7, 1.0, periodic=False, jitter=0.2, seed=3), (3, 4)),
+    (lambda: I.structured_tet_mesh(5, 1.0, periodic=False, jitter=0.1, seed=3), (2, 3)),
+    (lambda: I.structured_tet_mesh(4, 1.0, periodic=True), (3,)),
+    (lambda: I.mixed_element_mesh(5, nz=3, seed=13), (2, 3)),
+])
+def test_host_stencils_bit_exact_with_oracle(H, maker, orders):
+    """orders given as (order, step) compare every step-th cell (the oracle
+    builds a cell's operators when its stencil is asked for, slow at order 6
+    in 3D)."""
+    m = maker()
+    for order in orders:
+        order, step = order if isinstance(order, tuple) else (order, 1)
+        _compare_stencils(H, m, order, step)
+
+
+def test_host_stencils_bit_exact_on_the_quadrant_mesh(H):
+    """The 249,601-cell mixed mesh of the quadrant workload at order 3: every
+    seventh cell."""
+    m, _, kw = I.workload("quadrant")
+    _compare_stencils(H, m, kw["order"], step=7)
+
+
+def _hand_mesh(spec):
+    if spec["mesh"] == "quad":
+        return I.structured_quad_mesh(spec["n"], spec["n"], periodic=(spec["periodic"],) * 2)
+    return I.structured_hex_mesh(spec["n"], 1.0, periodic=spec["periodic"])
+
+
+def _hand():
+    with open(os.path.join(ROOT, "tests", "golden", "stencils_hand.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", _hand()["cases"], ids=lambda c: f'{c["mesh"]}{c["n"]}_o{c["order"]}_c{c["cell"]}')
+def test_host_stencils_against_hand_enumeration(H, case):
+    cen, dr = H.Mesh(_hand_mesh(case)).stencils(case["order"])
+    c = case["cell"]
+    assert cen[c].tolist() == case["stencil"]
+    if "directional" in case:
+        got = sorted(sorted(x for x in row.tolist() if x >= 0) for row in dr[c] if (row >= 0).any())
+        assert got == sorted(case["directional"])
+
+
+def test_host_stencils_errors(H):
+    g = H.Mesh(_hand_mesh(_hand()["too_small"]))
+    with pytest.raises(H.HfvError) as e:
+        g.stencils(_hand()["too_small"]["order"])
+    assert e.value.code == H.HFV_ERR_STENCIL
+    g = H.Mesh(I.structured_quad_mesh(5, 5))
+    for order in (1, 8):
+        with pytest.raises(H.HfvError) as e:
+            g.stencils(order)
+        assert e.value.code == H.HFV_ERR_ARG
