@@ -88,13 +88,22 @@ def test_mesh_errors(H):
     assert e.value.code == H.HFV_ERR_MESH
 
 
-def test_mixed_element_volumes_match_oracle(H):
+@pytest.mark.parametrize("maker", [
+    lambda: I.mixed_element_mesh(5, seed=7),
+    lambda: I.mixed_tri_quad_mesh(20, seed=2),
+    lambda: I.structured_tri_mesh(12, periodic=True, jitter=0.2, seed=1),
+    lambda: I.structured_hex_mesh(6, 1.0, periodic=False, jitter=0.2, seed=3),
+    lambda: I.structured_tet_mesh(4, 1.0, periodic=False, jitter=0.1, seed=3),
+])
+def test_volumes_match_oracle(H, maker):
     """The library's measures (prisms and pyramids by the divergence theorem
-    over their faces) against the oracle's volume rules."""
-    m = I.mixed_element_mesh(5, seed=7)
+    over their faces) against the oracle's volume rules, and their sum
+    against the measure of the domain (the unit square or cube)."""
+    m = maker()
     vg = H.Mesh(m).volumes()
     vo, _ = O.Mesh(m).geometry()
     assert np.abs(vg - vo).max() <= 1e-14 * vo.max()
+    assert (vg > 0).all() and abs(vg.sum() - 1.0) <= 1e-13
 
 
 def test_mesh_edge_cases(H):
