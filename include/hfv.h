@@ -354,7 +354,10 @@ HFV_API int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double 
 
 /* Class queues of the last residual (host outputs, caller-owned): counts[0]
  * = CWENOZ cells, counts[1] = MUSCL cells; queues may be NULL or hold
- * [2][n_cells] int32, each queue in ascending cell order.  sync. */
+ * [2][n_cells] int32, each queue in ascending cell order.  sync.  Errors:
+ * HFV_ERR_ARG (NULL scheme or counts), HFV_ERR_CUDA (a copy failed, or the
+ * device holds a queue length outside 0..n_cells; queues is then left
+ * unwritten). */
 HFV_API int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues);
 
 /* Sticky status bits (host output): bit0 = a state with rho <= 0, p <= 0 or

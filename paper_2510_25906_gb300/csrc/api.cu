@@ -347,8 +347,14 @@ extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream
         *knob = best;
         return r;
     };
+    auto sync = [&]() -> int {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) return HFV_OK;
+        set_error(std::string("hfv_autotune: ") + cudaGetErrorString(e));
+        return HFV_ERR_CUDA;
+    };
     if (rc == HFV_OK) rc = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);   // fills sms and the occupancy bound
-    if (rc == HFV_OK) API_CUDA(cudaStreamSynchronize(st));
+    if (rc == HFV_OK) rc = sync();
     if (rc == HFV_OK && s->linear_tiles > 1) {
         // the candidate kernel's tile shape first, each at its full occupancy
         static const int tiles[] = {0, 1};
@@ -356,7 +362,7 @@ extern "C" int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream
         s->tune_linear_per_sm = 0;
         rc = tune(&s->tune_linear_tile, tiles, 2);
         if (rc == HFV_OK) rc = launch_residual(s, U, s->a.Rs, nullptr, nullptr, st);   // the chosen shape's bound
-        if (rc == HFV_OK) API_CUDA(cudaStreamSynchronize(st));
+        if (rc == HFV_OK) rc = sync();
         if (rc != HFV_OK) s->tune_linear_per_sm = keep;
     }
     if (rc == HFV_OK) {
@@ -462,10 +468,14 @@ extern "C" int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* que
     if (!s || !counts) { set_error("hfv_get_queues: NULL argument"); return HFV_ERR_ARG; }
     API_CUDA(cudaDeviceSynchronize());
     API_CUDA(cudaMemcpy(counts, s->a.counts, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int64_t nc = s->mesh->nc;
+    if (counts[0] < 0 || counts[1] < 0 || counts[0] > nc || counts[1] > nc) {
+        set_error("hfv_get_queues: queue lengths outside 0..n_cells on the device");
+        return HFV_ERR_CUDA;
+    }
     if (queues) {
         // the device queues hold each block's cells in ascending order, the
         // blocks in the order of their range reservations: sort the copies
-        const int64_t nc = s->mesh->nc;
         API_CUDA(cudaMemcpy(queues, s->a.queue, 2 * nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
         for (int q = 0; q < 2; ++q) std::sort(queues + q * nc, queues + q * nc + counts[q]);
     }
@@ -507,7 +517,13 @@ extern "C" int hfv_kernel_timer(hfv_scheme* s, int enable)
         t.kid.assign(512, 0);
         for (auto& e : t.ev) {
             cudaEvent_t ev;
-            API_CUDA(cudaEventCreate(&ev));
+            const cudaError_t err = cudaEventCreate(&ev);
+            if (err != cudaSuccess) {
+                t.ev.erase(std::remove(t.ev.begin(), t.ev.end(), nullptr), t.ev.end());
+                timer_free(t);   // no half-built timer survives a failure
+                set_error(std::string("hfv_kernel_timer: ") + cudaGetErrorString(err));
+                return HFV_ERR_CUDA;
+            }
             e = ev;
         }
     }
