@@ -103,8 +103,9 @@ typedef struct {
     int64_t n_nodes, n_cells;
     const double* node_xyz;        /* [n_nodes][dim] */
     const uint8_t* cell_type;      /* [n_cells] HFV_TRI / HFV_QUAD (2D); HFV_TET / PRISM / PYRAMID / HEX (3D) */
-    const int64_t* cell_node_ptr;  /* [n_cells + 1] CSR offsets */
-    const int32_t* cell_node_idx;  /* [cell_node_ptr[n_cells]] vertex ids in local order */
+    const int64_t* cell_node_ptr;  /* [n_cells + 1] CSR offsets, from cell_node_ptr[0] >= 0 */
+    const int32_t* cell_node_idx;  /* [cell_node_ptr[n_cells]] vertex ids in local order: cell c's are
+                                      cell_node_idx[cell_node_ptr[c] .. cell_node_ptr[c+1] - 1] */
     const double* period;          /* [dim] periodic length per axis, 0 = open (transmissive) */
 } hfv_mesh_desc;
 
@@ -166,9 +167,14 @@ typedef struct {
 HFV_API int hfv_default_params(hfv_scheme_params* p);
 
 /* Build faces, face neighbours, periodic pairing and cell geometry.
- * Sec. 2 (mixed-element meshes).  sync.  Errors: HFV_ERR_ARG, HFV_ERR_MESH
- * (bad type/vertex count, zero or negative volume, face shared by more than
- * two cells, cell that is its own neighbour), HFV_ERR_OOM. */
+ * Sec. 2 (mixed-element meshes).  The offsets, vertex ids and coordinates are
+ * checked before anything is read through the offsets.  sync.  Errors:
+ * HFV_ERR_ARG (NULL array, dim not 2 or 3, no cells or nodes, 2^31 cells or
+ * more, a period negative or not finite), HFV_ERR_MESH (a type not of the
+ * dimension, offsets that are negative or do not step by each cell's vertex
+ * count, a vertex id outside 0..n_nodes-1, a non-finite coordinate, zero or
+ * negative volume, a face shared by more than two cells, a cell that is its
+ * own neighbour), HFV_ERR_OOM. */
 HFV_API int hfv_mesh_create(const hfv_mesh_desc* desc, hfv_mesh** out);
 
 /* A batch of independent problems as one mesh (the batched workload of many

@@ -7,6 +7,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <unordered_map>
 
 #include "hfv_internal.h"
@@ -217,6 +218,44 @@ double cell_measure(const hfv_mesh* m, int64_t c)
     return vol;
 }
 
+// a descriptor's cell types, CSR offsets (non-negative, each cell's count
+// that of its type), vertex ids, node coordinates and periods, checked before
+// anything is read through the offsets
+int check_desc(const hfv_mesh_desc& d, const std::string& who)
+{
+    const int64_t* ptr = d.cell_node_ptr;
+    if (ptr[0] < 0) {
+        set_error(who + ": cell_node_ptr[0] is negative");
+        return HFV_ERR_MESH;
+    }
+    for (int64_t c = 0; c < d.n_cells; ++c) {
+        const int t = d.cell_type[c];
+        const bool ok = ((d.dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) ||
+                         (d.dim == 3 && (t == HFV_HEX || t == HFV_TET || t == HFV_PRISM || t == HFV_PYRAMID))) &&
+                        ptr[c + 1] == ptr[c] + type_nverts(t);   // ptr[c] <= ptr[0] + 8c: no overflow
+        if (!ok) {
+            set_error(who + ": cell " + std::to_string(c) + " has an unsupported type or a vertex count not its type's");
+            return HFV_ERR_MESH;
+        }
+    }
+    for (int64_t k = ptr[0]; k < ptr[d.n_cells]; ++k)
+        if (d.cell_node_idx[k] < 0 || d.cell_node_idx[k] >= d.n_nodes) {
+            set_error(who + ": cell_node_idx[" + std::to_string(k) + "] is not a node id");
+            return HFV_ERR_MESH;
+        }
+    for (int64_t i = 0; i < d.n_nodes * d.dim; ++i)
+        if (!std::isfinite(d.node_xyz[i])) {
+            set_error(who + ": node " + std::to_string(i / d.dim) + " has a non-finite coordinate");
+            return HFV_ERR_MESH;
+        }
+    for (int k = 0; k < d.dim; ++k)
+        if (!(std::isfinite(d.period[k]) && d.period[k] >= 0.0)) {
+            set_error(who + ": periods must be finite and non-negative");
+            return HFV_ERR_ARG;
+        }
+    return HFV_OK;
+}
+
 }  // namespace
 }  // namespace hfv
 
@@ -230,6 +269,8 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
         return HFV_ERR_ARG;
     }
     *out = nullptr;
+    const int chk = check_desc(*d, "hfv_mesh_create");
+    if (chk != HFV_OK) return chk;
     hfv_mesh* m = nullptr;
     try {
         m = new hfv_mesh();
@@ -242,20 +283,8 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
             for (int k = 0; k < d->dim; ++k) m->xyz[3 * i + k] = d->node_xyz[d->dim * i + k];
         m->type.assign(d->cell_type, d->cell_type + nc);
         m->cptr.assign(d->cell_node_ptr, d->cell_node_ptr + nc + 1);
-        m->cidx.assign(d->cell_node_idx, d->cell_node_idx + m->cptr[nc]);
+        m->cidx.assign(d->cell_node_idx, d->cell_node_idx + m->cptr[nc]);   // offsets checked above
         for (int k = 0; k < 3; ++k) m->period[k] = k < d->dim ? d->period[k] : 0.0;
-        for (int64_t c = 0; c < nc; ++c) {
-            int t = m->type[c];
-            bool ok = (d->dim == 2 && (t == HFV_TRI || t == HFV_QUAD)) ||
-                      (d->dim == 3 && (t == HFV_HEX || t == HFV_TET || t == HFV_PRISM || t == HFV_PYRAMID));
-            ok = ok && m->cptr[c + 1] - m->cptr[c] == type_nverts(t);
-            for (int64_t k = m->cptr[c]; ok && k < m->cptr[c + 1]; ++k) ok = m->cidx[k] >= 0 && m->cidx[k] < m->nn;
-            if (!ok) {
-                set_error("hfv_mesh_create: cell " + std::to_string(c) + " has an unsupported type or bad vertices");
-                delete m;
-                return HFV_ERR_MESH;
-            }
-        }
         m->nbr.assign(nc * kMaxFaces, -1);
         m->nbrf.assign(nc * kMaxFaces, -1);
         m->nshift.assign(nc * kMaxFaces * 3, 0);
@@ -338,6 +367,11 @@ extern "C" int hfv_mesh_create(const hfv_mesh_desc* d, hfv_mesh** out)
                         int s = 0;
                         if (m->period[k] > 0)
                             s = (int)std::lround((x[k] / face_nverts(t, f) - y[k] / face_nverts(t2, f2)) / m->period[k]);
+                        if (s < -127 || s > 127) {
+                            set_error("hfv_mesh_create: periodic faces more than 127 periods apart");
+                            delete m;
+                            return HFV_ERR_MESH;
+                        }
                         m->nshift[(c * kMaxFaces + f) * 3 + k] = (int8_t)s;
                         m->nshift[(c2 * kMaxFaces + f2) * 3 + k] = (int8_t)(-s);
                     }
@@ -420,6 +454,8 @@ extern "C" int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, h
             set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " is invalid or of another dimension");
             return HFV_ERR_ARG;
         }
+        const int chk = check_desc(d, "hfv_mesh_create_batch: descriptor " + std::to_string(k));
+        if (chk != HFV_OK) return chk;
         for (int a = 0; a < dim; ++a)
             if (d.period[a] != 0.0) {
                 set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " is periodic; batched meshes are open");
@@ -427,7 +463,7 @@ extern "C" int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, h
             }
         nn += d.n_nodes;
         nc += d.n_cells;
-        nidx += d.cell_node_ptr[d.n_cells];
+        nidx += d.cell_node_ptr[d.n_cells] - d.cell_node_ptr[0];
     }
     if (nn >= (int64_t(1) << 31) || nc >= (int64_t(1) << 31)) {
         set_error("hfv_mesh_create_batch: more than 2^31 nodes or cells");
@@ -451,14 +487,8 @@ extern "C" int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, h
             type.insert(type.end(), d.cell_type, d.cell_type + d.n_cells);
             const int64_t base = ptr.back();
             for (int64_t c = 0; c < d.n_cells; ++c) ptr.push_back(base + d.cell_node_ptr[c + 1] - d.cell_node_ptr[0]);
-            for (int64_t i = d.cell_node_ptr[0]; i < d.cell_node_ptr[d.n_cells]; ++i) {
-                const int32_t v = d.cell_node_idx[i];
-                if (v < 0 || v >= d.n_nodes) {
-                    set_error("hfv_mesh_create_batch: descriptor " + std::to_string(k) + " has a vertex id out of range");
-                    return HFV_ERR_MESH;
-                }
-                idx.push_back((int32_t)(v + node0));
-            }
+            for (int64_t i = d.cell_node_ptr[0]; i < d.cell_node_ptr[d.n_cells]; ++i)
+                idx.push_back((int32_t)(d.cell_node_idx[i] + node0));   // ids checked by check_desc
             node0 += d.n_nodes;
             seg[k + 1] = seg[k] + d.n_cells;
         }

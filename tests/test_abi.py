@@ -222,3 +222,46 @@ def test_host_stencils_errors(H):
         with pytest.raises(H.HfvError) as e:
             g.stencils(order)
         assert e.value.code == H.HFV_ERR_ARG
+
+
+def test_descriptor_checked_before_its_offsets_are_followed(H):
+    """Offsets, vertex ids, coordinates and periods are checked before the
+    library reads through the CSR offsets; a descriptor whose offsets start
+    past 0 (with that many unused leading ids) describes the same mesh."""
+    m = I.mixed_tri_quad_mesh(6, seed=3)
+
+    def with_(**kw):
+        f = dict(dim=m.dim, nodes=m.nodes, cell_type=m.cell_type, cell_ptr=m.cell_ptr, cell_idx=m.cell_idx,
+                 period=m.period)
+        f.update(kw)
+        return I.Mesh(f["dim"], f["nodes"], f["cell_type"], f["cell_ptr"], f["cell_idx"], f["period"])
+
+    def code(mesh, batch=False):
+        with pytest.raises(H.HfvError) as e:
+            H.Mesh.batch([m, mesh]) if batch else H.Mesh(mesh)
+        return e.value.code
+
+    neg = m.cell_ptr - 1                                  # offsets from -1
+    assert code(with_(cell_ptr=neg)) == H.HFV_ERR_MESH
+    jump = m.cell_ptr.copy()
+    jump[5:] += 1                                         # cell 4 claims one vertex too many
+    assert code(with_(cell_ptr=jump)) == H.HFV_ERR_MESH
+    huge = m.cell_ptr.copy()
+    huge[-1] = 1 << 40                                    # the last cell would read far past the ids
+    assert code(with_(cell_ptr=huge)) == H.HFV_ERR_MESH
+    assert code(with_(cell_ptr=huge), batch=True) == H.HFV_ERR_MESH
+    bad_id = m.cell_idx.copy()
+    bad_id[7] = m.n_nodes
+    assert code(with_(cell_idx=bad_id)) == H.HFV_ERR_MESH
+    assert code(with_(cell_idx=bad_id), batch=True) == H.HFV_ERR_MESH
+    nan = m.nodes.copy()
+    nan[3, 1] = np.nan
+    assert code(with_(nodes=nan)) == H.HFV_ERR_MESH
+    assert code(with_(period=np.array([-1.0, 0.0]))) == H.HFV_ERR_ARG
+    assert code(with_(period=np.array([np.inf, 0.0]))) == H.HFV_ERR_ARG
+    shifted = with_(cell_ptr=m.cell_ptr + 3, cell_idx=np.concatenate([np.zeros(3, np.int32), m.cell_idx]))
+    a, b = H.Mesh(m).connectivity(), H.Mesh(shifted).connectivity()
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert np.array_equal(H.Mesh(m).volumes(), H.Mesh(shifted).volumes())
+    g = H.Mesh.batch([m, shifted])
+    assert g.n_cells == 2 * m.n_cells
