@@ -437,8 +437,8 @@ HFV_API int hfv_fma_rate(int kind, double target_ms, double* flops_per_s, void* 
  * device double [n], out device float [n], rounded to nearest, ties to even;
  * to_f32 = 0: in device float [n], out device double [n], exact.  Every
  * result equals the conversion instruction's, NaN payloads included.  async
- * on `stream`.  Errors: HFV_ERR_ARG (bad to_f32, n < 0, null buffer with
- * n > 0), HFV_ERR_CUDA. */
+ * on `stream`.  Errors: HFV_ERR_ARG (bad to_f32, n < 0 or above
+ * (2^31 - 1) * 255, null buffer with n > 0), HFV_ERR_CUDA. */
 HFV_API int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream);
 
 /* The FP64 kernels' reciprocal (the Riemann solvers, the pressure) applied
@@ -446,7 +446,7 @@ HFV_API int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* 
  * refined by two Newton-Raphson steps, within about an ulp for normal inputs
  * with normal reciprocals (instrumentation; the paper has no counterpart).
  * in, out: device double [n].  async on `stream`.  Errors: HFV_ERR_ARG
- * (n < 0, null buffer with n > 0), HFV_ERR_CUDA. */
+ * (n < 0 or above (2^31 - 1) * 255, null buffer with n > 0), HFV_ERR_CUDA. */
 HFV_API int hfv_rcp64(int64_t n, const double* in, double* out, void* stream);
 
 /* Class-queue compaction that allocates nothing (the paper has no

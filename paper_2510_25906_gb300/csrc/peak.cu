@@ -98,10 +98,13 @@ __global__ void k_convert(int to_f32, int64_t n, const void* __restrict__ in, vo
 
 using namespace hfv;
 
+// one thread per element in blocks of 256: the grid stays below 2^31 blocks
+static constexpr int64_t kMaxElems = ((int64_t(1) << 31) - 1) * 255;
+
 extern "C" int hfv_rcp64(int64_t n, const double* in, double* out, void* stream)
 {
-    if (n < 0 || (n > 0 && (!in || !out))) {
-        set_error("hfv_rcp64: n >= 0 and non-null buffers");
+    if (n < 0 || n > kMaxElems || (n > 0 && (!in || !out))) {
+        set_error("hfv_rcp64: 0 <= n <= (2^31 - 1) * 255 and non-null buffers");
         return HFV_ERR_ARG;
     }
     if (n == 0) return HFV_OK;
@@ -117,8 +120,8 @@ extern "C" int hfv_rcp64(int64_t n, const double* in, double* out, void* stream)
 
 extern "C" int hfv_convert(int to_f32, int64_t n, const void* in, void* out, void* stream)
 {
-    if (n < 0 || (n > 0 && (!in || !out)) || (to_f32 != 0 && to_f32 != 1)) {
-        set_error("hfv_convert: to_f32 must be 0 or 1, n >= 0, buffers non-null");
+    if (n < 0 || n > kMaxElems || (n > 0 && (!in || !out)) || (to_f32 != 0 && to_f32 != 1)) {
+        set_error("hfv_convert: to_f32 must be 0 or 1, 0 <= n <= (2^31 - 1) * 255, buffers non-null");
         return HFV_ERR_ARG;
     }
     if (n == 0) return HFV_OK;

@@ -265,3 +265,17 @@ def test_descriptor_checked_before_its_offsets_are_followed(H):
     assert np.array_equal(H.Mesh(m).volumes(), H.Mesh(shifted).volumes())
     g = H.Mesh.batch([m, shifted])
     assert g.n_cells == 2 * m.n_cells
+
+
+def test_elementwise_entry_points_check_sizes_before_any_cuda_call(H):
+    """hfv_convert and hfv_rcp64 refuse a negative count, a count whose grid
+    would pass 2^31 - 1 blocks and null buffers, and do nothing for n = 0,
+    all before any CUDA call (so without a GPU)."""
+    lib = H.load()
+    big = ((1 << 31) - 1) * 255 + 1
+    for n, buf in ((-1, 8), (big, 8), (4, None)):
+        assert lib.hfv_convert(1, n, buf, buf, None) == H.HFV_ERR_ARG
+        assert lib.hfv_rcp64(n, buf, buf, None) == H.HFV_ERR_ARG
+    assert lib.hfv_convert(2, 4, 8, 8, None) == H.HFV_ERR_ARG
+    assert lib.hfv_convert(0, 0, None, None, None) == H.HFV_OK
+    assert lib.hfv_rcp64(0, None, None, None) == H.HFV_OK
