@@ -279,3 +279,11 @@ def test_elementwise_entry_points_check_sizes_before_any_cuda_call(H):
     assert lib.hfv_convert(2, 4, 8, 8, None) == H.HFV_ERR_ARG
     assert lib.hfv_convert(0, 0, None, None, None) == H.HFV_OK
     assert lib.hfv_rcp64(0, None, None, None) == H.HFV_OK
+
+
+def test_static_queues_check_arguments_before_any_cuda_call(H):
+    lib = H.load()
+    for n, p in ((0, 8), (-5, 8), (16_777_217, 8), (10, None)):
+        assert lib.hfv_class_queues_static(p, n, p, p, None) == H.HFV_ERR_ARG
+    lib.hfv_class_queues_static(8, 16_777_217, 8, 8, None)
+    assert "static scratch limit of 16777216" in lib.hfv_last_error().decode()
