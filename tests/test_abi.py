@@ -287,3 +287,22 @@ def test_static_queues_check_arguments_before_any_cuda_call(H):
         assert lib.hfv_class_queues_static(p, n, p, p, None) == H.HFV_ERR_ARG
     lib.hfv_class_queues_static(8, 16_777_217, 8, 8, None)
     assert "static scratch limit of 16777216" in lib.hfv_last_error().decode()
+
+
+def test_abi_from_plain_c(H, tmp_path):
+    """include/hfv.h compiles as C99 and a C program linked against
+    libhfv.so builds a mesh, reads its measures and host stencils, and sees
+    the error codes and messages (tests/c/abi_from_c.c)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(H.LIB_PATH)
+    exe = str(tmp_path / "abi_from_c")
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-O1", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "c", "abi_from_c.c"), "-o", exe, "-L", lib_dir, "-lhfv", "-lm",
+           f"-Wl,-rpath,{lib_dir}"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True, timeout=120)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
