@@ -383,6 +383,67 @@ def test_smoothness_indicator_closed_form():
             assert abs(si - ex) < 1e-11
 
 
+def _tri_quadratic_integral(f, a, b, c):
+    """Exact integral of a quadratic over the triangle abc: the area times the
+    mean of f at the edge midpoints."""
+    area = 0.5 * abs((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]))
+    return area / 3.0 * (f((a + b) / 2) + f((b + c) / 2) + f((c + a) / 2))
+
+
+def test_reference_map_and_indicator_on_quadrilaterals():
+    """R4 and R5 on jittered quadrilaterals, independently of the oracle's own
+    map: the reference map is the affine map of the corner simplex v0 v1 v3
+    (v0 -> 0, v1 -> e1, v3 -> e2), so the cell's image has corners 0, e1,
+    w = J^-1 (v2 - v0), e2; the indicator of p = xi^2 is int (2 xi)^2 + 2^2
+    over that image (h_c = 1, Sec. 2.3), and of p = xi its area, both
+    integrated exactly over the image's two triangles."""
+    m = I.structured_quad_mesh(8, 8, jitter=0.2, seed=4)
+    s = O.Scheme(O.Mesh(m), order=3)
+    for c in (9, 27, 36, 50):
+        v = m.cell_vertices(c)
+        J = np.stack([v[1] - v[0], v[3] - v[0]], axis=1)
+        Ji = np.linalg.inv(J)
+        x0, Jo = s.refmap(c)
+        assert np.allclose(x0[:2], v[0], rtol=0, atol=1e-15)
+        assert np.allclose(Jo[:2, :2], Ji, rtol=1e-13, atol=0)
+        w = Ji @ (v[2] - v[0])
+        e0, e1, e2 = np.zeros(2), np.array([1.0, 0.0]), np.array([0.0, 1.0])
+        tris = ((e0, e1, w), (e0, w, e2))
+        area = sum(_tri_quadratic_integral(lambda q: 1.0, *t) for t in tris)
+        ixx = sum(_tri_quadratic_integral(lambda q: q[0] ** 2, *t) for t in tris)
+        xi = lambda x, y: Ji[0, 0] * (x - v[0][0]) + Ji[0, 1] * (y - v[0][1])
+        for f, ex in ((lambda x, y: xi(x, y) ** 2, 4.0 * ixx + 4.0 * area), (lambda x, y: xi(x, y), area)):
+            rho = I.cell_average_2d(m, f, npts=8)
+            st, _ = s.stencil(c)
+            a = s.operator(c, "P") @ (rho[st] - rho[c])
+            assert abs(a @ s.operator(c, "OI") @ a - ex) < 1e-10 * ex
+
+
+@pytest.mark.parametrize("h", [1.0, 1e-2])
+def test_indicator_is_scale_free_on_hexahedra(h):
+    """Uniform hexahedra of edge h: the corner simplex v0 v1 v3 v4 maps the
+    cell onto the unit cube whatever h is, so the indicator of p = xi^2
+    (xi = x / h about the cell's corner) is int (2 xi)^2 + 2^2 over the cube =
+    4/3 + 4 = 16/3 at every h (R4, R5); cell averages of the quadratic are
+    taken in closed form."""
+    n = 6
+    m = I.structured_hex_mesh(n, n * h, periodic=False)
+    s = O.Scheme(O.Mesh(m), order=3)
+    c = (2 * n + 2) * n + 3          # cell (3, 2, 2)
+    x0, Jo = s.refmap(c)
+    lo = m.cell_vertices(c)[0]
+    assert np.allclose(x0, lo, rtol=0, atol=1e-15 * n * h)
+    assert np.allclose(Jo, np.eye(3) / h, rtol=1e-13, atol=0)
+    # mean of ((x - lo_x) / h)^2 over the cell whose lower corner is at x = k h
+    # relative to lo_x: ((k + 1)^3 - k^3) / 3
+    vm = m.vertex_means()
+    k = np.rint((vm[:, 0] - h / 2 - lo[0]) / h)
+    rho = ((k + 1) ** 3 - k ** 3) / 3.0
+    st, _ = s.stencil(c)
+    a = s.operator(c, "P") @ (rho[st] - rho[c])
+    assert abs(a @ s.operator(c, "OI") @ a - 16.0 / 3.0) < 1e-10
+
+
 def test_cweno_weights_are_convex_and_favour_smooth_stencils():
     m = I.structured_quad_mesh(16, 16, jitter=0.1, seed=3)
     s = O.Scheme(O.Mesh(m), order=3)
