@@ -579,6 +579,32 @@ def test_step_on_quad_strip_flags_jump_and_its_neighbourhood():
             assert (tag[near] == cls).all() and (tag[~near] == O.LIN).all()
 
 
+def test_detector_watches_density_and_pressure_only():
+    """R10: the detector checks rho and p (the Harten variables of Sec. 2.4).
+    A shear layer -- tangential velocity jumping from +0.5 to -0.5 across
+    x = 0.5 with rho and p uniform -- leaves both flat, so every cell stays
+    linear, although momentum and energy jump; checking every conserved
+    variable instead flags the two cells at the jump.  A contact (rho jumps, p
+    uniform) is flagged under the default."""
+    nx, ny = 24, 12
+    m = I.structured_quad_mesh(nx, ny, 1.0, 0.5, periodic=(False, True))
+    vm = m.vertex_means()
+    left = vm[:, 0] < 0.5
+    one = np.ones(m.n_cells)
+    col = np.arange(m.n_cells) % nx
+    at_jump = (col == 11) | (col == 12)
+    shear = I.conserved_2d(one, 0 * one, np.where(left, 0.5, -0.5), one)
+    contact = I.conserved_2d(np.where(left, 1.0, 0.5), 0 * one, 0 * one, one)
+    for order in (3, 5):
+        s = O.Scheme(O.Mesh(m), order=order, flux="hllc")
+        assert (s.residual(shear)[1] == O.LIN).all()
+        raw = s.residual(contact)[1]
+        assert (raw[at_jump] != O.LIN).all() and (raw[~at_jump] == O.LIN).all()
+        s_all = O.Scheme(O.Mesh(m), order=order, flux="hllc", nad_vars=7)
+        raw = s_all.residual(shear)[1]
+        assert (raw[at_jump] != O.LIN).all() and (raw[~at_jump] == O.LIN).all()
+
+
 def test_hybrid_equals_linear_when_detector_is_deactivated():
     """Sec. 3.1: with no troubled cell the hybrid operates as the linear scheme."""
     m = I.structured_tri_mesh(16, periodic=True, jitter=0.2, seed=1)
