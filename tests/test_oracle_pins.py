@@ -605,6 +605,36 @@ def test_detector_watches_density_and_pressure_only():
         assert (raw[at_jump] != O.LIN).all() and (raw[~at_jump] == O.LIN).all()
 
 
+def test_detector_margins_act_in_the_direction_the_paper_describes():
+    """R11 and R12 on the quadrant problem: a larger beta_w > 0 widens the
+    linear band (Sec. 2.5 -- under the printed sign it would narrow it), so
+    the linear cells only ever grow with it, and a larger kappa deactivates
+    more cells.  With kappa = 0 nothing is deactivated and no raw class is
+    linear, not even in the uniform quadrants (the candidate there equals the
+    neighbours' extremes, outside the open band); with a huge kappa every cell
+    is deactivated."""
+    m = I.mixed_tri_quad_mesh(24, seed=2)
+    U = I.quadrant_state(m)
+
+    def linear(**kw):
+        return O.Scheme(O.Mesh(m), order=3, flux="hllc", **kw).residual(U)[1] == O.LIN
+
+    prev = None
+    for bw in (-0.5, 0.0, 1e-2, 0.1, 0.5):
+        lin = linear(beta_w=bw)
+        if prev is not None:
+            assert (lin >= prev).all(), bw
+        prev = lin
+    assert linear(beta_w=0.5).sum() > linear(beta_w=0.0).sum()
+    prev = None
+    for k in (0.0, 0.5, 1.0, 4.0, 1e3):
+        lin = linear(kappa=k)
+        if prev is not None:
+            assert (lin >= prev).all(), k
+        prev = lin
+    assert not linear(kappa=0.0).any() and linear(kappa=1e3).all()
+
+
 def test_hybrid_equals_linear_when_detector_is_deactivated():
     """Sec. 3.1: with no troubled cell the hybrid operates as the linear scheme."""
     m = I.structured_tri_mesh(16, periodic=True, jitter=0.2, seed=1)
