@@ -130,21 +130,21 @@ def _stream(stream):
 
 
 def default_params(**kw) -> hfv_scheme_params:
+    """hfv_default_params with the given fields replaced; enumerated fields
+    also take their names ("hllc", "fp32", ...).  An unknown field or name
+    raises instead of being ignored."""
     p = hfv_scheme_params()
     _check(load().hfv_default_params(C.byref(p)))
+    fields = {f[0] for f in hfv_scheme_params._fields_}
+    names = {"flux": FLUX, "scheme": SCHEME, "precision": PRECISION, "time_scheme": TIME_SCHEME,
+             "limiter": LIMITER, "cweno_vars": CWENO_VARS}
     for k, v in kw.items():
-        if k == "flux" and isinstance(v, str):
-            v = FLUX[v]
-        elif k == "scheme" and isinstance(v, str):
-            v = SCHEME[v]
-        elif k == "precision" and isinstance(v, str):
-            v = PRECISION[v]
-        elif k == "time_scheme" and isinstance(v, str):
-            v = TIME_SCHEME[v]
-        elif k == "limiter" and isinstance(v, str):
-            v = LIMITER[v]
-        elif k == "cweno_vars" and isinstance(v, str):
-            v = CWENO_VARS[v]
+        if k not in fields:
+            raise TypeError(f"unknown scheme parameter {k!r}; the fields are {sorted(fields)}")
+        if k in names and isinstance(v, str):
+            if v not in names[k]:
+                raise ValueError(f"{k} = {v!r}: one of {sorted(names[k])}")
+            v = names[k][v]
         setattr(p, k, v)
     return p
 

@@ -39,6 +39,20 @@ def test_exports_every_declared_symbol(H):
         assert hasattr(lib, n), n
 
 
+def test_unknown_scheme_parameters_raise(H):
+    """A misspelt field or an unknown name raises instead of leaving the
+    default silently in place."""
+    p = H.default_params(order=5, flux="hll", precision="fp32", limiter="venkatakrishnan", step_chain=1)
+    assert (p.order, p.flux, p.precision, p.limiter, p.step_chain) == (5, H.HFV_HLL, H.HFV_FP32,
+                                                                       H.LIMITER["venkatakrishnan"], 1)
+    with pytest.raises(TypeError):
+        H.default_params(presicion="fp32")
+    with pytest.raises(ValueError):
+        H.default_params(flux="roe")
+    with pytest.raises(ValueError):
+        H.default_params(precision="fp16")
+
+
 def test_default_params(H):
     p = H.default_params()
     assert (p.order, p.flux, p.scheme, p.nad_vars, p.precision) == (3, H.HFV_HLLC, H.HFV_HYBRID, 3, H.HFV_FP64)
