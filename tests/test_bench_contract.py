@@ -55,3 +55,34 @@ def test_kernel_times_are_the_median_over_steps():
     assert t["linear"][1] == 27 and abs(t["linear"][0] / t["linear"][1] - 0.030) < 1e-12
     assert abs(t["tag"][0] - 0.005 * 27) < 1e-12
     assert t["cvt"] == (0.0, 1)
+
+
+def test_byte_model_against_hand_counts():
+    """The algorithmic bytes behind the roofline, counted by hand at FP32
+    (b = 4): order 3 in 2D (M = 12, two points per face, nv = 4) a triangle
+    reads U 16 + stencil ids 48 + L 6*12*4 = 288 + face geometry 1.5*3*4 = 18 +
+    1/|V| 4 + face neighbours 12 and writes R 16: 402 B; a quadrilateral
+    16 + 48 + 384 + 24 + 4 + 16 + 16 = 508 B.  Order 4 on hexahedra (M = 40,
+    four points per face, nv = 5): 20 + 160 + 3840 + 48 + 4 + 24 + 20 = 4116 B.
+    The candidate kernel's own bytes add the face states written and drop the
+    flux kernel's geometry and R: 462 B per triangle, 590 B per quadrilateral,
+    125,981,518 B per launch on the 249,601-cell quadrant mesh."""
+    from types import SimpleNamespace as NS
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2510_25906_gb300 import inputs as I
+    s2 = NS(nv=4, M=12, N=5, Md=6, nfp=2)
+    tri = NS(dim=2, cell_type=np.full(5, I.TRI, np.uint8), n_cells=5)
+    quad = NS(dim=2, cell_type=np.full(5, I.QUAD, np.uint8), n_cells=5)
+    assert bench.path_model(tri, s2, 4)["B_lin"] == 402.0
+    assert bench.path_model(quad, s2, 4)["B_lin"] == 508.0
+    hexes = NS(dim=3, cell_type=np.full(5, I.HEX, np.uint8), n_cells=5)
+    assert bench.path_model(hexes, NS(nv=5, M=40, N=19, Md=8, nfp=4), 4)["B_lin"] == 4116.0
+    assert bench._k1_bytes(tri, s2, 4) == 5 * 462 and bench._k1_bytes(quad, s2, 4) == 5 * 590
+    m, _, _ = I.workload("quadrant")
+    ntri = int((m.cell_type == I.TRI).sum())
+    assert (ntri, m.n_cells - ntri) == (166_274, 83_327)
+    assert bench._k1_bytes(m, s2, 4) == 125_981_518
+    assert abs(bench.path_model(m, s2, 4)["B_lin"] * m.n_cells - 109_172_264) < 1.0
