@@ -86,3 +86,29 @@ def test_byte_model_against_hand_counts():
     assert (ntri, m.n_cells - ntri) == (166_274, 83_327)
     assert bench._k1_bytes(m, s2, 4) == 125_981_518
     assert abs(bench.path_model(m, s2, 4)["B_lin"] * m.n_cells - 109_172_264) < 1.0
+
+
+def test_path_roofline_takes_the_lower_ceiling():
+    """frac = value / min(HBM ceiling, FP64 FMA ceiling) for an FP64 path,
+    value x B_alg / HBM peak for an FP32 one; B_alg adds the queued classes'
+    bytes at their measured fractions."""
+    from types import SimpleNamespace as NS
+
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2510_25906_gb300 import inputs as I
+    mesh = NS(dim=2, cell_type=np.full(8, I.QUAD, np.uint8), n_cells=8)
+    sz = dict(nv=4, M=12, N=5, Md=6, nfp=2)
+    peaks = {"hbm_gbs": 6000.0, "fp64_flops": 1.0e12}
+    r32 = bench.path_roofline(mesh, NS(fp32=True, **sz), 1.0e9, (0.1, 0.05), peaks)
+    pm = bench.path_model(mesh, NS(**sz), 4)
+    B = pm["B_lin"] + 0.1 * pm["B_cweno"] + 0.05 * pm["B_muscl"]
+    assert r32["bound"] == "hbm" and abs(r32["frac"] - B * 1e9 / 6e12) < 1e-12
+    r64 = bench.path_roofline(mesh, NS(fp32=False, **sz), 1.0e8, (0.1, 0.05), peaks)
+    pm = bench.path_model(mesh, NS(**sz), 8)
+    B = pm["B_lin"] + 0.1 * pm["B_cweno"] + 0.05 * pm["B_muscl"]
+    F = pm["F_lin"] + 0.1 * pm["F_cweno"] + 0.05 * pm["F_muscl"]
+    hbm, alu = 6e12 / B, 1e12 / F
+    assert r64["bound"] == ("fp64_alu" if alu < hbm else "hbm")
+    assert abs(r64["frac"] - 1e8 / min(alu, hbm)) < 1e-12
