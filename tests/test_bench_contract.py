@@ -1,7 +1,8 @@
 """Host-side pieces of bench.py (CPU): the reference arm's JSON line (the
-oracle timed on the host cores) carries the contract's keys, and the DRAM
+oracle timed on the host cores) carries the contract's keys, the DRAM
 traffic figure is reported only while the candidate kernel's sources hash to
-the build it was captured on."""
+the build it was captured on, per-kernel times are medians over steps, and
+the roofline's byte model and ceiling choice match counts made by hand."""
 import json
 import os
 import subprocess
