@@ -13,14 +13,21 @@
  *   Sec. 2 (eq. EulerEquationsDetails)      finite-volume residual
  *   Sec. 2.1 (eqs. AVGVariables1/2, dofMatrix and the pseudo-inverse)
  *                                            least-squares reconstruction
- *   Sec. 2.2                                MUSCL with Barth-Jespersen
- *   Sec. 2.3 (CWENOZ weights, tau, SI, OI)  CWENOZ
+ *   Sec. 2.2                                MUSCL with Barth-Jespersen or
+ *                                            Venkatakrishnan's limiter
+ *   Sec. 2.3 (CWENOZ weights, tau, SI, OI)  CWENOZ, in conserved or
+ *                                            characteristic variables
  *   Sec. 2.4 (eq. harten_jump_fix)          TVD bound, first-order fallback
  *   Sec. 2.5 (eqs. DMP, NADMUSCL, NADCWENOZ, marginm, marginw,
  *             NADDeactivatedCriteria(_2)) and the closing description of
  *             the hybrid pipeline           detector, tagging, pipeline
+ *   Sec. 2 (eqs. EulerEquationsDetails, HeatConduct, viscous_jump)
+ *                                            viscous flux, heat conduction
+ *   SSP-RK3 (Shu-Osher) and SSP-RK(5,4) (Spiteri-Ruuth) time steps
  * Readings taken where the paper is silent or garbled are stated next to the
- * code that uses them.
+ * code that uses them.  Every step is pinned by the CPU tests
+ * (tests/test_oracle_*.py) to closed forms, invariants, library routines,
+ * brute force or the paper's own statements; none is left unpinned.
  *
  * Basis: monomials xi^a eta^b zeta^c of total degree 1..r in the reference
  * coordinates of the considered cell, made mean-free over that cell.  The
@@ -31,8 +38,12 @@
  *
  * Quadrature: every volume integral uses a tensor Gauss-Legendre rule with
  * r+2 points per direction on a map from the unit square / cube (collapsed
- * for triangles).  That rule is exact for every integrand used here.
- * Face integrals use Gauss-Legendre with ceil((r+1)/2) points per direction.
+ * for triangles, tetrahedra, prisms and pyramids).  That rule is exact for
+ * every integrand used here.  Face integrals use Gauss-Legendre with
+ * ceil((r+1)/2) points per direction on edges and on the quadrilaterals of
+ * all-hexahedral meshes; a mesh with triangular faces uses the collapsed
+ * rule with ceil((r+2)/2) points per direction on them, and as many per
+ * direction on its quadrilaterals.
  */
 #include <math.h>
 #include <stdint.h>
