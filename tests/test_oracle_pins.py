@@ -706,6 +706,41 @@ def test_rusanov_textbook():
     assert np.allclose(O.flux("rusanov", UL, UR, n), ex, rtol=1e-14)
 
 
+def test_hllc_star_flux_from_the_rankine_hugoniot_conditions():
+    """HLLC (R18) in the form derived from the Rankine-Hugoniot conditions
+    across the wave S_K and the contact (Toro, Riemann Solvers, Sec. 10.4):
+    F*_K = [S* (S_K U_K - F_K) + S_K p* D*] / (S_K - S*), D* = (0, n, S*),
+    p* = p_K + rho_K (S_K - u_K)(S* - u_K), which equals the flux of the
+    explicit star state F_K + S_K (U*_K - U_K) the oracle evaluates.  Random
+    subsonic pairs in 2D and 3D, on both sides of the contact."""
+    rng = np.random.default_rng(7)
+    g = 1.4
+    checked = [0, 0]
+    for trial in range(400):
+        d = 2 + trial % 2
+        n = rng.standard_normal(d)
+        n /= np.linalg.norm(n)
+        rl, rr = 0.5 + rng.random(2)
+        pl, pr = 0.5 + rng.random(2)
+        ul, ur = 0.6 * rng.standard_normal((2, d))
+        UL, UR = _cons(rl, ul, pl), _cons(rr, ur, pr)
+        unl, unr = ul @ n, ur @ n
+        cl, cr = math.sqrt(g * pl / rl), math.sqrt(g * pr / rr)
+        SL, SR = min(unl - cl, unr - cr), max(unl + cl, unr + cr)
+        if SL >= 0 or SR <= 0:
+            continue
+        Ss = (pr - pl + rl * unl * (SL - unl) - rr * unr * (SR - unr)) / (rl * (SL - unl) - rr * (SR - unr))
+        K = (UL, SL, rl, unl, pl) if Ss >= 0 else (UR, SR, rr, unr, pr)
+        UK, SK, rk, uk, pk = K
+        ps = pk + rk * (SK - uk) * (Ss - uk)
+        D = np.r_[0.0, n, Ss]
+        want = (Ss * (SK * UK - _phys(UK, n)) + SK * ps * D) / (SK - Ss)
+        got = O.flux("hllc", UL, UR, n)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12), (trial, got, want)
+        checked[int(Ss >= 0)] += 1
+    assert min(checked) >= 50
+
+
 # ---------------------------------------------------------------------------
 # residual, time stepping and order of accuracy
 # ---------------------------------------------------------------------------

@@ -116,6 +116,32 @@ def test_viscous_time_step_keeps_the_quadrant_problem_physical():
     assert np.isfinite(U).all() and (U[0] > 0).all() and (p > 0).all()
 
 
+@pytest.mark.parametrize("prandtl", [0.72, 2.0])
+def test_viscous_time_step_closed_form(prandtl):
+    """R29 on a uniform hx x hy quadrilateral mesh, where the face sums are
+    written by hand: sum_f (|u.n_f| + a)|S_f| = 2(|u| + a) hy + 2(|v| + a) hx
+    and sum_f |S_f|^2 / |V| = 2 (hx^2 + hy^2) / (hx hy); the diffusion limit
+    adds 4 nu times the latter, nu = max(4/3, gamma/Pr) mu / rho with
+    Sutherland's mu(T = p / rho).  Pr = 2 makes 4/3 the larger factor."""
+    g, T0, S, mu0 = 1.4, 1.0, 110.4 / 288.15, 0.05
+    nx, ny = 6, 4
+    hx, hy = 1.0 / nx, 1.0 / ny
+    m = I.structured_quad_mesh(nx, ny)
+    rng = np.random.default_rng(11)
+    n = m.n_cells
+    rho, p = 0.5 + rng.random(n), 0.5 + rng.random(n)
+    u, v = rng.uniform(-1.0, 1.0, (2, n))
+    U = np.stack([rho, rho * u, rho * v, p / (g - 1) + 0.5 * rho * (u * u + v * v)])
+    a = np.sqrt(g * p / rho)
+    T = p / rho
+    mu = mu0 * (T / T0) ** 1.5 * (T0 + S) / (T + S)
+    nu = max(4.0 / 3.0, g / prandtl) * mu / rho
+    lam = 2 * (np.abs(u) + a) * hy + 2 * (np.abs(v) + a) * hx + 4 * nu * 2 * (hx * hx + hy * hy) / (hx * hy)
+    want = 0.5 * np.min(hx * hy / lam)
+    got = O.Scheme(O.Mesh(m), order=2, mu0=mu0, t0=T0, suth_s=S, prandtl=prandtl).dt(U, 0.5)
+    assert abs(got - want) <= 1e-14 * want
+
+
 def _manufactured():
     sp = pytest.importorskip("sympy")
     x, y = sp.symbols("x y")
