@@ -635,6 +635,30 @@ def test_detector_margins_act_in_the_direction_the_paper_describes():
     assert not linear(kappa=0.0).any() and linear(kappa=1e3).all()
 
 
+@pytest.mark.parametrize("n_exp", [1.0, 2.0])
+def test_deactivation_threshold_flips_where_the_closed_form_says(n_exp):
+    """R12 (eq. NADDeactivatedCriteria): a cell is deactivated when the spread
+    of |U_j - U_i| over its face neighbours is below (kappa dx)^n, dx =
+    |V|^(1/d).  At a density contact (pressure and velocity uniform) on unit
+    squares of edge h, the two cells at the jump J see |dU| = {0, J, 0, 0}, a
+    spread of J, so they turn linear exactly when kappa passes J^(1/n) / h;
+    pressure, uniform, is deactivated for any kappa > 0."""
+    nx, ny = 24, 12
+    m = I.structured_quad_mesh(nx, ny, 1.0, 0.5, periodic=(False, True))
+    h = 1.0 / nx
+    vm = m.vertex_means()
+    J = 0.875
+    one = np.ones(m.n_cells)
+    U = I.conserved_2d(np.where(vm[:, 0] < 0.5, 1.0, 1.0 - J), 0 * one, 0 * one, one)
+    col = np.arange(m.n_cells) % nx
+    at_jump = (col == 11) | (col == 12)
+    k_flip = J ** (1.0 / n_exp) / h
+    below = O.Scheme(O.Mesh(m), order=3, flux="hllc", kappa=0.98 * k_flip, n_exp=n_exp).residual(U)[1]
+    above = O.Scheme(O.Mesh(m), order=3, flux="hllc", kappa=1.02 * k_flip, n_exp=n_exp).residual(U)[1]
+    assert (below[at_jump] != O.LIN).all() and (below[~at_jump] == O.LIN).all()
+    assert (above == O.LIN).all()
+
+
 def test_hybrid_equals_linear_when_detector_is_deactivated():
     """Sec. 3.1: with no troubled cell the hybrid operates as the linear scheme."""
     m = I.structured_tri_mesh(16, periodic=True, jitter=0.2, seed=1)
