@@ -118,6 +118,64 @@ def test_venkatakrishnan_limits_at_a_jump():
         assert np.allclose(d[np.abs(df) > 0] / df[np.abs(df) > 0], (d / np.where(df == 0, 1, df))[np.abs(df) > 0][0])
 
 
+def _venkat_theta(s, sfree, U, c, v):
+    """the limiter value of variable v at cell c, read off the reconstruction:
+    (V - u0) = theta (V_free - u0) at every face point, V_free the unlimited
+    (huge threshold) reconstruction of the same gradient; also the unlimited
+    increments"""
+    u0 = U[v, c]
+    d = s.reconstruct(U, c, O.MU)[:, v] - u0
+    df = sfree.reconstruct(U, c, O.MU)[:, v] - u0
+    k = int(np.argmax(np.abs(df)))
+    th = d[k] / df[k]
+    assert np.allclose(d, th * df, rtol=0, atol=1e-13 * (1.0 + abs(u0)))
+    return float(th), df
+
+
+def test_venkatakrishnan_limiter_values():
+    """R21, by two properties of the published limiter and its value.
+    (a) With K = 0 (eps = 0), phi(y) = (y^2 + 2y) / (y^2 + y + 2) of
+    y = Delta_1 / Delta_2 reaches 1 exactly at y = 2: a cell is limited
+    (theta < 1) exactly when some face point's increment exceeds half the
+    distance to the bound on its side (bounds over the cell and its face
+    neighbours); theta then equals the published value.  (b) eps^2 = (K dx)^3:
+    phi depends on Delta / eps only, so scaling every difference of the data
+    by sigma is the same as scaling K by sigma^(-2/3)."""
+    m = I.mixed_tri_quad_mesh(14, seed=6)
+    om = O.Mesh(m)
+    nbr, _ = om.connectivity()
+    vol, _ = om.geometry()
+    s0 = O.Scheme(om, order=3, limiter="venkatakrishnan", venkat_k=0.0)
+    sf = O.Scheme(om, order=3, limiter="venkatakrishnan", venkat_k=1e6)
+    U = _random_state(m, 4)
+    v = 1
+    limited = free = 0
+    for c in range(0, m.n_cells, 3):
+        th, df = _venkat_theta(s0, sf, U, c, v)
+        nb = [j for j in nbr[c] if j >= 0] + [c]
+        hi, lo = U[v, nb].max() - U[v, c], U[v, nb].min() - U[v, c]
+        d1 = np.where(df > 0, hi, lo)
+        y = d1[df != 0] / df[df != 0]
+        phi = np.minimum(1.0, (y * y + 2 * y) / (y * y + y + 2))
+        assert (th < 1.0 - 1e-12) == bool((y < 2.0 - 1e-9).any()), (c, th, y.min())
+        assert abs(th - phi.min()) < 1e-12
+        limited += th < 1.0
+        free += th == 1.0
+    assert limited >= 20 and free >= 5
+    sigma, K = 8.0, 0.3
+    Us = U.copy()
+    Us[v] = sigma * U[v]
+    sk = O.Scheme(om, order=3, limiter="venkatakrishnan", venkat_k=K)
+    sk2 = O.Scheme(om, order=3, limiter="venkatakrishnan", venkat_k=K * sigma ** (-2.0 / 3.0))
+    moved = 0
+    for c in range(0, m.n_cells, 3):
+        a, _ = _venkat_theta(sk, sf, Us, c, v)
+        b, _ = _venkat_theta(sk2, sf, U, c, v)
+        assert abs(a - b) < 1e-10, (c, a, b)
+        moved += abs(a - _venkat_theta(sk, sf, U, c, v)[0]) > 1e-6
+    assert moved >= 10
+
+
 # ---------------------------------------------------------------------------
 # CWENOZ in characteristic variables
 # ---------------------------------------------------------------------------
