@@ -765,6 +765,72 @@ def test_hllc_star_flux_from_the_rankine_hugoniot_conditions():
     assert min(checked) >= 50
 
 
+def _tiled_twice(small, shape):
+    """the periodic mesh `small` (structured, nodes numbered x fastest) and
+    its two periodic images side by side along x as one periodic mesh of
+    twice the length; returns (big, tile, first): big cell -> small cell, and
+    the big cells of the first image in small-cell order"""
+    dims = list(shape)                      # cells per direction, x first
+    nx = dims[0]
+    L = small.period[0]
+    if small.dim == 2:
+        big = I.structured_quad_mesh(2 * nx, dims[1], 2 * L, small.period[1], periodic=(True, True))
+    else:
+        big = I.structured_hex_mesh(2 * nx, 2 * L, periodic=True, ny=dims[1], nz=dims[2])
+        big = I.Mesh(3, big.nodes, big.cell_type, big.cell_ptr, big.cell_idx,
+                     np.array([2 * L, small.period[1], small.period[2]]))
+    npd = [d + 1 for d in dims]
+    nodes = big.nodes.copy()
+    for b in range(nodes.shape[0]):
+        i, rest = b % (2 * nx + 1), b // (2 * nx + 1)
+        k, r = divmod(i, nx)
+        if i == 2 * nx:
+            k, r = 1, nx
+        nodes[b] = small.nodes[rest * npd[0] + r] + np.r_[k * L, np.zeros(small.dim - 1)]
+    big = I.Mesh(small.dim, nodes, big.cell_type, big.cell_ptr, big.cell_idx, big.period)
+    rows = int(np.prod(dims[1:]))
+    tile = np.array([q * nx + (i % nx) for q in range(rows) for i in range(2 * nx)])
+    first = np.array([q * 2 * nx + i for q in range(rows) for i in range(nx)])
+    return big, tile, first
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_images_give_the_same_residual(dim):
+    """A jittered periodic mesh and two of its periodic images joined into
+    one periodic mesh describe the same flow: each cell of the first image
+    must get the small mesh's residual (hybrid, HLLC, with and without the
+    viscous terms) and class.  The small mesh's periodic seam is an interior
+    face of the big one, so every use of a periodic shift -- stencil cells,
+    directional stencils, face pairing, the viscous centre distance L_int --
+    is checked against the same computation without one."""
+    rng = np.random.default_rng(3 + dim)
+    if dim == 2:
+        shape = (8, 6)
+        small = I.structured_quad_mesh(*shape, 1.0, 1.0, periodic=(True, True), jitter=0.2, seed=5)
+        order = 3
+    else:
+        shape = (6, 6, 6)
+        small = I.structured_hex_mesh(6, 1.0, periodic=True, jitter=0.15, seed=5)
+        order = 2
+    big, tile, first = _tiled_twice(small, shape)
+    n = small.n_cells
+    rho, p = 0.8 + 0.4 * rng.random(n), 0.8 + 0.4 * rng.random(n)
+    vel = rng.uniform(-0.5, 0.5, (dim, n))
+    Us = np.concatenate([rho[None], rho * vel, (p / 0.4 + 0.5 * rho * (vel ** 2).sum(0))[None]])
+    vm = small.vertex_means()
+
+    def band(jump):     # a smooth wave and a density band: linear, CWENOZ, MUSCL and first-order cells
+        r = 1.0 + 0.2 * np.sin(2 * math.pi * vm[:, 0]) + np.where(np.abs(vm[:, 1] - 0.5) < 0.2, jump, 0.0)
+        return np.concatenate([r[None], 0.3 * r[None], np.zeros((dim - 1, n)), (1.0 / 0.4 + 0.045 * r)[None]])
+
+    for U in (Us, band(0.5), band(4.0)):
+        for kw in ({}, {"mu0": 0.05}):
+            Rs, _, _, fs = O.Scheme(O.Mesh(small), order=order, flux="hllc", **kw).residual(U)
+            Rb, _, _, fb = O.Scheme(O.Mesh(big), order=order, flux="hllc", **kw).residual(U[:, tile])
+            assert np.array_equal(fb[first], fs)
+            assert np.abs(Rb[:, first] - Rs).max() <= 1e-12 * np.abs(Rs).max(), kw
+
+
 # ---------------------------------------------------------------------------
 # residual, time stepping and order of accuracy
 # ---------------------------------------------------------------------------
