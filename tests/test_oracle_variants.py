@@ -254,6 +254,35 @@ def test_characteristic_cweno_conserves_and_preserves_free_stream():
     assert np.abs(R - Rc).max() > 1e-6 * np.abs(Rc).max()
 
 
+@pytest.mark.parametrize("seed", [3, 5])
+def test_characteristic_cweno_respects_the_mirror_symmetry(seed):
+    """R24 projects each face's points with the eigenvectors of that face's
+    normal.  On unit squares with data symmetric under the reflection x <-> y
+    (density and energy symmetric, the two momenta swapped), a cell on the
+    diagonal has mirror-image stencils and faces, so the value at each face
+    point must be the mirror of the value at the reflected point (momenta
+    swapped); projecting every face with one normal breaks that.  Random
+    symmetric data: every cell is non-smooth.  Order 3: its stencil is two
+    whole face layers, and so are its directional stencils (higher orders
+    break distance ties by cell id, which the reflection does not keep)."""
+    n = 8
+    m = I.structured_quad_mesh(n, n, periodic=(True, True))
+    rng = np.random.default_rng(seed)
+    r = 1.0 + rng.random((n, n))
+    E = 6.0 + rng.random((n, n))
+    pu = rng.standard_normal((n, n))
+    U = np.stack([(r + r.T).ravel(), pu.ravel(), pu.T.ravel(), (E + E.T).ravel()])   # cell (i, j) at [j, i]
+    s = O.Scheme(O.Mesh(m), order=3, cweno_vars="characteristic")
+    for c in (2 * n + 2, 5 * n + 5):
+        V = s.reconstruct(U, c, O.CW)
+        P = s.face_points(c)
+        for q in range(P.shape[0]):
+            k = int(np.argmin(np.hypot(P[:, 0] - P[q, 1], P[:, 1] - P[q, 0])))
+            assert np.hypot(P[k, 0] - P[q, 1], P[k, 1] - P[q, 0]) < 1e-12
+            assert np.allclose(V[q], V[k][[0, 2, 1, 3]], rtol=0, atol=1e-12), (c, q)
+        assert np.abs(V - U[:, c]).max() > 1e-3        # a real reconstruction, not the mean
+
+
 def test_characteristic_cweno_on_a_contact_is_density_cweno():
     """Across a contact (u, v and p constant, rho jumps) every difference of
     conserved states is a multiple of the entropy eigenvector (1, u, v, q^2/2),
