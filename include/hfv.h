@@ -163,7 +163,8 @@ typedef struct {
     int step_chain;
 } hfv_scheme_params;
 
-/* Fill *p with the defaults listed above.  Never fails for non-NULL p. */
+/* Fill *p with the defaults listed above (the paper's values of Sec. 2.3-2.5
+ * and Fig. NADMargin (a) where it gives them).  Errors: HFV_ERR_ARG (p NULL). */
 HFV_API int hfv_default_params(hfv_scheme_params* p);
 
 /* Build faces, face neighbours, periodic pairing and cell geometry.
@@ -192,20 +193,24 @@ HFV_API int hfv_mesh_create_batch(const hfv_mesh_desc* descs, int n_meshes, hfv_
 
 /* Problems of a mesh (1 for hfv_mesh_create): *n_segments, and when
  * cell_offsets (host, n_segments + 1 int64) is non-NULL their first cells
- * and the total.  sync. */
+ * and the total.  A property of this library's batching (the paper solves one
+ * problem at a time).  sync.  Errors: HFV_ERR_ARG (mesh or n_segments NULL). */
 HFV_API int hfv_mesh_segments(const hfv_mesh* mesh, int* n_segments, int64_t* cell_offsets);
 
 /* Cell measures |V_c| (host output, caller-owned, n_cells doubles): areas
- * in 2D, volumes in 3D, as the scheme uses them (Sec. 2).  sync. */
+ * in 2D, volumes in 3D, as the scheme uses them (Sec. 2).  sync.  Errors:
+ * HFV_ERR_ARG (NULL argument). */
 HFV_API int hfv_mesh_volumes(const hfv_mesh* mesh, double* vol);
 
-/* Sizes of a mesh.  Any output pointer may be NULL. */
+/* Sizes of a mesh (Sec. 2): cells, faces, dimension.  Any output pointer may
+ * be NULL.  sync.  Errors: HFV_ERR_ARG (mesh NULL). */
 HFV_API int hfv_mesh_info(const hfv_mesh* mesh, int64_t* n_cells, int64_t* n_faces, int* dim);
 
 /* Face neighbours in canonical per-cell form (host outputs, caller-owned):
  * nbr[c * 6 + f] = cell across local face f of c or -1 on an open boundary,
  * nbrf[c * 6 + f] = that face's local index inside the neighbour (or -1).
- * Unused slots (f >= faces of c) are -1.  sync. */
+ * Unused slots (f >= faces of c) are -1.  The face adjacency the stencils of
+ * Sec. 2.1 grow along.  sync.  Errors: HFV_ERR_ARG (NULL argument). */
 HFV_API int hfv_mesh_connectivity(const hfv_mesh* mesh, int32_t* nbr, int8_t* nbrf);
 
 /* Build the central and directional stencils (Sec. 2.1, 2.3), then, on the
@@ -220,16 +225,19 @@ HFV_API int hfv_mesh_connectivity(const hfv_mesh* mesh, int32_t* nbr, int8_t* nb
 HFV_API int hfv_scheme_create(hfv_mesh* mesh, const hfv_scheme_params* params, void* stream, hfv_scheme** out);
 
 /* Sizes: info[0..7] = N (unknown coefficients, K(r,d)-1), M (central stencil
- * size), Md (directional / MUSCL stencil size), nq (Gauss points per face
- * direction), nfp (points per face), nv, Q_total (sum over cells of face
- * points), precision. */
+ * size, 2 K(r,d); Sec. 2.1), Md (directional / MUSCL stencil size), nq (Gauss
+ * points per face direction), nfp (points per face), nv, Q_total (sum over
+ * cells of face points), precision.  Host output, 8 int64.  sync.  Errors:
+ * HFV_ERR_ARG (NULL argument). */
 HFV_API int hfv_scheme_info(const hfv_scheme* s, int64_t* info);
 
 /* Stencils, for bit-exact checks (host outputs, caller-owned):
  * central[c * M + m] = m-th cell of c's central stencil, in the order
  * (face layer, quantised distance, id); dir[(c * 6 + f) * Md + k] = local
  * index (0..M-1) of the k-th cell of the directional stencil of face f, or
- * -1 past its size; dir may be NULL.  sync. */
+ * -1 past its size; dir may be NULL.  The central stencil of Sec. 2.1 and
+ * the directional stencils of Sec. 2.3.  sync.  Errors: HFV_ERR_ARG (s or
+ * central NULL). */
 HFV_API int hfv_get_stencils(const hfv_scheme* s, int32_t* central, int32_t* dir);
 
 /* The same stencils without a scheme or a GPU: the host builder that
@@ -261,10 +269,16 @@ HFV_API int hfv_residual(hfv_scheme* s, const void* U, void* R, const uint8_t* f
 /* Stable time step dt = cfl * min_c |V_c| / sum_f (|u_c . n_f| + a_c) |S_f|
  * from the cell averages of U (device, FP64 [nv][n_cells]), the minimum taken
  * over each problem's cells; result written to dt_dev (device, one double per
- * problem of the mesh, hfv_mesh_segments).  async. */
+ * problem of the mesh, hfv_mesh_segments).  The time discretisation of
+ * Sec. 2.4 gives only the CFL number; this convective bound (with the
+ * diffusion limit 4 nu sum_f |S_f|^2 / |V| added when mu0 > 0) is the reading
+ * taken.  async.  Errors: HFV_ERR_ARG (NULL argument, cfl <= 0),
+ * HFV_ERR_CUDA. */
 HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* dt_dev, void* stream);
 
-/* One SSP Runge-Kutta step of U in place, Shu-Osher form.  time_scheme
+/* One SSP Runge-Kutta step of U in place, Shu-Osher form (the temporal
+ * discretisation of Sec. 2.4; the paper's own runs use the SSP scheme of
+ * Spiteri and Ruuth).  time_scheme
  * HFV_SSPRK3 (three stages):
  *   U1 = U + dt R(U);  U2 = 3/4 U + 1/4 (U1 + dt R(U1));
  *   U  = 1/3 U + 2/3 (U2 + dt R(U2));
@@ -276,7 +290,8 @@ HFV_API int hfv_compute_dt(hfv_scheme* s, const double* U, double cfl, double* d
  *       computed from U with `cfl` (hfv_compute_dt)
  *   dt_used  host double* (one per problem of the mesh) or NULL; non-NULL
  *       makes the call sync.
- * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG. */
+ * async otherwise; allocates nothing.  Errors: HFV_ERR_ARG (s or U NULL,
+ * neither dt nor cfl positive), HFV_ERR_CUDA. */
 HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt_used, void* stream);
 
 /* Vector-Jacobian product of the residual: g = lam^T dR/dU at U, with the
@@ -299,8 +314,8 @@ HFV_API int hfv_step(hfv_scheme* s, double* U, double cfl, double dt, double* dt
 HFV_API int hfv_residual_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, const double* lam, double* g,
                              void* stream);
 
-/* One SSP-RK3 step that records (forced = 0) or imposes (forced != 0) the
- * classes of its three stages: U (device FP64 [nv][n_cells], the step's
+/* One SSP-RK3 step (Sec. 2.4) that records (forced = 0) or imposes
+ * (forced != 0) the classes (Sec. 2.5) of its three stages: U (device FP64 [nv][n_cells], the step's
  * start) -> U_out (device, another buffer), with U1 = U + dt R(U),
  * U2 = 3/4 U + 1/4 (U1 + dt R(U1)), U_out = 1/3 U + 2/3 (U2 + dt R(U2));
  * cls device uint8 [3][n_cells], stage k's final classes (as hfv_residual's
@@ -321,7 +336,8 @@ HFV_API int hfv_step_classes(hfv_scheme* s, const double* U, double dt, uint8_t*
  * async.  Errors: HFV_ERR_ARG, HFV_ERR_OOM, HFV_ERR_CUDA. */
 HFV_API int hfv_step_vjp(hfv_scheme* s, const double* U, const uint8_t* cls, double dt, double* lam, void* stream);
 
-/* Autotuner of the residual's launch shape for this scheme and state: the
+/* Autotuner of the residual's launch shape for this scheme and state (a
+ * property of this library; the paper has no counterpart): the
  * persistent candidate kernel's tile shape (2D FP32 orders 2-3: 0 = tiles of
  * 48 cells, three CTAs per SM; 1 = tiles of 64 cells, two CTAs per SM; one
  * shape elsewhere) and resident CTAs per SM, and the CWENOZ / MUSCL
@@ -344,7 +360,7 @@ HFV_API int hfv_autotune(hfv_scheme* s, const void* U, int reps, void* stream, i
  * 0..64, blocks per SM 1..64, share 1..99 %, tile 0 or 1). */
 HFV_API int hfv_scheme_set_shape(hfv_scheme* s, const int* shape);
 
-/* hfv_step on several schemes at once, each on its own stream forked from
+/* hfv_step (Sec. 2.4) on several schemes at once, each on its own stream forked from
  * `stream` and joined back into it (so their kernels may run concurrently,
  * and a stream capture records one graph with one branch per scheme): the
  * form a batch of problems of different orders takes, one batched mesh per
@@ -354,12 +370,15 @@ HFV_API int hfv_scheme_set_shape(hfv_scheme* s, const int* shape);
  * failure still joins the branches forked before it into `stream`. */
 HFV_API int hfv_step_many(hfv_scheme* const* schemes, double* const* U, int n, double cfl, double dt, void* stream);
 
-/* End-to-end helper: copy U (host, FP64 [nv][n_cells]) to the device, take
- * n_steps steps as hfv_step, copy the result back into U.  sync. */
+/* End-to-end helper: copy U (host, FP64 [nv][n_cells], caller-owned) to the
+ * scheme's own device state, take n_steps steps as hfv_step (Sec. 2.4), copy
+ * the result back into U.  Allocates nothing; ends a step chain.  sync.
+ * Errors: HFV_ERR_ARG (s or U NULL, n_steps < 0), HFV_ERR_CUDA and those of
+ * hfv_step. */
 HFV_API int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double cfl, double dt, void* stream);
 
-/* Class queues of the last residual (host outputs, caller-owned): counts[0]
- * = CWENOZ cells, counts[1] = MUSCL cells; queues may be NULL or hold
+/* Class queues of the last residual (the tagged classes of Sec. 2.5; host
+ * outputs, caller-owned): counts[0] = CWENOZ cells, counts[1] = MUSCL cells; queues may be NULL or hold
  * [2][n_cells] int32, each queue in ascending cell order.  sync.  Errors:
  * HFV_ERR_ARG (NULL scheme or counts), HFV_ERR_CUDA (a copy failed, or the
  * device holds a queue length outside 0..n_cells; queues is then left
@@ -367,11 +386,13 @@ HFV_API int hfv_advance_host(hfv_scheme* s, double* U_host, int n_steps, double 
 HFV_API int hfv_get_queues(const hfv_scheme* s, int32_t* counts, int32_t* queues);
 
 /* Sticky status bits (host output): bit0 = a state with rho <= 0, p <= 0 or
- * a non-finite value reached hfv_residual; bit2 = a bounded wait on a bulk
+ * a non-finite value reached hfv_residual (the positivity the bound of
+ * Sec. 2.4 protects); bit2 = a bounded wait on a bulk
  * copy inside the candidate kernel gave up (the kernel skipped the rest of
  * its cells and returned; the residual of that launch is incomplete).
  * reset != 0 clears them.  sync.  Returns HFV_ERR_TIMEOUT when bit2 is set,
- * else HFV_ERR_NONPHYSICAL when bit0 is set, else HFV_OK. */
+ * else HFV_ERR_NONPHYSICAL when bit0 is set, else HFV_OK; HFV_ERR_ARG (s or
+ * flags NULL), HFV_ERR_CUDA. */
 HFV_API int hfv_status(hfv_scheme* s, int* flags, int reset);
 
 /* Testing aid for the bounded waits of the candidate kernel (the paper has no
@@ -385,7 +406,8 @@ HFV_API int hfv_status(hfv_scheme* s, int* flags, int reset);
 HFV_API int hfv_debug_wait(hfv_scheme* s, int64_t consumer_wait_ns, int withhold_copies);
 
 /* Wall time of hfv_scheme_create's two phases (host output, 2 doubles, ms):
- * ms[0] the stencils (host threads), ms[1] the operators (device, FP64). */
+ * ms[0] the stencils (host threads), ms[1] the operators (device, FP64).
+ * Instrumentation; sync.  Errors: HFV_ERR_ARG (NULL argument). */
 HFV_API int hfv_scheme_setup_ms(const hfv_scheme* s, double* ms);
 
 /* Switch an existing scheme between the detector-driven hybrid and the pure
@@ -396,13 +418,16 @@ HFV_API int hfv_scheme_setup_ms(const hfv_scheme* s, double* ms);
  * step chain.  Errors: HFV_ERR_ARG. */
 HFV_API int hfv_scheme_set_kind(hfv_scheme* s, int scheme);
 
-/* Device bytes held by the scheme (operators + scratch). */
+/* Device bytes held by the scheme (operators + scratch; host output).
+ * Instrumentation; sync.  Errors: HFV_ERR_ARG (NULL argument). */
 HFV_API int hfv_scheme_device_bytes(const hfv_scheme* s, int64_t* bytes);
 
 /* Per-kernel timer of the hot path (instrumentation for benchmarks).
  * enable != 0: every kernel the scheme launches afterwards is bracketed by a
  * pair of CUDA events recorded on its launch stream (at most 512 pending
- * launches between reads).  enable == 0 switches it off.  sync. */
+ * launches between reads).  enable == 0 switches it off.  Instrumentation
+ * (the paper has no counterpart).  sync.  Errors: HFV_ERR_ARG (s NULL),
+ * HFV_ERR_CUDA (event creation; the timer is then off). */
 HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
 
 /* Fold the pending event pairs into per-kernel totals and read them (host
@@ -411,11 +436,13 @@ HFV_API int hfv_kernel_timer(hfv_scheme* s, int enable);
  * compaction, 5 CWENOZ, 6 MUSCL, 7 fluxes, 8 Runge-Kutta stage, 9 time
  * step, 10 FP32 conversion, 11 viscous gradients, 12 flux VJP, 13
  * reconstruction VJPs (linear and first-order cells, CWENOZ and MUSCL
- * queues), 14 stencil gather of the VJP (2, 3, 4: no kernel).  reset != 0 zeroes the totals after
- * reading.  sync. */
+ * queues), 14 stencil gather of the VJP (2, 3, 4: no kernel).  reset != 0
+ * zeroes the totals after reading.  sync.  Errors: HFV_ERR_ARG (NULL
+ * argument), HFV_ERR_CUDA. */
 HFV_API int hfv_kernel_times(hfv_scheme* s, double* ms, int64_t* launches, int reset);
 
-/* Number of kernels launched by this library in this process so far. */
+/* Number of kernels launched by this library in this process so far (host
+ * output).  Instrumentation.  Errors: HFV_ERR_ARG (count NULL). */
 HFV_API int hfv_launch_count(int64_t* count);
 
 /* Fused multiply-add throughput of the current device's CUDA cores, the ALU
@@ -469,9 +496,13 @@ HFV_API int hfv_rcp64(int64_t n, const double* in, double* out, void* stream);
 HFV_API int hfv_class_queues_static(const uint8_t* classes, int64_t n_cells, int32_t* counts, int32_t* queues,
                                     void* stream);
 
-/* Message of the calling thread's last failure ("" if none). */
+/* Message of the calling thread's last failure ("" if none); the string
+ * belongs to the library and stays valid until the thread's next failing
+ * call.  Never fails. */
 HFV_API const char* hfv_last_error(void);
 
+/* Release a scheme (its device arena, streams, events and the adjoint's
+ * scratch) or a mesh; NULL is a no-op.  A mesh must outlive its schemes. */
 HFV_API void hfv_scheme_destroy(hfv_scheme* s);
 HFV_API void hfv_mesh_destroy(hfv_mesh* m);
 
