@@ -320,3 +320,17 @@ def test_abi_from_plain_c(H, tmp_path):
     subprocess.run(cmd, check=True, capture_output=True, text=True, timeout=120)
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_every_entry_point_documents_its_errors():
+    """Each declaration in include/hfv.h follows a comment that states its
+    error behaviour (the codes it returns, or that it never fails / is a
+    no-op)."""
+    src = open(os.path.join(ROOT, "include", "hfv.h")).read()
+    documented = set()
+    for m in re.finditer(r"(/\*(?:(?!\*/).)*\*/)\s*\n\s*((?:HFV_API[^;]*;\s*)+)", src, re.S):
+        com = m.group(1)
+        if re.search(r"Errors?:|HFV_ERR_|Never fails|no-op", com):
+            documented.update(re.findall(r"HFV_API[^;]*?(hfv_\w+)\s*\(", m.group(2)))
+    missing = sorted(set(_declared()) - documented)
+    assert not missing, missing
