@@ -260,7 +260,10 @@ HFV_API int hfv_stencils_host(const hfv_mesh* mesh, int order, int32_t* sizes, i
  *   R            device, same layout and type; written for every cell
  *   forced_class device uint8 [n_cells] or NULL.  Non-NULL: skip the
  *                detector and tagging and use these classes (0..3); the
- *                Harten bound still applies to classes 0..2.
+ *                Harten bound still applies to classes 0..2.  Other values
+ *                are not checked (the array is device memory): the kernels
+ *                use their low two bits, bit 7 reads as a failed Harten
+ *                test, and no memory access depends on them.
  *   class_out    device uint8 [n_cells] or NULL: the final class per cell.
  * async; allocates nothing; capturable in a CUDA graph.  Errors: HFV_ERR_ARG.
  * A non-physical state is recorded for hfv_status, not returned here. */
