@@ -15,6 +15,7 @@ import pytest
 
 import oracle as O
 from bounds import fp32_bar, rounded
+from margins import detector_margins
 from paper_2510_25906_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
@@ -216,6 +217,19 @@ def test_free_running_classes_and_queues(H, name):
     cg = cls.cpu().numpy()
     agree = (cg == fin).mean()
     mism = np.nonzero(cg != fin)[0]
+    nbr, _ = om.connectivity()
+    if mism.size:
+        # list the mismatches with their margins (diagnostic only)
+        vol, _ = om.geometry()
+        print(f"{name}: {mism.size} class mismatches -- cell, GPU, oracle, the cell's detector / "
+              "deactivation / Harten margins, the least detector margin of its face neighbours")
+        for c in mism[:20]:
+            try:
+                mc = detector_margins(osch, U, c, nbr, vol, cls=int(tag[c]) if tag[c] < 3 else None)
+                mn = min(detector_margins(osch, U, j, nbr, vol)[0] for j in nbr[c] if j >= 0)
+                print("  ", int(c), int(cg[c]), int(fin[c]), "%.2e %.2e %.2e" % mc, "%.2e" % mn)
+            except Exception as e:     # a diagnostic never fails the test
+                print("  ", int(c), int(cg[c]), int(fin[c]), "margins unavailable:", e)
     assert agree >= 0.999, (name, agree, [(int(c), int(cg[c]), int(fin[c])) for c in mism[:20]])
     # queues: bit-exact ascending lists of the CWENOZ and MUSCL cells of the
     # pipeline before the Harten bound turns some into first-order cells
@@ -223,7 +237,6 @@ def test_free_running_classes_and_queues(H, name):
     assert np.all(np.diff(qc) > 0) and np.all(np.diff(qm) > 0)
     assert set(qc.tolist()) == set(np.nonzero(tag == O.CW)[0].tolist())
     assert set(qm.tolist()) == set(np.nonzero(tag == O.MU)[0].tolist())
-    nbr, _ = om.connectivity()
     good = cg == fin
     for c in mism:
         good[nbr[c][nbr[c] >= 0]] = False
