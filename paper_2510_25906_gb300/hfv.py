@@ -194,6 +194,7 @@ class Mesh:
 
     @property
     def n_segments(self) -> int:
+        """Independent problems in the mesh (hfv_mesh_segments)."""
         return self.segments.size - 1
 
     def __del__(self):
@@ -202,6 +203,8 @@ class Mesh:
             self.h = None
 
     def connectivity(self):
+        """hfv_mesh_connectivity: (nbr, nbrf), [n_cells, 6] neighbour across
+        each local face (-1 open / unused) and that face's index inside it."""
         nbr = np.zeros((self.n_cells, 6), np.int32)
         nbrf = np.zeros((self.n_cells, 6), np.int8)
         _check(load().hfv_mesh_connectivity(self.h, nbr.ctypes.data, nbrf.ctypes.data))
@@ -242,15 +245,19 @@ class Scheme:
 
     @property
     def dtype(self):
+        """torch dtype of the residual's state and output (FP32 or FP64)."""
         import torch
         return torch.float32 if self.fp32 else torch.float64
 
     def device_bytes(self) -> int:
+        """hfv_scheme_device_bytes: device memory the scheme holds."""
         b = C.c_int64()
         _check(load().hfv_scheme_device_bytes(self.h, C.byref(b)))
         return b.value
 
     def stencils(self):
+        """hfv_get_stencils: (central [n_cells, M], dir [n_cells, 6, Md])
+        of the scheme, the directional entries local indices or -1."""
         cen = np.zeros((self.n_cells, self.M), np.int32)
         dr = np.zeros((self.n_cells, 6, self.Md), np.int32)
         _check(load().hfv_get_stencils(self.h, cen.ctypes.data, dr.ctypes.data))
@@ -279,6 +286,8 @@ class Scheme:
         return R
 
     def compute_dt(self, U, cfl: float, dt_out=None, stream=None):
+        """hfv_compute_dt: the CFL step of each problem from the FP64 CUDA
+        state U, as a device FP64 tensor (one entry per problem)."""
         import torch
         u = self._state(U, torch.float64)
         if dt_out is None:
@@ -370,21 +379,27 @@ class Scheme:
         _check(load().hfv_debug_wait(self.h, int(consumer_wait_ns), 1 if withhold_copies else 0))
 
     def queues(self):
+        """hfv_get_queues: (counts, [CWENOZ cells, MUSCL cells]) of the last
+        residual, each queue ascending."""
         counts = np.zeros(2, np.int32)
         q = np.zeros((2, self.n_cells), np.int32)
         _check(load().hfv_get_queues(self.h, counts.ctypes.data, q.ctypes.data))
         return counts, [q[0, :counts[0]].copy(), q[1, :counts[1]].copy()]
 
     def kernel_timer(self, enable: bool = True):
+        """hfv_kernel_timer: bracket every later launch with CUDA events."""
         _check(load().hfv_kernel_timer(self.h, 1 if enable else 0))
 
     def kernel_times(self, reset: bool = False):
+        """hfv_kernel_times: {kernel name: (total ms, launches)}."""
         ms = np.zeros(16)
         n = np.zeros(16, np.int64)
         _check(load().hfv_kernel_times(self.h, ms.ctypes.data, n.ctypes.data, 1 if reset else 0))
         return {KERNELS[k]: (float(ms[k]), int(n[k])) for k in range(len(KERNELS))}
 
     def status(self, reset: bool = False):
+        """hfv_status: the sticky status bits (bit 0 non-physical state);
+        raises HfvError on a timed-out device wait or a CUDA error."""
         flags = C.c_int(0)
         rc = load().hfv_status(self.h, C.byref(flags), 1 if reset else 0)
         if rc not in (HFV_OK, HFV_ERR_NONPHYSICAL):
@@ -404,6 +419,7 @@ def step_many(schemes, states, cfl: float = 0.5, dt: float = -1.0, stream=None):
 
 
 def launch_count() -> int:
+    """hfv_launch_count: kernels this library launched in the process."""
     n = C.c_int64()
     _check(load().hfv_launch_count(C.byref(n)))
     return n.value
