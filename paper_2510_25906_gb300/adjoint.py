@@ -31,6 +31,8 @@ class ResidualFunction:
 
     @classmethod
     def apply(cls, U, scheme):
+        """The residual of U under `scheme` (an FP64 hfv.Scheme), recorded
+        for autograd."""
         if cls._fn is None:
             torch = _torch()
 

@@ -7,13 +7,15 @@ and the CPU oracle consume exactly the arrays built here.
 Mesh format (shared by every consumer):
     dim        2 or 3
     nodes      float64 [n_nodes, dim]
-    cell_type  uint8   [n_cells]   TRI=1, QUAD=2, TET=3, HEX=4
+    cell_type  uint8   [n_cells]   TRI=1, QUAD=2, TET=3, HEX=4, PRISM=5, PYRAMID=6
     cell_ptr   int64   [n_cells+1] CSR offsets into cell_idx
     cell_idx   int32   [...]       vertex ids in the fixed local order below
     period     float64 [dim]       periodic length per axis, 0 = not periodic
 
-Local vertex order: TRI and QUAD counter-clockwise; HEX v0..v3 the bottom
-face counter-clockwise seen from +z, v4..v7 the top face above them.
+Local vertex order: TRI and QUAD counter-clockwise; TET v0..v3 of positive
+volume; HEX v0..v3 the bottom face counter-clockwise seen from +z, v4..v7 the
+top face above them; PRISM the triangles v0 v1 v2 and v3 v4 v5 (v3 above
+v0); PYRAMID the base v0..v3 counter-clockwise seen from the apex v4.
 Periodic meshes carry separate nodes on opposite sides (x=0 and x=L); faces
 are paired across the period by their positions.
 
@@ -21,18 +23,24 @@ State format: conserved variables, float64 [nv, n_cells] (structure of
 arrays), nv = dim + 2, order (rho, rho*u, rho*v[, rho*w], E).
 
 Workloads (seeded, synthetic, shaped like the paper's):
-  * ``density_wave_tri``: periodic unit square, structured n x n quads cut
+  * ``density_wave``: periodic unit square, structured n x n quads cut
     along one diagonal, interior nodes jittered by +-0.2h; rho = 1 + 0.2
     sin(2 pi (x + y)), u = v = 1, p = 1 (the smooth advected wave).
-  * ``quadrant_mixed``: [0,1]^2, n x n quads of which a seeded half are cut
+  * ``quadrant``: [0,1]^2, n x n quads of which a seeded half are cut
     into two triangles along a seeded diagonal, interior nodes jittered; the
     four constant states of the paper's 2D Riemann problem (Sec. 3.5, the
     2D Riemann problem equation), placed by quadrant about (0.5, 0.5).
-  * ``turbulence_hex``: periodic [0, 2 pi]^3, n^3 uniform hexahedra; uniform
+  * ``turbulence``: periodic [0, 2 pi]^3, n^3 uniform hexahedra; uniform
     density and pressure (rho = 1, p = 1/gamma, so c = 1) and a seeded
     solenoidal velocity with energy spectrum E(k) ~ k^4 exp(-2 k^2 / k0^2),
     k0 = 4, scaled to turbulent Mach number 0.6 (the decaying-turbulence
     stand-in for the paper's 128^3 Taylor-Green mesh, Sec. 3.6).
+  * the adjoint workload (``adjoint_problem``): 6 n^3 jittered tetrahedra of
+    the open unit cube with a density pulse ahead of a Mach 2 shock
+    (``shock_pulse_state``); the 3D mixed-element mesh
+    (``mixed_element_mesh``) carries the same state;
+  * the batched workload (``batched_problems``): independent open 2D
+    problems of uneven size and order.
 """
 from __future__ import annotations
 
@@ -58,13 +66,16 @@ class Mesh:
 
     @property
     def n_cells(self) -> int:
+        """Number of cells."""
         return int(self.cell_type.shape[0])
 
     @property
     def n_nodes(self) -> int:
+        """Number of nodes."""
         return int(self.nodes.shape[0])
 
     def cell_vertices(self, c: int) -> np.ndarray:
+        """Coordinates of cell c's vertices in its local order, [nv, dim]."""
         return self.nodes[self.cell_idx[self.cell_ptr[c]:self.cell_ptr[c + 1]]]
 
     def vertex_means(self) -> np.ndarray:
@@ -316,6 +327,7 @@ def cell_average_2d(mesh: Mesh, f, npts: int = 8) -> np.ndarray:
 
 
 def conserved_2d(rho, u, v, p, gamma: float = GAMMA) -> np.ndarray:
+    """Conserved 2D state [4, n] (rho, rho u, rho v, E) of primitive arrays."""
     rho, u, v, p = (np.asarray(a, dtype=np.float64) for a in (rho, u, v, p))
     return np.stack([rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)])
 
@@ -378,6 +390,8 @@ def solenoidal_velocity(n: int, seed: int = 3, k0: float = 4.0, mach_t: float = 
 
 def turbulence_state(mesh: Mesh, seed: int = 3, k0: float = 4.0, mach_t: float = 0.6,
                      gamma: float = GAMMA) -> np.ndarray:
+    """Conserved state on the n^3 periodic hexahedra of structured_hex_mesh:
+    rho = 1, p = 1 / gamma (unit sound speed) and solenoidal_velocity."""
     n = int(mesh.meta["n"])
     assert mesh.n_cells == n ** 3
     u = solenoidal_velocity(n, seed, k0, mach_t).reshape(3, -1)  # cell id (k*n+j)*n+i matches (k,j,i)
