@@ -154,6 +154,7 @@ def rk54_generic(U: np.ndarray, dt: float, rhs) -> np.ndarray:
 
 
 def gauss_legendre(n: int):
+    """The oracle's n-point Gauss-Legendre rule on [0, 1]: (points, weights)."""
     lib = _load()
     x, w = np.zeros(n), np.zeros(n)
     lib.or_gauss_legendre(n, _p(x), _p(w))
@@ -161,6 +162,7 @@ def gauss_legendre(n: int):
 
 
 def flux(kind: str, UL, UR, n, gamma: float = 1.4) -> np.ndarray:
+    """Riemann flux F(UL, UR, n) of kind rusanov / hll / hllc (Sec. 2.4), n a unit normal."""
     lib = _load()
     UL, UR = np.ascontiguousarray(UL, np.float64), np.ascontiguousarray(UR, np.float64)
     nn = np.ascontiguousarray(n, np.float64)
@@ -208,18 +210,23 @@ class Mesh:
             self.h = None
 
     def connectivity(self):
+        """(nbr, nbrf): [n_cells, 6] neighbour across each local face (-1 open
+        or unused) and that face's local index inside the neighbour."""
         nbr = np.zeros((self.n_cells, 6), np.int32)
         nbrf = np.zeros((self.n_cells, 6), np.int8)
         self.lib.or_mesh_connectivity(self.h, _p(nbr, C.c_int32), _p(nbrf, C.c_int8))
         return nbr, nbrf
 
     def geometry(self):
+        """(|V| [n_cells], centroids [n_cells, 3]) by the oracle's volume rules."""
         vol = np.zeros(self.n_cells)
         cen = np.zeros((self.n_cells, 3))
         self.lib.or_mesh_geometry(self.h, _p(vol), _p(cen))
         return vol, cen
 
     def faces(self):
+        """Per face: owner, neighbour (-1 open), unit normal out of the owner,
+        area, and the periodic shift that brings the neighbour next to the owner."""
         nf = self.n_faces
         fo, fn = np.zeros(nf, np.int32), np.zeros(nf, np.int32)
         nrm, area, sh = np.zeros((nf, 3)), np.zeros(nf), np.zeros((nf, 3))
@@ -227,6 +234,7 @@ class Mesh:
         return fo, fn, nrm, area, sh
 
     def monomial_integral(self, c: int, a: int, b: int, cz: int = 0, npts: int = 8) -> float:
+        """Integral of x^a y^b z^cz over cell c with npts points per direction."""
         return float(self.lib.or_cell_monomial_integral(self.h, c, a, b, cz, npts))
 
 
@@ -268,9 +276,12 @@ class Scheme:
         return {1: 3, 2: 4, 3: 4, 4: 6, 5: 5, 6: 5}[int(self.mesh.src.cell_type[c])]
 
     def Q(self, c):
+        """Face points of cell c."""
         return self._nf(c) * self.nfp
 
     def stencil(self, c: int):
+        """(central stencil [M] in stencil order, directional stencils [nf, Md]
+        as local indices; entries past each size are padding)."""
         s = np.zeros(self.M, np.int32)
         d = np.zeros(self._nf(c) * self.Md, np.int32)
         if self.lib.or_stencil(self.h, c, _p(s, C.c_int32), _p(d, C.c_int32)) != 0:
@@ -278,6 +289,7 @@ class Scheme:
         return s, d.reshape(self._nf(c), self.Md)
 
     def operator(self, c: int, which: str) -> np.ndarray:
+        """One of cell c's operators by name (P, Phi, OI, A, Vr, D, G, shift, nd)."""
         N, M, Md, d, nf, Q = self.N, self.M, self.Md, self.dim, self._nf(c), self.Q(c)
         shapes = {"P": (0, (N, M)), "Phi": (1, (Q, N)), "OI": (2, (N, N)), "A": (3, (M, N)),
                   "Vr": (4, (M + 1,)), "D": (5, (nf, d, Md)), "G": (6, (d, Md)), "shift": (7, (M, 3)), "nd": (8, (nf,))}
@@ -288,6 +300,7 @@ class Scheme:
         return out.reshape(shp)
 
     def face_points(self, c: int) -> np.ndarray:
+        """Physical coordinates of cell c's face quadrature points, [Q, 3]."""
         out = np.zeros((self.Q(c), 3))
         self.lib.or_cell_face_points(self.h, c, _p(out))
         return out
@@ -299,11 +312,14 @@ class Scheme:
         return out
 
     def refmap(self, c: int):
+        """(x0, J^-1) of cell c's reference map xi = J^-1 (x - x0)."""
         x0, Ji = np.zeros(3), np.zeros((3, 3))
         self.lib.or_cell_refmap(self.h, c, _p(x0), _p(Ji))
         return x0, Ji
 
     def reconstruct(self, U: np.ndarray, c: int, cls: int) -> np.ndarray:
+        """Face-point states [Q, nv] of cell c reconstructed as class cls
+        (LIN, CW or MU), before the Harten bound."""
         U = np.ascontiguousarray(U, np.float64)
         out = np.zeros((self.Q(c), self.nv))
         if self.lib.or_reconstruct(self.h, _p(U), c, cls, _p(out)) != 0:
@@ -311,15 +327,18 @@ class Scheme:
         return out
 
     def harten_ok(self, U: np.ndarray, c: int, V: np.ndarray) -> bool:
+        """Whether face states V [Q, nv] of cell c pass the Harten bound (Sec. 2.4)."""
         U = np.ascontiguousarray(U, np.float64)
         V = np.ascontiguousarray(V, np.float64)
         return bool(self.lib.or_harten_ok(self.h, _p(U), c, _p(V)))
 
     def nad_raw(self, U: np.ndarray, c: int) -> int:
+        """The detector's raw class of cell c (Sec. 2.5), before tagging."""
         U = np.ascontiguousarray(U, np.float64)
         return int(self.lib.or_nad_raw_cell(self.h, _p(U), c))
 
     def cweno_info(self, U: np.ndarray, c: int, v: int):
+        """(weights, indicators, CWENOZ coefficients) of variable v at cell c (Sec. 2.3)."""
         U = np.ascontiguousarray(U, np.float64)
         st = self._nf(c) + 1
         om, si, acw = np.zeros(st), np.zeros(st), np.zeros(self.N)
@@ -351,6 +370,7 @@ class Scheme:
         return R, raw, tag, fin
 
     def dt(self, U: np.ndarray, cfl: float) -> float:
+        """The CFL time step of state U (with the diffusion limit when mu0 > 0)."""
         U = np.ascontiguousarray(U, np.float64)
         return float(self.lib.or_dt(self.h, _p(U), cfl))
 
@@ -363,6 +383,7 @@ class Scheme:
         return U
 
     def rk3_step(self, U: np.ndarray, dt: float) -> np.ndarray:
+        """One three-stage SSP-RK step of U with step dt (a new array)."""
         U = np.ascontiguousarray(U, np.float64).copy()
         if self.lib.or_rk3_step(self.h, _p(U), dt) != 0:
             raise RuntimeError("oracle step: " + _err(self.lib))
