@@ -334,3 +334,27 @@ def test_every_entry_point_documents_its_errors():
             documented.update(re.findall(r"HFV_API[^;]*?(hfv_\w+)\s*\(", m.group(2)))
     missing = sorted(set(_declared()) - documented)
     assert not missing, missing
+
+
+def test_library_defaults_are_the_cited_constants(H):
+    """hfv_default_params against the cited fixtures: the detector margins of
+    Fig. NADMargin (a) and the CWENOZ / Harten / gas constants of Sec. 2,
+    2.3 and 2.4 -- the same files the oracle's pins read."""
+    gold = os.path.join(ROOT, "tests", "golden")
+    nad = json.load(open(os.path.join(gold, "nad_presets.json")))["default"]
+    cw = json.load(open(os.path.join(gold, "cweno_constants.json")))
+    p = H.default_params()
+    assert (p.alpha_m, p.beta_m, p.alpha_w, p.beta_w) == (nad["alpha_m"], nad["beta_m"], nad["alpha_w"], nad["beta_w"])
+    assert (p.cweno_eps, p.cweno_b, p.harten_theta, p.harten_eps, p.gamma) == (
+        cw["cw_eps"], cw["cw_b"], cw["harten_theta"], cw["harten_eps"], cw["gamma"])
+    assert p.lambda1_prime == cw["lambda1p_default"]
+    assert p.nad_vars == 3                       # density and pressure
+
+
+def test_batch_segments(H):
+    a = I.mixed_tri_quad_mesh(5, seed=1)
+    b = I.structured_tri_mesh(4, periodic=False)
+    g = H.Mesh.batch([a, b, a])
+    assert g.n_segments == 3
+    assert g.segments.tolist() == [0, a.n_cells, a.n_cells + b.n_cells, 2 * a.n_cells + b.n_cells]
+    assert g.n_cells == g.segments[-1]
